@@ -1,0 +1,214 @@
+"""GraphGuess oracle - TEST INFRASTRUCTURE ONLY.
+
+A plain CPU restatement of GraphGuess (arXiv 2104.10039) used to judge the
+CUDA library: the tests, ``__graft_entry__.smoke()`` and ``bench.py``'s
+CPU-baseline leg may import it; the product path never does. It shares no
+code with the CUDA library (``paper_2104_10039_gb300``) and neither imports
+the other. PageRank runs in FP64, the min applications in exact integers.
+
+The arithmetic lives in ``gg_oracle.c`` (compiled with gcc on first use);
+this module only marshals arguments. Each function cites the part of the
+paper it restates:
+
+* ``csc_from_csr``   - in-edge view for pull-based gathering (Sec. 3.1).
+* ``sample_mask``    - uniform sparsification with ratio sigma (Sec. 3.4).
+* ``iteration_mode`` - approximate window alpha, corrections, SP and SMS
+                       schedules (Sec. 3.4, Sec. 5.2).
+* ``run``            - the vertex program of Alg. 1 / Alg. 2 (GG-Gather with
+                       edge influence, GG-Apply, GG-VStatus, GG-EStatus) under
+                       the accurate / approximate modes of Sec. 3.3.
+
+Parity of approximate-mode PageRank beyond mask replay is unpinned: the paper
+prints no worked numeric example (its influence figures are missing).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import tempfile
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gg_oracle.c")
+_LIB = os.path.join(_HERE, "libggoracle.so")
+_lib = None
+
+PAGERANK, SSSP, BFS, CC = 0, 1, 2, 3
+APPS = {"pagerank": PAGERANK, "pr": PAGERANK, "sssp": SSSP, "bfs": BFS, "cc": CC}
+EXACT, NONE, STATIC_SWITCH, ADAPTIVE = 0, 1, 2, 3
+POLICIES = {"exact": EXACT, "none": NONE, "sp": NONE, "static_switch": STATIC_SWITCH,
+            "sms": STATIC_SWITCH, "adaptive": ADAPTIVE, "gg": ADAPTIVE}
+MODE_APPROX, MODE_ACCURATE, MODE_CORRECTION = 0, 1, 2
+STOP_QUIESCE, EST_STRICT = 1, 2
+INF = 0xFFFFFFFF
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("app", ctypes.c_int32), ("policy", ctypes.c_int32),
+                ("sample_ratio", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("alpha", ctypes.c_uint32), ("theta", ctypes.c_double),
+                ("max_iters", ctypes.c_uint32), ("damping", ctypes.c_double),
+                ("epsilon", ctypes.c_double), ("source", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("symmetric", ctypes.c_int32),
+                ("nthreads", ctypes.c_int32),
+                ("replay_masks", ctypes.POINTER(ctypes.c_uint8)),
+                ("n_replay", ctypes.c_int32), ("replay_tol", ctypes.c_double)]
+
+
+class _Out(ctypes.Structure):
+    _fields_ = [("pr_values", ctypes.POINTER(ctypes.c_double)),
+                ("int_values", ctypes.POINTER(ctypes.c_uint32)),
+                ("mask", ctypes.POINTER(ctypes.c_uint8)),
+                ("iter_arcs", ctypes.POINTER(ctypes.c_int64)),
+                ("iter_mode", ctypes.POINTER(ctypes.c_int32)),
+                ("iter_changed", ctypes.POINTER(ctypes.c_int64)),
+                ("iterations", ctypes.c_int32), ("corrections", ctypes.c_int32),
+                ("replay_mismatch", ctypes.c_int64), ("replay_max_margin", ctypes.c_double),
+                ("replay_violations", ctypes.c_int64)]
+
+
+def build(force: bool = False) -> str:
+    """Compile gg_oracle.c into libggoracle.so (gcc -O2, OpenMP) if stale."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    fd, tmp = tempfile.mkstemp(suffix=".so", dir=_HERE)
+    os.close(fd)
+    cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c11", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        i32p, u32p = ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_uint32)
+        u8p = ctypes.POINTER(ctypes.c_uint8)
+        lib.orc_splitmix64.restype = ctypes.c_uint64
+        lib.orc_splitmix64.argtypes = [ctypes.c_uint64]
+        lib.orc_arc_sampled.restype = ctypes.c_int
+        lib.orc_arc_sampled.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int,
+                                        ctypes.c_double, ctypes.c_uint64]
+        lib.orc_csc_from_csr.restype = ctypes.c_int
+        lib.orc_csc_from_csr.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, u32p,
+                                         i32p, i32p, u32p, i32p]
+        lib.orc_sample_mask.restype = None
+        lib.orc_sample_mask.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_int,
+                                        ctypes.c_double, ctypes.c_uint64, u8p]
+        lib.orc_iteration_mode.restype = ctypes.c_int
+        lib.orc_iteration_mode.argtypes = [ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32]
+        lib.orc_run.restype = ctypes.c_int
+        lib.orc_run.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, u32p,
+                                ctypes.POINTER(_Params), ctypes.POINTER(_Out)]
+        _lib = lib
+    return _lib
+
+
+def _p(a: Optional[np.ndarray], ct):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def splitmix64(state: int) -> int:
+    """SplitMix64 output for one state (the sampling hash's mixer)."""
+    return int(_load().orc_splitmix64(ctypes.c_uint64(state & 0xFFFFFFFFFFFFFFFF)))
+
+
+def arc_sampled(src: int, dst: int, sigma: float, seed: int, symmetric: bool = False) -> bool:
+    """Initial active flag of arc src->dst (Sec. 3.4)."""
+    return bool(_load().orc_arc_sampled(src, dst, int(symmetric), sigma, seed))
+
+
+def csc_from_csr(n, rowptr, colidx, weights=None):
+    """In-edge (CSC) view: (in_ptr, in_src, in_w, csr_pos); in-rows list their
+    sources in ascending order (Sec. 3.1's pull model gathers over them)."""
+    rowptr = np.ascontiguousarray(rowptr, np.int32)
+    colidx = np.ascontiguousarray(colidx, np.int32)
+    m = colidx.shape[0]
+    w = None if weights is None else np.ascontiguousarray(weights, np.uint32)
+    in_ptr = np.empty(n + 1, np.int32)
+    in_src = np.empty(max(m, 1), np.int32)
+    in_w = np.empty(max(m, 1), np.uint32)
+    pos = np.empty(max(m, 1), np.int32)
+    rc = _load().orc_csc_from_csr(n, m, _p(rowptr, ctypes.c_int32), _p(colidx, ctypes.c_int32),
+                                  _p(w, ctypes.c_uint32), _p(in_ptr, ctypes.c_int32),
+                                  _p(in_src, ctypes.c_int32), _p(in_w, ctypes.c_uint32),
+                                  _p(pos, ctypes.c_int32))
+    if rc != 0:
+        raise ValueError("bad graph")
+    return in_ptr, in_src[:m], in_w[:m], pos[:m]
+
+
+def sample_mask(n, in_ptr, in_src, sigma, seed, symmetric=False) -> np.ndarray:
+    """uint8 flag per CSC arc after sparsification with ratio sigma (Sec. 3.4)."""
+    in_ptr = np.ascontiguousarray(in_ptr, np.int32)
+    in_src = np.ascontiguousarray(in_src, np.int32)
+    mask = np.empty(max(in_src.shape[0], 1), np.uint8)
+    _load().orc_sample_mask(n, _p(in_ptr, ctypes.c_int32), _p(in_src, ctypes.c_int32),
+                            int(symmetric), sigma, seed, _p(mask, ctypes.c_uint8))
+    return mask[:in_src.shape[0]]
+
+
+def iteration_mode(policy, alpha: int, i: int) -> int:
+    """MODE_APPROX / MODE_ACCURATE / MODE_CORRECTION of iteration i."""
+    pol = POLICIES[policy] if isinstance(policy, str) else int(policy)
+    return int(_load().orc_iteration_mode(pol, alpha, i))
+
+
+def run(n, rowptr, colidx, weights=None, *, app="pagerank", policy="exact", sigma=1.0,
+        seed=0, alpha=4, theta=0.05, max_iters=20, damping=0.85, epsilon=0.0, source=0,
+        flags=0, symmetric=False, nthreads=1, replay_masks=None, replay_tol=1e-5):
+    """Run one GraphGuess execution on the CPU; returns a dict with ``values``
+    (float64 for PageRank, uint32 otherwise), the final CSC-order ``mask`` and
+    per-iteration statistics. ``damping`` and ``theta`` are given as the float32
+    values the CUDA library receives. ``replay_masks`` (list of uint8[m] CSC
+    masks, one per correction) makes the run adopt those flags after checking
+    that every decision it disagrees with lies within ``replay_tol`` of theta."""
+    a = APPS[app] if isinstance(app, str) else int(app)
+    pol = POLICIES[policy] if isinstance(policy, str) else int(policy)
+    rowptr = np.ascontiguousarray(rowptr, np.int32)
+    colidx = np.ascontiguousarray(colidx, np.int32)
+    m = int(colidx.shape[0])
+    w = None if weights is None else np.ascontiguousarray(weights, np.uint32)
+    rep = None
+    n_rep = 0
+    if replay_masks is not None and len(replay_masks):
+        rep = np.ascontiguousarray(np.stack([np.asarray(x, np.uint8) for x in replay_masks]))
+        n_rep = rep.shape[0]
+    prm = _Params(a, pol, float(sigma), seed & 0xFFFFFFFFFFFFFFFF, alpha,
+                  float(np.float32(theta)), max_iters, float(np.float32(damping)),
+                  float(np.float32(epsilon)), source, flags, int(symmetric), nthreads,
+                  _p(rep, ctypes.c_uint8), n_rep, replay_tol)
+    T = max(max_iters, 1)
+    pr = np.empty(n, np.float64) if a == PAGERANK else None
+    iv = np.empty(n, np.uint32) if a != PAGERANK else None
+    mask = np.empty(max(m, 1), np.uint8)
+    it_arcs = np.zeros(T, np.int64)
+    it_mode = np.full(T, -1, np.int32)
+    it_changed = np.zeros(T, np.int64)
+    out = _Out(_p(pr, ctypes.c_double), _p(iv, ctypes.c_uint32), _p(mask, ctypes.c_uint8),
+               _p(it_arcs, ctypes.c_int64), _p(it_mode, ctypes.c_int32),
+               _p(it_changed, ctypes.c_int64), 0, 0, 0, 0.0, 0)
+    rc = _load().orc_run(n, m, _p(rowptr, ctypes.c_int32), _p(colidx, ctypes.c_int32),
+                         _p(w, ctypes.c_uint32), ctypes.byref(prm), ctypes.byref(out))
+    if rc != 0:
+        raise ValueError("oracle rejected its arguments")
+    it = out.iterations
+    return {
+        "values": pr if a == PAGERANK else iv,
+        "mask": mask[:m],
+        "iterations": it,
+        "corrections": out.corrections,
+        "iter_arcs": it_arcs[:it],
+        "iter_mode": it_mode[:it],
+        "iter_changed": it_changed[:it],
+        "replay_mismatch": out.replay_mismatch,
+        "replay_max_margin": out.replay_max_margin,
+        "replay_violations": out.replay_violations,
+    }

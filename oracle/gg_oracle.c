@@ -1,0 +1,370 @@
+/*
+ * gg_oracle.c - TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, sequential-per-vertex CPU restatement of GraphGuess
+ * (Ramezani, Kandemir, Sivasubramaniam, "GraphGuess: Approximate Graph
+ * Processing System with Adaptive Correction", arXiv 2104.10039): exact and
+ * approximate pull-based vertex-centric execution with correction steps.
+ * Only the tests, the smoke check and the bench's CPU-baseline leg load this
+ * file; the product path never does, and it shares no code, header, table or
+ * helper with the CUDA library.
+ *
+ * Arithmetic: PageRank in FP64; SSSP / BFS / CC in exact integers
+ * (uint32 values, 0xFFFFFFFF = unreached).
+ *
+ * Readings of the paper taken here (each also listed in the design notes):
+ *  - Sec. 3.3: approximate mode gathers over active in-edges only, accurate
+ *    mode over all in-edges; one flag per edge, no new graph.
+ *  - Sec. 3.4: start from a sigma-fraction of active edges, run alpha
+ *    approximate iterations, then one correction ("superstep") iteration in
+ *    accurate mode that recomputes edge influence; afterwards exactly the
+ *    edges with influence > theta are active. Repeated every alpha
+ *    approximate iterations. Iteration i is a correction iff
+ *    i mod (alpha+1) == alpha.
+ *  - Sec. 3.4 sampling: independent Bernoulli(sigma) per arc decided by a
+ *    stateless hash: h = SplitMix64 output for state (seed XOR key),
+ *    key = src<<32 | dst (min<<32 | max on symmetric graphs), active iff
+ *    (h >> 32) < floor(sigma * 2^32).
+ *  - Alg. 2 GG-Gather: a separate accumulator starting at 0 (Alg. 1's
+ *    new_property); in-edges visited in CSC order (source id ascending);
+ *    influence = (acc_after - acc_before) / acc_after; v.degree = full
+ *    out-degree.
+ *  - Alg. 2 GG-Apply: rank = (1-d)/N + d * acc; initial rank 1/N; no
+ *    dangling redistribution.
+ *  - Alg. 2 GG-VStatus: vertex active iff |old - new| > epsilon (PageRank);
+ *    iff its value decreased (min applications).
+ *  - Alg. 2 GG-EStatus: edge active iff influence > theta.
+ *  - Min applications (SSSP, BFS, CC) use the same running-accumulator form
+ *    of influence on a min accumulator that starts "empty": the first
+ *    finite candidate has influence 1, a later candidate that lowers the
+ *    running minimum has (acc - cand) / acc, any other has 0. For CC the
+ *    influence is binary (1 if it lowers the running label, else 0), as
+ *    Sec. 5.2 states for WCC. The comparison with theta is done exactly in
+ *    integers against theta rounded down to a multiple of 2^-32.
+ *  - Arcs whose source is unreached (no candidate) keep their flag in a
+ *    correction (the reset of Sec. 3.4 applies to evaluated arcs), unless
+ *    ORC_EST_STRICT is set, which clears them too.
+ *  - Synchronous (Jacobi) iterations: every gather reads the previous
+ *    iteration's values.
+ *  - SP (policy NONE) never corrects; SMS (STATIC_SWITCH) corrects once at
+ *    iteration alpha and stays accurate afterwards (Sec. 5.2).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+enum { ORC_PAGERANK = 0, ORC_SSSP = 1, ORC_BFS = 2, ORC_CC = 3 };
+enum { ORC_EXACT = 0, ORC_NONE = 1, ORC_STATIC_SWITCH = 2, ORC_ADAPTIVE = 3 };
+enum { ORC_MODE_APPROX = 0, ORC_MODE_ACCURATE = 1, ORC_MODE_CORRECTION = 2 };
+#define ORC_STOP_QUIESCE 1u
+#define ORC_EST_STRICT 2u
+#define ORC_INF 0xFFFFFFFFu
+
+typedef struct {
+    int32_t app, policy;
+    double sample_ratio;         /* sigma */
+    uint64_t seed;
+    uint32_t alpha;
+    double theta;
+    uint32_t max_iters;
+    double damping;
+    double epsilon;
+    int32_t source;
+    uint32_t flags;
+    int32_t symmetric;
+    int32_t nthreads;            /* <= 0: OpenMP default */
+    const uint8_t *replay_masks; /* n_replay x m bytes in CSC order, or NULL */
+    int32_t n_replay;
+    double replay_tol;
+} orc_params;
+
+typedef struct {
+    double *pr_values;           /* n, PageRank */
+    uint32_t *int_values;        /* n, SSSP / BFS / CC */
+    uint8_t *mask;               /* m, final flags in CSC order (nullable) */
+    int64_t *iter_arcs;          /* max_iters: arcs in each iteration's edge set */
+    int32_t *iter_mode;          /* max_iters: ORC_MODE_* (-1 = skipped) */
+    int64_t *iter_changed;       /* max_iters: vertices active after VStatus */
+    int32_t iterations;          /* iterations counted (skipped no-ops included) */
+    int32_t corrections;
+    int64_t replay_mismatch;
+    double replay_max_margin;
+    int64_t replay_violations;
+} orc_out;
+
+/* SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): the output for a given
+ * state: advance by the golden gamma, then the variant-13 finaliser. */
+uint64_t orc_splitmix64(uint64_t state)
+{
+    uint64_t z = state + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* Initial flag of arc src->dst (Sec. 3.4, uniform sparsification). */
+int orc_arc_sampled(int32_t src, int32_t dst, int symmetric, double sigma, uint64_t seed)
+{
+    uint32_t a = (uint32_t)src, b = (uint32_t)dst;
+    if (symmetric && a > b) { uint32_t t = a; a = b; b = t; }
+    uint64_t key = ((uint64_t)a << 32) | (uint64_t)b;
+    uint64_t h = orc_splitmix64(seed ^ key);
+    uint64_t thr = (uint64_t)floor(sigma * 4294967296.0);
+    return (h >> 32) < thr;
+}
+
+/* In-edge (CSC) view of a CSR graph: a stable counting sort of the arcs by
+ * destination. CSR rows are visited in source order, so every in-row lists
+ * its sources in ascending order, duplicates in CSR order. csr_pos[k] is
+ * the CSR index of CSC arc k. */
+int orc_csc_from_csr(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx,
+                     const uint32_t *w, int32_t *in_ptr, int32_t *in_src, uint32_t *in_w,
+                     int32_t *csr_pos)
+{
+    for (int32_t u = 0; u <= n; ++u) in_ptr[u] = 0;
+    for (int64_t e = 0; e < m; ++e) {
+        if (colidx[e] < 0 || colidx[e] >= n) return -1;
+        in_ptr[colidx[e] + 1] += 1;
+    }
+    for (int32_t u = 0; u < n; ++u) in_ptr[u + 1] += in_ptr[u];
+    int32_t *next = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    if (!next) return -1;
+    memcpy(next, in_ptr, (size_t)n * sizeof(int32_t));
+    for (int32_t v = 0; v < n; ++v) {
+        for (int32_t e = rowptr[v]; e < rowptr[v + 1]; ++e) {
+            int32_t u = colidx[e];
+            int32_t k = next[u]++;
+            in_src[k] = v;
+            if (in_w) in_w[k] = w ? w[e] : 1u;
+            if (csr_pos) csr_pos[k] = e;
+        }
+    }
+    free(next);
+    return 0;
+}
+
+/* Flags of all CSC arcs after sampling with ratio sigma. */
+void orc_sample_mask(int32_t n, const int32_t *in_ptr, const int32_t *in_src, int symmetric,
+                     double sigma, uint64_t seed, uint8_t *mask)
+{
+    for (int32_t u = 0; u < n; ++u)
+        for (int32_t k = in_ptr[u]; k < in_ptr[u + 1]; ++k)
+            mask[k] = (uint8_t)orc_arc_sampled(in_src[k], u, symmetric, sigma, seed);
+}
+
+/* Mode of iteration i under each policy (Sec. 3.4 and Sec. 5.2). */
+int orc_iteration_mode(int policy, uint32_t alpha, uint32_t i)
+{
+    switch (policy) {
+    case ORC_EXACT: return ORC_MODE_ACCURATE;
+    case ORC_NONE: return ORC_MODE_APPROX;
+    case ORC_STATIC_SWITCH:
+        if (i < alpha) return ORC_MODE_APPROX;
+        return i == alpha ? ORC_MODE_CORRECTION : ORC_MODE_ACCURATE;
+    case ORC_ADAPTIVE:
+        return (i % (alpha + 1u)) == alpha ? ORC_MODE_CORRECTION : ORC_MODE_APPROX;
+    default: return -1;
+    }
+}
+
+/* First iteration index > i whose mode is a correction or accurate, or -1
+ * when the policy never leaves approximate mode again. */
+static int64_t next_accurate_iteration(int policy, uint32_t alpha, uint32_t i)
+{
+    if (policy == ORC_NONE) return -1;
+    if (policy == ORC_STATIC_SWITCH) return i < alpha ? (int64_t)alpha : (int64_t)i + 1;
+    if (policy == ORC_ADAPTIVE) {
+        uint64_t period = (uint64_t)alpha + 1u;
+        return (int64_t)(((uint64_t)i / period) * period + alpha);
+    }
+    return (int64_t)i + 1;
+}
+
+/* Edge status for a min application (integers only).
+ * returns 1 active, 0 inactive. */
+static int min_app_estatus(int app, uint32_t acc, uint32_t cand, double theta)
+{
+    int improving = cand < acc;
+    if (theta < 0.0) return 1;               /* influence >= 0 > theta */
+    if (theta >= 1.0) return 0;              /* influence <= 1 <= theta */
+    if (!improving) return 0;                /* influence 0 */
+    if (acc == ORC_INF || app == ORC_CC) return 1;   /* influence 1 */
+    uint64_t theta_fx = (uint64_t)floor(theta * 4294967296.0);
+    uint64_t lhs = (uint64_t)(acc - cand) << 32;
+    uint64_t rhs = theta_fx * (uint64_t)acc;
+    return lhs > rhs;
+}
+
+int orc_run(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx,
+            const uint32_t *weights, const orc_params *p, orc_out *o)
+{
+    if (n <= 0 || m < 0 || !p || !o) return -1;
+    if (p->app < ORC_PAGERANK || p->app > ORC_CC) return -1;
+    if (p->app != ORC_PAGERANK && p->app != ORC_CC && (p->source < 0 || p->source >= n)) return -1;
+    if (!(p->sample_ratio > 0.0 && p->sample_ratio <= 1.0)) return -1;
+#ifdef _OPENMP
+    if (p->nthreads > 0) omp_set_num_threads(p->nthreads);
+#endif
+    int rc = -1;
+    int32_t *in_ptr = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    int32_t *in_src = (int32_t *)malloc((size_t)(m ? m : 1) * sizeof(int32_t));
+    uint32_t *in_w = (uint32_t *)malloc((size_t)(m ? m : 1) * sizeof(uint32_t));
+    uint8_t *mask = (uint8_t *)malloc((size_t)(m ? m : 1));
+    uint8_t *new_mask = (uint8_t *)malloc((size_t)(m ? m : 1));
+    double *infl = (double *)malloc((size_t)(m ? m : 1) * sizeof(double));
+    int32_t *outdeg = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    double *rank = NULL, *rank_next = NULL;
+    uint32_t *val = NULL, *val_next = NULL;
+    if (!in_ptr || !in_src || !in_w || !mask || !new_mask || !infl || !outdeg) goto done;
+    if (orc_csc_from_csr(n, m, rowptr, colidx, weights, in_ptr, in_src, in_w, NULL) != 0) goto done;
+    for (int32_t v = 0; v < n; ++v) outdeg[v] = rowptr[v + 1] - rowptr[v];
+    orc_sample_mask(n, in_ptr, in_src, p->symmetric, p->sample_ratio, p->seed, mask);
+
+    const int is_pr = p->app == ORC_PAGERANK;
+    if (is_pr) {
+        rank = (double *)malloc((size_t)n * sizeof(double));
+        rank_next = (double *)malloc((size_t)n * sizeof(double));
+        if (!rank || !rank_next) goto done;
+        for (int32_t u = 0; u < n; ++u) rank[u] = 1.0 / (double)n;
+    } else {
+        val = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+        val_next = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+        if (!val || !val_next) goto done;
+        for (int32_t u = 0; u < n; ++u) val[u] = (p->app == ORC_CC) ? (uint32_t)u : ORC_INF;
+        if (p->app != ORC_CC) val[p->source] = 0;
+    }
+
+    o->iterations = 0;
+    o->corrections = 0;
+    o->replay_mismatch = 0;
+    o->replay_max_margin = 0.0;
+    o->replay_violations = 0;
+    const double d = p->damping;
+    const double base = (1.0 - d) / (double)n;
+    int32_t replay_next = 0;
+
+    for (uint32_t i = 0; i < p->max_iters; ++i) {
+        const int mode = orc_iteration_mode(p->policy, p->alpha, i);
+        if (mode < 0) goto done;
+        const int accurate = mode != ORC_MODE_APPROX;
+        const int correcting = mode == ORC_MODE_CORRECTION;
+        int64_t arcs = 0, changed = 0;
+
+        /* Gather (GG-Gather over in-edges, Alg. 1 / Alg. 2), Apply, VStatus */
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : arcs, changed)
+        for (int32_t u = 0; u < n; ++u) {
+            if (is_pr) {
+                double acc = 0.0;
+                for (int32_t k = in_ptr[u]; k < in_ptr[u + 1]; ++k) {
+                    if (!accurate && !mask[k]) continue;
+                    int32_t v = in_src[k];
+                    double before = acc;
+                    acc = rank[v] / (double)outdeg[v] + acc;
+                    arcs += 1;
+                    if (correcting) {
+                        double f = acc != 0.0 ? (acc - before) / acc : 0.0;
+                        infl[k] = f;
+                        new_mask[k] = (uint8_t)(f > p->theta);
+                    }
+                }
+                double old = rank[u];
+                double nw = base + d * acc;
+                rank_next[u] = nw;
+                changed += fabs(old - nw) > p->epsilon;
+            } else {
+                uint32_t acc = ORC_INF;
+                for (int32_t k = in_ptr[u]; k < in_ptr[u + 1]; ++k) {
+                    if (!accurate && !mask[k]) continue;
+                    arcs += 1;
+                    uint32_t vv = val[in_src[k]];
+                    uint32_t cand;
+                    if (p->app == ORC_CC) {
+                        cand = vv;
+                    } else {
+                        uint64_t step = (p->app == ORC_BFS) ? 1u : in_w[k];
+                        uint64_t c = (vv == ORC_INF) ? ORC_INF : (uint64_t)vv + step;
+                        cand = c >= ORC_INF ? ORC_INF : (uint32_t)c;
+                    }
+                    if (cand == ORC_INF) {      /* no candidate: arc unevaluated */
+                        if (correcting) {
+                            new_mask[k] = (p->flags & ORC_EST_STRICT) ? 0 : mask[k];
+                            infl[k] = -1.0;
+                        }
+                        continue;
+                    }
+                    if (correcting) {
+                        new_mask[k] = (uint8_t)min_app_estatus(p->app, acc, cand, p->theta);
+                        infl[k] = 0.0;
+                    }
+                    if (cand < acc) acc = cand;
+                }
+                uint32_t old = val[u];
+                uint32_t nw = acc < old ? acc : old;
+                val_next[u] = nw;
+                changed += nw < old;
+            }
+        }
+        if (!correcting) {
+            /* nothing to do for the flags */
+        } else if (p->replay_masks && replay_next < p->n_replay) {
+            /* Mask replay: adopt the given post-correction flags after
+             * checking each differing decision lies within tol of theta. */
+            const uint8_t *given = p->replay_masks + (size_t)replay_next * (size_t)m;
+            int64_t mism = 0, viol = 0;
+            double maxmargin = o->replay_max_margin;
+            for (int64_t k = 0; k < m; ++k) {
+                if ((given[k] != 0) != (new_mask[k] != 0)) {
+                    mism += 1;
+                    double margin = is_pr ? fabs(infl[k] - p->theta) : INFINITY;
+                    if (margin > maxmargin) maxmargin = margin;
+                    if (!(margin <= p->replay_tol)) viol += 1;
+                }
+                mask[k] = given[k] ? 1 : 0;
+            }
+            o->replay_mismatch += mism;
+            o->replay_violations += viol;
+            o->replay_max_margin = maxmargin;
+            replay_next += 1;
+        } else {
+            memcpy(mask, new_mask, (size_t)m);
+        }
+        if (is_pr) { double *t = rank; rank = rank_next; rank_next = t; }
+        else { uint32_t *t = val; val = val_next; val_next = t; }
+
+        if (o->iter_arcs) o->iter_arcs[i] = arcs;
+        if (o->iter_mode) o->iter_mode[i] = mode;
+        if (o->iter_changed) o->iter_changed[i] = changed;
+        o->iterations = (int32_t)i + 1;
+        o->corrections += correcting;
+
+        int stop_on_quiet = !is_pr || (p->flags & ORC_STOP_QUIESCE);
+        if (stop_on_quiet && changed == 0) {
+            if (accurate) break;                /* fixed point of the full graph */
+            /* An approximate iteration that changed nothing leaves the state
+             * as it was, so the approximate iterations until the next
+             * accurate one are no-ops: skip them (they still count). */
+            int64_t nxt = next_accurate_iteration(p->policy, p->alpha, i);
+            if (nxt < 0) break;                 /* SP: nothing will change again */
+            for (uint32_t j = i + 1; j < (uint32_t)nxt && j < p->max_iters; ++j) {
+                if (o->iter_arcs) o->iter_arcs[j] = 0;
+                if (o->iter_mode) o->iter_mode[j] = -1;
+                if (o->iter_changed) o->iter_changed[j] = 0;
+                o->iterations = (int32_t)j + 1;
+            }
+            if ((uint64_t)nxt >= p->max_iters) break;
+            i = (uint32_t)nxt - 1;
+        }
+    }
+    if (is_pr) { if (o->pr_values) memcpy(o->pr_values, rank, (size_t)n * sizeof(double)); }
+    else if (o->int_values) memcpy(o->int_values, val, (size_t)n * sizeof(uint32_t));
+    if (o->mask) memcpy(o->mask, mask, (size_t)m);
+    rc = 0;
+done:
+    free(in_ptr); free(in_src); free(in_w); free(mask); free(new_mask); free(infl); free(outdeg);
+    free(rank); free(rank_next); free(val); free(val_next);
+    return rc;
+}

@@ -1,0 +1,98 @@
+"""Textbook references used to pin the oracle on tiny graphs.
+
+Each is a different algorithm from the oracle's synchronous pull iteration:
+Dijkstra with a binary heap, FIFO breadth-first search, union-find, and
+PageRank as a dense FP64 matrix power iteration. None of them shares code with
+``oracle/`` or with the CUDA library.
+"""
+import heapq
+
+import numpy as np
+
+INF = 0xFFFFFFFF
+
+
+def arcs_of(g):
+    """(src, dst, w) triples of a graphgen.Graph in CSR order."""
+    out = []
+    for s in range(g.n):
+        for e in range(g.rowptr[s], g.rowptr[s + 1]):
+            w = 1 if g.weights is None else int(g.weights[e])
+            out.append((s, int(g.colidx[e]), w))
+    return out
+
+
+def dijkstra(g, source):
+    adj = [[] for _ in range(g.n)]
+    for s, d, w in arcs_of(g):
+        adj[s].append((d, w))
+    dist = [None] * g.n
+    heap = [(0, source)]
+    while heap:
+        dv, v = heapq.heappop(heap)
+        if dist[v] is not None:
+            continue
+        dist[v] = dv
+        for u, w in adj[v]:
+            if dist[u] is None:
+                heapq.heappush(heap, (dv + w, u))
+    return np.array([INF if x is None else x for x in dist], np.uint64).astype(np.uint32)
+
+
+def bfs_levels(g, source):
+    adj = [[] for _ in range(g.n)]
+    for s, d, _ in arcs_of(g):
+        adj[s].append(d)
+    lvl = [None] * g.n
+    lvl[source] = 0
+    queue = [source]
+    head = 0
+    while head < len(queue):
+        v = queue[head]
+        head += 1
+        for u in adj[v]:
+            if lvl[u] is None:
+                lvl[u] = lvl[v] + 1
+                queue.append(u)
+    return np.array([INF if x is None else x for x in lvl], np.uint64).astype(np.uint32)
+
+
+def cc_min_labels(g):
+    """Union-find over the (undirected) arcs; every vertex gets the smallest
+    vertex id of its component."""
+    parent = list(range(g.n))
+
+    def find(x):
+        while parent[x] != x:
+            parent[x] = parent[parent[x]]
+            x = parent[x]
+        return x
+
+    for s, d, _ in arcs_of(g):
+        a, b = find(s), find(d)
+        if a != b:
+            parent[max(a, b)] = min(a, b)
+    roots = [find(v) for v in range(g.n)]
+    smallest = {}
+    for v in range(g.n):
+        r = roots[v]
+        smallest[r] = min(smallest.get(r, v), v)
+    return np.array([smallest[roots[v]] for v in range(g.n)], np.uint32)
+
+
+def pagerank_dense(g, damping, iters):
+    """x_{t+1} = (1-d)/N + d * A^T D^-1 x_t with A counting parallel arcs and
+    D the full out-degree; vertices without out-arcs pass nothing on."""
+    n = g.n
+    d = float(np.float32(damping))
+    A = np.zeros((n, n), np.float64)
+    for s, t, _ in arcs_of(g):
+        A[s, t] += 1.0
+    outdeg = A.sum(axis=1)
+    P = np.zeros_like(A)
+    nz = outdeg > 0
+    P[nz] = A[nz] / outdeg[nz, None]
+    x = np.full(n, 1.0 / n)
+    for _ in range(iters):
+        x = (1.0 - d) / n + d * (P.T @ x)
+    return x
