@@ -1,0 +1,211 @@
+/*
+ * gg.h - C ABI of libgg.so, a GB300 (sm_103a) implementation of GraphGuess
+ * (Ramezani, Kandemir, Sivasubramaniam, "GraphGuess: Approximate Graph
+ * Processing System with Adaptive Correction", arXiv 2104.10039).
+ *
+ * The problem (Sec. 3): run a vertex program over an unchanged graph whose
+ * edges carry one active flag each (Sec. 3.3), starting from a sampled
+ * fraction sigma of active edges (Sec. 3.4), with approximate iterations
+ * (active in-edges only) and periodic correction iterations (all in-edges,
+ * edge influence recomputed, flags reset to influence > theta), trading
+ * accuracy for time.
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns a gg_status; nothing aborts the process. On failure
+ *    gg_last_error() returns a message (thread-local, valid until the next
+ *    call on the same thread).
+ *  - Pointers are host pointers unless a flag or argument says device.
+ *  - All device work is enqueued on the graph's stream (gg_set_stream,
+ *    default: the legacy default stream). Only gg_result and gg_run of the
+ *    min applications synchronise it.
+ *  - Indices are int32 (n < 2^31, m < 2^31). Vertex values of SSSP, BFS and
+ *    CC are uint32 with GG_INF = 0xFFFFFFFF meaning "unreached".
+ *  - The library owns all device memory it allocates; it is released by
+ *    gg_free_graph.
+ *  - A device-side wait that runs out of its iteration limit makes the call
+ *    return GG_ERR_TIMEOUT instead of hanging.
+ */
+#ifndef GG_H
+#define GG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GG_OK = 0,
+    GG_ERR_INVALID_ARG = 1,   /* null pointer, size or parameter out of range */
+    GG_ERR_BAD_GRAPH = 2,     /* CSR not monotone, rowptr[0] != 0, rowptr[n] != m, colidx out of range */
+    GG_ERR_OOM = 3,           /* a device allocation failed */
+    GG_ERR_CUDA = 4,          /* a CUDA call failed; the CUDA error string is in gg_last_error() */
+    GG_ERR_STATE = 5,         /* call not valid in the graph's current state */
+    GG_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
+    GG_ERR_UNSUPPORTED = 7    /* combination not implemented */
+} gg_status;
+
+typedef enum {
+    GG_APP_PAGERANK = 0,      /* Alg. 2: pull PageRank, FP32 ranks */
+    GG_APP_SSSP = 1,          /* Sec. 4.1: single-source shortest paths, uint32 weights */
+    GG_APP_BFS = 2,           /* unit-weight SSSP: levels */
+    GG_APP_CC = 3             /* Sec. 4.1 WCC: min-label propagation (symmetric graphs) */
+} gg_app;
+
+typedef enum {
+    GG_POLICY_EXACT = 0,          /* accurate mode every iteration (the paper's baseline, Sec. 5) */
+    GG_POLICY_NONE = 1,           /* SP: sparsify with sigma, never correct (Sec. 5.2) */
+    GG_POLICY_STATIC_SWITCH = 2,  /* SMS: approximate for alpha iterations, one correction,
+                                     then accurate to the end (Sec. 5.2) */
+    GG_POLICY_ADAPTIVE = 3        /* GG: a correction after every alpha approximate
+                                     iterations (Sec. 3.4) */
+} gg_policy;
+
+typedef enum {
+    GG_RESULT_VALUES = 0,     /* float[n] (PageRank) or uint32[n]: vertex values after the last run */
+    GG_RESULT_MASK = 1,       /* uint32[ceil(m/32)]: edge flags, bit (k & 31) of word k/32 = CSC arc k */
+    GG_RESULT_STATS = 2,      /* gg_stats */
+    GG_RESULT_ITER_STATS = 3, /* gg_iter_stats[iterations] of the last run */
+    GG_RESULT_CSC_PTR = 4,    /* int32[n+1]: in-edge row pointers */
+    GG_RESULT_CSC_SRC = 5,    /* int32[m]: in-edge sources, each row ascending */
+    GG_RESULT_CSC_W = 6,      /* uint32[m]: in-edge weights (graphs loaded with weights) */
+    GG_RESULT_SPARSE_PTR = 7, /* int32[n+1]: row pointers of the packed active in-edges */
+    GG_RESULT_SPARSE_SRC = 8, /* int32[nnz]: sources of the packed active in-edges */
+    GG_RESULT_OUT_TO_IN = 9   /* int32[m]: CSC position of every CSR arc */
+} gg_result_kind;
+
+/* gg_load_csr gflags */
+#define GG_DIRECTED 0u
+#define GG_SYMMETRIC 1u       /* every arc u->v has a matching v->u; sampling keys on the
+                                 unordered pair so both directions start with the same flag */
+#define GG_DEVICE_PTRS 2u     /* rowptr / colidx / weights are device pointers */
+
+/* gg_params.flags */
+#define GG_STOP_QUIESCE 1u    /* PageRank: stop after an accurate iteration with no active vertex */
+#define GG_EST_STRICT 2u      /* corrections also clear flags of arcs whose source is unreached */
+#define GG_FORCE_PULL 4u      /* min applications: never use the push frontier */
+#define GG_FORCE_PUSH 8u      /* min applications: always push from the frontier (no pull switch) */
+#define GG_TIMING 16u         /* record per-kernel-class device time with CUDA events */
+
+#define GG_INF 0xFFFFFFFFu
+
+typedef struct {
+    uint32_t alpha;       /* approximate window: approximate iterations between corrections (Sec. 3.4) */
+    float theta;          /* influence threshold (Sec. 3.4, GG-EStatus) */
+    uint32_t max_iters;   /* iteration cap T (PageRank runs exactly T unless GG_STOP_QUIESCE) */
+    float damping;        /* PageRank d (Alg. 2 GG-Apply), e.g. 0.85 */
+    float epsilon;        /* GG-VStatus threshold |old - new| > epsilon (PageRank) */
+    int32_t source;       /* SSSP / BFS source vertex */
+    uint64_t seed;        /* sampling seed (Sec. 3.4) */
+    uint32_t flags;       /* GG_* flags above */
+} gg_params;
+
+typedef struct {
+    uint32_t iterations;      /* iterations counted (no-op iterations skipped by R12 included) */
+    uint32_t corrections;     /* correction iterations executed */
+    uint32_t push_iterations; /* min applications: iterations done by the push frontier */
+    uint32_t pull_iterations; /* iterations done by a pull gather (including corrections) */
+    uint64_t arcs_processed;  /* sum over iterations of the iteration's edge-set size */
+    uint64_t active_arcs;     /* arcs active at the end of the run */
+    uint64_t changed_last;    /* vertices active after the last iteration */
+    uint32_t device_error;    /* nonzero if a bounded wait gave up (then the run failed) */
+    uint32_t reserved;
+    float ms_load;            /* device time of the last gg_load_csr (copy + validate + CSC build) */
+    float ms_sample;          /* device time of the last sampling */
+    float ms_run;             /* device time of the last gg_run (sampling included when it resampled) */
+    float ms_gather;          /* GG_TIMING: total time of approximate / accurate pull gathers */
+    float ms_correct;         /* GG_TIMING: total time of correction kernels */
+    float ms_push;            /* GG_TIMING: total time of push-frontier kernels */
+    uint32_t n_gather;        /* GG_TIMING: launches counted in ms_gather */
+    uint32_t n_correct;       /* GG_TIMING: launches counted in ms_correct */
+    uint32_t n_push;          /* GG_TIMING: launches counted in ms_push */
+    uint32_t kernels_launched;/* kernels this library launched during the last gg_run */
+} gg_stats;
+
+typedef struct {
+    uint32_t mode;            /* 0 approximate, 1 accurate, 2 correction, 3 skipped no-op */
+    uint32_t max_delta_bits;  /* max |old-new|: float bits (PageRank) or uint32 */
+    uint64_t arcs;            /* size of the iteration's edge set */
+    uint64_t changed;         /* vertices active after GG-VStatus */
+    uint64_t sum_delta;       /* sum |old-new|: fixed point 2^-40 (PageRank) or exact integer
+                                 over vertices that were reached before */
+    uint64_t active_after;    /* active arcs after the iteration */
+} gg_iter_stats;
+
+typedef struct gg_graph gg_graph;
+
+/*
+ * gg_load_csr - load a graph given by its out-edges (CSR) and build the
+ * in-edge view the pull engine gathers over (Sec. 2.1 GAS gather over
+ * incoming edges; Sec. 3.3 "one flag per edge", no new graph).
+ *   g        out: new handle (set only on GG_OK)
+ *   n, m     vertices and arcs; 1 <= n, 0 <= m < 2^31
+ *   rowptr   int32[n+1], rowptr[0] = 0, non-decreasing, rowptr[n] = m
+ *   colidx   int32[m], destinations in [0, n)
+ *   weights  uint32[m] arc weights (needed by SSSP) or NULL
+ *   gflags   GG_DIRECTED / GG_SYMMETRIC, | GG_DEVICE_PTRS for device inputs
+ * The arrays are copied into library-owned device memory; the caller may
+ * free them on return. The CSR is validated on the device; a bad graph
+ * returns GG_ERR_BAD_GRAPH. In-edge rows list their sources in ascending
+ * order (duplicates in CSR order); this order defines the running influence.
+ */
+gg_status gg_load_csr(gg_graph **g, int32_t n, int64_t m, const int32_t *rowptr,
+                      const int32_t *colidx, const uint32_t *weights, uint32_t gflags);
+
+/*
+ * gg_sample_edges - set the initial edge flags by uniform sparsification
+ * (Sec. 3.4, Fig. 1a): arc src->dst is active iff
+ * SplitMix64(seed ^ (src<<32 | dst)) >> 32 < floor(sample_ratio * 2^32)
+ * (the unordered pair on GG_SYMMETRIC graphs), and pack the active in-edges.
+ *   sample_ratio  sigma in (0, 1]
+ * Enqueued on the stream; returns before the work completes.
+ */
+gg_status gg_sample_edges(gg_graph *g, double sample_ratio, uint64_t seed);
+
+/*
+ * gg_run - one execution of a vertex program under a correction policy
+ * (Sec. 3.3 modes, Sec. 3.4 adaptive correction, Sec. 5.2 SP / SMS).
+ *   app           GG_APP_*; SSSP needs weights; CC expects a symmetric graph
+ *   sample_ratio  sigma; the edges are (re)sampled with (sample_ratio,
+ *                 p->seed) unless the current flags already are that
+ *                 untouched sample. Ignored by GG_POLICY_EXACT.
+ *   policy        GG_POLICY_*
+ *   p             parameters (see gg_params); p->max_iters >= 1
+ * PageRank runs p->max_iters iterations from rank 1/N. SSSP / BFS / CC run
+ * until an accurate iteration changes nothing (or max_iters) and synchronise
+ * the stream once per iteration to choose push or pull. Values stay on the
+ * device until gg_result.
+ */
+gg_status gg_run(gg_graph *g, gg_app app, double sample_ratio, gg_policy policy,
+                 const gg_params *p);
+
+/*
+ * gg_result - copy a result out (synchronises the stream).
+ *   kind           GG_RESULT_*; sizes as listed in gg_result_kind
+ *   dst            destination buffer (host, or device if dst_is_device)
+ *   bytes          size of dst; must be at least the result's size
+ * Returns GG_ERR_STATE if the result does not exist yet (e.g. VALUES before
+ * any run, SPARSE_* before any sampling).
+ */
+gg_status gg_result(gg_graph *g, gg_result_kind kind, void *dst, size_t bytes,
+                    int dst_is_device);
+
+/* Size in bytes of a result (0 if it does not exist yet). */
+size_t gg_result_size(gg_graph *g, gg_result_kind kind);
+
+/* gg_set_stream - enqueue all later work of g on this cudaStream_t (e.g.
+ * torch.cuda.current_stream().cuda_stream). NULL = the legacy default stream. */
+gg_status gg_set_stream(gg_graph *g, void *cuda_stream);
+
+/* gg_free_graph - release every device buffer of g (NULL is a no-op). */
+void gg_free_graph(gg_graph *g);
+
+/* gg_last_error - message of the last failure on this thread. */
+const char *gg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GG_H */

@@ -1,0 +1,735 @@
+// gg_api.cu - the C ABI (gg.h) and the host schedule of GraphGuess runs:
+// sampling (Sec. 3.4), the approximate / accurate / correction iteration
+// sequence of each policy (Sec. 3.4, Sec. 5.2), and the push/pull choice of
+// the min applications.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "gg_graph.cuh"
+
+namespace gg {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+}
+
+gg_status cuda_fail(cudaError_t e, const char *what)
+{
+    set_error("CUDA error in %s: %s", what, cudaGetErrorString(e));
+    return GG_ERR_CUDA;
+}
+
+// A frontier whose out-arcs number less than the list's arcs / this factor is
+// pushed instead of pulled (push pays atomics and a flag lookup per arc).
+constexpr uint64_t kPushFactor = 4;
+
+enum { MODE_APPROX = 0, MODE_ACCURATE = 1, MODE_CORRECTION = 2, MODE_SKIPPED = 3 };
+
+// Mode of iteration i (Sec. 3.4: alpha approximate iterations, then a
+// correction; Sec. 5.2: SP never corrects, SMS corrects once then stays
+// accurate; the exact baseline is accurate throughout).
+static int policy_mode(gg_policy p, uint32_t alpha, uint32_t i)
+{
+    switch (p) {
+    case GG_POLICY_EXACT: return MODE_ACCURATE;
+    case GG_POLICY_NONE: return MODE_APPROX;
+    case GG_POLICY_STATIC_SWITCH:
+        return i < alpha ? MODE_APPROX : (i == alpha ? MODE_CORRECTION : MODE_ACCURATE);
+    case GG_POLICY_ADAPTIVE: return (i % (alpha + 1u)) == alpha ? MODE_CORRECTION : MODE_APPROX;
+    }
+    return MODE_ACCURATE;
+}
+
+// First accurate or correction iteration after approximate iteration i, or
+// -1 if the policy stays approximate for good.
+static int64_t next_accurate(gg_policy p, uint32_t alpha, uint32_t i)
+{
+    if (p == GG_POLICY_NONE) return -1;
+    if (p == GG_POLICY_STATIC_SWITCH) return i < alpha ? (int64_t)alpha : (int64_t)i + 1;
+    if (p == GG_POLICY_ADAPTIVE) {
+        const uint64_t period = (uint64_t)alpha + 1u;
+        return (int64_t)(((uint64_t)i / period) * period + alpha);
+    }
+    return (int64_t)i + 1;
+}
+
+uint32_t next_epoch(gg_graph *g)
+{
+    if (g->epoch >= (1u << 30)) {
+        cudaMemsetAsync(g->st_carry, 0, sizeof(unsigned long long) * (g->max_tiles + 2), g->stream);
+        cudaMemsetAsync(g->st_count, 0, sizeof(unsigned long long) * (g->max_tiles + 2), g->stream);
+        g->epoch = 0;
+    }
+    return ++g->epoch;
+}
+
+static void timed_begin(gg_graph *g, bool on, int cls, size_t *slot)
+{
+    *slot = (size_t)-1;
+    if (!on) return;
+    if (g->timed_used == g->timed.size()) {
+        TimedLaunch t{};
+        t.cls = cls;
+        if (cudaEventCreate(&t.start) != cudaSuccess || cudaEventCreate(&t.stop) != cudaSuccess) return;
+        g->timed.push_back(t);
+    }
+    TimedLaunch &t = g->timed[g->timed_used];
+    t.cls = cls;
+    cudaEventRecord(t.start, g->stream);
+    *slot = g->timed_used++;
+}
+
+static void timed_end(gg_graph *g, size_t slot)
+{
+    if (slot != (size_t)-1) cudaEventRecord(g->timed[slot].stop, g->stream);
+}
+
+static void fill_list(const gg_graph *g, bool sparse, TileArgs &a)
+{
+    a.n = g->n;
+    a.out_ptr = g->out_ptr;
+    if (sparse) {
+        a.row_ptr = g->sp_ptr;
+        a.arc_src = g->sp_src;
+        a.arc_w = g->has_w ? g->sp_w : nullptr;
+        a.list_nnz = g->sp_nnz;
+        a.tile_row = g->sp_tile_row;
+        a.num_tiles = g->sp_num_tiles;
+    } else {
+        a.row_ptr = g->in_ptr;
+        a.arc_src = g->in_src;
+        a.arc_w = g->has_w ? g->in_w : nullptr;
+        a.list_nnz = g->full_nnz;
+        a.tile_row = g->full_tile_row;
+        a.num_tiles = g->full_num_tiles;
+    }
+    a.sched = g->sched;
+    a.st_carry = g->st_carry;
+    a.st_count = g->st_count;
+    a.err = g->dev_err;
+}
+
+gg_status sample_edges(gg_graph *g, double ratio, uint64_t seed)
+{
+    if (!(ratio > 0.0 && ratio <= 1.0)) {
+        set_error("sample_ratio must be in (0, 1], got %g", ratio);
+        return GG_ERR_INVALID_ARG;
+    }
+    GG_CUDA(cudaEventRecord(g->ev_s0, g->stream));
+    TileArgs a{};
+    fill_list(g, false, a);
+    a.mask = g->mask;
+    a.sp_ptr = g->sp_ptr;
+    a.sp_src = g->sp_src;
+    a.sp_w = g->has_w ? g->sp_w : nullptr;
+    a.sp_nnz = g->sp_nnz;
+    a.seed = seed;
+    a.thr = (unsigned long long)std::floor(ratio * 4294967296.0);
+    a.symmetric = g->symmetric ? 1 : 0;
+    a.epoch = next_epoch(g);
+    a.stats = nullptr;
+    GG_CUDA(launch_tile_sample(a, (int)g->max_tiles, g->num_sms, g->stream));
+    GG_CUDA(launch_partition(g->sp_ptr, g->n, g->sp_nnz, g->max_tiles, g->sp_tile_row, g->sp_num_tiles,
+                             g->stream));
+    g->launches += 2;
+    GG_CUDA(cudaEventRecord(g->ev_s1, g->stream));
+    g->sample_timed = true;
+    g->sampled = true;
+    g->sample_clean = true;
+    g->sample_ratio = ratio;
+    g->sample_seed = seed;
+    return GG_OK;
+}
+
+static gg_status ensure_iter_cap(gg_graph *g, uint32_t iters)
+{
+    if (g->iter_cap < iters) {
+        gg_status st = g->b_iter.alloc(sizeof(IterStatsDev) * iters);
+        if (st != GG_OK) return st;
+        g->iter_stats = (IterStatsDev *)g->b_iter.p;
+        g->iter_cap = iters;
+    }
+    GG_CUDA(cudaMemsetAsync(g->iter_stats, 0, sizeof(IterStatsDev) * iters, g->stream));
+    return GG_OK;
+}
+
+static gg_status run_pagerank(gg_graph *g, gg_policy policy, const gg_params *p)
+{
+    const bool timing = (p->flags & GG_TIMING) != 0;
+    g->cur = 0;
+    GG_CUDA(launch_init_pr(g->n, g->out_ptr, g->rank[0], g->contrib[0], g->num_sms, g->stream));
+    g->launches += 1;
+    const float base = (1.0f - p->damping) / (float)g->n;
+    for (uint32_t i = 0; i < p->max_iters; ++i) {
+        const int mode = policy_mode(policy, p->alpha, i);
+        const int kind = mode == MODE_CORRECTION ? K_CORRECT : K_GATHER;
+        TileArgs a{};
+        fill_list(g, mode == MODE_APPROX, a);
+        a.contrib_cur = g->contrib[g->cur];
+        a.rank_cur = g->rank[g->cur];
+        a.rank_next = g->rank[g->cur ^ 1];
+        a.contrib_next = g->contrib[g->cur ^ 1];
+        a.base = base;
+        a.damping = p->damping;
+        a.epsilon = p->epsilon;
+        a.epoch = next_epoch(g);
+        a.stats = g->iter_stats + i;
+        if (kind == K_CORRECT) {
+            a.mask = g->mask;
+            a.sp_ptr = g->sp_ptr;
+            a.sp_src = g->sp_src;
+            a.sp_w = nullptr;
+            a.sp_nnz = g->sp_nnz;
+            a.theta = p->theta;
+        }
+        GG_CUDA(launch_iter_header(a.stats, (uint32_t)mode, a.list_nnz, 0, g->stream));
+        size_t slot;
+        timed_begin(g, timing, kind == K_CORRECT ? 1 : 0, &slot);
+        GG_CUDA(launch_tile_pr(kind, a, (int)g->max_tiles, g->num_sms, g->stream));
+        timed_end(g, slot);
+        g->launches += 2;
+        if (kind == K_CORRECT) {
+            GG_CUDA(launch_partition(g->sp_ptr, g->n, g->sp_nnz, g->max_tiles, g->sp_tile_row,
+                                     g->sp_num_tiles, g->stream));
+            g->launches += 1;
+            g->sample_clean = false;
+            g->stats.corrections += 1;
+        }
+        g->stats.pull_iterations += 1;
+        g->cur ^= 1;
+        g->iterations = i + 1;
+        if ((p->flags & GG_STOP_QUIESCE) && mode != MODE_APPROX) {
+            unsigned long long changed = 0;
+            GG_CUDA(cudaMemcpyAsync(&changed, &g->iter_stats[i].changed, sizeof changed, cudaMemcpyDeviceToHost,
+                                    g->stream));
+            GG_CUDA(cudaStreamSynchronize(g->stream));
+            if (changed == 0) break;
+        }
+    }
+    return GG_OK;
+}
+
+// Read a device scalar (synchronises the stream).
+static gg_status read_u32(gg_graph *g, const uint32_t *d, uint32_t *h)
+{
+    GG_CUDA(cudaMemcpyAsync(h, d, sizeof(uint32_t), cudaMemcpyDeviceToHost, g->stream));
+    GG_CUDA(cudaStreamSynchronize(g->stream));
+    return GG_OK;
+}
+
+// Out-degree prefix of the frontier q[qc] (q_len known); returns its total.
+static gg_status frontier_degrees(gg_graph *g, int qc, uint32_t qlen, uint64_t *total)
+{
+    *total = 0;
+    if (qlen == 0) return GG_OK;
+    GG_CUDA(launch_qdeg(g->q[qc], &g->q_len[qc], g->out_ptr, g->q_deg, qlen, g->num_sms, g->stream));
+    GG_CUDA(launch_scan_u32(g->q_deg, g->q_deg, qlen, g->scan_tmp, g->stream));
+    g->launches += 4;
+    uint32_t t = 0;
+    gg_status st = read_u32(g, g->q_deg + qlen, &t);
+    *total = t;
+    return st;
+}
+
+static gg_status run_min(gg_graph *g, gg_app app, gg_policy policy, const gg_params *p)
+{
+    const bool timing = (p->flags & GG_TIMING) != 0;
+    g->cur = 0;
+    int qc = 0;
+    GG_CUDA(launch_init_min(g->n, (int)app, p->source, g->val[0], g->q[0], g->q_val[0], &g->q_len[0], g->num_sms,
+                            g->stream));
+    g->launches += 1;
+    uint32_t qlen = app == GG_APP_CC ? (uint32_t)g->n : 1u;
+    uint64_t front_arcs = 0;
+    gg_status st = frontier_degrees(g, qc, qlen, &front_arcs);
+    if (st != GG_OK) return st;
+    if (policy != GG_POLICY_EXACT) {
+        st = read_u32(g, g->sp_nnz, &g->sp_nnz_host);
+        if (st != GG_OK) return st;
+    }
+    int theta_case = 0;
+    unsigned long long theta_fx = 0;
+    const double th = (double)p->theta;
+    if (th < 0.0) theta_case = 1;
+    else if (th >= 1.0) theta_case = 2;
+    else theta_fx = (unsigned long long)std::floor(th * 4294967296.0);
+
+    for (uint32_t i = 0; i < p->max_iters; ++i) {
+        const int mode = policy_mode(policy, p->alpha, i);
+        const int nq = qc ^ 1;
+        GG_CUDA(cudaMemsetAsync(&g->q_len[nq], 0, sizeof(uint32_t), g->stream));
+        const uint64_t list_nnz = mode == MODE_APPROX ? g->sp_nnz_host : (uint64_t)g->m;
+        bool push = mode != MODE_CORRECTION && !(p->flags & GG_FORCE_PULL) &&
+                    ((p->flags & GG_FORCE_PUSH) || front_arcs * kPushFactor < list_nnz);
+        IterStatsDev *sti = g->iter_stats + i;
+        GG_CUDA(launch_iter_header(sti, (uint32_t)mode, nullptr, list_nnz, g->stream));
+        g->launches += 1;
+        if (push) {
+            if (++g->stamp_tag == 0) {
+                GG_CUDA(cudaMemsetAsync(g->stamp, 0, sizeof(uint32_t) * g->n, g->stream));
+                g->stamp_tag = 1;
+            }
+            PushArgs pa{};
+            pa.q = g->q[qc];
+            pa.q_val = g->q_val[qc];
+            pa.q_len = &g->q_len[qc];
+            pa.q_deg_ex = g->q_deg;
+            pa.out_ptr = g->out_ptr;
+            pa.out_dst = g->out_dst;
+            pa.out_w = g->out_w;
+            pa.out_to_in = g->out_to_in;
+            pa.mask = mode == MODE_APPROX ? g->mask : nullptr;
+            pa.val = g->val[g->cur];
+            pa.stamp = g->stamp;
+            pa.stamp_tag = g->stamp_tag;
+            pa.q_out = g->q[nq];
+            pa.q_out_len = &g->q_len[nq];
+            pa.sched = g->sched;
+            pa.err = g->dev_err;
+            pa.app = (int)app;
+            size_t slot;
+            timed_begin(g, timing, 2, &slot);
+            GG_CUDA(launch_push(pa, (uint32_t)front_arcs, g->num_sms * 8, g->stream));
+            timed_end(g, slot);
+            GG_CUDA(launch_snapshot(g->q[nq], &g->q_len[nq], g->val[g->cur], g->q_val[nq], (uint32_t)g->n,
+                                    g->num_sms, g->stream));
+            GG_CUDA(launch_iter_changed(sti, &g->q_len[nq], g->stream));
+            g->launches += 3;
+            g->stats.push_iterations += 1;
+        } else {
+            const int kind = mode == MODE_CORRECTION ? K_CORRECT : K_GATHER;
+            TileArgs a{};
+            fill_list(g, mode == MODE_APPROX, a);
+            a.val_cur = g->val[g->cur];
+            a.val_next = g->val[g->cur ^ 1];
+            a.epoch = next_epoch(g);
+            a.stats = sti;
+            a.q_out = g->q[nq];
+            a.q_out_val = g->q_val[nq];
+            a.q_out_len = &g->q_len[nq];
+            if (app != GG_APP_SSSP) a.arc_w = nullptr;
+            if (kind == K_CORRECT) {
+                a.mask = g->mask;
+                a.sp_ptr = g->sp_ptr;
+                a.sp_src = g->sp_src;
+                a.sp_w = (app == GG_APP_SSSP && g->has_w) ? g->sp_w : nullptr;
+                a.sp_nnz = g->sp_nnz;
+                a.theta_case = theta_case;
+                a.theta_fx = theta_fx;
+                a.est_strict = (p->flags & GG_EST_STRICT) ? 1 : 0;
+            }
+            size_t slot;
+            timed_begin(g, timing, kind == K_CORRECT ? 1 : 0, &slot);
+            GG_CUDA(launch_tile_min((int)app, kind, a, (int)g->max_tiles, g->num_sms, g->stream));
+            timed_end(g, slot);
+            g->launches += 1;
+            if (kind == K_CORRECT) {
+                GG_CUDA(launch_partition(g->sp_ptr, g->n, g->sp_nnz, g->max_tiles, g->sp_tile_row,
+                                         g->sp_num_tiles, g->stream));
+                g->launches += 1;
+                g->sample_clean = false;
+                g->stats.corrections += 1;
+                st = read_u32(g, g->sp_nnz, &g->sp_nnz_host);
+                if (st != GG_OK) return st;
+            }
+            g->cur ^= 1;
+            g->stats.pull_iterations += 1;
+        }
+        qc = nq;
+        st = read_u32(g, &g->q_len[qc], &qlen);
+        if (st != GG_OK) return st;
+        g->iterations = i + 1;
+        if (qlen == 0) {
+            // Quiet iteration: an accurate one means a fixed point of the full
+            // graph; an approximate one makes every approximate iteration up to
+            // the next accurate one a no-op (skipped, still counted).
+            if (mode != MODE_APPROX) break;
+            const int64_t nxt = next_accurate(policy, p->alpha, i);
+            if (nxt < 0) break;
+            for (uint32_t j = i + 1; j < (uint32_t)nxt && j < p->max_iters; ++j) {
+                GG_CUDA(launch_iter_header(g->iter_stats + j, MODE_SKIPPED, nullptr, 0, g->stream));
+                g->launches += 1;
+                g->iterations = j + 1;
+            }
+            if ((uint64_t)nxt >= p->max_iters) break;
+            i = (uint32_t)nxt - 1;
+            front_arcs = 0;
+            continue;
+        }
+        st = frontier_degrees(g, qc, qlen, &front_arcs);
+        if (st != GG_OK) return st;
+    }
+    uint32_t err = 0;
+    st = read_u32(g, g->dev_err, &err);
+    if (st != GG_OK) return st;
+    if (err & DEVERR_TIMEOUT) {
+        set_error("a bounded device-side wait gave up");
+        return GG_ERR_TIMEOUT;
+    }
+    return GG_OK;
+}
+
+gg_status run(gg_graph *g, gg_app app, double ratio, gg_policy policy, const gg_params *p)
+{
+    if (!p) { set_error("gg_run: params is NULL"); return GG_ERR_INVALID_ARG; }
+    if ((int)app < GG_APP_PAGERANK || (int)app > GG_APP_CC) { set_error("gg_run: unknown app %d", (int)app); return GG_ERR_INVALID_ARG; }
+    if ((int)policy < GG_POLICY_EXACT || (int)policy > GG_POLICY_ADAPTIVE) { set_error("gg_run: unknown policy %d", (int)policy); return GG_ERR_INVALID_ARG; }
+    if (p->max_iters < 1) { set_error("gg_run: max_iters must be >= 1"); return GG_ERR_INVALID_ARG; }
+    if (app == GG_APP_SSSP && !g->has_w) { set_error("gg_run: SSSP needs arc weights"); return GG_ERR_INVALID_ARG; }
+    if ((app == GG_APP_SSSP || app == GG_APP_BFS) && (p->source < 0 || p->source >= g->n)) {
+        set_error("gg_run: source %d outside [0, %d)", p->source, g->n);
+        return GG_ERR_INVALID_ARG;
+    }
+    if (app == GG_APP_PAGERANK && !(p->damping >= 0.0f && p->damping <= 1.0f)) {
+        set_error("gg_run: damping must be in [0, 1]");
+        return GG_ERR_INVALID_ARG;
+    }
+    if (policy != GG_POLICY_EXACT && !(ratio > 0.0 && ratio <= 1.0)) {
+        set_error("gg_run: sample_ratio must be in (0, 1], got %g", ratio);
+        return GG_ERR_INVALID_ARG;
+    }
+    if (p->alpha == 0xFFFFFFFFu) { set_error("gg_run: alpha too large"); return GG_ERR_INVALID_ARG; }
+    gg_status st = ensure_iter_cap(g, p->max_iters);
+    if (st != GG_OK) return st;
+    g->stats = gg_stats{};
+    g->timed_used = 0;
+    g->launches = 0;
+    g->iterations = 0;
+    g->last_app = -1;
+    GG_CUDA(cudaMemsetAsync(g->dev_err, 0, sizeof(uint32_t), g->stream));
+    GG_CUDA(cudaEventRecord(g->ev_run0, g->stream));
+    if (policy != GG_POLICY_EXACT &&
+        !(g->sampled && g->sample_clean && g->sample_ratio == ratio && g->sample_seed == p->seed)) {
+        st = sample_edges(g, ratio, p->seed);
+        if (st != GG_OK) return st;
+    }
+    st = app == GG_APP_PAGERANK ? run_pagerank(g, policy, p) : run_min(g, app, policy, p);
+    GG_CUDA(cudaEventRecord(g->ev_run1, g->stream));
+    g->run_timed = true;
+    if (st != GG_OK) return st;
+    g->last_app = (int)app;
+    g->stats.iterations = g->iterations;
+    g->stats.kernels_launched = g->launches;
+    return GG_OK;
+}
+
+}  // namespace gg
+
+using namespace gg;
+
+static gg_status alloc_graph(gg_graph *g)
+{
+    const size_t n = (size_t)g->n, m = (size_t)g->m;
+    gg_status st;
+#define GG_ALLOC(buf, bytes)                    \
+    do {                                        \
+        if ((st = (buf).alloc(bytes)) != GG_OK) \
+            return st;                          \
+    } while (0)
+    GG_ALLOC(g->b_out_ptr, 4 * (n + 1));
+    GG_ALLOC(g->b_out_dst, 4 * m);
+    GG_ALLOC(g->b_in_ptr, 4 * (n + 1));
+    GG_ALLOC(g->b_in_src, 4 * m);
+    GG_ALLOC(g->b_out_to_in, 4 * m);
+    GG_ALLOC(g->b_sp_ptr, 4 * (n + 1));
+    GG_ALLOC(g->b_sp_src, 4 * m);
+    if (g->has_w) {
+        GG_ALLOC(g->b_out_w, 4 * m);
+        GG_ALLOC(g->b_in_w, 4 * m);
+        GG_ALLOC(g->b_sp_w, 4 * m);
+    }
+    g->max_tiles = (uint32_t)(((uint64_t)n + m + kTile - 1) / kTile) + 1;
+    GG_ALLOC(g->b_full_tile_row, 4 * ((size_t)g->max_tiles + 2));
+    GG_ALLOC(g->b_sp_tile_row, 4 * ((size_t)g->max_tiles + 2));
+    GG_ALLOC(g->b_scalars, 4 * 16);
+    g->mask_words = (m + 31) / 32;
+    GG_ALLOC(g->b_mask, 4 * (g->mask_words + 1));
+    GG_ALLOC(g->b_vals, 4 * 4 * n);
+    GG_ALLOC(g->b_front, 4 * (6 * n + 2));
+    GG_ALLOC(g->b_sched, sizeof(TileSched) * 2);
+    GG_ALLOC(g->b_status, sizeof(unsigned long long) * 2 * ((size_t)g->max_tiles + 2));
+    GG_ALLOC(g->b_scan_tmp, 4 * scan_tmp_words(n + 1));
+#undef GG_ALLOC
+    g->out_ptr = g->b_out_ptr.i32();
+    g->out_dst = g->b_out_dst.i32();
+    g->out_w = g->has_w ? g->b_out_w.u32() : nullptr;
+    g->in_ptr = g->b_in_ptr.i32();
+    g->in_src = g->b_in_src.i32();
+    g->in_w = g->has_w ? g->b_in_w.u32() : nullptr;
+    g->out_to_in = g->b_out_to_in.i32();
+    g->sp_ptr = g->b_sp_ptr.i32();
+    g->sp_src = g->b_sp_src.i32();
+    g->sp_w = g->has_w ? g->b_sp_w.u32() : nullptr;
+    g->full_tile_row = g->b_full_tile_row.i32();
+    g->sp_tile_row = g->b_sp_tile_row.i32();
+    uint32_t *sc = g->b_scalars.u32();
+    g->full_num_tiles = sc + 0;
+    g->sp_num_tiles = sc + 1;
+    g->full_nnz = sc + 2;
+    g->sp_nnz = sc + 3;
+    g->dev_err = sc + 4;
+    g->q_len = sc + 6;  // two entries
+    g->mask = g->b_mask.u32();
+    float *v = g->b_vals.f32();
+    g->rank[0] = v;
+    g->rank[1] = v + n;
+    g->contrib[0] = v + 2 * n;
+    g->contrib[1] = v + 3 * n;
+    g->val[0] = (uint32_t *)g->rank[0];
+    g->val[1] = (uint32_t *)g->rank[1];
+    uint32_t *f = g->b_front.u32();
+    g->q[0] = (int32_t *)f;
+    g->q[1] = (int32_t *)(f + n);
+    g->q_val[0] = f + 2 * n;
+    g->q_val[1] = f + 3 * n;
+    g->stamp = f + 4 * n;
+    g->q_deg = f + 5 * n;
+    g->sched = (TileSched *)g->b_sched.p;
+    g->st_carry = (unsigned long long *)g->b_status.p;
+    g->st_count = g->st_carry + g->max_tiles + 2;
+    g->scan_tmp = g->b_scan_tmp.u32();
+    return GG_OK;
+}
+
+extern "C" {
+
+gg_status gg_load_csr(gg_graph **out, int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx,
+                      const uint32_t *weights, uint32_t gflags)
+{
+    if (!out) { set_error("gg_load_csr: out is NULL"); return GG_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (n < 1) { set_error("gg_load_csr: n must be >= 1, got %d", n); return GG_ERR_INVALID_ARG; }
+    if (m < 0 || m >= ((int64_t)1 << 31) - 1) { set_error("gg_load_csr: m must be in [0, 2^31-1), got %lld", (long long)m); return GG_ERR_INVALID_ARG; }
+    if (!rowptr || (m > 0 && !colidx)) { set_error("gg_load_csr: rowptr/colidx is NULL"); return GG_ERR_INVALID_ARG; }
+    if (gflags & ~(GG_SYMMETRIC | GG_DEVICE_PTRS)) { set_error("gg_load_csr: unknown flags 0x%x", gflags); return GG_ERR_INVALID_ARG; }
+    gg_graph *g = new (std::nothrow) gg_graph();
+    if (!g) { set_error("gg_load_csr: host allocation failed"); return GG_ERR_OOM; }
+    g->n = n;
+    g->m = m;
+    g->symmetric = (gflags & GG_SYMMETRIC) != 0;
+    g->has_w = weights != nullptr;
+    gg_status st = GG_OK;
+    cudaError_t e;
+    do {
+        if ((e = cudaGetDevice(&g->device)) != cudaSuccess) { st = cuda_fail(e, "cudaGetDevice"); break; }
+        if ((e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device)) != cudaSuccess) {
+            st = cuda_fail(e, "cudaDeviceGetAttribute");
+            break;
+        }
+        if ((e = cudaEventCreate(&g->ev_run0)) != cudaSuccess || (e = cudaEventCreate(&g->ev_run1)) != cudaSuccess ||
+            (e = cudaEventCreate(&g->ev_s0)) != cudaSuccess || (e = cudaEventCreate(&g->ev_s1)) != cudaSuccess) {
+            st = cuda_fail(e, "cudaEventCreate");
+            break;
+        }
+        if ((st = alloc_graph(g)) != GG_OK) break;
+        cudaEvent_t l0, l1;
+        cudaEventCreate(&l0);
+        cudaEventCreate(&l1);
+        cudaEventRecord(l0, g->stream);
+        const cudaMemcpyKind kind = (gflags & GG_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        if ((e = cudaMemcpyAsync(g->out_ptr, rowptr, 4 * ((size_t)n + 1), kind, g->stream)) != cudaSuccess ||
+            (m > 0 && (e = cudaMemcpyAsync(g->out_dst, colidx, 4 * (size_t)m, kind, g->stream)) != cudaSuccess) ||
+            (g->has_w && m > 0 && (e = cudaMemcpyAsync(g->out_w, weights, 4 * (size_t)m, kind, g->stream)) != cudaSuccess)) {
+            st = cuda_fail(e, "cudaMemcpyAsync (graph upload)");
+            cudaEventDestroy(l0);
+            cudaEventDestroy(l1);
+            break;
+        }
+        uint32_t mm = (uint32_t)m;
+        if ((st = validate_csr(g)) != GG_OK || (st = build_csc(g)) != GG_OK) {
+            cudaEventDestroy(l0);
+            cudaEventDestroy(l1);
+            break;
+        }
+        if ((e = cudaMemcpyAsync(g->full_nnz, &mm, 4, cudaMemcpyHostToDevice, g->stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(g->b_sched.p, 0, g->b_sched.bytes, g->stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(g->b_status.p, 0, g->b_status.bytes, g->stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(g->stamp, 0, 4 * (size_t)n, g->stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(g->mask, 0, 4 * (g->mask_words + 1), g->stream)) != cudaSuccess) {
+            st = cuda_fail(e, "cudaMemsetAsync (graph state)");
+            cudaEventDestroy(l0);
+            cudaEventDestroy(l1);
+            break;
+        }
+        if ((e = launch_partition(g->in_ptr, n, g->full_nnz, g->max_tiles, g->full_tile_row, g->full_num_tiles,
+                                  g->stream)) != cudaSuccess) {
+            st = cuda_fail(e, "partition");
+            cudaEventDestroy(l0);
+            cudaEventDestroy(l1);
+            break;
+        }
+        cudaEventRecord(l1, g->stream);
+        if ((e = cudaStreamSynchronize(g->stream)) != cudaSuccess) {
+            st = cuda_fail(e, "cudaStreamSynchronize (load)");
+            cudaEventDestroy(l0);
+            cudaEventDestroy(l1);
+            break;
+        }
+        cudaEventElapsedTime(&g->stats.ms_load, l0, l1);
+        cudaEventDestroy(l0);
+        cudaEventDestroy(l1);
+    } while (0);
+    if (st != GG_OK) {
+        gg_free_graph(g);
+        return st;
+    }
+    *out = g;
+    return GG_OK;
+}
+
+gg_status gg_sample_edges(gg_graph *g, double sample_ratio, uint64_t seed)
+{
+    if (!g) { set_error("gg_sample_edges: graph is NULL"); return GG_ERR_INVALID_ARG; }
+    return sample_edges(g, sample_ratio, seed);
+}
+
+gg_status gg_run(gg_graph *g, gg_app app, double sample_ratio, gg_policy policy, const gg_params *p)
+{
+    if (!g) { set_error("gg_run: graph is NULL"); return GG_ERR_INVALID_ARG; }
+    return run(g, app, sample_ratio, policy, p);
+}
+
+static size_t result_size(gg_graph *g, gg_result_kind kind, const void **src)
+{
+    *src = nullptr;
+    const size_t n = (size_t)g->n, m = (size_t)g->m;
+    switch (kind) {
+    case GG_RESULT_VALUES:
+        if (g->last_app < 0) return 0;
+        *src = g->last_app == GG_APP_PAGERANK ? (const void *)g->rank[g->cur] : (const void *)g->val[g->cur];
+        return 4 * n;
+    case GG_RESULT_MASK:
+        if (!g->sampled) return 0;
+        *src = g->mask;
+        return 4 * g->mask_words;
+    case GG_RESULT_STATS: return sizeof(gg_stats);
+    case GG_RESULT_ITER_STATS: *src = g->iter_stats; return sizeof(gg_iter_stats) * g->iterations;
+    case GG_RESULT_CSC_PTR: *src = g->in_ptr; return 4 * (n + 1);
+    case GG_RESULT_CSC_SRC: *src = g->in_src; return 4 * m;
+    case GG_RESULT_CSC_W: if (!g->has_w) return 0; *src = g->in_w; return 4 * m;
+    case GG_RESULT_SPARSE_PTR: if (!g->sampled) return 0; *src = g->sp_ptr; return 4 * (n + 1);
+    case GG_RESULT_SPARSE_SRC:
+        if (!g->sampled) return 0;
+        if (cudaMemcpy(&g->sp_nnz_host, g->sp_nnz, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return 0;
+        *src = g->sp_src;
+        return 4 * (size_t)g->sp_nnz_host;
+    case GG_RESULT_OUT_TO_IN: *src = g->out_to_in; return 4 * m;
+    }
+    return 0;
+}
+
+size_t gg_result_size(gg_graph *g, gg_result_kind kind)
+{
+    if (!g) return 0;
+    if (cudaStreamSynchronize(g->stream) != cudaSuccess) return 0;
+    const void *src;
+    return result_size(g, kind, &src);
+}
+
+static gg_status fill_stats(gg_graph *g)
+{
+    gg_stats &s = g->stats;
+    if (g->iterations > 0) {
+        gg_iter_stats *h = new (std::nothrow) gg_iter_stats[g->iterations];
+        if (!h) { set_error("host allocation failed"); return GG_ERR_OOM; }
+        cudaError_t e = cudaMemcpy(h, g->iter_stats, sizeof(gg_iter_stats) * g->iterations, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) { delete[] h; return cuda_fail(e, "cudaMemcpy (iteration stats)"); }
+        uint64_t arcs = 0;
+        for (uint32_t i = 0; i < g->iterations; ++i) arcs += h[i].mode == MODE_SKIPPED ? 0 : h[i].arcs;
+        s.arcs_processed = arcs;
+        s.changed_last = h[g->iterations - 1].changed;
+        delete[] h;
+    }
+    uint32_t nnz = (uint32_t)g->m;
+    if (g->sampled && !g->sample_clean) cudaMemcpy(&nnz, g->sp_nnz, 4, cudaMemcpyDeviceToHost);
+    else if (g->sampled) cudaMemcpy(&nnz, g->sp_nnz, 4, cudaMemcpyDeviceToHost);
+    s.active_arcs = nnz;
+    uint32_t err = 0;
+    cudaMemcpy(&err, g->dev_err, 4, cudaMemcpyDeviceToHost);
+    s.device_error = err;
+    if (g->run_timed) cudaEventElapsedTime(&s.ms_run, g->ev_run0, g->ev_run1);
+    if (g->sample_timed) cudaEventElapsedTime(&s.ms_sample, g->ev_s0, g->ev_s1);
+    s.ms_gather = s.ms_correct = s.ms_push = 0.0f;
+    s.n_gather = s.n_correct = s.n_push = 0;
+    for (size_t i = 0; i < g->timed_used; ++i) {
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, g->timed[i].start, g->timed[i].stop);
+        if (g->timed[i].cls == 0) { s.ms_gather += ms; s.n_gather++; }
+        else if (g->timed[i].cls == 1) { s.ms_correct += ms; s.n_correct++; }
+        else { s.ms_push += ms; s.n_push++; }
+    }
+    return GG_OK;
+}
+
+gg_status gg_result(gg_graph *g, gg_result_kind kind, void *dst, size_t bytes, int dst_is_device)
+{
+    if (!g || !dst) { set_error("gg_result: graph or dst is NULL"); return GG_ERR_INVALID_ARG; }
+    GG_CUDA(cudaStreamSynchronize(g->stream));
+    if (kind != GG_RESULT_STATS) {
+        uint32_t err = 0;
+        GG_CUDA(cudaMemcpy(&err, g->dev_err, sizeof err, cudaMemcpyDeviceToHost));
+        if (err & DEVERR_TIMEOUT) {
+            set_error("gg_result: a bounded device-side wait of the last run gave up");
+            return GG_ERR_TIMEOUT;
+        }
+    }
+    if ((int)kind < GG_RESULT_VALUES || (int)kind > GG_RESULT_OUT_TO_IN) {
+        set_error("gg_result: unknown kind %d", (int)kind);
+        return GG_ERR_INVALID_ARG;
+    }
+    if (kind == GG_RESULT_STATS) {
+        if (bytes < sizeof(gg_stats)) { set_error("gg_result: buffer too small"); return GG_ERR_INVALID_ARG; }
+        gg_status st = fill_stats(g);
+        if (st != GG_OK) return st;
+        if (dst_is_device) GG_CUDA(cudaMemcpy(dst, &g->stats, sizeof(gg_stats), cudaMemcpyHostToDevice));
+        else memcpy(dst, &g->stats, sizeof(gg_stats));
+        return GG_OK;
+    }
+    const void *src;
+    const size_t need = result_size(g, kind, &src);
+    if (!src && need == 0 && kind != GG_RESULT_SPARSE_SRC && kind != GG_RESULT_ITER_STATS) {
+        set_error("gg_result: result %d does not exist yet", (int)kind);
+        return GG_ERR_STATE;
+    }
+    if (bytes < need) {
+        set_error("gg_result: buffer of %zu bytes, result needs %zu", bytes, need);
+        return GG_ERR_INVALID_ARG;
+    }
+    if (need) GG_CUDA(cudaMemcpy(dst, src, need, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+    return GG_OK;
+}
+
+gg_status gg_set_stream(gg_graph *g, void *cuda_stream)
+{
+    if (!g) { set_error("gg_set_stream: graph is NULL"); return GG_ERR_INVALID_ARG; }
+    g->stream = (cudaStream_t)cuda_stream;
+    return GG_OK;
+}
+
+void gg_free_graph(gg_graph *g)
+{
+    if (!g) return;
+    cudaStreamSynchronize(g->stream);
+    for (auto &t : g->timed) {
+        cudaEventDestroy(t.start);
+        cudaEventDestroy(t.stop);
+    }
+    if (g->ev_run0) cudaEventDestroy(g->ev_run0);
+    if (g->ev_run1) cudaEventDestroy(g->ev_run1);
+    if (g->ev_s0) cudaEventDestroy(g->ev_s0);
+    if (g->ev_s1) cudaEventDestroy(g->ev_s1);
+    delete g;
+}
+
+const char *gg_last_error(void) { return g_err; }
+
+}  // extern "C"

@@ -1,0 +1,380 @@
+// gg_build.cu - graph loading on the device: CSR validation, in-edge (CSC)
+// construction by a stable LSD radix sort of the arcs by destination, the
+// merge-path partition of a list into tiles, and a device-wide exclusive scan.
+//
+// Ordering contract (the in-edge order defines the running edge influence of
+// Alg. 2): CSR arcs are taken in CSR order, which lists sources in ascending
+// order; a stable sort by destination therefore leaves every in-row sorted by
+// source, duplicates in CSR order.
+#include "gg_graph.cuh"
+
+namespace gg {
+
+// ------------------------------------------------------------- partition ----
+// tile_row[t] = rows whose end item precedes diagonal t*kTile of the merged
+// (row ends, arcs) sequence (Merrill-Garland merge-path search).
+__global__ void k_partition(const int32_t *__restrict__ row_ptr, int32_t n,
+                            const uint32_t *__restrict__ list_nnz, uint32_t max_tiles,
+                            int32_t *__restrict__ tile_row, uint32_t *__restrict__ num_tiles)
+{
+    const uint32_t nnz = *list_nnz;
+    const long long total = (long long)n + nnz;
+    const uint32_t nt = (uint32_t)((total + kTile - 1) / kTile);
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0) *num_tiles = nt;
+    if (t > nt || t > max_tiles) return;
+    long long d = (long long)t * kTile;
+    if (d > total) d = total;
+    long long lo = d - (long long)nnz > 0 ? d - (long long)nnz : 0;
+    long long hi = d < n ? d : n;
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if ((long long)row_ptr[mid + 1] <= d - mid - 1) lo = mid + 1;
+        else hi = mid;
+    }
+    tile_row[t] = (int32_t)lo;
+}
+
+cudaError_t launch_partition(const int32_t *row_ptr, int32_t n, const uint32_t *list_nnz,
+                             uint32_t max_tiles, int32_t *tile_row, uint32_t *num_tiles,
+                             cudaStream_t s)
+{
+    const uint32_t threads = 256;
+    const uint32_t blocks = (max_tiles + 1 + threads - 1) / threads;
+    k_partition<<<blocks, threads, 0, s>>>(row_ptr, n, list_nnz, max_tiles, tile_row, num_tiles);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ scan ----
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t *s_warp, uint32_t *total)
+{
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= (uint32_t)o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        uint32_t w = lane < (uint32_t)nw ? s_warp[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+            if (lane >= (uint32_t)o) wi += y;
+        }
+        if (lane < (uint32_t)nw) s_warp[lane] = wi - w;
+        if (lane == (uint32_t)nw - 1) s_warp[32] = wi;
+    }
+    __syncthreads();
+    const uint32_t r = s_warp[warp] + x - v;
+    if (total) *total = s_warp[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_reduce(const uint32_t *__restrict__ in, size_t n, uint32_t *__restrict__ partial)
+{
+    __shared__ uint32_t s_warp[33];
+    const size_t base = (size_t)blockIdx.x * kScanTile;
+    uint32_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const size_t k = base + threadIdx.x + (size_t)i * kScanThreads;
+        if (k < n) sum += in[k];
+    }
+    uint32_t tot;
+    block_excl_scan_u32(sum, s_warp, &tot);
+    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+// Single block: exclusive scan of the tile sums in place; total at [nb].
+__global__ void k_scan_partials(uint32_t *partial, uint32_t nb, uint32_t *out, size_t n)
+{
+    __shared__ uint32_t s_warp[33];
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < nb; base += blockDim.x) {
+        const uint32_t k = base + threadIdx.x;
+        const uint32_t v = k < nb ? partial[k] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_excl_scan_u32(v, s_warp, &tot);
+        if (k < nb) partial[k] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        partial[nb] = carry;
+        if (out) out[n] = carry;
+    }
+}
+
+__global__ void k_scan_down(const uint32_t *in, uint32_t *out, size_t n, const uint32_t *__restrict__ partial)
+{
+    __shared__ uint32_t s_data[kScanTile];
+    __shared__ uint32_t s_warp[33];
+    const size_t base = (size_t)blockIdx.x * kScanTile;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int j = threadIdx.x + i * kScanThreads;
+        s_data[j] = base + j < n ? in[base + j] : 0u;
+    }
+    __syncthreads();
+    uint32_t local[kScanItems];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        local[i] = s_data[threadIdx.x * kScanItems + i];
+        sum += local[i];
+    }
+    uint32_t run = partial[blockIdx.x] + block_excl_scan_u32(sum, s_warp, nullptr);
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        s_data[threadIdx.x * kScanItems + i] = run;
+        run += local[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int j = threadIdx.x + i * kScanThreads;
+        if (base + j < n) out[base + j] = s_data[j];
+    }
+}
+
+size_t scan_tmp_words(size_t n) { return (n + kScanTile - 1) / kScanTile + 2; }
+
+// out[0..n) = exclusive prefix of in[0..n); out[n] = total (out needs n+1
+// words). in and out may alias.
+cudaError_t launch_scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint32_t *tmp, cudaStream_t s)
+{
+    const uint32_t nb = (uint32_t)((n + kScanTile - 1) / kScanTile);
+    if (nb > 0) k_scan_reduce<<<nb, kScanThreads, 0, s>>>(in, n, tmp);
+    k_scan_partials<<<1, 1024, 0, s>>>(tmp, nb, out, n);
+    if (nb > 0) k_scan_down<<<nb, kScanThreads, 0, s>>>(in, out, n, tmp);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ validation ----
+__global__ void k_validate(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
+                           int32_t n, long long m, uint32_t *err)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)n + 1 || i < m; i += stride) {
+        if (i <= n) {
+            const int32_t r = rowptr[i];
+            bool bad = (i == 0 && r != 0) || (i == n && (long long)r != m) || r < 0 || (long long)r > m;
+            if (i < n && rowptr[i + 1] < r) bad = true;
+            if (bad) atomicOr(err, DEVERR_BAD_GRAPH);
+        }
+        if (i < m) {
+            const int32_t c = colidx[i];
+            if (c < 0 || c >= n) atomicOr(err, DEVERR_BAD_GRAPH);
+        }
+    }
+}
+
+// Source vertex of every CSR arc (one warp per row, grid-stride).
+__global__ void k_expand_src(const int32_t *__restrict__ rowptr, int32_t n, int32_t *__restrict__ src_of)
+{
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long v = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+        const int32_t b = rowptr[v], e = rowptr[v + 1];
+        for (int32_t k = b + lane; k < e; k += 32) src_of[k] = (int32_t)v;
+    }
+}
+
+// ------------------------------------------------------------ radix sort ----
+constexpr int kRadixThreads = 256;
+constexpr int kRadixItems = 16;
+constexpr int kRadixTile = kRadixThreads * kRadixItems;
+constexpr int kRadixWarps = kRadixThreads / 32;
+
+__global__ void k_radix_upsweep(const uint32_t *__restrict__ keys, long long m, int shift,
+                                uint32_t num_tiles, uint32_t *__restrict__ counts)
+{
+    __shared__ uint32_t hist[256];
+    hist[threadIdx.x] = 0;
+    __syncthreads();
+    const long long base = (long long)blockIdx.x * kRadixTile;
+#pragma unroll
+    for (int i = 0; i < kRadixItems; ++i) {
+        const long long k = base + threadIdx.x + (long long)i * kRadixThreads;
+        if (k < m) atomicAdd(&hist[(keys[k] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    counts[(size_t)threadIdx.x * num_tiles + blockIdx.x] = hist[threadIdx.x];
+}
+
+// Stable scatter of one 8-bit digit. Warp w ranks positions
+// [w*512, w*512+512) of the tile in rounds of 32, so the order of equal
+// digits inside the tile is (warp, round, lane) = input order.
+__global__ void __launch_bounds__(kRadixThreads)
+k_radix_downsweep(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
+                  uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, long long m,
+                  int shift, uint32_t num_tiles, const uint32_t *__restrict__ offsets)
+{
+    __shared__ uint32_t s_keys[kRadixTile];
+    __shared__ uint32_t s_vals[kRadixTile];
+    __shared__ uint32_t s_whist[kRadixWarps][256];
+    __shared__ uint32_t s_tile_excl[256];
+    __shared__ uint32_t s_glob[256];
+    __shared__ uint32_t s_warp[33];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long base = (long long)blockIdx.x * kRadixTile;
+    const int count = (int)((m - base) < kRadixTile ? (m - base) : kRadixTile);
+    for (int i = tid; i < kRadixWarps * 256; i += kRadixThreads) (&s_whist[0][0])[i] = 0;
+    __syncthreads();
+
+    uint32_t key[kRadixItems], val[kRadixItems], rank[kRadixItems];
+    const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int r = 0; r < kRadixItems; ++r) {
+        const int p = warp * (kRadixItems * 32) + r * 32 + lane;
+        const bool valid = p < count;
+        key[r] = valid ? keys_in[base + p] : 0u;
+        val[r] = valid ? vals_in[base + p] : 0u;
+        const uint32_t digit = valid ? ((key[r] >> shift) & 255u) : 256u;
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, digit);
+        uint32_t before = 0;
+        if (valid) before = s_whist[warp][digit];
+        __syncwarp();
+        if (valid && (peers & lt) == 0) s_whist[warp][digit] = before + __popc(peers);
+        __syncwarp();
+        rank[r] = before + __popc(peers & lt);
+    }
+    __syncthreads();
+    {
+        const int d = tid;   // 256 threads = 256 digits
+        uint32_t run = 0;
+        for (int w = 0; w < kRadixWarps; ++w) {
+            const uint32_t c = s_whist[w][d];
+            s_whist[w][d] = run;
+            run += c;
+        }
+        s_glob[d] = offsets[(size_t)d * num_tiles + blockIdx.x];
+        s_tile_excl[d] = block_excl_scan_u32(run, s_warp, nullptr);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kRadixItems; ++r) {
+        const int p = warp * (kRadixItems * 32) + r * 32 + lane;
+        if (p < count) {
+            const uint32_t digit = (key[r] >> shift) & 255u;
+            const uint32_t lp = s_tile_excl[digit] + s_whist[warp][digit] + rank[r];
+            s_keys[lp] = key[r];
+            s_vals[lp] = val[r];
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < count; i += kRadixThreads) {
+        const uint32_t k = s_keys[i];
+        const uint32_t digit = (k >> shift) & 255u;
+        const uint32_t g = s_glob[digit] + (uint32_t)i - s_tile_excl[digit];
+        keys_out[g] = k;
+        vals_out[g] = s_vals[i];
+    }
+}
+
+// in_ptr from destination-sorted keys: every boundary writes the row starts
+// of the rows it opens (empty rows included).
+__global__ void k_csc_rowptr(const uint32_t *__restrict__ keys, long long m, int32_t n, int32_t *__restrict__ in_ptr)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += stride) {
+        const int32_t u = (int32_t)keys[k];
+        const int32_t prev = k == 0 ? -1 : (int32_t)keys[k - 1];
+        for (int32_t v = prev + 1; v <= u; ++v) in_ptr[v] = (int32_t)k;
+        if (k == m - 1)
+            for (int32_t v = u + 1; v <= n; ++v) in_ptr[v] = (int32_t)m;
+    }
+}
+
+__global__ void k_csc_finalize(const uint32_t *__restrict__ vals, long long m, const int32_t *__restrict__ src_of,
+                               const uint32_t *__restrict__ w_out, int32_t *__restrict__ in_src,
+                               uint32_t *__restrict__ in_w, int32_t *__restrict__ out_to_in)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += stride) {
+        const uint32_t e = vals[k];
+        in_src[k] = src_of[e];
+        if (w_out) in_w[k] = w_out[e];
+        out_to_in[e] = (int32_t)k;
+    }
+}
+
+__global__ void k_iota(uint32_t *v, long long m)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += stride) v[k] = (uint32_t)k;
+}
+
+// -------------------------------------------------------------- host side ----
+gg_status build_csc(gg_graph *g)
+{
+    cudaStream_t s = g->stream;
+    const long long m = g->m;
+    const int32_t n = g->n;
+    const int grid = g->num_sms * 8;
+    if (m == 0) {
+        GG_CUDA(cudaMemsetAsync(g->in_ptr, 0, sizeof(int32_t) * ((size_t)n + 1), s));
+        return GG_OK;
+    }
+    int bits = 1;
+    while (bits < 31 && ((int64_t)1 << bits) < (int64_t)n) ++bits;
+    const int passes = (bits + 7) / 8;
+    const uint32_t num_tiles = (uint32_t)((m + kRadixTile - 1) / kRadixTile);
+    const size_t ncounts = (size_t)256 * num_tiles;
+
+    DevBuf tmp;
+    const size_t words = 4 * (size_t)m + ncounts + 1 + scan_tmp_words(ncounts) + (size_t)m;
+    gg_status st = tmp.alloc(words * sizeof(uint32_t));
+    if (st != GG_OK) return st;
+    uint32_t *keys[2] = {tmp.u32(), tmp.u32() + m};
+    uint32_t *vals[2] = {tmp.u32() + 2 * m, tmp.u32() + 3 * m};
+    uint32_t *counts = tmp.u32() + 4 * m;
+    uint32_t *scan_tmp = counts + ncounts + 1;
+    int32_t *src_of = (int32_t *)(scan_tmp + scan_tmp_words(ncounts));
+
+    GG_CUDA(cudaMemcpyAsync(keys[0], g->out_dst, sizeof(uint32_t) * m, cudaMemcpyDeviceToDevice, s));
+    k_iota<<<grid, 256, 0, s>>>(vals[0], m);
+    k_expand_src<<<grid, 256, 0, s>>>(g->out_ptr, n, src_of);
+    int cur = 0;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        k_radix_upsweep<<<num_tiles, kRadixThreads, 0, s>>>(keys[cur], m, shift, num_tiles, counts);
+        GG_CUDA(launch_scan_u32(counts, counts, ncounts, scan_tmp, s));
+        k_radix_downsweep<<<num_tiles, kRadixThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1],
+                                                              vals[cur ^ 1], m, shift, num_tiles, counts);
+        cur ^= 1;
+    }
+    k_csc_rowptr<<<grid, 256, 0, s>>>(keys[cur], m, n, g->in_ptr);
+    k_csc_finalize<<<grid, 256, 0, s>>>(vals[cur], m, src_of, g->out_w, g->in_src, g->in_w, g->out_to_in);
+    GG_CUDA(cudaGetLastError());
+    // the temporaries are released only after the queued work has used them
+    GG_CUDA(cudaStreamSynchronize(s));
+    return GG_OK;
+}
+
+gg_status validate_csr(gg_graph *g)
+{
+    cudaStream_t s = g->stream;
+    GG_CUDA(cudaMemsetAsync(g->dev_err, 0, sizeof(uint32_t), s));
+    k_validate<<<g->num_sms * 8, 256, 0, s>>>(g->out_ptr, g->out_dst, g->n, g->m, g->dev_err);
+    GG_CUDA(cudaGetLastError());
+    uint32_t err = 0;
+    GG_CUDA(cudaMemcpyAsync(&err, g->dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    GG_CUDA(cudaStreamSynchronize(s));
+    if (err & DEVERR_BAD_GRAPH) {
+        set_error("gg_load_csr: invalid CSR (rowptr not monotone / not 0..m, or colidx outside [0,n))");
+        return GG_ERR_BAD_GRAPH;
+    }
+    return GG_OK;
+}
+
+}  // namespace gg

@@ -1,0 +1,123 @@
+// gg_graph.cuh - host-side state of a loaded graph (not part of the ABI).
+#pragma once
+
+#include <vector>
+
+#include "gg_internal.cuh"
+
+namespace gg {
+
+// Owning device buffer.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    gg_status alloc(size_t b)
+    {
+        release();
+        if (b == 0) b = 16;
+        cudaError_t e = cudaMalloc(&p, b);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            set_error("device allocation of %zu bytes failed: %s", b, cudaGetErrorString(e));
+            return GG_ERR_OOM;
+        }
+        bytes = b;
+        return GG_OK;
+    }
+    uint32_t *u32() const { return (uint32_t *)p; }
+    int32_t *i32() const { return (int32_t *)p; }
+    float *f32() const { return (float *)p; }
+};
+
+struct TimedLaunch {
+    int cls;               // 0 gather, 1 correct, 2 push
+    cudaEvent_t start, stop;
+};
+
+}  // namespace gg
+
+struct gg_graph {
+    int32_t n = 0;
+    int64_t m = 0;
+    bool symmetric = false;
+    bool has_w = false;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+
+    // CSR (out-arcs)
+    gg::DevBuf b_out_ptr, b_out_dst, b_out_w;
+    int32_t *out_ptr = nullptr, *out_dst = nullptr;
+    uint32_t *out_w = nullptr;
+    // CSC (in-arcs), CSR -> CSC positions
+    gg::DevBuf b_in_ptr, b_in_src, b_in_w, b_out_to_in;
+    int32_t *in_ptr = nullptr, *in_src = nullptr, *out_to_in = nullptr;
+    uint32_t *in_w = nullptr;
+    // partitions: full CSC and packed active CSC
+    gg::DevBuf b_full_tile_row, b_sp_tile_row, b_scalars;
+    int32_t *full_tile_row = nullptr, *sp_tile_row = nullptr;
+    uint32_t *full_num_tiles = nullptr, *sp_num_tiles = nullptr, *full_nnz = nullptr, *sp_nnz = nullptr;
+    uint32_t *dev_err = nullptr, *q_len = nullptr;  // q_len[2]
+    uint32_t max_tiles = 0;
+    // flags and packed active in-edges
+    gg::DevBuf b_mask, b_sp_ptr, b_sp_src, b_sp_w;
+    uint32_t *mask = nullptr;
+    size_t mask_words = 0;
+    int32_t *sp_ptr = nullptr, *sp_src = nullptr;
+    uint32_t *sp_w = nullptr;
+    bool sampled = false;        // sp_* / mask hold a sample
+    bool sample_clean = false;   // ... and no correction has changed it since
+    double sample_ratio = 0.0;
+    uint64_t sample_seed = 0;
+    uint32_t sp_nnz_host = 0;
+    // vertex values (double-buffered)
+    gg::DevBuf b_vals;
+    float *rank[2] = {nullptr, nullptr}, *contrib[2] = {nullptr, nullptr};
+    uint32_t *val[2] = {nullptr, nullptr};
+    int cur = 0;
+    int last_app = -1;
+    // frontier
+    gg::DevBuf b_front;
+    int32_t *q[2] = {nullptr, nullptr};
+    uint32_t *q_val[2] = {nullptr, nullptr};
+    uint32_t *q_deg = nullptr;
+    uint32_t *stamp = nullptr;
+    uint32_t stamp_tag = 0;
+    // scheduling and look-back
+    gg::DevBuf b_sched, b_status;
+    gg::TileSched *sched = nullptr;
+    unsigned long long *st_carry = nullptr, *st_count = nullptr;
+    uint32_t epoch = 0;
+    gg::DevBuf b_scan_tmp;
+    uint32_t *scan_tmp = nullptr;
+    // statistics
+    gg::DevBuf b_iter;
+    gg::IterStatsDev *iter_stats = nullptr;
+    uint32_t iter_cap = 0;
+    uint32_t iterations = 0;
+    gg_stats stats{};
+    cudaEvent_t ev_run0 = nullptr, ev_run1 = nullptr, ev_s0 = nullptr, ev_s1 = nullptr;
+    bool run_timed = false, sample_timed = false;
+    std::vector<gg::TimedLaunch> timed;
+    size_t timed_used = 0;
+    uint32_t launches = 0;
+};
+
+namespace gg {
+gg_status build_csc(gg_graph *g);
+gg_status validate_csr(gg_graph *g);
+gg_status sample_edges(gg_graph *g, double ratio, uint64_t seed);
+gg_status run(gg_graph *g, gg_app app, double ratio, gg_policy policy, const gg_params *p);
+uint32_t next_epoch(gg_graph *g);
+}  // namespace gg

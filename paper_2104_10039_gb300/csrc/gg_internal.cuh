@@ -1,0 +1,228 @@
+// gg_internal.cuh - shared definitions of the libgg CUDA sources (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "gg.h"
+
+namespace gg {
+
+// ---------------------------------------------------------------- tiling ----
+// Every gather-type kernel walks a merged list of row ends and arcs
+// ("merge path", Merrill & Garland 2016) cut into tiles of kTile items, so a
+// tile costs the same whatever the degree skew.
+constexpr int kThreads = 256;
+constexpr int kIPT = 8;
+constexpr int kTile = kThreads * kIPT;
+constexpr int kWarps = kThreads / 32;
+constexpr uint32_t kInf = 0xFFFFFFFFu;
+
+// Bounded device waits: a wait gives up after this many polls (each an L2
+// round trip plus a short sleep, about a second in total), flags
+// DEVERR_TIMEOUT and returns; once the flag is up, later waits give up at
+// their next check instead of spending their own second.
+constexpr int kSpinLimit = 1 << 21;
+constexpr int kSpinCheck = 1 << 10;
+
+enum DevErr : uint32_t {
+    DEVERR_TIMEOUT = 1u,
+    DEVERR_BAD_GRAPH = 2u,
+    DEVERR_QUEUE = 4u,
+};
+
+// Per-launch dynamic tile scheduler. Tiles are handed out in increasing order
+// by an atomic counter, so every tile a tile waits on has already started.
+// The last block to leave resets both counters for the next launch.
+struct TileSched {
+    uint32_t next_tile;
+    uint32_t done_blocks;
+};
+
+// Per-iteration statistics as the kernels accumulate them (same layout as
+// gg_iter_stats).
+struct IterStatsDev {
+    uint32_t mode;
+    uint32_t max_delta_bits;
+    unsigned long long arcs;
+    unsigned long long changed;
+    unsigned long long sum_delta;
+    unsigned long long active_after;
+};
+static_assert(sizeof(IterStatsDev) == sizeof(gg_iter_stats), "stats layout");
+
+// Arguments of the tile kernels (one struct for every kind; unused fields are
+// ignored by a given instantiation).
+struct TileArgs {
+    // the list being walked: CSC rows (full, or packed active in-edges)
+    const int32_t *row_ptr;     // n+1
+    const int32_t *arc_src;     // list arcs: source vertex
+    const uint32_t *arc_w;      // list arcs: weight (SSSP) or nullptr
+    int32_t n;
+    const uint32_t *list_nnz;   // device scalar: arcs in the list
+    const int32_t *tile_row;    // rows consumed before each tile (num_tiles + 1)
+    const uint32_t *num_tiles;  // device scalar
+    // vertex state
+    const float *contrib_cur;
+    const float *rank_cur;
+    float *rank_next;
+    float *contrib_next;
+    const int32_t *out_ptr;     // CSR row pointers (full out-degree)
+    const uint32_t *val_cur;
+    uint32_t *val_next;
+    float base;                 // (1-d)/N
+    float damping;
+    float epsilon;
+    // flags and compaction (correction, sampling)
+    uint32_t *mask;             // CSC-order bitmap
+    int32_t *sp_ptr;
+    int32_t *sp_src;
+    uint32_t *sp_w;
+    uint32_t *sp_nnz;
+    float theta;
+    unsigned long long theta_fx;
+    int theta_case;             // 0 compare, 1 theta < 0, 2 theta >= 1
+    int est_strict;
+    unsigned long long seed;
+    unsigned long long thr;     // floor(sigma * 2^32)
+    int symmetric;
+    // scheduling and look-back
+    TileSched *sched;
+    unsigned long long *st_carry;
+    unsigned long long *st_count;
+    uint32_t epoch;
+    uint32_t *err;
+    // statistics and frontier output
+    IterStatsDev *stats;
+    int32_t *q_out;
+    uint32_t *q_out_val;
+    uint32_t *q_out_len;
+};
+
+enum TileKind { K_GATHER = 0, K_CORRECT = 1, K_SAMPLE = 2 };
+
+struct PushArgs {
+    const int32_t *q;           // frontier vertices
+    const uint32_t *q_val;      // their values at the end of the previous iteration
+    const uint32_t *q_len;      // device scalar
+    const uint32_t *q_deg_ex;   // exclusive prefix of their out-degrees (q_len + 1)
+    const int32_t *out_ptr;
+    const int32_t *out_dst;
+    const uint32_t *out_w;
+    const int32_t *out_to_in;
+    const uint32_t *mask;       // nullptr: accurate mode (every arc)
+    uint32_t *val;              // relaxed in place (atomicMin)
+    uint32_t *stamp;
+    uint32_t stamp_tag;
+    int32_t *q_out;
+    uint32_t *q_out_len;
+    TileSched *sched;
+    uint32_t *err;
+    int app;
+};
+
+// ------------------------------------------------------- device helpers ----
+#ifdef __CUDACC__
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Status word of a tile: [epoch:31 | flag:1 | value:32]. A word is ready for a
+// launch when its epoch field equals the launch's epoch, so the arrays never
+// need clearing between launches.
+__device__ __forceinline__ unsigned long long pack_status(uint32_t epoch, uint32_t flag, uint32_t value)
+{
+    return ((unsigned long long)epoch << 33) | ((unsigned long long)(flag & 1u) << 32) | value;
+}
+__device__ __forceinline__ uint32_t status_epoch(unsigned long long w) { return (uint32_t)(w >> 33); }
+__device__ __forceinline__ uint32_t status_flag(unsigned long long w) { return (uint32_t)(w >> 32) & 1u; }
+__device__ __forceinline__ uint32_t status_value(unsigned long long w) { return (uint32_t)w; }
+
+// Poll a status word until it carries `epoch`; on running out of polls, flag
+// a timeout and return `fallback`.
+__device__ __forceinline__ unsigned long long wait_status(const unsigned long long *p, uint32_t epoch,
+                                                         uint32_t *err, unsigned long long fallback)
+{
+    for (int it = 0; it < kSpinLimit; ++it) {
+        unsigned long long w = ld_acquire_u64(p);
+        if (status_epoch(w) == epoch) return w;
+        if ((it & (kSpinCheck - 1)) == kSpinCheck - 1 &&
+            (*(volatile uint32_t *)err & DEVERR_TIMEOUT)) return fallback;
+        __nanosleep(64);
+    }
+    atomicOr(err, DEVERR_TIMEOUT);
+    return fallback;
+}
+
+// Fetch the next tile of a launch (block-uniform); returns -1 when exhausted.
+__device__ __forceinline__ int next_tile(TileSched *s, uint32_t num_tiles, int *s_slot)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) *s_slot = (int)atomicAdd(&s->next_tile, 1u);
+    __syncthreads();
+    int t = *s_slot;
+    return (uint32_t)t < num_tiles ? t : -1;
+}
+
+// Called by every block once it has left its tile loop.
+__device__ __forceinline__ void sched_leave(TileSched *s)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        uint32_t done = atomicAdd(&s->done_blocks, 1u);
+        if (done == gridDim.x - 1) {
+            s->next_tile = 0;
+            s->done_blocks = 0;
+            __threadfence();
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+#endif
+
+// ------------------------------------------------------------ host side ----
+void set_error(const char *fmt, ...);
+gg_status cuda_fail(cudaError_t e, const char *what);
+
+#define GG_CUDA(call)                                   \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+// Launchers (each defined in its own translation unit).
+struct Graph;
+cudaError_t launch_partition(const int32_t *row_ptr, int32_t n, const uint32_t *list_nnz,
+                             uint32_t max_tiles, int32_t *tile_row, uint32_t *num_tiles,
+                             cudaStream_t s);
+// Tile kernels run a persistent grid: min(max_tiles, resident blocks).
+cudaError_t launch_tile_pr(int kind, const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s);
+cudaError_t launch_tile_min(int app, int kind, const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s);
+cudaError_t launch_tile_sample(const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s);
+cudaError_t launch_push(const PushArgs &a, uint32_t max_arcs, int grid, cudaStream_t s);
+cudaError_t launch_scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint32_t *tmp, cudaStream_t s);
+size_t scan_tmp_words(size_t n);
+cudaError_t launch_qdeg(const int32_t *q, const uint32_t *q_len, const int32_t *out_ptr, uint32_t *deg,
+                        uint32_t max_n, int num_sms, cudaStream_t s);
+cudaError_t launch_snapshot(const int32_t *q, const uint32_t *q_len, const uint32_t *val, uint32_t *q_val,
+                            uint32_t max_n, int num_sms, cudaStream_t s);
+cudaError_t launch_init_pr(int32_t n, const int32_t *out_ptr, float *rank, float *contrib, int num_sms,
+                           cudaStream_t s);
+cudaError_t launch_init_min(int32_t n, int app, int32_t source, uint32_t *val, int32_t *q, uint32_t *q_val,
+                            uint32_t *q_len, int num_sms, cudaStream_t s);
+cudaError_t launch_iter_header(IterStatsDev *st, uint32_t mode, const uint32_t *arcs_dev,
+                               unsigned long long arcs, cudaStream_t s);
+cudaError_t launch_iter_changed(IterStatsDev *st, const uint32_t *q_len, cudaStream_t s);
+
+}  // namespace gg

@@ -1,0 +1,197 @@
+// gg_push.cu - the push frontier of the min applications (SSSP, BFS, CC) and
+// the small per-vertex kernels around the iterations (initial values, frontier
+// degrees and value snapshots).
+//
+// Active vertices (Sec. 2.1): only vertices whose value changed in the last
+// iteration can lower a neighbour, so an iteration may relax just their
+// out-arcs (the active ones in approximate mode, Sec. 3.3) instead of
+// pulling over every in-edge. Values pushed are the frontier's values at the
+// end of the previous iteration (q_val), and targets are lowered in place with
+// atomicMin, which gives exactly the synchronous pull result.
+#include "gg_internal.cuh"
+
+namespace gg {
+
+__global__ void __launch_bounds__(kThreads) k_push(PushArgs a)
+{
+    __shared__ int slot;
+    const uint32_t qn = *a.q_len;
+    const uint32_t total = qn ? a.q_deg_ex[qn] : 0u;
+    const uint32_t num_tiles = (total + kTile - 1) / kTile;
+    const uint32_t lane = lane_id();
+    const uint32_t lt = (1u << lane) - 1u;
+    for (;;) {
+        const int t = next_tile(a.sched, num_tiles, &slot);
+        if (t < 0) break;
+        const uint32_t g0 = (uint32_t)t * kTile;
+#pragma unroll 1
+        for (int r = 0; r < kIPT; ++r) {
+            const uint32_t g = g0 + (uint32_t)r * kThreads + threadIdx.x;
+            bool want = false;
+            int32_t u = 0;
+            if (g < total) {
+                uint32_t lo = 0, hi = qn;
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (a.q_deg_ex[mid] <= g) lo = mid;
+                    else hi = mid;
+                }
+                const int32_t v = a.q[lo];
+                const int32_t e = a.out_ptr[v] + (int32_t)(g - a.q_deg_ex[lo]);
+                bool active = true;
+                if (a.mask) {
+                    const int32_t k = a.out_to_in[e];
+                    active = (a.mask[k >> 5] >> (k & 31)) & 1u;
+                }
+                if (active) {
+                    u = a.out_dst[e];
+                    const uint32_t vv = a.q_val[lo];
+                    uint32_t cand;
+                    if (a.app == GG_APP_CC) {
+                        cand = vv;
+                    } else {
+                        const uint32_t step = a.app == GG_APP_BFS ? 1u : a.out_w[e];
+                        const unsigned long long c = (unsigned long long)vv + step;
+                        cand = (vv == kInf || c >= kInf) ? kInf : (uint32_t)c;
+                    }
+                    if (cand != kInf && cand < a.val[u]) {
+                        const uint32_t old = atomicMin(&a.val[u], cand);
+                        if (cand < old) want = atomicExch(&a.stamp[u], a.stamp_tag) != a.stamp_tag;
+                    }
+                }
+            }
+            const uint32_t b = __ballot_sync(0xFFFFFFFFu, want);
+            if (b) {
+                const int leader = __ffs(b) - 1;
+                uint32_t base = 0;
+                if ((int)lane == leader) base = atomicAdd(a.q_out_len, (uint32_t)__popc(b));
+                base = __shfl_sync(0xFFFFFFFFu, base, leader);
+                if (want) a.q_out[base + __popc(b & lt)] = u;
+            }
+        }
+    }
+    sched_leave(a.sched);
+}
+
+cudaError_t launch_push(const PushArgs &a, uint32_t max_arcs, int grid, cudaStream_t s)
+{
+    const uint32_t tiles = (max_arcs + kTile - 1) / kTile;
+    int g = grid < (int)tiles ? grid : (int)tiles;
+    if (g < 1) g = 1;
+    k_push<<<g, kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// Out-degrees of the frontier vertices (scanned afterwards into q_deg).
+__global__ void k_qdeg(const int32_t *__restrict__ q, const uint32_t *__restrict__ q_len,
+                       const int32_t *__restrict__ out_ptr, uint32_t *__restrict__ deg)
+{
+    const uint32_t qn = *q_len;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < qn; i += gridDim.x * blockDim.x) {
+        const int32_t v = q[i];
+        deg[i] = (uint32_t)(out_ptr[v + 1] - out_ptr[v]);
+    }
+}
+
+// Values of the frontier vertices at the end of a push iteration.
+__global__ void k_snapshot(const int32_t *__restrict__ q, const uint32_t *__restrict__ q_len,
+                           const uint32_t *__restrict__ val, uint32_t *__restrict__ q_val)
+{
+    const uint32_t qn = *q_len;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < qn; i += gridDim.x * blockDim.x)
+        q_val[i] = val[q[i]];
+}
+
+// GG-Apply's starting point for PageRank: rank 1/N, contribution rank/outdeg.
+__global__ void k_init_pr(int32_t n, const int32_t *__restrict__ out_ptr, float *__restrict__ rank,
+                          float *__restrict__ contrib)
+{
+    const float r0 = __fdiv_rn(1.0f, (float)n);
+    for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+        const int deg = out_ptr[u + 1] - out_ptr[u];
+        rank[u] = r0;
+        contrib[u] = deg > 0 ? __fdiv_rn(r0, (float)deg) : 0.0f;
+    }
+}
+
+// Min applications: unreached everywhere but the source (SSSP, BFS), or own
+// id (CC); the first frontier is the source, or every vertex.
+__global__ void k_init_min(int32_t n, int app, int32_t source, uint32_t *__restrict__ val,
+                           int32_t *__restrict__ q, uint32_t *__restrict__ q_val, uint32_t *__restrict__ q_len)
+{
+    for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+        if (app == GG_APP_CC) {
+            val[u] = (uint32_t)u;
+            q[u] = u;
+            q_val[u] = (uint32_t)u;
+        } else {
+            val[u] = u == source ? 0u : kInf;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (app == GG_APP_CC) {
+            *q_len = (uint32_t)n;
+        } else {
+            q[0] = source;
+            q_val[0] = 0u;
+            *q_len = 1u;
+        }
+    }
+}
+
+__global__ void k_iter_header(IterStatsDev *s, uint32_t mode, const uint32_t *arcs_dev, unsigned long long arcs)
+{
+    s->mode = mode;
+    s->arcs = arcs_dev ? (unsigned long long)*arcs_dev : arcs;
+}
+
+__global__ void k_iter_changed(IterStatsDev *s, const uint32_t *q_len) { s->changed = *q_len; }
+
+cudaError_t launch_qdeg(const int32_t *q, const uint32_t *q_len, const int32_t *out_ptr, uint32_t *deg,
+                        uint32_t max_n, int num_sms, cudaStream_t s)
+{
+    int blocks = (int)((max_n + 255) / 256);
+    if (blocks > num_sms * 8) blocks = num_sms * 8;
+    if (blocks < 1) blocks = 1;
+    k_qdeg<<<blocks, 256, 0, s>>>(q, q_len, out_ptr, deg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_snapshot(const int32_t *q, const uint32_t *q_len, const uint32_t *val, uint32_t *q_val,
+                            uint32_t max_n, int num_sms, cudaStream_t s)
+{
+    int blocks = (int)((max_n + 255) / 256);
+    if (blocks > num_sms * 8) blocks = num_sms * 8;
+    if (blocks < 1) blocks = 1;
+    k_snapshot<<<blocks, 256, 0, s>>>(q, q_len, val, q_val);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_pr(int32_t n, const int32_t *out_ptr, float *rank, float *contrib, int num_sms,
+                           cudaStream_t s)
+{
+    k_init_pr<<<num_sms * 8, 256, 0, s>>>(n, out_ptr, rank, contrib);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_min(int32_t n, int app, int32_t source, uint32_t *val, int32_t *q, uint32_t *q_val,
+                            uint32_t *q_len, int num_sms, cudaStream_t s)
+{
+    k_init_min<<<num_sms * 8, 256, 0, s>>>(n, app, source, val, q, q_val, q_len);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_iter_header(IterStatsDev *st, uint32_t mode, const uint32_t *arcs_dev,
+                               unsigned long long arcs, cudaStream_t s)
+{
+    k_iter_header<<<1, 1, 0, s>>>(st, mode, arcs_dev, arcs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_iter_changed(IterStatsDev *st, const uint32_t *q_len, cudaStream_t s)
+{
+    k_iter_changed<<<1, 1, 0, s>>>(st, q_len);
+    return cudaGetLastError();
+}
+
+}  // namespace gg
