@@ -66,7 +66,6 @@ uint32_t next_epoch(gg_graph *g)
 {
     if (g->epoch >= (1u << 30)) {
         cudaMemsetAsync(g->st_carry, 0, sizeof(unsigned long long) * (g->max_tiles + 2), g->stream);
-        cudaMemsetAsync(g->st_count, 0, sizeof(unsigned long long) * (g->max_tiles + 2), g->stream);
         g->epoch = 0;
     }
     return ++g->epoch;
@@ -102,20 +101,37 @@ static void fill_list(const gg_graph *g, bool sparse, TileArgs &a)
         a.arc_src = g->sp_src;
         a.arc_w = g->has_w ? g->sp_w : nullptr;
         a.list_nnz = g->sp_nnz;
-        a.tile_row = g->sp_tile_row;
+        a.tile_info = g->sp_tile_info;
         a.num_tiles = g->sp_num_tiles;
     } else {
         a.row_ptr = g->in_ptr;
         a.arc_src = g->in_src;
         a.arc_w = g->has_w ? g->in_w : nullptr;
         a.list_nnz = g->full_nnz;
-        a.tile_row = g->full_tile_row;
+        a.tile_info = g->full_tile_info;
         a.num_tiles = g->full_num_tiles;
     }
-    a.sched = g->sched;
     a.st_carry = g->st_carry;
-    a.st_count = g->st_count;
     a.err = g->dev_err;
+    a.tl_src = g->tl_src;
+    a.tile_cnt = g->tile_cnt;
+    a.part = g->part;
+    a.part_head = g->part_head;
+    a.stash = g->stash;
+}
+
+// After a correction or sampling pass: place the tiles' local packs into the
+// packed active in-edge list and partition it for the next gathers.
+static gg_status finish_pack(gg_graph *g, bool weighted, IterStatsDev *stats)
+{
+    GG_CUDA(launch_scan_u32(g->tile_cnt, g->tile_off, g->full_tiles, g->scan_tmp, g->stream));
+    GG_CUDA(launch_move(g->full_tile_info, g->tile_off, g->full_tiles, g->tl_src, weighted ? g->tl_w : nullptr,
+                        g->sp_ptr, g->sp_src, weighted ? g->sp_w : nullptr, g->sp_nnz, stats, g->num_sms,
+                        g->stream));
+    GG_CUDA(launch_partition(g->sp_ptr, g->n, g->sp_nnz, g->max_tiles, g->sp_tile_info, g->sp_num_tiles,
+                             g->stream));
+    g->launches += 5;
+    return GG_OK;
 }
 
 gg_status sample_edges(gg_graph *g, double ratio, uint64_t seed)
@@ -129,18 +145,16 @@ gg_status sample_edges(gg_graph *g, double ratio, uint64_t seed)
     fill_list(g, false, a);
     a.mask = g->mask;
     a.sp_ptr = g->sp_ptr;
-    a.sp_src = g->sp_src;
-    a.sp_w = g->has_w ? g->sp_w : nullptr;
-    a.sp_nnz = g->sp_nnz;
+    a.tl_w = g->has_w ? g->tl_w : nullptr;
     a.seed = seed;
     a.thr = (unsigned long long)std::floor(ratio * 4294967296.0);
     a.symmetric = g->symmetric ? 1 : 0;
     a.epoch = next_epoch(g);
     a.stats = nullptr;
     GG_CUDA(launch_tile_sample(a, (int)g->max_tiles, g->num_sms, g->stream));
-    GG_CUDA(launch_partition(g->sp_ptr, g->n, g->sp_nnz, g->max_tiles, g->sp_tile_row, g->sp_num_tiles,
-                             g->stream));
-    g->launches += 2;
+    g->launches += 1;
+    gg_status st = finish_pack(g, g->has_w, nullptr);
+    if (st != GG_OK) return st;
     GG_CUDA(cudaEventRecord(g->ev_s1, g->stream));
     g->sample_timed = true;
     g->sampled = true;
@@ -186,21 +200,19 @@ static gg_status run_pagerank(gg_graph *g, gg_policy policy, const gg_params *p)
         if (kind == K_CORRECT) {
             a.mask = g->mask;
             a.sp_ptr = g->sp_ptr;
-            a.sp_src = g->sp_src;
-            a.sp_w = nullptr;
-            a.sp_nnz = g->sp_nnz;
+            a.tl_w = nullptr;
             a.theta = p->theta;
         }
         GG_CUDA(launch_iter_header(a.stats, (uint32_t)mode, a.list_nnz, 0, g->stream));
         size_t slot;
         timed_begin(g, timing, kind == K_CORRECT ? 1 : 0, &slot);
         GG_CUDA(launch_tile_pr(kind, a, (int)g->max_tiles, g->num_sms, g->stream));
+        if (kind == K_GATHER) GG_CUDA(launch_fixup(GG_APP_PAGERANK, a, (int)g->max_tiles, g->num_sms, g->stream));
         timed_end(g, slot);
-        g->launches += 2;
+        g->launches += 3;
         if (kind == K_CORRECT) {
-            GG_CUDA(launch_partition(g->sp_ptr, g->n, g->sp_nnz, g->max_tiles, g->sp_tile_row,
-                                     g->sp_num_tiles, g->stream));
-            g->launches += 1;
+            gg_status st = finish_pack(g, false, a.stats);
+            if (st != GG_OK) return st;
             g->sample_clean = false;
             g->stats.corrections += 1;
         }
@@ -320,9 +332,7 @@ static gg_status run_min(gg_graph *g, gg_app app, gg_policy policy, const gg_par
             if (kind == K_CORRECT) {
                 a.mask = g->mask;
                 a.sp_ptr = g->sp_ptr;
-                a.sp_src = g->sp_src;
-                a.sp_w = (app == GG_APP_SSSP && g->has_w) ? g->sp_w : nullptr;
-                a.sp_nnz = g->sp_nnz;
+                a.tl_w = (app == GG_APP_SSSP && g->has_w) ? g->tl_w : nullptr;
                 a.theta_case = theta_case;
                 a.theta_fx = theta_fx;
                 a.est_strict = (p->flags & GG_EST_STRICT) ? 1 : 0;
@@ -330,12 +340,12 @@ static gg_status run_min(gg_graph *g, gg_app app, gg_policy policy, const gg_par
             size_t slot;
             timed_begin(g, timing, kind == K_CORRECT ? 1 : 0, &slot);
             GG_CUDA(launch_tile_min((int)app, kind, a, (int)g->max_tiles, g->num_sms, g->stream));
+            if (kind == K_GATHER) GG_CUDA(launch_fixup((int)app, a, (int)g->max_tiles, g->num_sms, g->stream));
             timed_end(g, slot);
-            g->launches += 1;
+            g->launches += 2;
             if (kind == K_CORRECT) {
-                GG_CUDA(launch_partition(g->sp_ptr, g->n, g->sp_nnz, g->max_tiles, g->sp_tile_row,
-                                         g->sp_num_tiles, g->stream));
-                g->launches += 1;
+                st = finish_pack(g, app == GG_APP_SSSP && g->has_w, sti);
+                if (st != GG_OK) return st;
                 g->sample_clean = false;
                 g->stats.corrections += 1;
                 st = read_u32(g, g->sp_nnz, &g->sp_nnz_host);
@@ -447,17 +457,23 @@ static gg_status alloc_graph(gg_graph *g)
         GG_ALLOC(g->b_in_w, 4 * m);
         GG_ALLOC(g->b_sp_w, 4 * m);
     }
-    g->max_tiles = (uint32_t)(((uint64_t)n + m + kTile - 1) / kTile) + 1;
-    GG_ALLOC(g->b_full_tile_row, 4 * ((size_t)g->max_tiles + 2));
-    GG_ALLOC(g->b_sp_tile_row, 4 * ((size_t)g->max_tiles + 2));
+    g->full_tiles = (uint32_t)(((uint64_t)n + m + kWT - 1) / kWT);
+    g->max_tiles = g->full_tiles + 1;
+    GG_ALLOC(g->b_full_tile_info, 4 * ((size_t)g->max_tiles + 2));
+    GG_ALLOC(g->b_sp_tile_info, 4 * ((size_t)g->max_tiles + 2));
+    GG_ALLOC(g->b_tile_cnt, 4 * (2 * (size_t)g->max_tiles + 4));
+    GG_ALLOC(g->b_part, 12 * ((size_t)g->max_tiles + 2));
+    GG_ALLOC(g->b_tl_src, 4 * m);
+    GG_ALLOC(g->b_stash, 4 * m);
+    if (g->has_w) GG_ALLOC(g->b_tl_w, 4 * m);
     GG_ALLOC(g->b_scalars, 4 * 16);
     g->mask_words = (m + 31) / 32;
     GG_ALLOC(g->b_mask, 4 * (g->mask_words + 1));
     GG_ALLOC(g->b_vals, 4 * 4 * n);
     GG_ALLOC(g->b_front, 4 * (6 * n + 2));
     GG_ALLOC(g->b_sched, sizeof(TileSched) * 2);
-    GG_ALLOC(g->b_status, sizeof(unsigned long long) * 2 * ((size_t)g->max_tiles + 2));
-    GG_ALLOC(g->b_scan_tmp, 4 * scan_tmp_words(n + 1));
+    GG_ALLOC(g->b_status, sizeof(unsigned long long) * ((size_t)g->max_tiles + 2));
+    GG_ALLOC(g->b_scan_tmp, 4 * scan_tmp_words((n + 1 > (size_t)g->max_tiles + 1 ? n + 1 : (size_t)g->max_tiles + 1)));
 #undef GG_ALLOC
     g->out_ptr = g->b_out_ptr.i32();
     g->out_dst = g->b_out_dst.i32();
@@ -469,8 +485,15 @@ static gg_status alloc_graph(gg_graph *g)
     g->sp_ptr = g->b_sp_ptr.i32();
     g->sp_src = g->b_sp_src.i32();
     g->sp_w = g->has_w ? g->b_sp_w.u32() : nullptr;
-    g->full_tile_row = g->b_full_tile_row.i32();
-    g->sp_tile_row = g->b_sp_tile_row.i32();
+    g->full_tile_info = g->b_full_tile_info.i32();
+    g->sp_tile_info = g->b_sp_tile_info.i32();
+    g->tile_cnt = g->b_tile_cnt.u32();
+    g->tile_off = g->tile_cnt + g->max_tiles + 2;
+    g->part = (uint2 *)g->b_part.p;
+    g->part_head = (uint32_t *)(g->part + g->max_tiles + 2);
+    g->tl_src = g->b_tl_src.i32();
+    g->stash = g->b_stash.u32();
+    g->tl_w = g->has_w ? g->b_tl_w.u32() : nullptr;
     uint32_t *sc = g->b_scalars.u32();
     g->full_num_tiles = sc + 0;
     g->sp_num_tiles = sc + 1;
@@ -495,7 +518,6 @@ static gg_status alloc_graph(gg_graph *g)
     g->q_deg = f + 5 * n;
     g->sched = (TileSched *)g->b_sched.p;
     g->st_carry = (unsigned long long *)g->b_status.p;
-    g->st_count = g->st_carry + g->max_tiles + 2;
     g->scan_tmp = g->b_scan_tmp.u32();
     return GG_OK;
 }
@@ -560,7 +582,7 @@ gg_status gg_load_csr(gg_graph **out, int32_t n, int64_t m, const int32_t *rowpt
             cudaEventDestroy(l1);
             break;
         }
-        if ((e = launch_partition(g->in_ptr, n, g->full_nnz, g->max_tiles, g->full_tile_row, g->full_num_tiles,
+        if ((e = launch_partition(g->in_ptr, n, g->full_nnz, g->max_tiles, g->full_tile_info, g->full_num_tiles,
                                   g->stream)) != cudaSuccess) {
             st = cuda_fail(e, "partition");
             cudaEventDestroy(l0);

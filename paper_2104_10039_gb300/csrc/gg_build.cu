@@ -11,19 +11,20 @@
 namespace gg {
 
 // ------------------------------------------------------------- partition ----
-// tile_row[t] = rows whose end item precedes diagonal t*kTile of the merged
-// (row ends, arcs) sequence (Merrill-Garland merge-path search).
+// tile_info[t] = rows whose end item precedes diagonal t*kWT of the merged
+// (row ends, arcs) sequence (Merrill-Garland merge-path search), with bit 31
+// set when the row open at that diagonal already has arcs in earlier tiles.
 __global__ void k_partition(const int32_t *__restrict__ row_ptr, int32_t n,
                             const uint32_t *__restrict__ list_nnz, uint32_t max_tiles,
-                            int32_t *__restrict__ tile_row, uint32_t *__restrict__ num_tiles)
+                            int32_t *__restrict__ tile_info, uint32_t *__restrict__ num_tiles)
 {
     const uint32_t nnz = *list_nnz;
     const long long total = (long long)n + nnz;
-    const uint32_t nt = (uint32_t)((total + kTile - 1) / kTile);
+    const uint32_t nt = (uint32_t)((total + kWT - 1) / kWT);
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t == 0) *num_tiles = nt;
     if (t > nt || t > max_tiles) return;
-    long long d = (long long)t * kTile;
+    long long d = (long long)t * kWT;
     if (d > total) d = total;
     long long lo = d - (long long)nnz > 0 ? d - (long long)nnz : 0;
     long long hi = d < n ? d : n;
@@ -32,16 +33,60 @@ __global__ void k_partition(const int32_t *__restrict__ row_ptr, int32_t n,
         if ((long long)row_ptr[mid + 1] <= d - mid - 1) lo = mid + 1;
         else hi = mid;
     }
-    tile_row[t] = (int32_t)lo;
+    const int32_t r = (int32_t)lo;
+    const long long arcs_before = d - lo;
+    const bool open = t < nt && r < n && arcs_before > row_ptr[r];
+    tile_info[t] = (int32_t)((uint32_t)r | (open ? 0x80000000u : 0u));
 }
 
 cudaError_t launch_partition(const int32_t *row_ptr, int32_t n, const uint32_t *list_nnz,
-                             uint32_t max_tiles, int32_t *tile_row, uint32_t *num_tiles,
+                             uint32_t max_tiles, int32_t *tile_info, uint32_t *num_tiles,
                              cudaStream_t s)
 {
     const uint32_t threads = 256;
     const uint32_t blocks = (max_tiles + 1 + threads - 1) / threads;
-    k_partition<<<blocks, threads, 0, s>>>(row_ptr, n, list_nnz, max_tiles, tile_row, num_tiles);
+    k_partition<<<blocks, threads, 0, s>>>(row_ptr, n, list_nnz, max_tiles, tile_info, num_tiles);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- move ----
+// One warp per tile: copy the tile's locally packed active arcs to their
+// place in the packed list and turn the tile-local row ends into global
+// ones. Tile order = list order, so rows split over tiles end up contiguous.
+__global__ void k_move(const int32_t *__restrict__ tile_info, const uint32_t *__restrict__ tile_off,
+                       uint32_t num_tiles, const int32_t *__restrict__ tl_src,
+                       const uint32_t *__restrict__ tl_w, int32_t *__restrict__ sp_ptr,
+                       int32_t *__restrict__ sp_src, uint32_t *__restrict__ sp_w,
+                       uint32_t *__restrict__ sp_nnz, IterStatsDev *stats)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < num_tiles; t += warps) {
+        const int32_t r0 = tile_info[t] & 0x7FFFFFFF, r1 = tile_info[t + 1] & 0x7FFFFFFF;
+        const long long a0 = t * kWT - r0;
+        const uint32_t off = tile_off[t], cnt = tile_off[t + 1] - off;
+        for (uint32_t i = lane; i < cnt; i += 32) {
+            sp_src[off + i] = tl_src[a0 + i];
+            if (sp_w) sp_w[off + i] = tl_w[a0 + i];
+        }
+        for (int32_t u = r0 + (int32_t)lane; u < r1; u += 32) sp_ptr[u + 1] += (int32_t)off;
+        if (t == 0 && lane == 0) {
+            sp_ptr[0] = 0;
+            *sp_nnz = tile_off[num_tiles];
+            if (stats) stats->active_after = tile_off[num_tiles];
+        }
+    }
+}
+
+cudaError_t launch_move(const int32_t *tile_info, const uint32_t *tile_off, uint32_t num_tiles,
+                        const int32_t *tl_src, const uint32_t *tl_w, int32_t *sp_ptr, int32_t *sp_src,
+                        uint32_t *sp_w, uint32_t *sp_nnz, IterStatsDev *stats, int num_sms, cudaStream_t s)
+{
+    long long blocks = ((long long)num_tiles * 32 + 255) / 256;
+    if (blocks > (long long)num_sms * 16) blocks = (long long)num_sms * 16;
+    if (blocks < 1) blocks = 1;
+    k_move<<<(unsigned)blocks, 256, 0, s>>>(tile_info, tile_off, num_tiles, tl_src, tl_w, sp_ptr, sp_src,
+                                            sp_w, sp_nnz, stats);
     return cudaGetLastError();
 }
 

@@ -65,11 +65,19 @@ struct gg_graph {
     int32_t *in_ptr = nullptr, *in_src = nullptr, *out_to_in = nullptr;
     uint32_t *in_w = nullptr;
     // partitions: full CSC and packed active CSC
-    gg::DevBuf b_full_tile_row, b_sp_tile_row, b_scalars;
-    int32_t *full_tile_row = nullptr, *sp_tile_row = nullptr;
+    gg::DevBuf b_full_tile_info, b_sp_tile_info, b_scalars;
+    int32_t *full_tile_info = nullptr, *sp_tile_info = nullptr;
     uint32_t *full_num_tiles = nullptr, *sp_num_tiles = nullptr, *full_nnz = nullptr, *sp_nnz = nullptr;
     uint32_t *dev_err = nullptr, *q_len = nullptr;  // q_len[2]
-    uint32_t max_tiles = 0;
+    uint32_t max_tiles = 0;     // upper bound on tiles of any list
+    uint32_t full_tiles = 0;    // tiles of the full in-edge list
+    // tile-local packs of the correction / sampler, their counts and offsets
+    gg::DevBuf b_tl_src, b_tl_w, b_tile_cnt, b_part, b_stash;
+    uint32_t *stash = nullptr;
+    uint2 *part = nullptr;
+    uint32_t *part_head = nullptr;
+    int32_t *tl_src = nullptr;
+    uint32_t *tl_w = nullptr, *tile_cnt = nullptr, *tile_off = nullptr;
     // flags and packed active in-edges
     gg::DevBuf b_mask, b_sp_ptr, b_sp_src, b_sp_w;
     uint32_t *mask = nullptr;
@@ -97,7 +105,7 @@ struct gg_graph {
     // scheduling and look-back
     gg::DevBuf b_sched, b_status;
     gg::TileSched *sched = nullptr;
-    unsigned long long *st_carry = nullptr, *st_count = nullptr;
+    unsigned long long *st_carry = nullptr;
     uint32_t epoch = 0;
     gg::DevBuf b_scan_tmp;
     uint32_t *scan_tmp = nullptr;

@@ -11,11 +11,12 @@ namespace gg {
 
 // ---------------------------------------------------------------- tiling ----
 // Every gather-type kernel walks a merged list of row ends and arcs
-// ("merge path", Merrill & Garland 2016) cut into tiles of kTile items, so a
-// tile costs the same whatever the degree skew.
+// ("merge path", Merrill & Garland 2016) cut into warp tiles of kWT items
+// (kIPT per lane), so a tile costs the same whatever the degree skew.
 constexpr int kThreads = 256;
 constexpr int kIPT = 8;
-constexpr int kTile = kThreads * kIPT;
+constexpr int kWT = 32 * kIPT;
+constexpr int kTile = kThreads * kIPT;   // push-frontier tiles (block-wide)
 constexpr int kWarps = kThreads / 32;
 constexpr uint32_t kInf = 0xFFFFFFFFu;
 
@@ -61,7 +62,7 @@ struct TileArgs {
     const uint32_t *arc_w;      // list arcs: weight (SSSP) or nullptr
     int32_t n;
     const uint32_t *list_nnz;   // device scalar: arcs in the list
-    const int32_t *tile_row;    // rows consumed before each tile (num_tiles + 1)
+    const int32_t *tile_info;   // per tile: rows before it | (row open at its start began earlier) << 31
     const uint32_t *num_tiles;  // device scalar
     // vertex state
     const float *contrib_cur;
@@ -87,10 +88,18 @@ struct TileArgs {
     unsigned long long seed;
     unsigned long long thr;     // floor(sigma * 2^32)
     int symmetric;
-    // scheduling and look-back
-    TileSched *sched;
+    // per-tile partials of a gather for k_fixup: (has row end, part after the
+    // last end) and the part before the first end
+    uint2 *part;
+    uint32_t *part_head;
+    // correction: arc values (candidates) in list order, written by K_STASH
+    uint32_t *stash;
+    // tile-local packing (correction, sampling)
+    int32_t *tl_src;
+    uint32_t *tl_w;
+    uint32_t *tile_cnt;
+    // look-back
     unsigned long long *st_carry;
-    unsigned long long *st_count;
     uint32_t epoch;
     uint32_t *err;
     // statistics and frontier output
@@ -100,7 +109,9 @@ struct TileArgs {
     uint32_t *q_out_len;
 };
 
-enum TileKind { K_GATHER = 0, K_CORRECT = 1, K_SAMPLE = 2 };
+// K_GATHER: approximate / accurate pull iteration. K_STASH + K_CORRECT: the
+// two launches of a correction iteration. K_SAMPLE: sparsification.
+enum TileKind { K_GATHER = 0, K_CORRECT = 1, K_SAMPLE = 2, K_STASH = 3 };
 
 struct PushArgs {
     const int32_t *q;           // frontier vertices
@@ -204,12 +215,19 @@ gg_status cuda_fail(cudaError_t e, const char *what);
 // Launchers (each defined in its own translation unit).
 struct Graph;
 cudaError_t launch_partition(const int32_t *row_ptr, int32_t n, const uint32_t *list_nnz,
-                             uint32_t max_tiles, int32_t *tile_row, uint32_t *num_tiles,
+                             uint32_t max_tiles, int32_t *tile_info, uint32_t *num_tiles,
                              cudaStream_t s);
-// Tile kernels run a persistent grid: min(max_tiles, resident blocks).
+// Packed active in-edges from the tiles' local packs: tile_off is the
+// exclusive scan of the tile counts (num_tiles + 1 entries).
+cudaError_t launch_move(const int32_t *tile_info, const uint32_t *tile_off, uint32_t num_tiles,
+                        const int32_t *tl_src, const uint32_t *tl_w, int32_t *sp_ptr, int32_t *sp_src,
+                        uint32_t *sp_w, uint32_t *sp_nnz, IterStatsDev *stats, int num_sms, cudaStream_t s);
+// Tile kernels run a cooperative persistent grid: min(max_tiles, resident warps).
 cudaError_t launch_tile_pr(int kind, const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s);
 cudaError_t launch_tile_min(int app, int kind, const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s);
 cudaError_t launch_tile_sample(const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s);
+// Rows a gather left open at tile starts (one launch after every gather).
+cudaError_t launch_fixup(int app, const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s);
 cudaError_t launch_push(const PushArgs &a, uint32_t max_arcs, int grid, cudaStream_t s);
 cudaError_t launch_scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint32_t *tmp, cudaStream_t s);
 size_t scan_tmp_words(size_t n);

@@ -3,21 +3,28 @@
 //
 // A list (CSC rows: row_ptr + per-arc source/weight) is viewed as the merged
 // sequence "arcs of row 0, end of row 0, arcs of row 1, end of row 1, ...".
-// Tile t owns kTile consecutive items of that sequence; its first row and
-// arc come from a precomputed partition (tile_row). Within a tile:
-//   load    row ends into shared memory; arcs' values gathered into shared
-//           memory with coalesced loads of the arc arrays and random loads of
-//           the source values (the GG-Gather reads of Alg. 1 / Alg. 2);
-//   pass 1  each thread folds its kIPT items into (has_row_end, partial);
-//           a block segmented scan gives every thread the running value of
-//           the row open at its start;
-//   carry   a row that began in earlier tiles takes the sum of those tiles'
-//           published partials, added in tile order (deterministic);
-//   pass 2  walk again with the carry: per arc, influence and new flag
-//           (correction, Alg. 2 GG-Gather + GG-EStatus) or sampled flag
-//           (Sec. 3.4); per row end, GG-Apply + GG-VStatus;
-//   pass 3  (correction, sampling) stream-compact the active arcs into the
-//           packed active-CSC through a decoupled look-back over tile counts.
+// Warp tile t owns kWT consecutive items of that sequence; its first row (and
+// whether that row began in an earlier tile) comes from a precomputed
+// partition. Every warp works on its own tiles (t = warp, warp + W, ...) with
+// no barrier and no wait on another warp, and loads the next tile's header
+// and arc data while it works on the current one:
+//   load    the tile's row ends and its rows' vertex data into shared memory,
+//           and the arcs' values with random loads (the GG-Gather reads of
+//           Alg. 1 / Alg. 2), staged in shared memory;
+//   walk    each lane takes its kIPT items into registers once;
+//   scan    a warp segmented scan gives every lane the running value of the
+//           row open at its start; the tile publishes its partials;
+//   pass 2  per arc, influence and new flag (correction, Alg. 2 GG-EStatus)
+//           or sampled flag (Sec. 3.4); per row end, GG-Apply + GG-VStatus;
+//   pack    (correction, sampling) the tile's active arcs are packed at the
+//           start of its own arc range; a tile-count scan and k_move then
+//           place them in the packed active-CSC.
+// A row that began in an earlier tile needs those tiles' partials. The gather
+// leaves that row to k_fixup. The correction, whose per-arc influence needs
+// the running value before each arc (Alg. 2, GG-Gather's return), runs in two
+// launches: K_STASH gathers the values, publishes the partials and stashes
+// the values in arc order; K_CORRECT then reads them back with coalesced loads
+// and takes its carry from the finished partials.
 #pragma once
 
 #include "gg_internal.cuh"
@@ -58,9 +65,14 @@ __device__ __forceinline__ uint32_t sampled_flag(int32_t src, int32_t dst, int s
 {
     uint32_t a = (uint32_t)src, b = (uint32_t)dst;
     if (symmetric && a > b) { uint32_t t = a; a = b; b = t; }
-    unsigned long long key = ((unsigned long long)a << 32) | b;
+    const unsigned long long key = ((unsigned long long)a << 32) | b;
     return (splitmix64(seed ^ key) >> 32) < thr ? 1u : 0u;
 }
+
+// Shared-memory slot of tile-local item k: one padding word per 8 items, so
+// lanes reading their own 8 consecutive items hit distinct banks.
+__device__ __forceinline__ int pad(int k) { return k + (k >> 3); }
+constexpr int kPadded = kWT + kWT / 8 + 1;
 
 // ------------------------------------------------------------ warp scans ----
 template <int APP>
@@ -69,8 +81,8 @@ __device__ __forceinline__ void warp_seg_scan_incl(typename Acc<APP>::T &v, uint
     const uint32_t lane = lane_id();
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        typename Acc<APP>::T ov = __shfl_up_sync(0xFFFFFFFFu, v, o);
-        uint32_t of = __shfl_up_sync(0xFFFFFFFFu, f, o);
+        const typename Acc<APP>::T ov = __shfl_up_sync(0xFFFFFFFFu, v, o);
+        const uint32_t of = __shfl_up_sync(0xFFFFFFFFu, f, o);
         if (lane >= (uint32_t)o) {
             if (!f) v = Acc<APP>::op(ov, v);
             f |= of;
@@ -83,63 +95,27 @@ __device__ __forceinline__ uint32_t warp_incl_sum_u32(uint32_t v)
     const uint32_t lane = lane_id();
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        uint32_t ov = __shfl_up_sync(0xFFFFFFFFu, v, o);
+        const uint32_t ov = __shfl_up_sync(0xFFFFFFFFu, v, o);
         if (lane >= (uint32_t)o) v += ov;
     }
     return v;
 }
 
-__device__ __forceinline__ uint32_t warp_sum_u32(uint32_t v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-    return v;
-}
-
-// Exclusive prefix (over earlier tiles) of the published per-tile counts:
-// decoupled look-back with a warp; integer sums, so the grouping does not
-// matter. Call with the whole warp; the result is valid in every lane.
-__device__ __forceinline__ uint32_t lookback_count(unsigned long long *st, int t, uint32_t epoch,
-                                                   uint32_t *err)
-{
-    const uint32_t lane = lane_id();
-    uint32_t excl = 0;
-    for (int base = t - 1; base >= 0; base -= 32) {
-        int j = base - (int)lane;
-        uint32_t flag = 0, val = 0;
-        bool valid = j >= 0;
-        if (valid) {
-            unsigned long long w = wait_status(&st[j], epoch, err, pack_status(epoch, 1u, 0u));
-            flag = status_flag(w);
-            val = status_value(w);
-        }
-        unsigned ball = __ballot_sync(0xFFFFFFFFu, valid && flag);
-        if (ball) {
-            int stop = __ffs(ball) - 1;
-            excl += warp_sum_u32((int)lane <= stop ? val : 0u);
-            break;
-        }
-        excl += warp_sum_u32(valid ? val : 0u);
-    }
-    return excl;
-}
-
-// Carry of the row open at the start of tile t: the partials published by
-// the tiles from the one where that row began (the nearest earlier tile with
-// a row end) up to t-1, combined in tile order. Whole warp; valid in lane 0.
+// Carry of the row open at the start of tile t, from the finished partials of
+// earlier tiles: the part after the last row end of the nearest tile with a
+// row end, then every later tile whole, in tile order. Whole warp; valid in
+// all lanes. `prev` is part[t-1], already loaded.
 template <int APP>
-__device__ __forceinline__ typename Acc<APP>::T lookback_carry(unsigned long long *st, int t,
-                                                               uint32_t epoch, uint32_t *err)
+__device__ __forceinline__ typename Acc<APP>::T carry_from_parts(const uint2 *part, int t, uint2 prev)
 {
     using T = typename Acc<APP>::T;
+    if (prev.x) return Acc<APP>::from_bits(prev.y);
     const uint32_t lane = lane_id();
     int jstar = 0;
-    const unsigned long long fallback = pack_status(epoch, 1u, Acc<APP>::bits(Acc<APP>::id()));
-    for (int base = t - 1; base >= 0; base -= 32) {
-        int j = base - (int)lane;
-        uint32_t f = 0;
-        if (j >= 0) f = status_flag(wait_status(&st[j], epoch, err, fallback));
-        unsigned ball = __ballot_sync(0xFFFFFFFFu, f != 0u);
+    for (int base = t - 2; base >= 0; base -= 32) {
+        const int j = base - (int)lane;
+        const uint32_t f = j >= 0 ? part[j].x : 0u;
+        const unsigned ball = __ballot_sync(0xFFFFFFFFu, f != 0u);
         if (ball) {
             jstar = base - (__ffs(ball) - 1);
             break;
@@ -147,15 +123,11 @@ __device__ __forceinline__ typename Acc<APP>::T lookback_carry(unsigned long lon
     }
     T acc = Acc<APP>::id();
     for (int s0 = jstar; s0 < t; s0 += 32) {
-        int j = s0 + (int)lane;
-        T v = Acc<APP>::id();
-        if (j < t) {
-            unsigned long long w = ld_acquire_u64(&st[j]);
-            if (status_epoch(w) == epoch) v = Acc<APP>::from_bits(status_value(w));
-        }
+        const int j = s0 + (int)lane;
+        T v = j < t ? Acc<APP>::from_bits(part[j].y) : Acc<APP>::id();
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            T ov = __shfl_down_sync(0xFFFFFFFFu, v, o);
+            const T ov = __shfl_down_sync(0xFFFFFFFFu, v, o);
             v = Acc<APP>::op(v, ov);
         }
         acc = Acc<APP>::op(acc, __shfl_sync(0xFFFFFFFFu, v, 0));
@@ -163,120 +135,211 @@ __device__ __forceinline__ typename Acc<APP>::T lookback_carry(unsigned long lon
     return acc;
 }
 
-// ----------------------------------------------------------- tile kernel ----
+// ------------------------------------------------------------- row apply ----
+// GG-Apply + GG-VStatus of Alg. 2 for PageRank; min for the min applications
+// (a vertex is active when its value decreased). Shared by k_tile and k_fixup.
+struct ApplyStats {
+    unsigned long long changed = 0, sum = 0;
+    uint32_t max = 0;
+};
+
+__device__ __forceinline__ void apply_pr(const TileArgs &a, int32_t u, float acc, float old, int deg,
+                                         ApplyStats &st)
+{
+    const float nw = __fmaf_rn(a.damping, acc, a.base);
+    const float delta = fabsf(__fsub_rn(nw, old));
+    a.rank_next[u] = nw;
+    a.contrib_next[u] = deg > 0 ? __fdiv_rn(nw, (float)deg) : 0.0f;
+    st.changed += delta > a.epsilon ? 1ull : 0ull;
+    st.sum += __float2ull_rz(delta * 1099511627776.0f);   // fixed point 2^-40
+    const uint32_t db = __float_as_uint(delta);
+    st.max = db > st.max ? db : st.max;
+}
+
+// Returns the new value; *changed tells whether it decreased.
+__device__ __forceinline__ uint32_t apply_min(const TileArgs &a, int32_t u, uint32_t acc, uint32_t old,
+                                              ApplyStats &st, bool *changed)
+{
+    const uint32_t nw = acc < old ? acc : old;
+    a.val_next[u] = nw;
+    *changed = nw < old;
+    if (nw < old) {
+        st.changed += 1;
+        if (old != kInf) {
+            st.sum += old - nw;
+            st.max = (old - nw) > st.max ? (old - nw) : st.max;
+        }
+    }
+    return nw;
+}
+
+// Warp-aggregated append of this lane's (vertex, value) pairs to the frontier.
+__device__ __forceinline__ void frontier_append(const TileArgs &a, const int32_t *qu, const uint32_t *qv, int qn)
+{
+    const uint32_t lane = lane_id();
+    const uint32_t incl = warp_incl_sum_u32((uint32_t)qn);
+    const uint32_t wtot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    if (wtot == 0) return;
+    uint32_t base = 0;
+    if (lane == 31) base = atomicAdd(a.q_out_len, wtot);
+    base = __shfl_sync(0xFFFFFFFFu, base, 31);
+    const uint32_t pos = base + incl - (uint32_t)qn;
+    for (int i = 0; i < qn; ++i) {
+        a.q_out[pos + i] = qu[i];
+        a.q_out_val[pos + i] = qv[i];
+    }
+}
+
+__device__ __forceinline__ void flush_stats(const TileArgs &a, ApplyStats st)
+{
+    if (!a.stats) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        st.changed += __shfl_xor_sync(0xFFFFFFFFu, st.changed, o);
+        st.sum += __shfl_xor_sync(0xFFFFFFFFu, st.sum, o);
+        const uint32_t om = __shfl_xor_sync(0xFFFFFFFFu, st.max, o);
+        st.max = om > st.max ? om : st.max;
+    }
+    if (lane_id() == 0 && (st.changed | st.sum | st.max)) {
+        atomicAdd(&a.stats->changed, st.changed);
+        atomicAdd(&a.stats->sum_delta, st.sum);
+        atomicMax(&a.stats->max_delta_bits, st.max);
+    }
+}
+
+// ------------------------------------------------------------ tile kernel ----
 template <int APP, int KIND>
-struct TileSmem {
-    using T = typename Acc<APP>::T;
-    int32_t rowend[kTile + 1];
-    T val[kTile];
-    int32_t src[(KIND == K_GATHER) ? 1 : kTile];
-    uint32_t w[(KIND == K_GATHER) ? 1 : kTile];
-    uint8_t flag[(KIND == K_GATHER) ? 1 : kTile];
-    uint32_t oldw[(KIND == K_CORRECT && APP != GG_APP_PAGERANK) ? (kTile / 32 + 2) : 1];
-    T warp_v[kWarps];
-    uint32_t warp_f[kWarps];
-    uint32_t warp_c[kWarps];
-    T carry;
-    uint32_t tile_excl;
-    int32_t r0, r1, a0, a1, row_start;
-    int slot;
+struct WarpSmem {
+    int32_t rowend[kWT + 1];
+    uint32_t val[kPadded];   // arc values (bits of T), or arc sources when sampling
+    uint32_t vtx[(KIND == K_SAMPLE || KIND == K_STASH) ? 1 : kWT];   // rows' current value
+    int32_t deg[(KIND != K_SAMPLE && KIND != K_STASH && APP == GG_APP_PAGERANK) ? kWT : 1];  // rows' out-degree
+    uint32_t bits[(KIND == K_GATHER) ? 1 : (kWT / 32 + 2)];
+    uint32_t oldw[(KIND == K_CORRECT && APP != GG_APP_PAGERANK) ? (kWT / 32 + 2) : 1];
 };
 
 template <int APP, int KIND>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 4)
 k_tile(TileArgs a)
 {
     using T = typename Acc<APP>::T;
     using A = Acc<APP>;
-    constexpr bool kCarry = KIND != K_SAMPLE;
-    constexpr bool kCompact = KIND != K_GATHER;
+    constexpr bool kPack = KIND == K_CORRECT || KIND == K_SAMPLE;
     constexpr bool kMin = APP != GG_APP_PAGERANK;
-    constexpr bool kWeighted = APP == GG_APP_SSSP;
-    __shared__ TileSmem<APP, KIND> sm;
+    constexpr bool kWeighted = APP == GG_APP_SSSP && (KIND == K_GATHER || KIND == K_STASH);
+    constexpr bool kApply = KIND == K_GATHER || KIND == K_CORRECT;
+    constexpr bool kStashed = KIND == K_CORRECT;   // values come from the stash, in arc order
+    __shared__ WarpSmem<APP, KIND> smem[kWarps];
+    WarpSmem<APP, KIND> &s = smem[threadIdx.x >> 5];
 
-    const int tid = threadIdx.x;
     const uint32_t lane = lane_id();
-    const int warp = tid >> 5;
+    const int gw = (int)((blockIdx.x * kThreads + threadIdx.x) >> 5);
+    const int W = (int)((gridDim.x * kThreads) >> 5);
     const uint32_t nnz = *a.list_nnz;
-    const uint32_t num_tiles = *a.num_tiles;
+    const int num_tiles = (int)*a.num_tiles;
     const long long total = (long long)a.n + nnz;
-    const bool has_w = (a.arc_w != nullptr);
+    const bool load_w = kWeighted && a.arc_w != nullptr;
 
-    unsigned long long my_changed = 0, my_sum = 0;
-    uint32_t my_max = 0;
+    ApplyStats st;
 
-    for (;;) {
-        const int t = next_tile(a.sched, num_tiles, &sm.slot);
-        if (t < 0) break;
-        const long long d0 = (long long)t * kTile;
-        const long long d1 = d0 + kTile < total ? d0 + kTile : total;
-        if (tid == 0) {
-            int32_t r0 = a.tile_row[t], r1 = a.tile_row[t + 1];
-            sm.r0 = r0;
-            sm.r1 = r1;
-            sm.a0 = (int32_t)(d0 - r0);
-            sm.a1 = (int32_t)(d1 - r1);
-            sm.row_start = a.row_ptr[r0 < a.n ? r0 : a.n];
+    // ---- software pipeline: headers two tiles ahead, sources one ahead ------
+    uint32_t hdr_cur = 0, hdr_nxt = 0;
+    if (lane < 2 && gw < num_tiles) hdr_cur = (uint32_t)a.tile_info[gw + (int)lane];
+    if (lane < 2 && gw + W < num_tiles) hdr_nxt = (uint32_t)a.tile_info[gw + W + (int)lane];
+    int32_t src_cur[kIPT];
+    uint32_t w_cur[kWeighted ? kIPT : 1];
+    auto load_arcs = [&](int tt, uint32_t hdr, int32_t *srcv, uint32_t *wv) {
+        const uint32_t h0 = __shfl_sync(0xFFFFFFFFu, hdr, 0), h1 = __shfl_sync(0xFFFFFFFFu, hdr, 1);
+        const long long e0 = (long long)tt * kWT;
+        const long long e1 = e0 + kWT < total ? e0 + kWT : total;
+        const int32_t b0 = (int32_t)(e0 - (int32_t)(h0 & 0x7FFFFFFFu));
+        const int32_t b1 = (int32_t)(e1 - (int32_t)(h1 & 0x7FFFFFFFu));
+        const bool live = tt < num_tiles;
+#pragma unroll
+        for (int i = 0; i < kIPT; ++i) {
+            const int k = (int)lane + 32 * i;
+            const bool ok = live && k < b1 - b0;
+            if constexpr (kStashed) srcv[i] = ok ? (int32_t)__ldcs(a.stash + b0 + k) : 0;
+            else srcv[i] = ok ? __ldg(a.arc_src + b0 + k) : 0;
+            if constexpr (kWeighted) wv[i] = (ok && load_w) ? __ldg(a.arc_w + b0 + k) : 1u;
         }
-        __syncthreads();
-        const int32_t r0 = sm.r0, r1 = sm.r1, a0 = sm.a0, a1 = sm.a1;
-        const int nrows = r1 - r0;     // row ends inside the tile
-        const int narcs = a1 - a0;     // arcs inside the tile
+    };
+    load_arcs(gw, hdr_cur, src_cur, w_cur);
 
-        // ---- load: row ends and arc values ---------------------------------
-        for (int i = tid; i < nrows; i += kThreads) sm.rowend[i] = a.row_ptr[r0 + i + 1];
-        if (tid == 0) sm.rowend[nrows] = 0x7FFFFFFF;   // row r1 stays open past the tile
-        if (KIND == K_CORRECT && kMin) {
-            if (narcs > 0) {
-                const int w0 = a0 >> 5, w1 = (a1 - 1) >> 5;
-                for (int w = w0 + tid; w <= w1; w += kThreads) sm.oldw[w - w0] = a.mask[w];
+    for (int t = gw; t < num_tiles; t += W) {
+        const uint32_t i0 = __shfl_sync(0xFFFFFFFFu, hdr_cur, 0);
+        const uint32_t i1 = __shfl_sync(0xFFFFFFFFu, hdr_cur, 1);
+        const int32_t r0 = (int32_t)(i0 & 0x7FFFFFFFu), r1 = (int32_t)(i1 & 0x7FFFFFFFu);
+        const bool need_carry = (i0 >> 31) != 0u;
+        const long long d0 = (long long)t * kWT;
+        const long long d1 = d0 + kWT < total ? d0 + kWT : total;
+        const int32_t a0 = (int32_t)(d0 - r0), a1 = (int32_t)(d1 - r1);
+        const int nrows = r1 - r0, narcs = a1 - a0;
+        const int w0 = a0 >> 5;
+        const int nwords = narcs > 0 ? ((a1 - 1) >> 5) - w0 + 1 : 0;
+
+        // ---- issue this tile's value gathers and row loads ------------------
+        uint32_t gv[kIPT];
+#pragma unroll
+        for (int i = 0; i < kIPT; ++i) {
+            const int k = (int)lane + 32 * i;
+            if constexpr (KIND == K_SAMPLE || kStashed) {
+                gv[i] = (uint32_t)src_cur[i];
+            } else if constexpr (APP == GG_APP_PAGERANK) {
+                gv[i] = k < narcs ? __float_as_uint(__ldg(a.contrib_cur + src_cur[i])) : 0u;
+            } else {
+                gv[i] = k < narcs ? __ldg(a.val_cur + src_cur[i]) : kInf;
             }
         }
-        {
-            int32_t s[kIPT];
-#pragma unroll
-            for (int i = 0; i < kIPT; ++i) {
-                const int k = tid + i * kThreads;
-                s[i] = k < narcs ? __ldg(a.arc_src + a0 + k) : 0;
-            }
-            uint32_t wv[kIPT];
-#pragma unroll
-            for (int i = 0; i < kIPT; ++i) {
-                const int k = tid + i * kThreads;
-                wv[i] = (has_w && (kWeighted || KIND == K_SAMPLE) && k < narcs) ? __ldg(a.arc_w + a0 + k) : 1u;
-            }
-#pragma unroll
-            for (int i = 0; i < kIPT; ++i) {
-                const int k = tid + i * kThreads;
-                if (k < narcs) {
-                    if (KIND != K_GATHER) {
-                        sm.src[k] = s[i];
-                        sm.w[k] = wv[i];
-                    }
-                    if (KIND != K_SAMPLE) {
-                        if constexpr (APP == GG_APP_PAGERANK) {
-                            sm.val[k] = __ldg(a.contrib_cur + s[i]);
-                        } else {
-                            const uint32_t vv = __ldg(a.val_cur + s[i]);
-                            uint32_t cand;
-                            if constexpr (APP == GG_APP_CC) {
-                                cand = vv;
-                            } else {
-                                const uint32_t step = (APP == GG_APP_BFS) ? 1u : wv[i];
-                                const unsigned long long c = (unsigned long long)vv + step;
-                                cand = (vv == kInf || c >= kInf) ? kInf : (uint32_t)c;
-                            }
-                            sm.val[k] = cand;
-                        }
-                    }
+        uint2 prev_part = make_uint2(1u, A::bits(A::id()));
+        if constexpr (kStashed) {
+            if (need_carry && lane == 0) prev_part = a.part[t - 1];
+        }
+        for (int i = (int)lane; i < nrows; i += 32) {
+            s.rowend[i] = a.row_ptr[r0 + i + 1];
+            if constexpr (kApply) {
+                if constexpr (APP == GG_APP_PAGERANK) {
+                    s.vtx[i] = __float_as_uint(a.rank_cur[r0 + i]);
+                    s.deg[i] = a.out_ptr[r0 + i + 1] - a.out_ptr[r0 + i];
+                } else {
+                    s.vtx[i] = a.val_cur[r0 + i];
                 }
             }
         }
-        __syncthreads();
+        if (lane == 0) s.rowend[nrows] = 0x7FFFFFFF;   // row r1 stays open past the tile
+        if constexpr (KIND == K_CORRECT && kMin) {
+            for (int i = (int)lane; i < nwords; i += 32) s.oldw[i] = a.mask[w0 + i];
+        }
+        if constexpr (kPack) {
+            for (int i = (int)lane; i < nwords; i += 32) s.bits[i] = 0u;
+        }
+        // ---- prefetch: next tile's sources, header two tiles ahead ---------
+        int32_t src_nxt[kIPT];
+        uint32_t w_nxt[kWeighted ? kIPT : 1];
+        load_arcs(t + W, hdr_nxt, src_nxt, w_nxt);
+        uint32_t hdr_far = 0;
+        if (lane < 2 && t + 2 * W < num_tiles) hdr_far = (uint32_t)a.tile_info[t + 2 * W + (int)lane];
 
-        // ---- per-thread merge-path coordinates inside the tile -------------
+        // ---- stage values (candidates for the min applications) ------------
+#pragma unroll
+        for (int i = 0; i < kIPT; ++i) {
+            const int k = (int)lane + 32 * i;
+            if (k < narcs) {
+                uint32_t v = gv[i];
+                if constexpr ((KIND == K_GATHER || KIND == K_STASH) && kMin && APP != GG_APP_CC) {
+                    const uint32_t step = (APP == GG_APP_BFS) ? 1u : w_cur[kWeighted ? i : 0];
+                    const unsigned long long c = (unsigned long long)v + step;
+                    v = (v == kInf || c >= kInf) ? kInf : (uint32_t)c;
+                }
+                s.val[pad(k)] = v;
+                if constexpr (KIND == K_STASH) __stcs(a.stash + a0 + k, v);
+            }
+        }
+        __syncwarp();
+
+        // ---- this lane's items into registers ------------------------------
         const int tile_items = (int)(d1 - d0);
-        const int ld = tid * kIPT < tile_items ? tid * kIPT : tile_items;
+        const int ld = (int)lane * kIPT < tile_items ? (int)lane * kIPT : tile_items;
         int cnt = tile_items - ld;
         cnt = cnt < kIPT ? cnt : kIPT;
         int lx, ly;
@@ -284,74 +347,99 @@ k_tile(TileArgs a)
             int lo = ld - narcs > 0 ? ld - narcs : 0;
             int hi = ld < nrows ? ld : nrows;
             while (lo < hi) {
-                int mid = (lo + hi) >> 1;
-                if (sm.rowend[mid] - a0 <= ld - mid - 1) lo = mid + 1;
+                const int mid = (lo + hi) >> 1;
+                if (s.rowend[mid] - a0 <= ld - mid - 1) lo = mid + 1;
                 else hi = mid;
             }
             lx = lo;
             ly = ld - lo;
         }
-
-        // ---- pass 1 + block segmented scan + carry ---------------------------
-        T carry_in = A::id();
-        if constexpr (kCarry) {
-            T v = A::id();
-            uint32_t f = 0;
-            {
-                int x = lx, y = ly;
-                for (int i = 0; i < cnt; ++i) {
-                    if (y < sm.rowend[x] - a0) { v = A::op(v, sm.val[y]); ++y; }
-                    else { f = 1; v = A::id(); ++x; }
+        uint32_t item_v[kIPT];
+        uint32_t arcmask = 0;   // bit i: item i is an arc (else a row end)
+        {
+            int x = lx, y = ly;
+#pragma unroll
+            for (int i = 0; i < kIPT; ++i) {
+                item_v[i] = 0;
+                if (i < cnt) {
+                    if (y < s.rowend[x] - a0) {
+                        item_v[i] = s.val[pad(y)];
+                        arcmask |= 1u << i;
+                        ++y;
+                    } else {
+                        ++x;
+                    }
                 }
             }
-            warp_seg_scan_incl<APP>(v, f);
-            T lane_ev = __shfl_up_sync(0xFFFFFFFFu, v, 1);
-            uint32_t lane_ef = __shfl_up_sync(0xFFFFFFFFu, f, 1);
-            if (lane == 0) { lane_ev = A::id(); lane_ef = 0; }
-            if (lane == 31) { sm.warp_v[warp] = v; sm.warp_f[warp] = f; }
-            __syncthreads();
-            if (warp == 0) {
-                T wv = lane < kWarps ? sm.warp_v[lane] : A::id();
-                uint32_t wf = lane < kWarps ? sm.warp_f[lane] : 0u;
-                warp_seg_scan_incl<APP>(wv, wf);
-                T ev = __shfl_up_sync(0xFFFFFFFFu, wv, 1);
-                uint32_t ef = __shfl_up_sync(0xFFFFFFFFu, wf, 1);
-                if (lane == 0) { ev = A::id(); ef = 0; }
-                // publish the tile's own partial (the open row's part in this tile)
-                T tv = __shfl_sync(0xFFFFFFFFu, wv, kWarps - 1);
-                uint32_t tf = __shfl_sync(0xFFFFFFFFu, wf, kWarps - 1);
-                if (lane == 0) st_release_u64(&a.st_carry[t], pack_status(a.epoch, tf, A::bits(tv)));
-                if (lane < kWarps) { sm.warp_v[lane] = ev; sm.warp_f[lane] = ef; }
-                // the carry of the row open at the tile start
-                T c = A::id();
-                if (a0 > sm.row_start) c = lookback_carry<APP>(a.st_carry, t, a.epoch, a.err);
-                if (lane == 0) sm.carry = c;
+        }
+        const uint32_t endmask = ((1u << cnt) - 1u) & ~arcmask;
+
+        // ---- fold + warp segmented scan --------------------------------------
+        T carry_in = A::id();
+        bool defer_first = false;   // gather: the tile's first row end waits for k_fixup
+        if constexpr (KIND != K_SAMPLE) {
+            T v = A::id(), head = A::id();
+            uint32_t f = 0;
+#pragma unroll
+            for (int i = 0; i < kIPT; ++i) {
+                if ((arcmask >> i) & 1u) {
+                    v = A::op(v, A::from_bits(item_v[i]));
+                } else if ((endmask >> i) & 1u) {
+                    if (!f) head = v;
+                    f = 1u;
+                    v = A::id();
+                }
             }
-            __syncthreads();
-            // exclusive prefix of this thread = warp prefix (+) lane prefix, behind the carry
-            T ex_v = sm.warp_v[warp];
-            uint32_t ex_f = sm.warp_f[warp];
-            if (lane_ef) ex_v = lane_ev; else ex_v = A::op(ex_v, lane_ev);
-            ex_f |= lane_ef;
-            carry_in = ex_f ? ex_v : A::op(sm.carry, ex_v);
+            if (!f) head = v;
+            const uint32_t lane_f = f;
+            warp_seg_scan_incl<APP>(v, f);
+            T ex_v = __shfl_up_sync(0xFFFFFFFFu, v, 1);
+            uint32_t ex_f = __shfl_up_sync(0xFFFFFFFFu, f, 1);
+            if (lane == 0) { ex_v = A::id(); ex_f = 0u; }
+            const T tail = __shfl_sync(0xFFFFFFFFu, v, 31);
+            const uint32_t tf = __shfl_sync(0xFFFFFFFFu, f, 31);
+            if constexpr (KIND == K_GATHER || KIND == K_STASH) {
+                // partials for k_fixup / K_CORRECT: (has a row end, part after
+                // the last end) and the part before the first end
+                const unsigned first_end = __ballot_sync(0xFFFFFFFFu, lane_f != 0u);
+                const int lstar = first_end ? __ffs(first_end) - 1 : 31;
+                const T head_t = __shfl_sync(0xFFFFFFFFu, A::op(ex_v, head), lstar);
+                if (lane == 0) {
+                    a.part[t] = make_uint2(tf, A::bits(tail));
+                    a.part_head[t] = A::bits(first_end ? head_t : tail);
+                }
+                carry_in = ex_v;                    // rows open at the tile start: see k_fixup
+                defer_first = need_carry && !ex_f;
+            } else {
+                T c = A::id();
+                if (need_carry) {
+                    prev_part.x = __shfl_sync(0xFFFFFFFFu, prev_part.x, 0);
+                    prev_part.y = __shfl_sync(0xFFFFFFFFu, prev_part.y, 0);
+                    c = carry_from_parts<APP>(a.part, t, prev_part);
+                }
+                carry_in = ex_f ? ex_v : A::op(c, ex_v);
+                (void)tail;
+                (void)tf;
+            }
         }
 
-        // ---- pass 2: influence / flags per arc, apply per row end ----------
-        uint32_t my_active = 0;
+        // ---- pass 2: flags per arc, apply per row end ------------------------
+        uint32_t my_active = 0, my_flags = 0;
         int32_t q_u[kMin ? kIPT : 1];
         uint32_t q_v[kMin ? kIPT : 1];
         int q_n = 0;
-        {
+        if constexpr (KIND != K_STASH) {
             T acc = carry_in;
             int x = lx, y = ly;
-            for (int i = 0; i < cnt; ++i) {
-                if (y < sm.rowend[x] - a0) {
+#pragma unroll
+            for (int i = 0; i < kIPT; ++i) {
+                if ((arcmask >> i) & 1u) {
                     if constexpr (KIND == K_SAMPLE) {
-                        const uint32_t fl = sampled_flag(sm.src[y], r0 + x, a.symmetric, a.seed, a.thr);
-                        sm.flag[y] = (uint8_t)fl;
+                        const uint32_t fl = sampled_flag((int32_t)item_v[i], r0 + x, a.symmetric, a.seed, a.thr);
+                        my_flags |= fl << i;
                         my_active += fl;
                     } else {
-                        const T v = sm.val[y];
+                        const T v = A::from_bits(item_v[i]);
                         if constexpr (KIND == K_CORRECT) {
                             uint32_t fl;
                             if constexpr (APP == GG_APP_PAGERANK) {
@@ -362,7 +450,7 @@ k_tile(TileArgs a)
                             } else {
                                 if (v == kInf) {   // no candidate: the arc keeps its flag
                                     const int k = a0 + y;
-                                    fl = a.est_strict ? 0u : (sm.oldw[(k >> 5) - (a0 >> 5)] >> (k & 31)) & 1u;
+                                    fl = a.est_strict ? 0u : (s.oldw[(k >> 5) - w0] >> (k & 31)) & 1u;
                                 } else if (a.theta_case == 1) {
                                     fl = 1u;
                                 } else if (a.theta_case == 2) {
@@ -374,40 +462,28 @@ k_tile(TileArgs a)
                                     fl = 0u;
                                 }
                             }
-                            sm.flag[y] = (uint8_t)fl;
+                            my_flags |= fl << i;
                             my_active += fl;
                         }
                         acc = A::op(acc, v);
                     }
                     ++y;
-                } else {
-                    if constexpr (KIND != K_SAMPLE) {
-                        const int32_t u = r0 + x;
-                        if constexpr (APP == GG_APP_PAGERANK) {
-                            // GG-Apply + GG-VStatus (Alg. 2)
-                            const float nw = __fmaf_rn(a.damping, acc, a.base);
-                            const float old = a.rank_cur[u];
-                            const float delta = fabsf(__fsub_rn(nw, old));
-                            const int deg = a.out_ptr[u + 1] - a.out_ptr[u];
-                            a.rank_next[u] = nw;
-                            a.contrib_next[u] = deg > 0 ? __fdiv_rn(nw, (float)deg) : 0.0f;
-                            my_changed += delta > a.epsilon ? 1ull : 0ull;
-                            my_sum += __float2ull_rz(delta * 1099511627776.0f);
-                            const uint32_t db = __float_as_uint(delta);
-                            my_max = db > my_max ? db : my_max;
+                } else if ((endmask >> i) & 1u) {
+                    if constexpr (kApply) {
+                        if (defer_first) {
+                            defer_first = false;   // completed by k_fixup
                         } else {
-                            const uint32_t old = a.val_cur[u];
-                            const uint32_t nw = acc < old ? acc : old;
-                            a.val_next[u] = nw;
-                            if (nw < old) {
-                                my_changed += 1;
-                                if (old != kInf) {
-                                    my_sum += old - nw;
-                                    my_max = (old - nw) > my_max ? (old - nw) : my_max;
+                            const int32_t u = r0 + x;
+                            if constexpr (APP == GG_APP_PAGERANK) {
+                                apply_pr(a, u, acc, __uint_as_float(s.vtx[x]), s.deg[x], st);
+                            } else {
+                                bool ch;
+                                const uint32_t nw = apply_min(a, u, acc, s.vtx[x], st, &ch);
+                                if (ch) {
+                                    q_u[q_n] = u;
+                                    q_v[q_n] = nw;
+                                    ++q_n;
                                 }
-                                q_u[q_n] = u;
-                                q_v[q_n] = nw;
-                                ++q_n;
                             }
                         }
                     }
@@ -416,103 +492,112 @@ k_tile(TileArgs a)
                 }
             }
         }
-
-        // ---- frontier output (min applications) ----------------------------
-        if constexpr (kMin && KIND != K_SAMPLE) {
-            if (a.q_out) {
-                const uint32_t incl = warp_incl_sum_u32((uint32_t)q_n);
-                const uint32_t wtot = __shfl_sync(0xFFFFFFFFu, incl, 31);
-                uint32_t base = 0;
-                if (lane == 31 && wtot) base = atomicAdd(a.q_out_len, wtot);
-                base = __shfl_sync(0xFFFFFFFFu, base, 31);
-                const uint32_t pos = base + incl - (uint32_t)q_n;
-                for (int i = 0; i < q_n; ++i) {
-                    a.q_out[pos + i] = q_u[i];
-                    a.q_out_val[pos + i] = q_v[i];
-                }
-            }
+        if constexpr (kMin && kApply) {
+            if (a.q_out) frontier_append(a, q_u, q_v, q_n);
         }
 
-        // ---- pass 3: flags to the bitmap, compaction of active arcs --------
-        if constexpr (kCompact) {
+        // ---- pack the active arcs at the start of the tile's arc range -----
+        if constexpr (kPack) {
             const uint32_t incl = warp_incl_sum_u32(my_active);
-            if (lane == 31) sm.warp_c[warp] = incl;
-            __syncthreads();
-            if (warp == 0) {
-                uint32_t wc = lane < kWarps ? sm.warp_c[lane] : 0u;
-                const uint32_t wincl = warp_incl_sum_u32(wc);
-                const uint32_t tile_total = __shfl_sync(0xFFFFFFFFu, wincl, kWarps - 1);
-                if (lane < kWarps) sm.warp_c[lane] = wincl - wc;
-                if (lane == 0) {
-                    st_release_u64(&a.st_count[t], pack_status(a.epoch, t == 0 ? 1u : 0u, tile_total));
-                }
-                uint32_t excl = 0;
-                if (t > 0) excl = lookback_count(a.st_count, t, a.epoch, a.err);
-                if (lane == 0) {
-                    if (t > 0) st_release_u64(&a.st_count[t], pack_status(a.epoch, 1u, excl + tile_total));
-                    sm.tile_excl = excl;
-                    if (t == (int)num_tiles - 1) {
-                        *a.sp_nnz = excl + tile_total;
-                        if (a.stats) a.stats->active_after = excl + tile_total;
-                    }
-                    if (t == 0) a.sp_ptr[0] = 0;
-                }
-            }
-            __syncthreads();
-            uint32_t off = sm.tile_excl + sm.warp_c[warp] + incl - my_active;
+            if (lane == 31) a.tile_cnt[t] = incl;
+            uint32_t off = incl - my_active;   // tile-local position of this lane's first active arc
             {
                 int x = lx, y = ly;
-                for (int i = 0; i < cnt; ++i) {
-                    if (y < sm.rowend[x] - a0) {
-                        if (sm.flag[y]) {
-                            a.sp_src[off] = sm.src[y];
-                            if (a.sp_w && has_w) a.sp_w[off] = sm.w[y];
+#pragma unroll
+                for (int i = 0; i < kIPT; ++i) {
+                    if ((arcmask >> i) & 1u) {
+                        if ((my_flags >> i) & 1u) {
+                            const int k = a0 + y;
+                            a.tl_src[a0 + off] = (KIND == K_SAMPLE) ? (int32_t)item_v[i] : a.arc_src[k];
+                            if (a.tl_w) a.tl_w[a0 + off] = a.arc_w[k];
+                            atomicOr(&s.bits[(k >> 5) - w0], 1u << (k & 31));
                             ++off;
                         }
                         ++y;
-                    } else {
-                        a.sp_ptr[r0 + x + 1] = (int32_t)off;
+                    } else if ((endmask >> i) & 1u) {
+                        a.sp_ptr[r0 + x + 1] = (int32_t)off;   // tile-local; k_move adds the tile offset
                         ++x;
                     }
                 }
             }
-            if (narcs > 0) {
-                const int w0 = a0 >> 5, w1 = (a1 - 1) >> 5;
-                for (int w = w0 + tid; w <= w1; w += kThreads) {
-                    const int lo = a0 > w * 32 ? a0 : w * 32;
-                    const int hi = a1 < w * 32 + 32 ? a1 : w * 32 + 32;
-                    uint32_t bits = 0;
-                    for (int k = lo; k < hi; ++k) bits |= (uint32_t)sm.flag[k - a0] << (k & 31);
-                    if (hi - lo == 32) {
-                        a.mask[w] = bits;
-                    } else {
-                        const uint32_t range = ((1u << (hi - lo)) - 1u) << (lo & 31);
-                        atomicAnd(&a.mask[w], ~range);
-                        atomicOr(&a.mask[w], bits);
+            __syncwarp();
+            for (int i = (int)lane; i < nwords; i += 32) {
+                const int w = w0 + i;
+                const int lo = a0 > w * 32 ? a0 : w * 32;
+                const int hi = a1 < w * 32 + 32 ? a1 : w * 32 + 32;
+                const uint32_t bits = s.bits[i];
+                if (hi - lo == 32) {
+                    a.mask[w] = bits;
+                } else {
+                    const uint32_t range = ((1u << (hi - lo)) - 1u) << (lo & 31);
+                    atomicAnd(&a.mask[w], ~range);
+                    atomicOr(&a.mask[w], bits);
+                }
+            }
+        }
+        __syncwarp();
+
+        // ---- rotate the pipeline --------------------------------------------
+        hdr_cur = hdr_nxt;
+        hdr_nxt = hdr_far;
+#pragma unroll
+        for (int i = 0; i < kIPT; ++i) {
+            src_cur[i] = src_nxt[i];
+            if constexpr (kWeighted) w_cur[i] = w_nxt[i];
+        }
+    }
+    if constexpr (kApply) flush_stats(a, st);
+}
+
+// ----------------------------------------------------------------- fixup ----
+// Rows of a gather that began in an earlier tile and end in tile t: their
+// value is the partials of the tiles from the one where the row began up to
+// t-1, then tile t's part before its first row end, added in tile order.
+// One thread per tile (warp-uniform loop); runs after k_tile<., K_GATHER>.
+template <int APP>
+__global__ void __launch_bounds__(kThreads)
+k_fixup(TileArgs a)
+{
+    using T = typename Acc<APP>::T;
+    using A = Acc<APP>;
+    constexpr bool kMin = APP != GG_APP_PAGERANK;
+    const long long num_tiles = (long long)*a.num_tiles;
+    const uint32_t lane = lane_id();
+    ApplyStats st;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long wb = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); wb < num_tiles; wb += stride) {
+        const long long t = wb + lane;
+        int32_t qu[1];
+        uint32_t qv[1];
+        int qn = 0;
+        if (t < num_tiles) {
+            const uint32_t info = (uint32_t)a.tile_info[t];
+            const uint2 me = a.part[t];
+            if ((info >> 31) && me.x) {
+                long long j = t - 1;
+                while (j > 0 && a.part[j].x == 0u) --j;
+                T acc = A::from_bits(a.part[j].y);
+                for (long long k = j + 1; k < t; ++k) acc = A::op(acc, A::from_bits(a.part[k].y));
+                acc = A::op(acc, A::from_bits(a.part_head[t]));
+                const int32_t u = (int32_t)(info & 0x7FFFFFFFu);
+                if constexpr (APP == GG_APP_PAGERANK) {
+                    apply_pr(a, u, acc, a.rank_cur[u], a.out_ptr[u + 1] - a.out_ptr[u], st);
+                } else {
+                    bool ch;
+                    const uint32_t nw = apply_min(a, u, acc, a.val_cur[u], st, &ch);
+                    if (ch) {
+                        qu[0] = u;
+                        qv[0] = nw;
+                        qn = 1;
                     }
                 }
             }
         }
-    }
-
-    // ---- statistics of this launch -----------------------------------------
-    if constexpr (KIND != K_SAMPLE) {
-        if (a.stats) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                my_changed += __shfl_xor_sync(0xFFFFFFFFu, my_changed, o);
-                my_sum += __shfl_xor_sync(0xFFFFFFFFu, my_sum, o);
-                const uint32_t om = __shfl_xor_sync(0xFFFFFFFFu, my_max, o);
-                my_max = om > my_max ? om : my_max;
-            }
-            if (lane == 0 && (my_changed | my_sum | my_max)) {
-                atomicAdd(&a.stats->changed, my_changed);
-                atomicAdd(&a.stats->sum_delta, my_sum);
-                atomicMax(&a.stats->max_delta_bits, my_max);
-            }
+        if constexpr (kMin) {
+            if (a.q_out) frontier_append(a, qu, qv, qn);
         }
     }
-    sched_leave(a.sched);
+    flush_stats(a, st);
 }
 
 }  // namespace gg
