@@ -1,0 +1,451 @@
+#!/usr/bin/env python
+"""Bench of the GraphGuess hot path on one GB300 (or N replicas).
+
+One step = one pass over every step of the hot path on the R-MAT scale-22
+workload (4 194 304 vertices, 67 108 864 directed arcs, weights in [1, 255]):
+  load the CSR already resident in HBM and build the in-edge view (gg_load_csr),
+  exact PageRank (20 iterations) and exact SSSP (the baselines of Sec. 5),
+  then for every sample ratio sigma in {0.1, 0.3, 0.5, 0.7, 0.9}: PageRank
+  and SSSP under adaptive correction (alpha 4, theta 0.05), each re-sampling
+  its edges (Sec. 3.4) and running the approximate gathers, corrections,
+  push frontier and change statistics.
+
+value = GTEPS = arcs gathered by all runs of the step (the size of every
+iteration's edge set) / step time, summed over ranks. e2e = the same with the
+CSR in pinned host memory (host-to-device copies inside the step) and every
+run's vertex values copied back to the host.
+
+--impl reference times the CPU oracle (the reference arm of this repository)
+on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+SCALE = 22
+EDGEFACTOR = 16
+GRAPH_SEED, WEIGHT_SEED, SOURCE_SEED, SAMPLE_SEED = 1, 7, 2, 1
+SIGMAS = (0.1, 0.3, 0.5, 0.7, 0.9)
+ALPHA, THETA, PR_ITERS, DAMPING = 4, 0.05, 20, 0.85
+MAX_ITERS_MIN = 1 << 20
+METRIC = "GTEPS & HBM-roofline fraction; time-to-accuracy vs exact, same GB300"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=int, default=SCALE, help="R-MAT scale (the workload is 22)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(scale):
+    import graphgen
+    g = graphgen.rmat(scale, EDGEFACTOR, seed=GRAPH_SEED)
+    graphgen.add_weights(g, seed=WEIGHT_SEED)
+    source = int(graphgen.sources(g, 1, seed=SOURCE_SEED)[0])
+    return g, source
+
+
+def run_list(source):
+    runs = [("pagerank", 1.0, "exact"), ("sssp", 1.0, "exact")]
+    for s in SIGMAS:
+        runs += [("pagerank", s, "adaptive"), ("sssp", s, "adaptive")]
+    return runs
+
+
+def params(gg, app, source, timing=True):
+    flags = gg.GG_TIMING if timing else 0
+    if app == "pagerank":
+        return gg.make_params(alpha=ALPHA, theta=THETA, max_iters=PR_ITERS, damping=DAMPING,
+                              seed=SAMPLE_SEED, flags=flags)
+    return gg.make_params(alpha=ALPHA, theta=THETA, max_iters=MAX_ITERS_MIN, source=source,
+                          seed=SAMPLE_SEED, flags=flags)
+
+
+# --------------------------------------------------------- algorithmic bytes --
+# Bytes an iteration must move by the method's definition (value vectors are
+# gathered from L2; see the design notes). n = vertices, e = arcs of the
+# iteration's edge set, e_new = arcs active after a correction, m = all arcs.
+def gather_bytes(app, n, e):
+    if app == "pagerank":        # sources 4e; row ptr, rank, degree, rank', contrib' 20n; contrib 4n
+        return 4 * e + 24 * n
+    return 8 * e + 16 * n         # sources + weights 8e; row ptr, value, value', gathered value 16n
+
+
+def correct_bytes(app, n, m, e_new):
+    if app == "pagerank":
+        return 4 * m + 4 * e_new + m // 8 + 28 * n
+    return 8 * m + 8 * e_new + m // 4 + 20 * n
+
+
+def clocks_sampler():
+    """nvidia-smi sampling of SM clocks and throttle reasons, started before and
+    stopped after the timed region."""
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                              "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except OSError:
+        return None
+    lines = []
+    t = threading.Thread(target=lambda: lines.extend(p.stdout), daemon=True)
+    t.start()
+    return p, t, lines
+
+
+def clocks_summary(handle, device):
+    if handle is None:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+    p, t, lines = handle
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except subprocess.TimeoutExpired:
+        p.kill()
+    t.join(timeout=5)
+    sm, smax, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for ln in lines:
+        f = [x.strip() for x in ln.split(",")]
+        if len(f) < 9 or f[0] != str(device):
+            continue
+        try:
+            sm.append(float(f[1]))
+            smax.append(float(f[2]))
+        except ValueError:
+            continue
+        for name, v in zip(names, f[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(name)
+    return {"sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(smax) if smax else None,
+            "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def peak_hbm():
+    try:
+        with open(PEAKS) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2104_10039_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(cls):
+    """DRAM bytes per launch of a kernel class from the committed ncu summary,
+    if it was taken on the current kernel sources."""
+    try:
+        with open(TRAFFIC) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if t.get("kernel_hash") != kernel_hash():
+        return None
+    return t.get("bytes_per_launch", {}).get(cls)
+
+
+# ------------------------------------------------------------------ our arm --
+def bench_ours(a, rank, world, local):
+    import torch
+    from paper_2104_10039_gb300 import build
+    build.build()
+    from paper_2104_10039_gb300 import gg, metrics
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    g, source = workload(a.scale)
+    n, m = g.n, g.m
+    d_rowptr = torch.from_numpy(g.rowptr).cuda()
+    d_colidx = torch.from_numpy(g.colidx).cuda()
+    d_w = torch.from_numpy(g.weights.view(np.int32)).cuda()
+    h_rowptr = torch.from_numpy(g.rowptr).pin_memory()
+    h_colidx = torch.from_numpy(g.colidx).pin_memory()
+    h_w = torch.from_numpy(g.weights.view(np.int32)).pin_memory()
+    out_host = torch.empty(n, dtype=torch.int32).pin_memory()
+    runs = run_list(source)
+    stream = torch.cuda.current_stream()
+
+    def step(e2e=False, collect=None):
+        if e2e:
+            h = gg.gg_load_csr(n, m, h_rowptr, h_colidx, h_w, gg.GG_DIRECTED)
+        else:
+            h = gg.gg_load_csr(n, m, d_rowptr, d_colidx, d_w, gg.GG_DIRECTED | gg.GG_DEVICE_PTRS)
+        arcs = 0
+        launches = gg.stats(h).kernels_load
+        per = {"load_ms": gg.stats(h).ms_load}
+        try:
+            for app, sigma, policy in runs:
+                gg.gg_run(h, app, sigma, policy, params(gg, app, source))
+                st = gg.stats(h)
+                arcs += st.arcs_processed
+                launches += st.kernels_launched
+                if e2e:
+                    gg.gg_result(h, gg.GG_RESULT_VALUES, out_host, 4 * n)
+                if collect is not None:
+                    collect.append((app, sigma, policy, st, gg.result_array(h, gg.GG_RESULT_ITER_STATS)))
+        finally:
+            gg.gg_free_graph(h)
+        return arcs, launches, per
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x):
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    for _ in range(a.warmup):
+        step()
+    # ---- timed region: device-resident inputs ------------------------------
+    clk = clocks_sampler() if rank == 0 else None
+    collected = []
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    arcs_total, launches_total = 0, 0
+    for k in range(a.steps):
+        arcs, launches, _ = step(collect=collected if k == a.steps - 1 else None)
+        arcs_total += arcs
+        launches_total += launches
+    ev1.record(stream)
+    barrier()
+    ms = max_over_ranks(ev0.elapsed_time(ev1))
+    clocks = clocks_summary(clk, local) if rank == 0 else None
+    arcs_all = sum_over_ranks(arcs_total)
+    value = arcs_all / (ms * 1e-3) / 1e9
+
+    # ---- end to end: host buffers, copies inside ---------------------------
+    for _ in range(1):
+        step(e2e=True)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    e_arcs = 0
+    for _ in range(a.steps):
+        e_arcs += step(e2e=True)[0]
+    e1.record(stream)
+    barrier()
+    e_ms = max_over_ranks(e0.elapsed_time(e1))
+    e_value = sum_over_ranks(e_arcs) / (e_ms * 1e-3) / 1e9
+
+    if rank != 0:
+        return None
+
+    # ---- roofline of the dominant kernel class (last timed step) ------------
+    classes = {"gather": [0.0, 0, 0.0], "correct": [0.0, 0, 0.0], "push": [0.0, 0, 0.0]}
+    for app, sigma, policy, st, it in collected:
+        classes["gather"][0] += st.ms_gather
+        classes["gather"][1] += st.n_gather
+        classes["correct"][0] += st.ms_correct
+        classes["correct"][1] += st.n_correct
+        classes["push"][0] += st.ms_push
+        classes["push"][1] += st.n_push
+        for row in it:
+            mode = int(row["mode"])
+            if mode in (0, 1):    # pull gathers (push iterations carry the GG_ITER_PUSH bit)
+                classes["gather"][2] += gather_bytes(app, n, int(row["arcs"]))
+            elif mode == 2:
+                classes["correct"][2] += correct_bytes(app, n, m, int(row["active_after"]))
+    dom = max(classes, key=lambda c: classes[c][0])
+    peak, peak_kind = peak_hbm()
+    roof = None
+    if classes[dom][1] and classes[dom][2] > 0:
+        avg_s = classes[dom][0] * 1e-3 / classes[dom][1]
+        bytes_per = classes[dom][2] / classes[dom][1]
+        achieved = bytes_per / avg_s / 1e9
+        roof = {"kernel": {"gather": "k_tile<*, K_GATHER> + k_fixup",
+                           "correct": "k_tile<*, K_STASH> + k_tile<*, K_CORRECT>",
+                           "push": "k_push"}[dom],
+                "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                "traffic": recorded_traffic(dom),
+                "algorithmic_bytes_per_launch": int(bytes_per),
+                "avg_launch_ms": round(classes[dom][0] / classes[dom][1], 4),
+                "class_ms_last_step": {c: round(v[0], 3) for c, v in classes.items()}}
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "GTEPS", "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms / a.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/u32",
+        "data": "synthetic (seeded R-MAT; the paper's datasets are not available)",
+        "config": {"workload": f"rmat{a.scale}-ef{EDGEFACTOR}-directed: load + exact PageRank/SSSP + "
+                               f"adaptive-correction PageRank/SSSP at sigma {list(SIGMAS)}",
+                   "vertices": n, "arcs": m, "alpha": ALPHA, "theta": THETA,
+                   "pagerank_iters": PR_ITERS, "damping": DAMPING, "sssp_source": source,
+                   "runs_per_step": len(runs), "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (268 MB of arcs + 268 MB of weights per load)"},
+        "roofline": roof,
+        "e2e": {"value": round(e_value, 3), "unit": "GTEPS",
+                "h2d_bytes_per_step": int(4 * (n + 1) + 8 * m),
+                "d2h_bytes_per_step": int(4 * n * len(runs))},
+        "gpu_launches": int(launches_total),
+        "clocks": clocks,
+    }
+    return out, g, source, collected
+
+
+def accuracy_table(g, source, collected):
+    """Speedup (device time of the run) and accuracy (Sec. 4.2) of every
+    adaptive run of the last timed step against the exact run of the same
+    step; time to accuracy = the fastest configuration within 1 % error."""
+    from paper_2104_10039_gb300 import gg, metrics
+    # values are recomputed per configuration (one run each, untimed)
+    h = gg.gg_load_csr(g.n, g.m, g.rowptr, g.colidx, g.weights, gg.GG_DIRECTED)
+    try:
+        ref = {}
+        rows = []
+        for app, sigma, policy in run_list(source):
+            gg.gg_run(h, app, sigma, policy, params(gg, app, source, timing=False))
+            vals = gg.values(h, app)
+            ms = next(st.ms_run for a2, s2, p2, st, _ in collected
+                      if (a2, s2, p2) == (app, sigma, policy))
+            if policy == "exact":
+                ref[app] = (vals, ms)
+                continue
+            ev, ems = ref[app]
+            if app == "pagerank":
+                err = metrics.top_k_error(vals, ev, 100)
+                extra = {}
+            else:
+                se = metrics.stretch_error(vals, ev, source)
+                err = se["error"]
+                extra = {"unreached": se["unreached"]}
+            rows.append({"app": app, "sigma": sigma, "ms": round(ms, 3), "exact_ms": round(ems, 3),
+                         "speedup": round(ems / ms, 3), "error": round(err, 5),
+                         "accuracy_pct": round(metrics.accuracy(err), 3), **extra})
+    finally:
+        gg.gg_free_graph(h)
+    best = {}
+    for app in ("pagerank", "sssp"):
+        ok = [r for r in rows if r["app"] == app and r["error"] <= 0.01]
+        best[app] = min(ok, key=lambda r: r["ms"]) if ok else None
+    return {"target_error": 0.01, "metric": {"pagerank": "top-100 error", "sssp": "mean stretch error"},
+            "runs": rows, "best": best}
+
+
+# ------------------------------------------------------------- oracle (CPU) --
+def cpu_sample(g):
+    """The oracle as it stands on the host cores: one adaptive-correction
+    PageRank run (sigma 0.5) over the workload graph, in-edge build and
+    sampling included."""
+    import oracle
+    t0 = time.perf_counter()
+    r = oracle.run(g.n, g.rowptr, g.colidx, app="pagerank", policy="adaptive", sigma=0.5,
+                   seed=SAMPLE_SEED, alpha=ALPHA, theta=THETA, max_iters=PR_ITERS, damping=DAMPING,
+                   nthreads=0)
+    dt = time.perf_counter() - t0
+    return float(r["iter_arcs"].sum()), dt
+
+
+def omp_threads():
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v and v.isdigit() else os.cpu_count()
+
+
+def bench_reference(a, rank, world):
+    if rank != 0:
+        return None
+    g, _ = workload(a.scale)
+    for _ in range(a.warmup):
+        cpu_sample(g)
+    arcs, secs = 0.0, 0.0
+    for _ in range(a.steps):
+        x, dt = cpu_sample(g)
+        arcs += x
+        secs += dt
+    v = arcs / secs / 1e9
+    sample = (f"adaptive-correction PageRank (sigma 0.5, alpha {ALPHA}, theta {THETA}, "
+              f"{PR_ITERS} iterations) on rmat{a.scale}, in-edge build and sampling included")
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GTEPS",
+            "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": round(1e3 * secs / a.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded R-MAT)",
+            "config": {"workload": f"rmat{a.scale}-ef{EDGEFACTOR}-directed (oracle sample)"},
+            "cpu_baseline": {"value": round(v, 4), "unit": "GTEPS", "cores": omp_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(v, 4), "unit": "GTEPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    a = parse()
+    rank, world, local = dist_info()
+    if a.impl == "reference":
+        out = bench_reference(a, rank, world)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    res = bench_ours(a, rank, world, local)
+    if res is None:
+        return
+    out, g, source, collected = res
+    if not a.no_accuracy:
+        out["time_to_accuracy"] = accuracy_table(g, source, collected)
+    if not a.no_cpu_baseline and world >= 1:
+        arcs, secs = cpu_sample(g)
+        out["cpu_baseline"] = {"value": round(arcs / secs / 1e9, 4), "unit": "GTEPS",
+                               "cores": omp_threads(), "kind": "oracle",
+                               "sample": f"one adaptive-correction PageRank run (sigma 0.5, {PR_ITERS} "
+                                         f"iterations) on the same graph, {secs:.1f} s"}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -89,6 +89,7 @@ typedef enum {
 #define GG_TIMING 16u         /* record per-kernel-class device time with CUDA events */
 
 #define GG_INF 0xFFFFFFFFu
+#define GG_ITER_PUSH 0x100u   /* gg_iter_stats.mode bit: iteration done by the push frontier */
 
 typedef struct {
     uint32_t alpha;       /* approximate window: approximate iterations between corrections (Sec. 3.4) */
@@ -110,7 +111,7 @@ typedef struct {
     uint64_t active_arcs;     /* arcs active at the end of the run */
     uint64_t changed_last;    /* vertices active after the last iteration */
     uint32_t device_error;    /* nonzero if a bounded wait gave up (then the run failed) */
-    uint32_t reserved;
+    uint32_t kernels_load;    /* kernels this library launched during gg_load_csr */
     float ms_load;            /* device time of the last gg_load_csr (copy + validate + CSC build) */
     float ms_sample;          /* device time of the last sampling */
     float ms_run;             /* device time of the last gg_run (sampling included when it resampled) */
@@ -124,7 +125,8 @@ typedef struct {
 } gg_stats;
 
 typedef struct {
-    uint32_t mode;            /* 0 approximate, 1 accurate, 2 correction, 3 skipped no-op */
+    uint32_t mode;            /* 0 approximate, 1 accurate, 2 correction, 3 skipped no-op;
+                                 | GG_ITER_PUSH when the push frontier ran the iteration */
     uint32_t max_delta_bits;  /* max |old-new|: float bits (PageRank) or uint32 */
     uint64_t arcs;            /* size of the iteration's edge set */
     uint64_t changed;         /* vertices active after GG-VStatus */

@@ -28,6 +28,25 @@ gg_status cuda_fail(cudaError_t e, const char *what)
     return GG_ERR_CUDA;
 }
 
+cudaMemPool_t device_pool()
+{
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!pools[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
+        uint64_t keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        pools[dev] = pool;
+    }
+    return pools[dev];
+}
+
 // A frontier whose out-arcs number less than the list's arcs / this factor is
 // pushed instead of pulled (push pays atomics and a flag lookup per arc).
 constexpr uint64_t kPushFactor = 4;
@@ -283,7 +302,8 @@ static gg_status run_min(gg_graph *g, gg_app app, gg_policy policy, const gg_par
         bool push = mode != MODE_CORRECTION && !(p->flags & GG_FORCE_PULL) &&
                     ((p->flags & GG_FORCE_PUSH) || front_arcs * kPushFactor < list_nnz);
         IterStatsDev *sti = g->iter_stats + i;
-        GG_CUDA(launch_iter_header(sti, (uint32_t)mode, nullptr, list_nnz, g->stream));
+        GG_CUDA(launch_iter_header(sti, (uint32_t)mode | (push ? GG_ITER_PUSH : 0u), nullptr, list_nnz,
+                                   g->stream));
         g->launches += 1;
         if (push) {
             if (++g->stamp_tag == 0) {
@@ -410,7 +430,13 @@ gg_status run(gg_graph *g, gg_app app, double ratio, gg_policy policy, const gg_
     if (p->alpha == 0xFFFFFFFFu) { set_error("gg_run: alpha too large"); return GG_ERR_INVALID_ARG; }
     gg_status st = ensure_iter_cap(g, p->max_iters);
     if (st != GG_OK) return st;
-    g->stats = gg_stats{};
+    {
+        const float ms_load = g->stats.ms_load;
+        const uint32_t kl = g->stats.kernels_load;
+        g->stats = gg_stats{};
+        g->stats.ms_load = ms_load;
+        g->stats.kernels_load = kl;
+    }
     g->timed_used = 0;
     g->launches = 0;
     g->iterations = 0;
@@ -597,6 +623,7 @@ gg_status gg_load_csr(gg_graph **out, int32_t n, int64_t m, const int32_t *rowpt
             break;
         }
         cudaEventElapsedTime(&g->stats.ms_load, l0, l1);
+        g->stats.kernels_load = g->load_launches;
         cudaEventDestroy(l0);
         cudaEventDestroy(l1);
     } while (0);
@@ -666,7 +693,7 @@ static gg_status fill_stats(gg_graph *g)
         cudaError_t e = cudaMemcpy(h, g->iter_stats, sizeof(gg_iter_stats) * g->iterations, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) { delete[] h; return cuda_fail(e, "cudaMemcpy (iteration stats)"); }
         uint64_t arcs = 0;
-        for (uint32_t i = 0; i < g->iterations; ++i) arcs += h[i].mode == MODE_SKIPPED ? 0 : h[i].arcs;
+        for (uint32_t i = 0; i < g->iterations; ++i) arcs += (h[i].mode & 0xFFu) == MODE_SKIPPED ? 0 : h[i].arcs;
         s.arcs_processed = arcs;
         s.changed_last = h[g->iterations - 1].changed;
         delete[] h;

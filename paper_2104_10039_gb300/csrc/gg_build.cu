@@ -378,7 +378,7 @@ gg_status build_csc(gg_graph *g)
 
     DevBuf tmp;
     const size_t words = 4 * (size_t)m + ncounts + 1 + scan_tmp_words(ncounts) + (size_t)m;
-    gg_status st = tmp.alloc(words * sizeof(uint32_t));
+    gg_status st = tmp.alloc(words * sizeof(uint32_t), s);
     if (st != GG_OK) return st;
     uint32_t *keys[2] = {tmp.u32(), tmp.u32() + m};
     uint32_t *vals[2] = {tmp.u32() + 2 * m, tmp.u32() + 3 * m};
@@ -400,6 +400,7 @@ gg_status build_csc(gg_graph *g)
     }
     k_csc_rowptr<<<grid, 256, 0, s>>>(keys[cur], m, n, g->in_ptr);
     k_csc_finalize<<<grid, 256, 0, s>>>(vals[cur], m, src_of, g->out_w, g->in_src, g->in_w, g->out_to_in);
+    g->load_launches += 4 + 5 * passes;
     GG_CUDA(cudaGetLastError());
     // the temporaries are released only after the queued work has used them
     GG_CUDA(cudaStreamSynchronize(s));
@@ -411,6 +412,7 @@ gg_status validate_csr(gg_graph *g)
     cudaStream_t s = g->stream;
     GG_CUDA(cudaMemsetAsync(g->dev_err, 0, sizeof(uint32_t), s));
     k_validate<<<g->num_sms * 8, 256, 0, s>>>(g->out_ptr, g->out_dst, g->n, g->m, g->dev_err);
+    g->load_launches += 1;
     GG_CUDA(cudaGetLastError());
     uint32_t err = 0;
     GG_CUDA(cudaMemcpyAsync(&err, g->dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));

@@ -7,25 +7,33 @@
 
 namespace gg {
 
-// Owning device buffer.
+// The library's stream-ordered memory pool on the current device: freed
+// blocks stay in the pool (release threshold = unlimited), so loading graph
+// after graph reuses memory instead of calling the driver each time.
+cudaMemPool_t device_pool();
+
+// Owning device buffer, allocated from device_pool() in stream order.
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
+    cudaStream_t s = nullptr;
     DevBuf() = default;
     DevBuf(const DevBuf &) = delete;
     DevBuf &operator=(const DevBuf &) = delete;
     ~DevBuf() { release(); }
     void release()
     {
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, s);
         p = nullptr;
         bytes = 0;
     }
-    gg_status alloc(size_t b)
+    gg_status alloc(size_t b, cudaStream_t stream = nullptr)
     {
         release();
         if (b == 0) b = 16;
-        cudaError_t e = cudaMalloc(&p, b);
+        s = stream;
+        cudaMemPool_t pool = device_pool();
+        cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, b, pool, s) : cudaErrorMemoryAllocation;
         if (e != cudaSuccess) {
             cudaGetLastError();
             p = nullptr;
@@ -120,6 +128,7 @@ struct gg_graph {
     std::vector<gg::TimedLaunch> timed;
     size_t timed_used = 0;
     uint32_t launches = 0;
+    uint32_t load_launches = 0;
 };
 
 namespace gg {

@@ -34,6 +34,7 @@ GG_POLICY_EXACT, GG_POLICY_NONE, GG_POLICY_STATIC_SWITCH, GG_POLICY_ADAPTIVE = r
 GG_DIRECTED, GG_SYMMETRIC, GG_DEVICE_PTRS = 0, 1, 2
 GG_STOP_QUIESCE, GG_EST_STRICT, GG_FORCE_PULL, GG_FORCE_PUSH, GG_TIMING = 1, 2, 4, 8, 16
 GG_INF = 0xFFFFFFFF
+GG_ITER_PUSH = 0x100
 
 APPS = {"pagerank": GG_APP_PAGERANK, "pr": GG_APP_PAGERANK, "sssp": GG_APP_SSSP,
         "bfs": GG_APP_BFS, "cc": GG_APP_CC}
@@ -54,7 +55,7 @@ class gg_stats(ctypes.Structure):
                 ("push_iterations", ctypes.c_uint32), ("pull_iterations", ctypes.c_uint32),
                 ("arcs_processed", ctypes.c_uint64), ("active_arcs", ctypes.c_uint64),
                 ("changed_last", ctypes.c_uint64), ("device_error", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32), ("ms_load", ctypes.c_float),
+                ("kernels_load", ctypes.c_uint32), ("ms_load", ctypes.c_float),
                 ("ms_sample", ctypes.c_float), ("ms_run", ctypes.c_float),
                 ("ms_gather", ctypes.c_float), ("ms_correct", ctypes.c_float),
                 ("ms_push", ctypes.c_float), ("n_gather", ctypes.c_uint32),
