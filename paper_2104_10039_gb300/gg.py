@@ -85,6 +85,10 @@ _lib.gg_free_graph.restype = None
 _lib.gg_free_graph.argtypes = [_vp]
 _lib.gg_last_error.restype = ctypes.c_char_p
 _lib.gg_last_error.argtypes = []
+_lib.gg_sample_csc_noalloc.restype = ctypes.c_int
+_lib.gg_sample_csc_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int64, _vp, _vp, ctypes.c_double,
+                                       ctypes.c_uint64, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
+GG_NOALLOC_MAX_ITEMS = 1 << 24
 
 
 class GGError(RuntimeError):
@@ -155,6 +159,17 @@ def gg_set_stream(g: int, stream):
 
 def gg_free_graph(g: int):
     _lib.gg_free_graph(g)
+
+
+def gg_sample_csc_noalloc(n: int, m: int, in_ptr, in_src, sample_ratio: float, seed: int,
+                          symmetric: bool, mask, sp_ptr, sp_src, sp_nnz, stream=None):
+    """Sampling of caller-owned device arrays without any device allocation
+    (see gg.h); every array argument is device memory."""
+    _check(_lib.gg_sample_csc_noalloc(n, m, _addr(in_ptr), _addr(in_src), sample_ratio,
+                                      seed & 0xFFFFFFFFFFFFFFFF, int(symmetric), _addr(mask),
+                                      _addr(sp_ptr), _addr(sp_src), _addr(sp_nnz),
+                                      None if stream is None else int(stream)),
+           "gg_sample_csc_noalloc")
 
 
 # ---- convenience wrappers (still only marshalling) -----------------------
