@@ -66,6 +66,20 @@ def dist_info():
     return rank, world, local
 
 
+def aggregate(ms_local, units_local, world, device="cpu"):
+    """Whole-job figures of one timed region: the slowest rank's time and the
+    units all ranks processed (torch.distributed; NCCL on GPUs, gloo on CPU)."""
+    if world == 1:
+        return ms_local, units_local
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def workload(scale):
     import graphgen
     g = graphgen.rmat(scale, EDGEFACTOR, seed=GRAPH_SEED)
@@ -234,22 +248,6 @@ def bench_ours(a, rank, world, local):
             import torch.distributed as dist
             dist.barrier()
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def sum_over_ranks(x):
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
-
     for _ in range(a.warmup):
         step()
     # ---- timed region: device-resident inputs ------------------------------
@@ -265,9 +263,8 @@ def bench_ours(a, rank, world, local):
         launches_total += launches
     ev1.record(stream)
     barrier()
-    ms = max_over_ranks(ev0.elapsed_time(ev1))
     clocks = clocks_summary(clk, local) if rank == 0 else None
-    arcs_all = sum_over_ranks(arcs_total)
+    ms, arcs_all = aggregate(ev0.elapsed_time(ev1), arcs_total, world, "cuda")
     value = arcs_all / (ms * 1e-3) / 1e9
 
     # ---- end to end: host buffers, copies inside ---------------------------
@@ -281,43 +278,42 @@ def bench_ours(a, rank, world, local):
         e_arcs += step(e2e=True)[0]
     e1.record(stream)
     barrier()
-    e_ms = max_over_ranks(e0.elapsed_time(e1))
-    e_value = sum_over_ranks(e_arcs) / (e_ms * 1e-3) / 1e9
+    e_ms, e_arcs_all = aggregate(e0.elapsed_time(e1), e_arcs, world, "cuda")
+    e_value = e_arcs_all / (e_ms * 1e-3) / 1e9
 
     if rank != 0:
         return None
 
-    # ---- roofline of the dominant kernel class (last timed step) ------------
-    classes = {"gather": [0.0, 0, 0.0], "correct": [0.0, 0, 0.0], "push": [0.0, 0, 0.0]}
+    # ---- roofline of the dominant kernel (last timed step) -----------------
+    # per (application, kernel class): device time, launches, algorithmic bytes
+    classes = {}
     for app, sigma, policy, st, it in collected:
-        classes["gather"][0] += st.ms_gather
-        classes["gather"][1] += st.n_gather
-        classes["correct"][0] += st.ms_correct
-        classes["correct"][1] += st.n_correct
-        classes["push"][0] += st.ms_push
-        classes["push"][1] += st.n_push
+        for cls, ms_c, n_c in (("gather", st.ms_gather, st.n_gather), ("correct", st.ms_correct, st.n_correct),
+                               ("push", st.ms_push, st.n_push)):
+            c = classes.setdefault((app, cls), [0.0, 0, 0.0])
+            c[0] += ms_c
+            c[1] += n_c
         for row in it:
             mode = int(row["mode"])
             if mode in (0, 1):    # pull gathers (push iterations carry the GG_ITER_PUSH bit)
-                classes["gather"][2] += gather_bytes(app, n, int(row["arcs"]))
+                classes[(app, "gather")][2] += gather_bytes(app, n, int(row["arcs"]))
             elif mode == 2:
-                classes["correct"][2] += correct_bytes(app, n, m, int(row["active_after"]))
-    dom = max(classes, key=lambda c: classes[c][0])
+                classes[(app, "correct")][2] += correct_bytes(app, n, m, int(row["active_after"]))
+    dom = max((k for k in classes if classes[k][2] > 0), key=lambda k: classes[k][0])
     peak, peak_kind = peak_hbm()
     roof = None
-    if classes[dom][1] and classes[dom][2] > 0:
+    if classes[dom][1]:
         avg_s = classes[dom][0] * 1e-3 / classes[dom][1]
         bytes_per = classes[dom][2] / classes[dom][1]
         achieved = bytes_per / avg_s / 1e9
-        roof = {"kernel": {"gather": "k_tile<*, K_GATHER> + k_fixup",
-                           "correct": "k_tile<*, K_STASH> + k_tile<*, K_CORRECT>",
-                           "push": "k_push"}[dom],
-                "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "peak_source": peak_kind,
-                "traffic": recorded_traffic(dom),
+        name = {"gather": "k_tile<{a}, K_GATHER> + k_fixup<{a}>",
+                "correct": "k_tile<{a}, K_STASH> + k_tile<{a}, K_CORRECT>"}[dom[1]].format(a=dom[0])
+        roof = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                "traffic": recorded_traffic(f"{dom[0]}/{dom[1]}"),
                 "algorithmic_bytes_per_launch": int(bytes_per),
                 "avg_launch_ms": round(classes[dom][0] / classes[dom][1], 4),
-                "class_ms_last_step": {c: round(v[0], 3) for c, v in classes.items()}}
+                "ms_last_step": {f"{k[0]}/{k[1]}": round(v[0], 3) for k, v in classes.items()}}
 
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "GTEPS", "n_gpus": world,

@@ -1,0 +1,117 @@
+"""GPU parity at the workloads' full sizes, in the configuration bench.py
+times: R-MAT scale 22 (67 108 864 directed arcs) for PageRank and SSSP, and
+the symmetrised R-MAT scale-24 and Erdos-Renyi graphs (268 435 456 arcs) for
+BFS, SSSP and CC at sample ratio 0.3. The oracle runs on every host core
+(its results do not depend on the thread count).
+
+Bars as in test_gpu_parity: bit-exact for the in-edge build, the sampled
+flags and the integer applications (values and post-correction flags);
+PageRank within 1e-5 relative L1, through mask replay when it corrects.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+from tests import gpu_common as gc
+
+pytestmark = pytest.mark.gpu
+
+ALPHA, THETA, PR_ITERS = 4, 0.05, 20
+BIG = 1 << 20
+
+
+@pytest.fixture(scope="module")
+def gg():
+    return gc.lib()
+
+
+@pytest.fixture(scope="module")
+def rmat22():
+    g = graphgen.rmat(22, 16, seed=1)
+    graphgen.add_weights(g, seed=7)
+    return g, int(graphgen.sources(g, 1, seed=2)[0])
+
+
+def test_rmat22_csc_and_sampler(gg, rmat22):
+    g, _ = rmat22
+    h = gc.load(gg, g, device_ptrs=True)
+    try:
+        ip, isrc, iw, pos = oracle.csc_from_csr(g.n, g.rowptr, g.colidx, g.weights)
+        assert np.array_equal(gg.result_array(h, gg.GG_RESULT_CSC_PTR), ip)
+        assert np.array_equal(gg.result_array(h, gg.GG_RESULT_CSC_SRC), isrc)
+        assert np.array_equal(gg.result_array(h, gg.GG_RESULT_CSC_W), iw)
+        o2i = gg.result_array(h, gg.GG_RESULT_OUT_TO_IN)
+        sample = np.random.default_rng(0).integers(0, g.m, 100000)
+        assert np.array_equal(pos[o2i[sample]], sample)
+        gg.gg_sample_edges(h, 0.5, 1)
+        want = oracle.sample_mask(g.n, ip, isrc, 0.5, 1)
+        assert np.array_equal(gg.mask_bits(h, g.m), want)
+        cs = np.concatenate([[0], np.cumsum(want.astype(np.int64))])
+        assert np.array_equal(gg.result_array(h, gg.GG_RESULT_SPARSE_PTR), cs[ip])
+    finally:
+        gg.gg_free_graph(h)
+
+
+def test_rmat22_pagerank_exact_and_adaptive(gg, rmat22):
+    g, _ = rmat22
+    h = gc.load(gg, g)
+    try:
+        got, _, _ = gc.gpu_run(gg, h, g, "pagerank", "exact", T=PR_ITERS)
+        ref = oracle.run(g.n, g.rowptr, g.colidx, app="pagerank", policy="exact", max_iters=PR_ITERS,
+                         nthreads=0)
+        assert gc.rel_l1(got, ref["values"]) <= 1e-5
+        for sigma in (0.1, 0.5):
+            vals, ref, st = gc.pagerank_with_replay(gg, h, g, "adaptive", sigma, ALPHA, THETA, PR_ITERS, seed=1)
+            assert ref["replay_violations"] == 0, ref["replay_max_margin"]
+            assert ref["replay_mismatch"] <= g.m // 10000
+            assert gc.rel_l1(vals, ref["values"]) <= 1e-5
+            assert st.corrections == 4
+    finally:
+        gg.gg_free_graph(h)
+
+
+def test_rmat22_sssp_bit_exact(gg, rmat22):
+    g, s = rmat22
+    h = gc.load(gg, g)
+    try:
+        for policy, sigma in (("exact", 1.0), ("adaptive", 0.5), ("adaptive", 0.1)):
+            got, mask, st = gc.gpu_run(gg, h, g, "sssp", policy, sigma=sigma, alpha=ALPHA, theta=THETA,
+                                       T=BIG, source=s, seed=1)
+            ref = oracle.run(g.n, g.rowptr, g.colidx, g.weights, app="sssp", policy=policy, sigma=sigma,
+                             seed=1, alpha=ALPHA, theta=THETA, max_iters=BIG, source=s, nthreads=0)
+            assert np.array_equal(got, ref["values"]), policy
+            if mask is not None:
+                assert np.array_equal(mask, ref["mask"]), policy
+            assert st.iterations == ref["iterations"]
+    finally:
+        gg.gg_free_graph(h)
+
+
+@pytest.fixture(scope="module", params=["rmat24", "er24"])
+def sym24(request):
+    if request.param == "rmat24":
+        g = graphgen.rmat(24, 16, seed=1, symmetric=True)
+    else:
+        g = graphgen.erdos_renyi(1 << 24, avg_degree=16, seed=1, symmetric=True)
+    graphgen.add_weights(g, seed=7)
+    return g, int(graphgen.sources(g, 1, seed=2)[0])
+
+
+@pytest.mark.parametrize("app", ["bfs", "sssp", "cc"])
+def test_scale24_symmetric_bit_exact(gg, sym24, app):
+    g, s = sym24
+    h = gc.load(gg, g)
+    try:
+        got, mask, st = gc.gpu_run(gg, h, g, app, "adaptive", sigma=0.3, alpha=ALPHA, theta=THETA,
+                                   T=BIG, source=s, seed=1)
+        ref = oracle.run(g.n, g.rowptr, g.colidx, g.weights if app == "sssp" else None, app=app,
+                         policy="adaptive", sigma=0.3, seed=1, alpha=ALPHA, theta=THETA, max_iters=BIG,
+                         source=s, symmetric=True, nthreads=0)
+        assert np.array_equal(got, ref["values"])
+        assert np.array_equal(mask, ref["mask"])
+        assert st.iterations == ref["iterations"]
+    finally:
+        gg.gg_free_graph(h)
