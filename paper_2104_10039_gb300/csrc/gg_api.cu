@@ -132,7 +132,6 @@ static void fill_list(const gg_graph *g, bool sparse, TileArgs &a)
     }
     a.st_carry = g->st_carry;
     a.err = g->dev_err;
-    a.tl_src = g->tl_src;
     a.tile_cnt = g->tile_cnt;
     a.part = g->part;
     a.part_head = g->part_head;
@@ -144,9 +143,9 @@ static void fill_list(const gg_graph *g, bool sparse, TileArgs &a)
 static gg_status finish_pack(gg_graph *g, bool weighted, IterStatsDev *stats)
 {
     GG_CUDA(launch_scan_u32(g->tile_cnt, g->tile_off, g->full_tiles, g->scan_tmp, g->stream));
-    GG_CUDA(launch_move(g->full_tile_info, g->tile_off, g->full_tiles, g->tl_src, weighted ? g->tl_w : nullptr,
-                        g->sp_ptr, g->sp_src, weighted ? g->sp_w : nullptr, g->sp_nnz, stats, g->num_sms,
-                        g->stream));
+    GG_CUDA(launch_pack(g->full_tile_info, g->tile_off, g->full_tiles, (long long)g->n + g->m, g->mask, g->in_src,
+                        weighted ? g->in_w : nullptr, g->sp_ptr, g->sp_src, weighted ? g->sp_w : nullptr, g->sp_nnz,
+                        stats, g->num_sms, g->stream));
     GG_CUDA(launch_partition(g->sp_ptr, g->n, g->sp_nnz, g->max_tiles, g->sp_tile_info, g->sp_num_tiles,
                              g->stream));
     g->launches += 5;
@@ -164,7 +163,6 @@ gg_status sample_edges(gg_graph *g, double ratio, uint64_t seed)
     fill_list(g, false, a);
     a.mask = g->mask;
     a.sp_ptr = g->sp_ptr;
-    a.tl_w = g->has_w ? g->tl_w : nullptr;
     a.seed = seed;
     a.thr = (unsigned long long)std::floor(ratio * 4294967296.0);
     a.symmetric = g->symmetric ? 1 : 0;
@@ -219,7 +217,6 @@ static gg_status run_pagerank(gg_graph *g, gg_policy policy, const gg_params *p)
         if (kind == K_CORRECT) {
             a.mask = g->mask;
             a.sp_ptr = g->sp_ptr;
-            a.tl_w = nullptr;
             a.theta = p->theta;
         }
         GG_CUDA(launch_iter_header(a.stats, (uint32_t)mode, a.list_nnz, 0, g->stream));
@@ -352,7 +349,6 @@ static gg_status run_min(gg_graph *g, gg_app app, gg_policy policy, const gg_par
             if (kind == K_CORRECT) {
                 a.mask = g->mask;
                 a.sp_ptr = g->sp_ptr;
-                a.tl_w = (app == GG_APP_SSSP && g->has_w) ? g->tl_w : nullptr;
                 a.theta_case = theta_case;
                 a.theta_fx = theta_fx;
                 a.est_strict = (p->flags & GG_EST_STRICT) ? 1 : 0;
@@ -489,9 +485,7 @@ static gg_status alloc_graph(gg_graph *g)
     GG_ALLOC(g->b_sp_tile_info, 4 * ((size_t)g->max_tiles + 2));
     GG_ALLOC(g->b_tile_cnt, 4 * (2 * (size_t)g->max_tiles + 4));
     GG_ALLOC(g->b_part, 12 * ((size_t)g->max_tiles + 2));
-    GG_ALLOC(g->b_tl_src, 4 * m);
     GG_ALLOC(g->b_stash, 4 * m);
-    if (g->has_w) GG_ALLOC(g->b_tl_w, 4 * m);
     GG_ALLOC(g->b_scalars, 4 * 16);
     g->mask_words = (m + 31) / 32;
     GG_ALLOC(g->b_mask, 4 * (g->mask_words + 1));
@@ -517,9 +511,7 @@ static gg_status alloc_graph(gg_graph *g)
     g->tile_off = g->tile_cnt + g->max_tiles + 2;
     g->part = (uint2 *)g->b_part.p;
     g->part_head = (uint32_t *)(g->part + g->max_tiles + 2);
-    g->tl_src = g->b_tl_src.i32();
     g->stash = g->b_stash.u32();
-    g->tl_w = g->has_w ? g->b_tl_w.u32() : nullptr;
     uint32_t *sc = g->b_scalars.u32();
     g->full_num_tiles = sc + 0;
     g->sp_num_tiles = sc + 1;

@@ -79,13 +79,13 @@ struct gg_graph {
     uint32_t *dev_err = nullptr, *q_len = nullptr;  // q_len[2]
     uint32_t max_tiles = 0;     // upper bound on tiles of any list
     uint32_t full_tiles = 0;    // tiles of the full in-edge list
-    // tile-local packs of the correction / sampler, their counts and offsets
-    gg::DevBuf b_tl_src, b_tl_w, b_tile_cnt, b_part, b_stash;
+    // active arcs per tile of a correction / sampling pass and their scan;
+    // gather partials; the correction's value stash
+    gg::DevBuf b_tile_cnt, b_part, b_stash;
     uint32_t *stash = nullptr;
     uint2 *part = nullptr;
     uint32_t *part_head = nullptr;
-    int32_t *tl_src = nullptr;
-    uint32_t *tl_w = nullptr, *tile_cnt = nullptr, *tile_off = nullptr;
+    uint32_t *tile_cnt = nullptr, *tile_off = nullptr;
     // flags and packed active in-edges
     gg::DevBuf b_mask, b_sp_ptr, b_sp_src, b_sp_w;
     uint32_t *mask = nullptr;

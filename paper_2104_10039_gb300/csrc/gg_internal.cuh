@@ -94,9 +94,7 @@ struct TileArgs {
     uint32_t *part_head;
     // correction: arc values (candidates) in list order, written by K_STASH
     uint32_t *stash;
-    // tile-local packing (correction, sampling)
-    int32_t *tl_src;
-    uint32_t *tl_w;
+    // active arcs per tile (correction, sampling)
     uint32_t *tile_cnt;
     // look-back
     unsigned long long *st_carry;
@@ -217,12 +215,13 @@ struct Graph;
 cudaError_t launch_partition(const int32_t *row_ptr, int32_t n, const uint32_t *list_nnz,
                              uint32_t max_tiles, int32_t *tile_info, uint32_t *num_tiles,
                              cudaStream_t s);
-// Packed active in-edges from the tiles' local packs: tile_off is the
-// exclusive scan of the tile counts (num_tiles + 1 entries).
-cudaError_t launch_move(const int32_t *tile_info, const uint32_t *tile_off, uint32_t num_tiles,
-                        const int32_t *tl_src, const uint32_t *tl_w, int32_t *sp_ptr, int32_t *sp_src,
-                        uint32_t *sp_w, uint32_t *sp_nnz, IterStatsDev *stats, int num_sms, cudaStream_t s);
-// Tile kernels run a cooperative persistent grid: min(max_tiles, resident warps).
+// Packed active in-edges from the flag bitmap of the full in-edge list:
+// tile_off is the exclusive scan of the tiles' active counts (num_tiles + 1).
+cudaError_t launch_pack(const int32_t *tile_info, const uint32_t *tile_off, uint32_t num_tiles, long long total_items,
+                        const uint32_t *mask, const int32_t *in_src, const uint32_t *in_w, int32_t *sp_ptr,
+                        int32_t *sp_src, uint32_t *sp_w, uint32_t *sp_nnz, IterStatsDev *stats, int num_sms,
+                        cudaStream_t s);
+// Tile kernels run a persistent grid: min(max_tiles, resident warps).
 cudaError_t launch_tile_pr(int kind, const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s);
 cudaError_t launch_tile_min(int app, int kind, const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s);
 cudaError_t launch_tile_sample(const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s);

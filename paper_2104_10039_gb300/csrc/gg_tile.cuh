@@ -16,9 +16,9 @@
 //           row open at its start; the tile publishes its partials;
 //   pass 2  per arc, influence and new flag (correction, Alg. 2 GG-EStatus)
 //           or sampled flag (Sec. 3.4); per row end, GG-Apply + GG-VStatus;
-//   pack    (correction, sampling) the tile's active arcs are packed at the
-//           start of its own arc range; a tile-count scan and k_move then
-//           place them in the packed active-CSC.
+//   flags   (correction, sampling) the new flags go to the bitmap with the
+//           tile's active count and the tile-local row ends; a tile-count
+//           scan and k_pack then build the packed active-CSC from the bitmap.
 // A row that began in an earlier tile needs those tiles' partials. The gather
 // leaves that row to k_fixup. The correction, whose per-arc influence needs
 // the running value before each arc (Alg. 2, GG-Gather's return), runs in two
@@ -496,11 +496,11 @@ k_tile(TileArgs a)
             if (a.q_out) frontier_append(a, q_u, q_v, q_n);
         }
 
-        // ---- pack the active arcs at the start of the tile's arc range -----
+        // ---- new flags into the bitmap; tile count and tile-local row ends --
         if constexpr (kPack) {
             const uint32_t incl = warp_incl_sum_u32(my_active);
             if (lane == 31) a.tile_cnt[t] = incl;
-            uint32_t off = incl - my_active;   // tile-local position of this lane's first active arc
+            uint32_t off = incl - my_active;   // active arcs of the tile before this lane's items
             {
                 int x = lx, y = ly;
 #pragma unroll
@@ -508,14 +508,12 @@ k_tile(TileArgs a)
                     if ((arcmask >> i) & 1u) {
                         if ((my_flags >> i) & 1u) {
                             const int k = a0 + y;
-                            a.tl_src[a0 + off] = (KIND == K_SAMPLE) ? (int32_t)item_v[i] : a.arc_src[k];
-                            if (a.tl_w) a.tl_w[a0 + off] = a.arc_w[k];
                             atomicOr(&s.bits[(k >> 5) - w0], 1u << (k & 31));
                             ++off;
                         }
                         ++y;
                     } else if ((endmask >> i) & 1u) {
-                        a.sp_ptr[r0 + x + 1] = (int32_t)off;   // tile-local; k_move adds the tile offset
+                        a.sp_ptr[r0 + x + 1] = (int32_t)off;   // tile-local; k_pack adds the tile offset
                         ++x;
                     }
                 }
