@@ -95,12 +95,16 @@ def run_list(source):
     return runs
 
 
-def params(gg, app, source, timing=True):
+def params(gg, app, source, timing=True, iters=None, theta=THETA):
+    """PageRank runs PR_ITERS iterations. The exact SSSP run goes to its fixed
+    point; the adaptive SSSP runs get the same number of iterations as the
+    exact one (the paper compares executions of equal iteration counts,
+    Sec. 5)."""
     flags = gg.GG_TIMING if timing else 0
     if app == "pagerank":
-        return gg.make_params(alpha=ALPHA, theta=THETA, max_iters=PR_ITERS, damping=DAMPING,
+        return gg.make_params(alpha=ALPHA, theta=theta, max_iters=iters or PR_ITERS, damping=DAMPING,
                               seed=SAMPLE_SEED, flags=flags)
-    return gg.make_params(alpha=ALPHA, theta=THETA, max_iters=MAX_ITERS_MIN, source=source,
+    return gg.make_params(alpha=ALPHA, theta=theta, max_iters=iters or MAX_ITERS_MIN, source=source,
                           seed=SAMPLE_SEED, flags=flags)
 
 
@@ -228,10 +232,14 @@ def bench_ours(a, rank, world, local):
         arcs = 0
         launches = gg.stats(h).kernels_load
         per = {"load_ms": gg.stats(h).ms_load}
+        sssp_iters = None
         try:
             for app, sigma, policy in runs:
-                gg.gg_run(h, app, sigma, policy, params(gg, app, source))
+                iters = sssp_iters if (app == "sssp" and policy != "exact") else None
+                gg.gg_run(h, app, sigma, policy, params(gg, app, source, iters=iters))
                 st = gg.stats(h)
+                if app == "sssp" and policy == "exact":
+                    sssp_iters = st.iterations
                 arcs += st.arcs_processed
                 launches += st.kernels_launched
                 if e2e:
@@ -324,6 +332,7 @@ def bench_ours(a, rank, world, local):
                                f"adaptive-correction PageRank/SSSP at sigma {list(SIGMAS)}",
                    "vertices": n, "arcs": m, "alpha": ALPHA, "theta": THETA,
                    "pagerank_iters": PR_ITERS, "damping": DAMPING, "sssp_source": source,
+                   "sssp_iters": "exact run to its fixed point; adaptive runs the same count",
                    "runs_per_step": len(runs), "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (268 MB of arcs + 268 MB of weights per load)"},
         "roofline": roof,
@@ -337,42 +346,76 @@ def bench_ours(a, rank, world, local):
 
 
 def accuracy_table(g, source, collected):
-    """Speedup (device time of the run) and accuracy (Sec. 4.2) of every
-    adaptive run of the last timed step against the exact run of the same
-    step; time to accuracy = the fastest configuration within 1 % error."""
+    """Time to accuracy (Sec. 4.2 metrics, target error <= 1 %): for the exact
+    run and for adaptive correction over sigma x theta, the fewest iterations T
+    whose result is within 1 % of the reference (the exact run at its full
+    iteration count) and the device time of that run; plus the accuracy of
+    every adaptive run of the timed step."""
     from paper_2104_10039_gb300 import gg, metrics
-    # values are recomputed per configuration (one run each, untimed)
     h = gg.gg_load_csr(g.n, g.m, g.rowptr, g.colidx, g.weights, gg.GG_DIRECTED)
+    target = 0.01
     try:
-        ref = {}
-        rows = []
-        for app, sigma, policy in run_list(source):
-            gg.gg_run(h, app, sigma, policy, params(gg, app, source, timing=False))
-            vals = gg.values(h, app)
-            ms = next(st.ms_run for a2, s2, p2, st, _ in collected
-                      if (a2, s2, p2) == (app, sigma, policy))
-            if policy == "exact":
-                ref[app] = (vals, ms)
-                continue
-            ev, ems = ref[app]
+        def run(app, sigma, policy, iters, theta=THETA):
+            gg.gg_run(h, app, sigma, policy, params(gg, app, source, timing=False, iters=iters, theta=theta))
+            return gg.values(h, app), gg.stats(h)
+
+        def error(app, vals, ref):
             if app == "pagerank":
-                err = metrics.top_k_error(vals, ev, 100)
-                extra = {}
-            else:
-                se = metrics.stretch_error(vals, ev, source)
-                err = se["error"]
-                extra = {"unreached": se["unreached"]}
-            rows.append({"app": app, "sigma": sigma, "ms": round(ms, 3), "exact_ms": round(ems, 3),
-                         "speedup": round(ems / ms, 3), "error": round(err, 5),
-                         "accuracy_pct": round(metrics.accuracy(err), 3), **extra})
+                return metrics.top_k_error(vals, ref, 100)
+            return metrics.stretch_error(vals, ref, source)["error"]
+
+        ref, full_iters = {}, {}
+        for app in ("pagerank", "sssp"):
+            v, st = run(app, 1.0, "exact", None)
+            ref[app], full_iters[app] = v, st.iterations
+        timed = []
+        for app, sigma, policy, st, _ in collected:
+            if policy == "exact":
+                continue
+            vals, _ = run(app, sigma, policy, full_iters[app])
+            err = error(app, vals, ref[app])
+            timed.append({"app": app, "sigma": sigma, "theta": THETA, "iters": st.iterations,
+                          "ms": round(st.ms_run, 3), "error": round(err, 5),
+                          "accuracy_pct": round(metrics.accuracy(err), 3)})
+
+        def first_within(app, sigma, policy, theta, t_max):
+            """Fewest iterations within the target: doubling, then bisection."""
+            memo = {}
+
+            def ok(t):
+                if t not in memo:
+                    vals, st = run(app, sigma, policy, t, theta)
+                    memo[t] = (error(app, vals, ref[app]) <= target, st.ms_run)
+                return memo[t][0]
+            lo, hi = 0, 1
+            while hi < t_max and not ok(hi):
+                lo, hi = hi, min(2 * hi, t_max)
+            if not ok(hi):
+                return None
+            while hi - lo > 1:
+                mid = (lo + hi) // 2
+                if ok(mid):
+                    hi = mid
+                else:
+                    lo = mid
+            return {"iters": hi, "ms": round(memo[hi][1], 3)}
+
+        tta = {}
+        for app in ("pagerank", "sssp"):
+            ex = first_within(app, 1.0, "exact", THETA, full_iters[app])
+            best = None
+            for theta in (0.05, 0.005):
+                for sigma in (0.3, 0.9):
+                    r = first_within(app, sigma, "adaptive", theta, 3 * full_iters[app])
+                    if r and (best is None or r["ms"] < best["ms"]):
+                        best = {"sigma": sigma, "theta": theta, **r}
+            if best and ex:
+                best["speedup_vs_exact"] = round(ex["ms"] / best["ms"], 3)
+            tta[app] = {"exact": ex, "adaptive_best": best}
     finally:
         gg.gg_free_graph(h)
-    best = {}
-    for app in ("pagerank", "sssp"):
-        ok = [r for r in rows if r["app"] == app and r["error"] <= 0.01]
-        best[app] = min(ok, key=lambda r: r["ms"]) if ok else None
-    return {"target_error": 0.01, "metric": {"pagerank": "top-100 error", "sssp": "mean stretch error"},
-            "runs": rows, "best": best}
+    return {"target_error": target, "metric": {"pagerank": "top-100 error", "sssp": "mean stretch error"},
+            "reference_iters": full_iters, "time_to_target": tta, "timed_runs": timed}
 
 
 # ------------------------------------------------------------- oracle (CPU) --

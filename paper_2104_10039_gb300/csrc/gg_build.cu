@@ -353,16 +353,38 @@ __global__ void k_csc_rowptr(const uint32_t *__restrict__ keys, long long m, int
     }
 }
 
+// CSC sources / weights from the sorted CSR positions, and the CSR -> CSC map.
+// Every access is random, so each thread keeps four arcs in flight.
 __global__ void k_csc_finalize(const uint32_t *__restrict__ vals, long long m, const int32_t *__restrict__ src_of,
                                const uint32_t *__restrict__ w_out, int32_t *__restrict__ in_src,
                                uint32_t *__restrict__ in_w, int32_t *__restrict__ out_to_in)
 {
+    constexpr int U = 4;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += stride) {
-        const uint32_t e = vals[k];
-        in_src[k] = src_of[e];
-        if (w_out) in_w[k] = w_out[e];
-        out_to_in[e] = (int32_t)k;
+    for (long long k0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; k0 < m; k0 += U * stride) {
+        uint32_t e[U];
+        int32_t sv[U];
+        uint32_t wv[U];
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+            const long long k = k0 + i * stride;
+            e[i] = k < m ? __ldcs(vals + k) : 0u;
+        }
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+            const long long k = k0 + i * stride;
+            sv[i] = k < m ? __ldg(src_of + e[i]) : 0;
+            wv[i] = (k < m && w_out) ? __ldg(w_out + e[i]) : 0u;
+        }
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+            const long long k = k0 + i * stride;
+            if (k < m) {
+                in_src[k] = sv[i];
+                if (w_out) in_w[k] = wv[i];
+                out_to_in[e[i]] = (int32_t)k;
+            }
+        }
     }
 }
 
