@@ -26,7 +26,7 @@ def gg():
 
 
 def _graphs():
-    gs = [graphgen.rmat(12, seed=1),                       # 4096 vertices, 65536 arcs, 34 tiles
+    gs = [graphgen.rmat(12, seed=1),                       # 4096 vertices, 65536 arcs, 272 tiles
           graphgen.rmat(9, edgefactor=5, seed=3),
           graphgen.erdos_renyi(3001, avg_degree=7, seed=2, symmetric=False),
           graphgen.from_arcs(7, [(0, 1), (0, 1), (1, 1), (2, 0), (6, 3), (3, 6), (5, 0)]),
