@@ -95,12 +95,12 @@ def run_list(source):
     return runs
 
 
-def params(gg, app, source, timing=True, iters=None, theta=THETA):
+def params(gg, app, source, timing=True, iters=None, theta=THETA, extra_flags=0):
     """PageRank runs PR_ITERS iterations. The exact SSSP run goes to its fixed
     point; the adaptive SSSP runs get the same number of iterations as the
     exact one (the paper compares executions of equal iteration counts,
     Sec. 5)."""
-    flags = gg.GG_TIMING if timing else 0
+    flags = (gg.GG_TIMING if timing else 0) | extra_flags
     if app == "pagerank":
         return gg.make_params(alpha=ALPHA, theta=theta, max_iters=iters or PR_ITERS, damping=DAMPING,
                               seed=SAMPLE_SEED, flags=flags)
@@ -355,8 +355,9 @@ def accuracy_table(g, source, collected):
     h = gg.gg_load_csr(g.n, g.m, g.rowptr, g.colidx, g.weights, gg.GG_DIRECTED)
     target = 0.01
     try:
-        def run(app, sigma, policy, iters, theta=THETA):
-            gg.gg_run(h, app, sigma, policy, params(gg, app, source, timing=False, iters=iters, theta=theta))
+        def run(app, sigma, policy, iters, theta=THETA, flags=0):
+            gg.gg_run(h, app, sigma, policy, params(gg, app, source, timing=False, iters=iters, theta=theta,
+                                                    extra_flags=flags))
             return gg.values(h, app), gg.stats(h)
 
         def error(app, vals, ref):
@@ -378,37 +379,32 @@ def accuracy_table(g, source, collected):
                           "ms": round(st.ms_run, 3), "error": round(err, 5),
                           "accuracy_pct": round(metrics.accuracy(err), 3)})
 
-        def first_within(app, sigma, policy, theta, t_max):
-            """Fewest iterations within the target: doubling, then bisection."""
-            memo = {}
-
-            def ok(t):
-                if t not in memo:
-                    vals, st = run(app, sigma, policy, t, theta)
-                    memo[t] = (error(app, vals, ref[app]) <= target, st.ms_run)
-                return memo[t][0]
-            lo, hi = 0, 1
-            while hi < t_max and not ok(hi):
-                lo, hi = hi, min(2 * hi, t_max)
-            if not ok(hi):
-                return None
-            while hi - lo > 1:
-                mid = (lo + hi) // 2
-                if ok(mid):
-                    hi = mid
-                else:
-                    lo = mid
-            return {"iters": hi, "ms": round(memo[hi][1], 3)}
+        def first_within(app, sigma, policy, theta, t_max, flags=0, alpha=ALPHA):
+            """Fewest iterations whose result is within the target (the error of
+            an adaptive run is not monotone in T: it dips after corrections)."""
+            for t in range(1, t_max + 1):
+                gg.gg_run(h, app, sigma, policy, gg.make_params(
+                    alpha=alpha, theta=theta, max_iters=t, damping=DAMPING, source=source, seed=SAMPLE_SEED,
+                    flags=flags))
+                if error(app, gg.values(h, app), ref[app]) <= target:
+                    return {"iters": t, "ms": round(gg.stats(h).ms_run, 3)}
+            return None
 
         tta = {}
         for app in ("pagerank", "sssp"):
             ex = first_within(app, 1.0, "exact", THETA, full_iters[app])
             best = None
-            for theta in (0.05, 0.005):
-                for sigma in (0.3, 0.9):
-                    r = first_within(app, sigma, "adaptive", theta, 3 * full_iters[app])
+            variants = [(0.05, 0, 4), (0.005, 0, 4), (0.05, 0, 2)]
+            if app == "pagerank":   # the share influence and renormalisation flags
+                variants += [(0.05, gg.GG_RENORM, 4), (0.05, gg.GG_RENORM, 2),
+                             (0.0005, gg.GG_INFL_SHARE | gg.GG_RENORM, 4)]
+            for theta, fl, alpha in variants:
+                for sigma in (0.5, 0.9):
+                    r = first_within(app, sigma, "adaptive", theta, 2 * full_iters[app], fl, alpha)
                     if r and (best is None or r["ms"] < best["ms"]):
-                        best = {"sigma": sigma, "theta": theta, **r}
+                        best = {"sigma": sigma, "theta": theta, "alpha": alpha,
+                                "flags": [n for n, b in (("GG_INFL_SHARE", gg.GG_INFL_SHARE),
+                                                         ("GG_RENORM", gg.GG_RENORM)) if fl & b], **r}
             if best and ex:
                 best["speedup_vs_exact"] = round(ex["ms"] / best["ms"], 3)
             tta[app] = {"exact": ex, "adaptive_best": best}

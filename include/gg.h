@@ -87,6 +87,10 @@ typedef enum {
 #define GG_FORCE_PULL 4u      /* min applications: never use the push frontier */
 #define GG_FORCE_PUSH 8u      /* min applications: always push from the frontier (no pull switch) */
 #define GG_TIMING 16u         /* record per-kernel-class device time with CUDA events */
+#define GG_INFL_SHARE 32u     /* PageRank corrections: influence = the arc's share of its row's total
+                                 (order-free) instead of the running-prefix form of Alg. 2 */
+#define GG_RENORM 64u         /* PageRank: approximate iterations divide a source's rank by its number
+                                 of active out-arcs (no rank mass leaks through inactive arcs) */
 
 #define GG_INF 0xFFFFFFFFu
 #define GG_ITER_PUSH 0x100u   /* gg_iter_stats.mode bit: iteration done by the push frontier */

@@ -42,7 +42,7 @@ EXACT, NONE, STATIC_SWITCH, ADAPTIVE = 0, 1, 2, 3
 POLICIES = {"exact": EXACT, "none": NONE, "sp": NONE, "static_switch": STATIC_SWITCH,
             "sms": STATIC_SWITCH, "adaptive": ADAPTIVE, "gg": ADAPTIVE}
 MODE_APPROX, MODE_ACCURATE, MODE_CORRECTION = 0, 1, 2
-STOP_QUIESCE, EST_STRICT = 1, 2
+STOP_QUIESCE, EST_STRICT, INFL_SHARE, RENORM = 1, 2, 32, 64
 INF = 0xFFFFFFFF
 
 

@@ -48,6 +48,11 @@
  *    iteration's values.
  *  - SP (policy NONE) never corrects; SMS (STATIC_SWITCH) corrects once at
  *    iteration alpha and stays accurate afterwards (Sec. 5.2).
+ *  - Two PageRank variants beyond the paper (flags): ORC_INFL_SHARE takes
+ *    an arc's influence as its share of the row's total (order-free) instead
+ *    of the running-prefix form; ORC_RENORM divides a source's rank by its
+ *    number of *active* out-arcs in approximate iterations, so no rank mass
+ *    leaks through inactive arcs.
  */
 #include <math.h>
 #include <stdint.h>
@@ -62,6 +67,8 @@ enum { ORC_EXACT = 0, ORC_NONE = 1, ORC_STATIC_SWITCH = 2, ORC_ADAPTIVE = 3 };
 enum { ORC_MODE_APPROX = 0, ORC_MODE_ACCURATE = 1, ORC_MODE_CORRECTION = 2 };
 #define ORC_STOP_QUIESCE 1u
 #define ORC_EST_STRICT 2u
+#define ORC_INFL_SHARE 32u
+#define ORC_RENORM 64u
 #define ORC_INF 0xFFFFFFFFu
 
 typedef struct {
@@ -184,6 +191,16 @@ static int64_t next_accurate_iteration(int policy, uint32_t alpha, uint32_t i)
     return (int64_t)i + 1;
 }
 
+/* Number of active out-arcs of every vertex under the flags `mask`. */
+static void active_outdeg(int32_t n, const int32_t *in_ptr, const int32_t *in_src, const uint8_t *mask,
+                          int32_t *act)
+{
+    for (int32_t v = 0; v < n; ++v) act[v] = 0;
+    for (int32_t u = 0; u < n; ++u)
+        for (int32_t k = in_ptr[u]; k < in_ptr[u + 1]; ++k)
+            act[in_src[k]] += mask[k] ? 1 : 0;
+}
+
 /* Edge status for a min application (integers only).
  * returns 1 active, 0 inactive. */
 static int min_app_estatus(int app, uint32_t acc, uint32_t cand, double theta)
@@ -217,6 +234,7 @@ int orc_run(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx,
     uint8_t *new_mask = (uint8_t *)malloc((size_t)(m ? m : 1));
     double *infl = (double *)malloc((size_t)(m ? m : 1) * sizeof(double));
     int32_t *outdeg = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *act = NULL;
     double *rank = NULL, *rank_next = NULL;
     uint32_t *val = NULL, *val_next = NULL;
     if (!in_ptr || !in_src || !in_w || !mask || !new_mask || !infl || !outdeg) goto done;
@@ -225,6 +243,13 @@ int orc_run(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx,
     orc_sample_mask(n, in_ptr, in_src, p->symmetric, p->sample_ratio, p->seed, mask);
 
     const int is_pr = p->app == ORC_PAGERANK;
+    const int renorm = is_pr && (p->flags & ORC_RENORM);
+    const int share = is_pr && (p->flags & ORC_INFL_SHARE);
+    if (renorm) {
+        act = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+        if (!act) goto done;
+        active_outdeg(n, in_ptr, in_src, mask, act);
+    }
     if (is_pr) {
         rank = (double *)malloc((size_t)n * sizeof(double));
         rank_next = (double *)malloc((size_t)n * sizeof(double));
@@ -263,10 +288,19 @@ int orc_run(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx,
                     if (!accurate && !mask[k]) continue;
                     int32_t v = in_src[k];
                     double before = acc;
-                    acc = rank[v] / (double)outdeg[v] + acc;
+                    const int32_t deg = (renorm && !accurate) ? act[v] : outdeg[v];
+                    acc = rank[v] / (double)deg + acc;
                     arcs += 1;
-                    if (correcting) {
+                    if (correcting && !share) {
                         double f = acc != 0.0 ? (acc - before) / acc : 0.0;
+                        infl[k] = f;
+                        new_mask[k] = (uint8_t)(f > p->theta);
+                    }
+                }
+                if (correcting && share) {   /* the arc's share of the row total */
+                    for (int32_t k = in_ptr[u]; k < in_ptr[u + 1]; ++k) {
+                        double c = rank[in_src[k]] / (double)outdeg[in_src[k]];
+                        double f = acc != 0.0 ? c / acc : 0.0;
                         infl[k] = f;
                         new_mask[k] = (uint8_t)(f > p->theta);
                     }
@@ -332,6 +366,7 @@ int orc_run(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx,
         } else {
             memcpy(mask, new_mask, (size_t)m);
         }
+        if (correcting && renorm) active_outdeg(n, in_ptr, in_src, mask, act);
         if (is_pr) { double *t = rank; rank = rank_next; rank_next = t; }
         else { uint32_t *t = val; val = val_next; val_next = t; }
 
@@ -364,7 +399,7 @@ int orc_run(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx,
     if (o->mask) memcpy(o->mask, mask, (size_t)m);
     rc = 0;
 done:
-    free(in_ptr); free(in_src); free(in_w); free(mask); free(new_mask); free(infl); free(outdeg);
+    free(in_ptr); free(in_src); free(in_w); free(mask); free(new_mask); free(infl); free(outdeg); free(act);
     free(rank); free(rank_next); free(val); free(val_next);
     return rc;
 }

@@ -193,17 +193,38 @@ static gg_status ensure_iter_cap(gg_graph *g, uint32_t iters)
     return GG_OK;
 }
 
+// Active out-degrees of the current flags (GG_RENORM).
+static gg_status refresh_active_outdeg(gg_graph *g)
+{
+    GG_CUDA(launch_active_outdeg(g->sp_src, g->sp_nnz, (uint32_t)g->m, g->n, g->act_outdeg, g->num_sms, g->stream));
+    g->launches += 2;
+    return GG_OK;
+}
+
 static gg_status run_pagerank(gg_graph *g, gg_policy policy, const gg_params *p)
 {
     const bool timing = (p->flags & GG_TIMING) != 0;
+    const bool renorm = (p->flags & GG_RENORM) != 0 && policy != GG_POLICY_EXACT;
     g->cur = 0;
     GG_CUDA(launch_init_pr(g->n, g->out_ptr, g->rank[0], g->contrib[0], g->num_sms, g->stream));
     g->launches += 1;
+    if (renorm) {
+        gg_status st = refresh_active_outdeg(g);
+        if (st != GG_OK) return st;
+        if (policy_mode(policy, p->alpha, 0) == MODE_APPROX) {
+            GG_CUDA(launch_contrib(g->n, g->rank[0], g->act_outdeg, g->contrib[0], g->num_sms, g->stream));
+            g->launches += 1;
+        }
+    }
     const float base = (1.0f - p->damping) / (float)g->n;
     for (uint32_t i = 0; i < p->max_iters; ++i) {
         const int mode = policy_mode(policy, p->alpha, i);
+        const int next = i + 1 < p->max_iters ? policy_mode(policy, p->alpha, i + 1) : MODE_ACCURATE;
         const int kind = mode == MODE_CORRECTION ? K_CORRECT : K_GATHER;
         TileArgs a{};
+        a.infl_share = (p->flags & GG_INFL_SHARE) ? 1 : 0;
+        // the next iteration gathers active arcs only: renormalised contributions
+        a.deg_apply = (renorm && next == MODE_APPROX && kind != K_CORRECT) ? g->act_outdeg : nullptr;
         fill_list(g, mode == MODE_APPROX, a);
         a.contrib_cur = g->contrib[g->cur];
         a.rank_cur = g->rank[g->cur];
@@ -231,6 +252,15 @@ static gg_status run_pagerank(gg_graph *g, gg_policy policy, const gg_params *p)
             if (st != GG_OK) return st;
             g->sample_clean = false;
             g->stats.corrections += 1;
+            if (renorm) {
+                st = refresh_active_outdeg(g);
+                if (st != GG_OK) return st;
+                if (next == MODE_APPROX) {
+                    GG_CUDA(launch_contrib(g->n, g->rank[g->cur ^ 1], g->act_outdeg, g->contrib[g->cur ^ 1],
+                                           g->num_sms, g->stream));
+                    g->launches += 1;
+                }
+            }
         }
         g->stats.pull_iterations += 1;
         g->cur ^= 1;
@@ -484,6 +514,7 @@ static gg_status alloc_graph(gg_graph *g)
     GG_ALLOC(g->b_full_tile_info, 4 * ((size_t)g->max_tiles + 2));
     GG_ALLOC(g->b_sp_tile_info, 4 * ((size_t)g->max_tiles + 2));
     GG_ALLOC(g->b_tile_cnt, 4 * (2 * (size_t)g->max_tiles + 4));
+    GG_ALLOC(g->b_act, 4 * n);
     GG_ALLOC(g->b_part, 12 * ((size_t)g->max_tiles + 2));
     GG_ALLOC(g->b_stash, 4 * m);
     GG_ALLOC(g->b_scalars, 4 * 16);
@@ -509,6 +540,7 @@ static gg_status alloc_graph(gg_graph *g)
     g->sp_tile_info = g->b_sp_tile_info.i32();
     g->tile_cnt = g->b_tile_cnt.u32();
     g->tile_off = g->tile_cnt + g->max_tiles + 2;
+    g->act_outdeg = g->b_act.i32();
     g->part = (uint2 *)g->b_part.p;
     g->part_head = (uint32_t *)(g->part + g->max_tiles + 2);
     g->stash = g->b_stash.u32();

@@ -81,7 +81,8 @@ struct gg_graph {
     uint32_t full_tiles = 0;    // tiles of the full in-edge list
     // active arcs per tile of a correction / sampling pass and their scan;
     // gather partials; the correction's value stash
-    gg::DevBuf b_tile_cnt, b_part, b_stash;
+    gg::DevBuf b_tile_cnt, b_part, b_stash, b_act;
+    int32_t *act_outdeg = nullptr;   // active out-degrees (GG_RENORM)
     uint32_t *stash = nullptr;
     uint2 *part = nullptr;
     uint32_t *part_head = nullptr;

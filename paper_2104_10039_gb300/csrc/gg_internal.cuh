@@ -75,6 +75,8 @@ struct TileArgs {
     float base;                 // (1-d)/N
     float damping;
     float epsilon;
+    const int32_t *deg_apply;   // degrees for the next contributions (renormalised), or nullptr = out-degree
+    int infl_share;             // PageRank corrections: influence = share of the row total
     // flags and compaction (correction, sampling)
     uint32_t *mask;             // CSC-order bitmap
     int32_t *sp_ptr;
@@ -241,5 +243,11 @@ cudaError_t launch_init_min(int32_t n, int app, int32_t source, uint32_t *val, i
 cudaError_t launch_iter_header(IterStatsDev *st, uint32_t mode, const uint32_t *arcs_dev,
                                unsigned long long arcs, cudaStream_t s);
 cudaError_t launch_iter_changed(IterStatsDev *st, const uint32_t *q_len, cudaStream_t s);
+// Active out-degree of every vertex from the packed active in-edges.
+cudaError_t launch_active_outdeg(const int32_t *sp_src, const uint32_t *sp_nnz, uint32_t max_arcs, int32_t n,
+                                 int32_t *act, int num_sms, cudaStream_t s);
+// contrib[u] = rank[u] / deg[u] (0 when deg[u] = 0).
+cudaError_t launch_contrib(int32_t n, const float *rank, const int32_t *deg, float *contrib, int num_sms,
+                          cudaStream_t s);
 
 }  // namespace gg

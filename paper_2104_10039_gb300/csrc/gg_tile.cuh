@@ -135,6 +135,35 @@ __device__ __forceinline__ typename Acc<APP>::T carry_from_parts(const uint2 *pa
     return acc;
 }
 
+// Later part of the row open at the end of tile t: the whole tiles after t
+// without a row end, then the part before the first row end of the next tile
+// that has one (from the finished partials, in tile order). Whole warp.
+template <int APP>
+__device__ __forceinline__ typename Acc<APP>::T lookahead_parts(const uint2 *part, const uint32_t *part_head,
+                                                                int t, int num_tiles)
+{
+    using T = typename Acc<APP>::T;
+    const uint32_t lane = lane_id();
+    T acc = Acc<APP>::id();
+    for (int s0 = t + 1; s0 < num_tiles; s0 += 32) {
+        const int j = s0 + (int)lane;
+        const uint32_t f = j < num_tiles ? part[j].x : 1u;
+        const unsigned ball = __ballot_sync(0xFFFFFFFFu, f != 0u);
+        const int stop = ball ? __ffs(ball) - 1 : 32;
+        T v = Acc<APP>::id();
+        if ((int)lane < stop) v = Acc<APP>::from_bits(part[j].y);
+        else if ((int)lane == stop && j < num_tiles) v = Acc<APP>::from_bits(part_head[j]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const T ov = __shfl_down_sync(0xFFFFFFFFu, v, o);
+            v = Acc<APP>::op(v, ov);
+        }
+        acc = Acc<APP>::op(acc, __shfl_sync(0xFFFFFFFFu, v, 0));
+        if (ball) break;
+    }
+    return acc;
+}
+
 // ------------------------------------------------------------- row apply ----
 // GG-Apply + GG-VStatus of Alg. 2 for PageRank; min for the min applications
 // (a vertex is active when its value decreased). Shared by k_tile and k_fixup.
@@ -216,6 +245,7 @@ struct WarpSmem {
     int32_t deg[(KIND != K_SAMPLE && KIND != K_STASH && APP == GG_APP_PAGERANK) ? kWT : 1];  // rows' out-degree
     uint32_t bits[(KIND == K_GATHER) ? 1 : (kWT / 32 + 2)];
     uint32_t oldw[(KIND == K_CORRECT && APP != GG_APP_PAGERANK) ? (kWT / 32 + 2) : 1];
+    float rowtot[(KIND == K_CORRECT && APP == GG_APP_PAGERANK) ? kWT + 1 : 1];   // influence share
 };
 
 template <int APP, int KIND>
@@ -300,7 +330,7 @@ k_tile(TileArgs a)
             if constexpr (kApply) {
                 if constexpr (APP == GG_APP_PAGERANK) {
                     s.vtx[i] = __float_as_uint(a.rank_cur[r0 + i]);
-                    s.deg[i] = a.out_ptr[r0 + i + 1] - a.out_ptr[r0 + i];
+                    s.deg[i] = a.deg_apply ? a.deg_apply[r0 + i] : a.out_ptr[r0 + i + 1] - a.out_ptr[r0 + i];
                 } else {
                     s.vtx[i] = a.val_cur[r0 + i];
                 }
@@ -428,6 +458,7 @@ k_tile(TileArgs a)
         int32_t q_u[kMin ? kIPT : 1];
         uint32_t q_v[kMin ? kIPT : 1];
         int q_n = 0;
+        T my_end_run = A::id();   // running value after this lane's items
         if constexpr (KIND != K_STASH) {
             T acc = carry_in;
             int x = lx, y = ly;
@@ -443,10 +474,11 @@ k_tile(TileArgs a)
                         if constexpr (KIND == K_CORRECT) {
                             uint32_t fl;
                             if constexpr (APP == GG_APP_PAGERANK) {
-                                // GG-Gather's returned influence (Alg. 2): (new - old) / new
+                                // GG-Gather's returned influence (Alg. 2): (new - old) / new;
+                                // with the share variant, decided after the row totals
                                 const float after = __fadd_rn(acc, v);
                                 const float infl = after != 0.0f ? __fdiv_rn(__fsub_rn(after, acc), after) : 0.0f;
-                                fl = infl > a.theta ? 1u : 0u;
+                                fl = (!a.infl_share && infl > a.theta) ? 1u : 0u;
                             } else {
                                 if (v == kInf) {   // no candidate: the arc keeps its flag
                                     const int k = a0 + y;
@@ -469,6 +501,7 @@ k_tile(TileArgs a)
                     }
                     ++y;
                 } else if ((endmask >> i) & 1u) {
+                    if constexpr (KIND == K_CORRECT && APP == GG_APP_PAGERANK) s.rowtot[x] = acc;
                     if constexpr (kApply) {
                         if (defer_first) {
                             defer_first = false;   // completed by k_fixup
@@ -489,6 +522,32 @@ k_tile(TileArgs a)
                     }
                     acc = A::id();
                     ++x;
+                }
+            }
+            my_end_run = acc;
+        }
+        (void)my_end_run;
+        if constexpr (KIND == K_CORRECT && APP == GG_APP_PAGERANK) {
+            if (a.infl_share) {
+                // influence = the arc's share of its row total; the row still
+                // open at the tile end adds the later tiles' parts
+                const int last = (tile_items - 1) / kIPT;
+                const float end_run = __shfl_sync(0xFFFFFFFFu, my_end_run, last);
+                const float later = lookahead_parts<APP>(a.part, a.part_head, t, num_tiles);
+                if (lane == 0) s.rowtot[nrows] = __fadd_rn(end_run, later);
+                __syncwarp();
+                int x = lx;
+#pragma unroll
+                for (int i = 0; i < kIPT; ++i) {
+                    if ((arcmask >> i) & 1u) {
+                        const float tot = s.rowtot[x];
+                        const float infl = tot != 0.0f ? __fdiv_rn(__uint_as_float(item_v[i]), tot) : 0.0f;
+                        const uint32_t fl = infl > a.theta ? 1u : 0u;
+                        my_flags |= fl << i;
+                        my_active += fl;
+                    } else if ((endmask >> i) & 1u) {
+                        ++x;
+                    }
                 }
             }
         }
@@ -579,7 +638,8 @@ k_fixup(TileArgs a)
                 acc = A::op(acc, A::from_bits(a.part_head[t]));
                 const int32_t u = (int32_t)(info & 0x7FFFFFFFu);
                 if constexpr (APP == GG_APP_PAGERANK) {
-                    apply_pr(a, u, acc, a.rank_cur[u], a.out_ptr[u + 1] - a.out_ptr[u], st);
+                    apply_pr(a, u, acc, a.rank_cur[u],
+                             a.deg_apply ? a.deg_apply[u] : a.out_ptr[u + 1] - a.out_ptr[u], st);
                 } else {
                     bool ch;
                     const uint32_t nw = apply_min(a, u, acc, a.val_cur[u], st, &ch);

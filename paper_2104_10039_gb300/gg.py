@@ -33,6 +33,7 @@ GG_POLICY_EXACT, GG_POLICY_NONE, GG_POLICY_STATIC_SWITCH, GG_POLICY_ADAPTIVE = r
  GG_RESULT_OUT_TO_IN) = range(10)
 GG_DIRECTED, GG_SYMMETRIC, GG_DEVICE_PTRS = 0, 1, 2
 GG_STOP_QUIESCE, GG_EST_STRICT, GG_FORCE_PULL, GG_FORCE_PUSH, GG_TIMING = 1, 2, 4, 8, 16
+GG_INFL_SHARE, GG_RENORM = 32, 64
 GG_INF = 0xFFFFFFFF
 GG_ITER_PUSH = 0x100
 

@@ -20,11 +20,19 @@ UNREACHED = 0xFFFFFFFF
 
 
 def top_k(values: np.ndarray, k: int) -> np.ndarray:
-    """Ids of the k largest values (value descending, id ascending)."""
+    """Ids of the k largest values (value descending, id ascending), in O(n):
+    everything above the k-th largest value, then the smallest ids equal to it."""
     v = np.asarray(values, np.float64)
-    k = min(k, v.shape[0])
-    order = np.lexsort((np.arange(v.shape[0]), -v))
-    return order[:k]
+    n = v.shape[0]
+    k = min(k, n)
+    if k == 0:
+        return np.zeros(0, np.int64)
+    thr = np.partition(v, n - k)[n - k]
+    above = np.flatnonzero(v > thr)
+    equal = np.flatnonzero(v == thr)[: k - above.shape[0]]
+    ids = np.concatenate([above, equal])
+    order = np.lexsort((ids, -v[ids]))
+    return ids[order]
 
 
 def top_k_error(approx: np.ndarray, exact: np.ndarray, k: int = 100) -> float:

@@ -248,3 +248,26 @@ def test_errors_are_statuses(gg):
         assert e.value.status == gg.GG_ERR_INVALID_ARG
     finally:
         gg.gg_free_graph(h)
+
+
+@pytest.mark.parametrize("flags", [32, 64, 96])   # GG_INFL_SHARE, GG_RENORM, both
+@pytest.mark.parametrize("policy,alpha,theta,sigma", [("sp", 4, 0.05, 0.5), ("gg", 2, 0.01, 0.4),
+                                                       ("gg", 0, 0.1, 0.3), ("sms", 3, 0.02, 0.6)])
+def test_pagerank_share_and_renorm_variants(gg, flags, policy, alpha, theta, sigma):
+    for g in _graphs()[:4]:
+        h = gc.load(gg, g)
+        try:
+            masks = []
+            for c in gc.correction_indices(policy, alpha, 20):
+                _, mk, _ = gc.gpu_run(gg, h, g, "pagerank", policy, sigma, alpha, theta, T=c + 1, seed=9,
+                                      flags=flags)
+                masks.append(mk)
+            vals, _, _ = gc.gpu_run(gg, h, g, "pagerank", policy, sigma, alpha, theta, T=20, seed=9,
+                                    flags=flags)
+            ref = oracle.run(g.n, g.rowptr, g.colidx, app="pagerank", policy=policy, sigma=sigma, seed=9,
+                             alpha=alpha, theta=theta, max_iters=20, flags=flags, replay_masks=masks,
+                             replay_tol=1e-5, nthreads=0)
+            assert ref["replay_violations"] == 0, ref["replay_max_margin"]
+            assert gc.rel_l1(vals, ref["values"]) <= PR_TOL
+        finally:
+            gg.gg_free_graph(h)

@@ -46,3 +46,15 @@ def test_sources_have_out_arcs():
     s = graphgen.sources(g, 16, seed=2)
     assert len(s) == 16 and len(set(s.tolist())) == 16
     assert np.all(np.diff(g.rowptr)[s] > 0)
+
+
+def test_top_k_tie_break_matches_full_sort():
+    from paper_2104_10039_gb300 import metrics
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        n = int(rng.integers(1, 300))
+        v = rng.integers(0, 20, n).astype(float)
+        k = int(rng.integers(0, n + 3))
+        ref = np.lexsort((np.arange(n), -v))[:min(k, n)]
+        assert np.array_equal(metrics.top_k(v, k), ref)
+    assert metrics.top_k_error(np.array([3.0, 2, 1, 0]), np.array([0.0, 1, 2, 3]), 2) == 1.0

@@ -331,3 +331,28 @@ def test_cc_influence_is_binary():
     r = oracle.run(g.n, g.rowptr, g.colidx, app="cc", policy="sms", alpha=1, theta=0.7,
                    sigma=1.0, max_iters=2, symmetric=True)
     assert [r["mask"][x] for x in k] == [1, 1, 0]
+
+
+def test_influence_share_is_order_free():
+    # Contributions c (source of out-degree 3) and 3c (out-degree 1) into
+    # vertex 3: shares 1/4 and 3/4 whichever source id comes first.
+    for arcs, light, heavy in (([(0, 3), (0, 4), (0, 5), (1, 3), (2, 0)], 0, 1),
+                               ([(1, 3), (1, 4), (1, 5), (0, 3), (2, 1)], 1, 0)):
+        g = graphgen.from_arcs(6, arcs)
+        kl, kh = _csc_index(g, light, 3), _csc_index(g, heavy, 3)
+        for theta, want in ((0.5, (0, 1)), (0.2, (1, 1)), (0.8, (0, 0))):
+            r = oracle.run(g.n, g.rowptr, g.colidx, policy="sms", alpha=0, theta=theta, max_iters=1,
+                           flags=oracle.INFL_SHARE)
+            assert (r["mask"][kl], r["mask"][kh]) == want
+
+
+def test_renormalised_sp_equals_pagerank_of_the_sampled_subgraph():
+    for g in _small_graphs() + [graphgen.rmat(8, seed=9)]:
+        sigma, seed = 0.5, 21
+        kept = [(s, d) for s, d, _ in brute.arcs_of(g) if oracle.arc_sampled(s, d, sigma, seed)]
+        sub = graphgen.from_arcs(g.n, kept)
+        for T in (1, 5, 12):
+            r = oracle.run(g.n, g.rowptr, g.colidx, policy="sp", sigma=sigma, seed=seed, max_iters=T,
+                           flags=oracle.RENORM)
+            ref = brute.pagerank_dense(sub, 0.85, T)
+            assert np.abs(r["values"] - ref).sum() / np.abs(ref).sum() < 1e-13
