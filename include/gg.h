@@ -58,8 +58,15 @@ typedef enum {
     GG_POLICY_NONE = 1,           /* SP: sparsify with sigma, never correct (Sec. 5.2) */
     GG_POLICY_STATIC_SWITCH = 2,  /* SMS: approximate for alpha iterations, one correction,
                                      then accurate to the end (Sec. 5.2) */
-    GG_POLICY_ADAPTIVE = 3        /* GG: a correction after every alpha approximate
+    GG_POLICY_ADAPTIVE = 3,       /* GG: a correction after every alpha approximate
                                      iterations (Sec. 3.4) */
+    GG_POLICY_TRIGGERED = 4       /* beyond the paper (which notes the correction points could
+                                     vary, Sec. 3.4): a correction follows the approximate
+                                     iteration whose change statistic is at most trigger_ratio
+                                     times that of the first approximate iteration since the last
+                                     correction, or the alpha-th one. Statistic: vertices changed
+                                     (SSSP/BFS/CC, exact) or sum |old-new| (PageRank, the
+                                     fixed-point sum of gg_iter_stats.sum_delta) */
 } gg_policy;
 
 typedef enum {
@@ -104,6 +111,8 @@ typedef struct {
     int32_t source;       /* SSSP / BFS source vertex */
     uint64_t seed;        /* sampling seed (Sec. 3.4) */
     uint32_t flags;       /* GG_* flags above */
+    float trigger_ratio;  /* GG_POLICY_TRIGGERED: fraction of the window's first change statistic
+                             at or below which a correction follows; finite, >= 0 */
 } gg_params;
 
 typedef struct {

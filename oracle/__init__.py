@@ -38,9 +38,9 @@ _lib = None
 
 PAGERANK, SSSP, BFS, CC = 0, 1, 2, 3
 APPS = {"pagerank": PAGERANK, "pr": PAGERANK, "sssp": SSSP, "bfs": BFS, "cc": CC}
-EXACT, NONE, STATIC_SWITCH, ADAPTIVE = 0, 1, 2, 3
+EXACT, NONE, STATIC_SWITCH, ADAPTIVE, TRIGGERED = 0, 1, 2, 3, 4
 POLICIES = {"exact": EXACT, "none": NONE, "sp": NONE, "static_switch": STATIC_SWITCH,
-            "sms": STATIC_SWITCH, "adaptive": ADAPTIVE, "gg": ADAPTIVE}
+            "sms": STATIC_SWITCH, "adaptive": ADAPTIVE, "gg": ADAPTIVE, "triggered": TRIGGERED}
 MODE_APPROX, MODE_ACCURATE, MODE_CORRECTION = 0, 1, 2
 STOP_QUIESCE, EST_STRICT, INFL_SHARE, RENORM = 1, 2, 32, 64
 INF = 0xFFFFFFFF
@@ -55,7 +55,8 @@ class _Params(ctypes.Structure):
                 ("flags", ctypes.c_uint32), ("symmetric", ctypes.c_int32),
                 ("nthreads", ctypes.c_int32),
                 ("replay_masks", ctypes.POINTER(ctypes.c_uint8)),
-                ("n_replay", ctypes.c_int32), ("replay_tol", ctypes.c_double)]
+                ("n_replay", ctypes.c_int32), ("replay_tol", ctypes.c_double),
+                ("trigger_ratio", ctypes.c_double), ("replay_modes", ctypes.POINTER(ctypes.c_int8))]
 
 
 class _Out(ctypes.Structure):
@@ -65,6 +66,7 @@ class _Out(ctypes.Structure):
                 ("iter_arcs", ctypes.POINTER(ctypes.c_int64)),
                 ("iter_mode", ctypes.POINTER(ctypes.c_int32)),
                 ("iter_changed", ctypes.POINTER(ctypes.c_int64)),
+                ("iter_sum_delta", ctypes.POINTER(ctypes.c_double)),
                 ("iterations", ctypes.c_int32), ("corrections", ctypes.c_int32),
                 ("replay_mismatch", ctypes.c_int64), ("replay_max_margin", ctypes.c_double),
                 ("replay_violations", ctypes.c_int64)]
@@ -163,13 +165,20 @@ def iteration_mode(policy, alpha: int, i: int) -> int:
 
 def run(n, rowptr, colidx, weights=None, *, app="pagerank", policy="exact", sigma=1.0,
         seed=0, alpha=4, theta=0.05, max_iters=20, damping=0.85, epsilon=0.0, source=0,
-        flags=0, symmetric=False, nthreads=1, replay_masks=None, replay_tol=1e-5):
+        flags=0, symmetric=False, nthreads=1, replay_masks=None, replay_tol=1e-5,
+        trigger_ratio=0.5, replay_modes=None):
     """Run one GraphGuess execution on the CPU; returns a dict with ``values``
     (float64 for PageRank, uint32 otherwise), the final CSC-order ``mask`` and
     per-iteration statistics. ``damping`` and ``theta`` are given as the float32
     values the CUDA library receives. ``replay_masks`` (list of uint8[m] CSC
     masks, one per correction) makes the run adopt those flags after checking
-    that every decision it disagrees with lies within ``replay_tol`` of theta."""
+    that every decision it disagrees with lies within ``replay_tol`` of theta.
+    ``policy="triggered"`` corrects after the approximate iteration whose change
+    statistic (changed vertices; sum |old-new| for PageRank) is at most
+    ``trigger_ratio`` times the window's first, or after ``alpha`` approximate
+    iterations. ``replay_modes`` (int per iteration, MODE_*) makes the run
+    follow the given modes instead of its policy's (iterations past the given
+    ones are approximate)."""
     a = APPS[app] if isinstance(app, str) else int(app)
     pol = POLICIES[policy] if isinstance(policy, str) else int(policy)
     rowptr = np.ascontiguousarray(rowptr, np.int32)
@@ -181,10 +190,15 @@ def run(n, rowptr, colidx, weights=None, *, app="pagerank", policy="exact", sigm
     if replay_masks is not None and len(replay_masks):
         rep = np.ascontiguousarray(np.stack([np.asarray(x, np.uint8) for x in replay_masks]))
         n_rep = rep.shape[0]
+    modes = None
+    if replay_modes is not None:
+        modes = np.full(max(max_iters, 1), 0, np.int8)
+        modes[:len(replay_modes)] = np.asarray(replay_modes, np.int8)
     prm = _Params(a, pol, float(sigma), seed & 0xFFFFFFFFFFFFFFFF, alpha,
                   float(np.float32(theta)), max_iters, float(np.float32(damping)),
                   float(np.float32(epsilon)), source, flags, int(symmetric), nthreads,
-                  _p(rep, ctypes.c_uint8), n_rep, replay_tol)
+                  _p(rep, ctypes.c_uint8), n_rep, replay_tol, float(np.float32(trigger_ratio)),
+                  _p(modes, ctypes.c_int8))
     T = max(max_iters, 1)
     pr = np.empty(n, np.float64) if a == PAGERANK else None
     iv = np.empty(n, np.uint32) if a != PAGERANK else None
@@ -192,9 +206,10 @@ def run(n, rowptr, colidx, weights=None, *, app="pagerank", policy="exact", sigm
     it_arcs = np.zeros(T, np.int64)
     it_mode = np.full(T, -1, np.int32)
     it_changed = np.zeros(T, np.int64)
+    it_sum = np.zeros(T, np.float64)
     out = _Out(_p(pr, ctypes.c_double), _p(iv, ctypes.c_uint32), _p(mask, ctypes.c_uint8),
                _p(it_arcs, ctypes.c_int64), _p(it_mode, ctypes.c_int32),
-               _p(it_changed, ctypes.c_int64), 0, 0, 0, 0.0, 0)
+               _p(it_changed, ctypes.c_int64), _p(it_sum, ctypes.c_double), 0, 0, 0, 0.0, 0)
     rc = _load().orc_run(n, m, _p(rowptr, ctypes.c_int32), _p(colidx, ctypes.c_int32),
                          _p(w, ctypes.c_uint32), ctypes.byref(prm), ctypes.byref(out))
     if rc != 0:
@@ -208,6 +223,7 @@ def run(n, rowptr, colidx, weights=None, *, app="pagerank", policy="exact", sigm
         "iter_arcs": it_arcs[:it],
         "iter_mode": it_mode[:it],
         "iter_changed": it_changed[:it],
+        "iter_sum_delta": it_sum[:it],
         "replay_mismatch": out.replay_mismatch,
         "replay_max_margin": out.replay_max_margin,
         "replay_violations": out.replay_violations,

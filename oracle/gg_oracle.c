@@ -48,6 +48,12 @@
  *    iteration's values.
  *  - SP (policy NONE) never corrects; SMS (STATIC_SWITCH) corrects once at
  *    iteration alpha and stays accurate afterwards (Sec. 5.2).
+ *  - ORC_TRIGGERED (beyond the paper, which notes the correction points
+ *    could vary, Sec. 3.4): a correction follows the approximate iteration
+ *    whose change statistic (vertices that changed for the min
+ *    applications, sum |old-new| for PageRank) is at most trigger_ratio times
+ *    that of the window's first approximate iteration, or the alpha-th
+ *    approximate iteration of the window.
  *  - Two PageRank variants beyond the paper (flags): ORC_INFL_SHARE takes
  *    an arc's influence as its share of the row's total (order-free) instead
  *    of the running-prefix form; ORC_RENORM divides a source's rank by its
@@ -63,7 +69,7 @@
 #endif
 
 enum { ORC_PAGERANK = 0, ORC_SSSP = 1, ORC_BFS = 2, ORC_CC = 3 };
-enum { ORC_EXACT = 0, ORC_NONE = 1, ORC_STATIC_SWITCH = 2, ORC_ADAPTIVE = 3 };
+enum { ORC_EXACT = 0, ORC_NONE = 1, ORC_STATIC_SWITCH = 2, ORC_ADAPTIVE = 3, ORC_TRIGGERED = 4 };
 enum { ORC_MODE_APPROX = 0, ORC_MODE_ACCURATE = 1, ORC_MODE_CORRECTION = 2 };
 #define ORC_STOP_QUIESCE 1u
 #define ORC_EST_STRICT 2u
@@ -87,6 +93,8 @@ typedef struct {
     const uint8_t *replay_masks; /* n_replay x m bytes in CSC order, or NULL */
     int32_t n_replay;
     double replay_tol;
+    double trigger_ratio;        /* ORC_TRIGGERED: correct when the window's change falls to this fraction */
+    const int8_t *replay_modes;  /* per iteration ORC_MODE_* to follow instead of the trigger, or NULL */
 } orc_params;
 
 typedef struct {
@@ -96,6 +104,7 @@ typedef struct {
     int64_t *iter_arcs;          /* max_iters: arcs in each iteration's edge set */
     int32_t *iter_mode;          /* max_iters: ORC_MODE_* (-1 = skipped) */
     int64_t *iter_changed;       /* max_iters: vertices active after VStatus */
+    double *iter_sum_delta;      /* max_iters: sum |old-new| over vertices (nullable) */
     int32_t iterations;          /* iterations counted (skipped no-ops included) */
     int32_t corrections;
     int64_t replay_mismatch;
@@ -188,7 +197,7 @@ static int64_t next_accurate_iteration(int policy, uint32_t alpha, uint32_t i)
         uint64_t period = (uint64_t)alpha + 1u;
         return (int64_t)(((uint64_t)i / period) * period + alpha);
     }
-    return (int64_t)i + 1;
+    return (int64_t)i + 1;   /* EXACT, and TRIGGERED (a quiet window triggers at once) */
 }
 
 /* Number of active out-arcs of every vertex under the flags `mask`. */
@@ -271,16 +280,23 @@ int orc_run(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx,
     const double d = p->damping;
     const double base = (1.0 - d) / (double)n;
     int32_t replay_next = 0;
+    int trig_next = p->policy == ORC_TRIGGERED && p->alpha == 0;   /* correction comes next */
+    uint32_t window = 0;
+    double window_first = 0.0;
 
     for (uint32_t i = 0; i < p->max_iters; ++i) {
-        const int mode = orc_iteration_mode(p->policy, p->alpha, i);
-        if (mode < 0) goto done;
+        int mode;
+        if (p->replay_modes) mode = p->replay_modes[i];
+        else if (p->policy == ORC_TRIGGERED) mode = trig_next ? ORC_MODE_CORRECTION : ORC_MODE_APPROX;
+        else mode = orc_iteration_mode(p->policy, p->alpha, i);
+        if (mode < 0 || mode > ORC_MODE_CORRECTION) goto done;
+        double sum_delta = 0.0;
         const int accurate = mode != ORC_MODE_APPROX;
         const int correcting = mode == ORC_MODE_CORRECTION;
         int64_t arcs = 0, changed = 0;
 
         /* Gather (GG-Gather over in-edges, Alg. 1 / Alg. 2), Apply, VStatus */
-#pragma omp parallel for schedule(dynamic, 256) reduction(+ : arcs, changed)
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : arcs, changed, sum_delta)
         for (int32_t u = 0; u < n; ++u) {
             if (is_pr) {
                 double acc = 0.0;
@@ -309,6 +325,7 @@ int orc_run(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx,
                 double nw = base + d * acc;
                 rank_next[u] = nw;
                 changed += fabs(old - nw) > p->epsilon;
+                sum_delta += fabs(old - nw);
             } else {
                 uint32_t acc = ORC_INF;
                 for (int32_t k = in_ptr[u]; k < in_ptr[u + 1]; ++k) {
@@ -373,8 +390,20 @@ int orc_run(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx,
         if (o->iter_arcs) o->iter_arcs[i] = arcs;
         if (o->iter_mode) o->iter_mode[i] = mode;
         if (o->iter_changed) o->iter_changed[i] = changed;
+        if (o->iter_sum_delta) o->iter_sum_delta[i] = sum_delta;
         o->iterations = (int32_t)i + 1;
         o->corrections += correcting;
+        if (p->policy == ORC_TRIGGERED) {
+            if (correcting) {
+                window = 0;
+                trig_next = p->alpha == 0;
+            } else {
+                const double metric = is_pr ? sum_delta : (double)changed;
+                window += 1;
+                if (window == 1) window_first = metric;
+                trig_next = window >= p->alpha || metric <= p->trigger_ratio * window_first;
+            }
+        }
 
         int stop_on_quiet = !is_pr || (p->flags & ORC_STOP_QUIESCE);
         if (stop_on_quiet && changed == 0) {
@@ -388,6 +417,7 @@ int orc_run(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx,
                 if (o->iter_arcs) o->iter_arcs[j] = 0;
                 if (o->iter_mode) o->iter_mode[j] = -1;
                 if (o->iter_changed) o->iter_changed[j] = 0;
+                if (o->iter_sum_delta) o->iter_sum_delta[j] = 0.0;
                 o->iterations = (int32_t)j + 1;
             }
             if ((uint64_t)nxt >= p->max_iters) break;

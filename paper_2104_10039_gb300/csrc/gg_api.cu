@@ -81,6 +81,52 @@ static int64_t next_accurate(gg_policy p, uint32_t alpha, uint32_t i)
     return (int64_t)i + 1;
 }
 
+// GG_POLICY_TRIGGERED: a window starts at the run's start and after every
+// correction; a correction follows the approximate iteration whose change
+// statistic is at most ratio x that of the window's first approximate
+// iteration, or the alpha-th approximate iteration of the window.
+struct Trigger {
+    bool on = false;
+    uint32_t alpha = 0;
+    double ratio = 0.0;
+    bool correct_next = false;
+    uint32_t window = 0;
+    double first = 0.0;
+
+    Trigger(gg_policy p, const gg_params *prm)
+    {
+        on = p == GG_POLICY_TRIGGERED;
+        alpha = prm->alpha;
+        ratio = (double)prm->trigger_ratio;
+        correct_next = on && alpha == 0;
+    }
+    int mode(gg_policy p, uint32_t i) const
+    {
+        if (!on) return policy_mode(p, alpha, i);
+        return correct_next ? MODE_CORRECTION : MODE_APPROX;
+    }
+    // The mode iteration i+1 gets if iteration i (of mode `cur`) does not
+    // trigger a correction by its statistic.
+    int next_unless_triggered(gg_policy p, uint32_t i, int cur) const
+    {
+        if (!on) return policy_mode(p, alpha, i + 1);
+        if (cur == MODE_CORRECTION) return alpha == 0 ? MODE_CORRECTION : MODE_APPROX;
+        return window + 1 >= alpha ? MODE_CORRECTION : MODE_APPROX;
+    }
+    void after(bool correcting, double metric)
+    {
+        if (!on) return;
+        if (correcting) {
+            window = 0;
+            correct_next = alpha == 0;
+            return;
+        }
+        window += 1;
+        if (window == 1) first = metric;
+        correct_next = window >= alpha || metric <= ratio * first;
+    }
+};
+
 uint32_t next_epoch(gg_graph *g)
 {
     if (g->epoch >= (1u << 30)) {
@@ -205,21 +251,23 @@ static gg_status run_pagerank(gg_graph *g, gg_policy policy, const gg_params *p)
 {
     const bool timing = (p->flags & GG_TIMING) != 0;
     const bool renorm = (p->flags & GG_RENORM) != 0 && policy != GG_POLICY_EXACT;
+    Trigger trig(policy, p);
     g->cur = 0;
     GG_CUDA(launch_init_pr(g->n, g->out_ptr, g->rank[0], g->contrib[0], g->num_sms, g->stream));
     g->launches += 1;
     if (renorm) {
         gg_status st = refresh_active_outdeg(g);
         if (st != GG_OK) return st;
-        if (policy_mode(policy, p->alpha, 0) == MODE_APPROX) {
-            GG_CUDA(launch_contrib(g->n, g->rank[0], g->act_outdeg, g->contrib[0], g->num_sms, g->stream));
+        if (trig.mode(policy, 0) == MODE_APPROX) {
+            GG_CUDA(launch_contrib(g->n, g->rank[0], g->act_outdeg, nullptr, g->contrib[0], g->num_sms,
+                                   g->stream));
             g->launches += 1;
         }
     }
     const float base = (1.0f - p->damping) / (float)g->n;
     for (uint32_t i = 0; i < p->max_iters; ++i) {
-        const int mode = policy_mode(policy, p->alpha, i);
-        const int next = i + 1 < p->max_iters ? policy_mode(policy, p->alpha, i + 1) : MODE_ACCURATE;
+        const int mode = trig.mode(policy, i);
+        const int next = i + 1 < p->max_iters ? trig.next_unless_triggered(policy, i, mode) : MODE_ACCURATE;
         const int kind = mode == MODE_CORRECTION ? K_CORRECT : K_GATHER;
         TileArgs a{};
         a.infl_share = (p->flags & GG_INFL_SHARE) ? 1 : 0;
@@ -256,8 +304,8 @@ static gg_status run_pagerank(gg_graph *g, gg_policy policy, const gg_params *p)
                 st = refresh_active_outdeg(g);
                 if (st != GG_OK) return st;
                 if (next == MODE_APPROX) {
-                    GG_CUDA(launch_contrib(g->n, g->rank[g->cur ^ 1], g->act_outdeg, g->contrib[g->cur ^ 1],
-                                           g->num_sms, g->stream));
+                    GG_CUDA(launch_contrib(g->n, g->rank[g->cur ^ 1], g->act_outdeg, nullptr,
+                                           g->contrib[g->cur ^ 1], g->num_sms, g->stream));
                     g->launches += 1;
                 }
             }
@@ -265,6 +313,24 @@ static gg_status run_pagerank(gg_graph *g, gg_policy policy, const gg_params *p)
         g->stats.pull_iterations += 1;
         g->cur ^= 1;
         g->iterations = i + 1;
+        if (trig.on) {
+            double metric = 0.0;
+            if (mode == MODE_APPROX) {
+                unsigned long long sd = 0;
+                GG_CUDA(cudaMemcpyAsync(&sd, &g->iter_stats[i].sum_delta, sizeof sd, cudaMemcpyDeviceToHost,
+                                        g->stream));
+                GG_CUDA(cudaStreamSynchronize(g->stream));
+                metric = (double)sd;
+            }
+            trig.after(mode == MODE_CORRECTION, metric);
+            if (renorm && next == MODE_APPROX && trig.correct_next && i + 1 < p->max_iters) {
+                // contributions were divided by active out-degrees for an
+                // approximate iteration; the correction needs full degrees
+                GG_CUDA(launch_contrib(g->n, g->rank[g->cur], nullptr, g->out_ptr, g->contrib[g->cur],
+                                       g->num_sms, g->stream));
+                g->launches += 1;
+            }
+        }
         if ((p->flags & GG_STOP_QUIESCE) && mode != MODE_APPROX) {
             unsigned long long changed = 0;
             GG_CUDA(cudaMemcpyAsync(&changed, &g->iter_stats[i].changed, sizeof changed, cudaMemcpyDeviceToHost,
@@ -321,8 +387,9 @@ static gg_status run_min(gg_graph *g, gg_app app, gg_policy policy, const gg_par
     else if (th >= 1.0) theta_case = 2;
     else theta_fx = (unsigned long long)std::floor(th * 4294967296.0);
 
+    Trigger trig(policy, p);
     for (uint32_t i = 0; i < p->max_iters; ++i) {
-        const int mode = policy_mode(policy, p->alpha, i);
+        const int mode = trig.mode(policy, i);
         const int nq = qc ^ 1;
         GG_CUDA(cudaMemsetAsync(&g->q_len[nq], 0, sizeof(uint32_t), g->stream));
         const uint64_t list_nnz = mode == MODE_APPROX ? g->sp_nnz_host : (uint64_t)g->m;
@@ -404,6 +471,7 @@ static gg_status run_min(gg_graph *g, gg_app app, gg_policy policy, const gg_par
         st = read_u32(g, &g->q_len[qc], &qlen);
         if (st != GG_OK) return st;
         g->iterations = i + 1;
+        trig.after(mode == MODE_CORRECTION, (double)qlen);
         if (qlen == 0) {
             // Quiet iteration: an accurate one means a fixed point of the full
             // graph; an approximate one makes every approximate iteration up to
@@ -438,7 +506,11 @@ gg_status run(gg_graph *g, gg_app app, double ratio, gg_policy policy, const gg_
 {
     if (!p) { set_error("gg_run: params is NULL"); return GG_ERR_INVALID_ARG; }
     if ((int)app < GG_APP_PAGERANK || (int)app > GG_APP_CC) { set_error("gg_run: unknown app %d", (int)app); return GG_ERR_INVALID_ARG; }
-    if ((int)policy < GG_POLICY_EXACT || (int)policy > GG_POLICY_ADAPTIVE) { set_error("gg_run: unknown policy %d", (int)policy); return GG_ERR_INVALID_ARG; }
+    if ((int)policy < GG_POLICY_EXACT || (int)policy > GG_POLICY_TRIGGERED) { set_error("gg_run: unknown policy %d", (int)policy); return GG_ERR_INVALID_ARG; }
+    if (policy == GG_POLICY_TRIGGERED && !(p->trigger_ratio >= 0.0f && p->trigger_ratio <= 3.0e38f)) {
+        set_error("gg_run: trigger_ratio must be finite and >= 0");
+        return GG_ERR_INVALID_ARG;
+    }
     if (p->max_iters < 1) { set_error("gg_run: max_iters must be >= 1"); return GG_ERR_INVALID_ARG; }
     if (app == GG_APP_SSSP && !g->has_w) { set_error("gg_run: SSSP needs arc weights"); return GG_ERR_INVALID_ARG; }
     if ((app == GG_APP_SSSP || app == GG_APP_BFS) && (p->source < 0 || p->source >= g->n)) {

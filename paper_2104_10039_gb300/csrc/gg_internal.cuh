@@ -246,8 +246,8 @@ cudaError_t launch_iter_changed(IterStatsDev *st, const uint32_t *q_len, cudaStr
 // Active out-degree of every vertex from the packed active in-edges.
 cudaError_t launch_active_outdeg(const int32_t *sp_src, const uint32_t *sp_nnz, uint32_t max_arcs, int32_t n,
                                  int32_t *act, int num_sms, cudaStream_t s);
-// contrib[u] = rank[u] / deg[u] (0 when deg[u] = 0).
-cudaError_t launch_contrib(int32_t n, const float *rank, const int32_t *deg, float *contrib, int num_sms,
-                          cudaStream_t s);
+// contrib[u] = rank[u] / deg[u], or / the full out-degree when deg is null (0 when the degree is 0).
+cudaError_t launch_contrib(int32_t n, const float *rank, const int32_t *deg, const int32_t *out_ptr,
+                           float *contrib, int num_sms, cudaStream_t s);
 
 }  // namespace gg

@@ -214,19 +214,21 @@ cudaError_t launch_active_outdeg(const int32_t *sp_src, const uint32_t *sp_nnz, 
     return cudaGetLastError();
 }
 
+// contrib = rank / degree, the degree being deg[u] (active out-arcs) or, when
+// deg is null, the full out-degree from out_ptr.
 __global__ void k_contrib(int32_t n, const float *__restrict__ rank, const int32_t *__restrict__ deg,
-                          float *__restrict__ contrib)
+                          const int32_t *__restrict__ out_ptr, float *__restrict__ contrib)
 {
     for (int32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
-        const int d = deg[u];
+        const int d = deg ? deg[u] : out_ptr[u + 1] - out_ptr[u];
         contrib[u] = d > 0 ? __fdiv_rn(rank[u], (float)d) : 0.0f;
     }
 }
 
-cudaError_t launch_contrib(int32_t n, const float *rank, const int32_t *deg, float *contrib, int num_sms,
-                          cudaStream_t s)
+cudaError_t launch_contrib(int32_t n, const float *rank, const int32_t *deg, const int32_t *out_ptr,
+                           float *contrib, int num_sms, cudaStream_t s)
 {
-    k_contrib<<<num_sms * 8, 256, 0, s>>>(n, rank, deg, contrib);
+    k_contrib<<<num_sms * 8, 256, 0, s>>>(n, rank, deg, out_ptr, contrib);
     return cudaGetLastError();
 }
 

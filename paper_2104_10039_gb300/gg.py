@@ -27,7 +27,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 GG_OK, GG_ERR_INVALID_ARG, GG_ERR_BAD_GRAPH, GG_ERR_OOM, GG_ERR_CUDA, GG_ERR_STATE, \
     GG_ERR_TIMEOUT, GG_ERR_UNSUPPORTED = range(8)
 GG_APP_PAGERANK, GG_APP_SSSP, GG_APP_BFS, GG_APP_CC = range(4)
-GG_POLICY_EXACT, GG_POLICY_NONE, GG_POLICY_STATIC_SWITCH, GG_POLICY_ADAPTIVE = range(4)
+GG_POLICY_EXACT, GG_POLICY_NONE, GG_POLICY_STATIC_SWITCH, GG_POLICY_ADAPTIVE, GG_POLICY_TRIGGERED = range(5)
 (GG_RESULT_VALUES, GG_RESULT_MASK, GG_RESULT_STATS, GG_RESULT_ITER_STATS, GG_RESULT_CSC_PTR,
  GG_RESULT_CSC_SRC, GG_RESULT_CSC_W, GG_RESULT_SPARSE_PTR, GG_RESULT_SPARSE_SRC,
  GG_RESULT_OUT_TO_IN) = range(10)
@@ -41,14 +41,16 @@ APPS = {"pagerank": GG_APP_PAGERANK, "pr": GG_APP_PAGERANK, "sssp": GG_APP_SSSP,
         "bfs": GG_APP_BFS, "cc": GG_APP_CC}
 POLICIES = {"exact": GG_POLICY_EXACT, "none": GG_POLICY_NONE, "sp": GG_POLICY_NONE,
             "static_switch": GG_POLICY_STATIC_SWITCH, "sms": GG_POLICY_STATIC_SWITCH,
-            "adaptive": GG_POLICY_ADAPTIVE, "gg": GG_POLICY_ADAPTIVE}
+            "adaptive": GG_POLICY_ADAPTIVE, "gg": GG_POLICY_ADAPTIVE,
+            "triggered": GG_POLICY_TRIGGERED}
 
 
 class gg_params(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_uint32), ("theta", ctypes.c_float),
                 ("max_iters", ctypes.c_uint32), ("damping", ctypes.c_float),
                 ("epsilon", ctypes.c_float), ("source", ctypes.c_int32),
-                ("seed", ctypes.c_uint64), ("flags", ctypes.c_uint32)]
+                ("seed", ctypes.c_uint64), ("flags", ctypes.c_uint32),
+                ("trigger_ratio", ctypes.c_float)]
 
 
 class gg_stats(ctypes.Structure):
@@ -134,9 +136,9 @@ def gg_sample_edges(g: int, sample_ratio: float, seed: int):
 
 
 def make_params(alpha=4, theta=0.05, max_iters=20, damping=0.85, epsilon=0.0, source=0, seed=0,
-                flags=0) -> gg_params:
+                flags=0, trigger_ratio=0.5) -> gg_params:
     return gg_params(alpha, theta, max_iters, damping, epsilon, source,
-                     seed & 0xFFFFFFFFFFFFFFFF, flags)
+                     seed & 0xFFFFFFFFFFFFFFFF, flags, trigger_ratio)
 
 
 def gg_run(g: int, app, sample_ratio: float, policy, params: gg_params):

@@ -42,9 +42,9 @@ def correction_indices(policy, alpha, T):
 
 
 def gpu_run(gg, h, g, app, policy, sigma=0.5, alpha=4, theta=0.05, T=20, source=0, seed=1,
-            flags=0, damping=0.85, epsilon=0.0):
+            flags=0, damping=0.85, epsilon=0.0, trigger_ratio=0.5):
     p = gg.make_params(alpha=alpha, theta=theta, max_iters=T, damping=damping, epsilon=epsilon,
-                       source=source, seed=seed, flags=flags)
+                       source=source, seed=seed, flags=flags, trigger_ratio=trigger_ratio)
     gg.gg_run(h, app, sigma, policy, p)
     vals = gg.values(h, app)
     mask = gg.mask_bits(h, g.m) if policy != "exact" else None

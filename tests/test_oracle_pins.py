@@ -356,3 +356,102 @@ def test_renormalised_sp_equals_pagerank_of_the_sampled_subgraph():
                            flags=oracle.RENORM)
             ref = brute.pagerank_dense(sub, 0.85, T)
             assert np.abs(r["values"] - ref).sum() / np.abs(ref).sum() < 1e-13
+
+
+# ------------------------------------------------ triggered corrections --
+
+def _broom():
+    # BFS levels of sizes 1, 8, 4, 2, 1 from vertex 0: iteration i of a run
+    # on all arcs changes exactly the vertices of level i + 1.
+    arcs = [(0, v) for v in range(1, 9)] + [(1, 9), (2, 10), (3, 11), (4, 12), (9, 13), (10, 14),
+                                             (13, 15)]
+    return graphgen.from_arcs(16, arcs)
+
+
+@pytest.mark.parametrize("ratio,alpha,modes", [
+    # changed per iteration 8, 4, 2, 1, 0: 4 <= 0.5 * 8 triggers after the
+    # second; the next window starts at 1 and triggers when it reaches 0
+    (0.5, 10, "AACAAC"),
+    (0.4, 10, "AAACAC"),     # 2 <= 0.4 * 8 after the third
+    (0.0, 3, "AAACAC"),      # only the window length (3), then the quiet iteration
+    (0.0, 2, "AACAAC"),
+    (2.0, 10, "ACACAC"),     # a ratio >= 1 triggers after every approximate iteration
+])
+def test_triggered_schedule_hand_example(ratio, alpha, modes):
+    g = _broom()
+    r = oracle.run(g.n, g.rowptr, g.colidx, app="bfs", policy="triggered", sigma=1.0, alpha=alpha,
+                   trigger_ratio=ratio, source=0, max_iters=50)
+    code = {oracle.MODE_APPROX: "A", oracle.MODE_CORRECTION: "C"}
+    assert "".join(code[int(x)] for x in r["iter_mode"]) == modes
+    assert list(r["iter_changed"]) == [8, 4, 2, 1, 0, 0]
+    assert np.array_equal(r["values"], brute.bfs_levels(g, 0))
+
+
+def _trigger_rule_holds(r, alpha, ratio, pagerank):
+    """Every mode of the run follows the triggered rule from the run's own
+    per-iteration change statistics."""
+    A, C = oracle.MODE_APPROX, oracle.MODE_CORRECTION
+    modes = [int(x) for x in r["iter_mode"]]
+    stat = r["iter_sum_delta"] if pagerank else r["iter_changed"]
+    ratio = float(np.float32(ratio))
+    want_c = alpha == 0
+    window, first = 0, 0.0
+    for i, md in enumerate(modes):
+        assert md == (C if want_c else A), (i, modes)
+        if md == C:
+            window, want_c = 0, alpha == 0
+        else:
+            window += 1
+            if window == 1:
+                first = float(stat[i])
+            want_c = window >= alpha or float(stat[i]) <= ratio * first
+
+
+@pytest.mark.parametrize("app", ["pagerank", "sssp", "bfs", "cc"])
+def test_triggered_schedule_follows_its_rule(app):
+    sym = app == "cc"
+    for g in _small_graphs(weighted=True, symmetric=sym) + [graphgen.rmat(9, seed=3, symmetric=sym)]:
+        if g.weights is None:
+            graphgen.add_weights(g, seed=11)
+        s = int(graphgen.sources(g, 1, seed=2)[0])
+        for alpha, ratio in ((4, 0.5), (6, 0.2), (1, 0.0), (0, 0.5)):
+            r = oracle.run(g.n, g.rowptr, g.colidx, g.weights, app=app, policy="triggered", sigma=0.4,
+                           seed=3, alpha=alpha, theta=0.1, trigger_ratio=ratio, source=s,
+                           max_iters=15 if app == "pagerank" else 1000, symmetric=sym)
+            _trigger_rule_holds(r, alpha, ratio, app == "pagerank")
+
+
+def test_triggered_special_cases_reduce_to_adaptive():
+    for g in _small_graphs(weighted=True):
+        s = int(graphgen.sources(g, 1, seed=2)[0])
+        for app, T in (("pagerank", 12), ("sssp", 1000), ("bfs", 1000)):
+            kw = dict(app=app, source=s, max_iters=T, sigma=0.3, seed=5, theta=0.1)
+            for alpha_gg, alpha_tr, ratio in ((0, 0, 0.5), (1, 1, 0.0), (1, 5, 1.0), (1, 3, 7.0)):
+                gg = oracle.run(g.n, g.rowptr, g.colidx, g.weights, policy="gg", alpha=alpha_gg, **kw)
+                tr = oracle.run(g.n, g.rowptr, g.colidx, g.weights, policy="triggered", alpha=alpha_tr,
+                                trigger_ratio=ratio, **kw)
+                assert np.array_equal(tr["values"], gg["values"]), (app, alpha_tr, ratio)
+                assert np.array_equal(tr["mask"], gg["mask"])
+
+
+def test_triggered_min_apps_reach_the_exact_fixed_point():
+    for g in _small_graphs(weighted=True):
+        s = int(graphgen.sources(g, 1, seed=2)[0])
+        r = oracle.run(g.n, g.rowptr, g.colidx, g.weights, app="sssp", policy="triggered", sigma=0.3,
+                       seed=6, alpha=5, theta=0.3, trigger_ratio=0.3, source=s, max_iters=1000)
+        assert np.array_equal(r["values"], brute.dijkstra(g, s))
+    for g in _small_graphs(symmetric=True):
+        r = oracle.run(g.n, g.rowptr, g.colidx, app="cc", policy="triggered", sigma=0.3, seed=6,
+                       alpha=5, theta=0.3, trigger_ratio=0.3, max_iters=1000, symmetric=True)
+        assert np.array_equal(r["values"], brute.cc_min_labels(g))
+
+
+def test_replayed_modes_reproduce_the_run():
+    g = graphgen.rmat(8, seed=4)
+    for policy, alpha in (("gg", 3), ("sms", 4), ("triggered", 5)):
+        r = oracle.run(g.n, g.rowptr, g.colidx, policy=policy, sigma=0.4, seed=2, alpha=alpha,
+                       theta=0.05, trigger_ratio=0.5, max_iters=14)
+        rr = oracle.run(g.n, g.rowptr, g.colidx, policy="triggered", sigma=0.4, seed=2, alpha=1,
+                        theta=0.05, trigger_ratio=0.0, max_iters=14, replay_modes=r["iter_mode"])
+        assert np.array_equal(rr["iter_mode"], r["iter_mode"])
+        assert np.array_equal(rr["values"], r["values"]) and np.array_equal(rr["mask"], r["mask"])
