@@ -379,13 +379,13 @@ def accuracy_table(g, source, collected):
                           "ms": round(st.ms_run, 3), "error": round(err, 5),
                           "accuracy_pct": round(metrics.accuracy(err), 3)})
 
-        def first_within(app, sigma, policy, theta, t_max, flags=0, alpha=ALPHA):
+        def first_within(app, sigma, policy, theta, t_max, flags=0, alpha=ALPHA, ratio=0.5):
             """Fewest iterations whose result is within the target (the error of
             an adaptive run is not monotone in T: it dips after corrections)."""
             for t in range(1, t_max + 1):
                 gg.gg_run(h, app, sigma, policy, gg.make_params(
                     alpha=alpha, theta=theta, max_iters=t, damping=DAMPING, source=source, seed=SAMPLE_SEED,
-                    flags=flags))
+                    flags=flags, trigger_ratio=ratio))
                 if error(app, gg.values(h, app), ref[app]) <= target:
                     return {"iters": t, "ms": round(gg.stats(h).ms_run, 3)}
             return None
@@ -394,15 +394,19 @@ def accuracy_table(g, source, collected):
         for app in ("pagerank", "sssp"):
             ex = first_within(app, 1.0, "exact", THETA, full_iters[app])
             best = None
-            variants = [(0.05, 0, 4), (0.005, 0, 4), (0.05, 0, 2)]
+            # (policy, theta, flags, alpha, trigger ratio)
+            variants = [("adaptive", 0.05, 0, 4, 0), ("adaptive", 0.005, 0, 4, 0), ("adaptive", 0.05, 0, 2, 0),
+                        ("triggered", 0.05, 0, 8, 0.3), ("triggered", 0.005, 0, 8, 0.1)]
             if app == "pagerank":   # the share influence and renormalisation flags
-                variants += [(0.05, gg.GG_RENORM, 4), (0.05, gg.GG_RENORM, 2),
-                             (0.0005, gg.GG_INFL_SHARE | gg.GG_RENORM, 4)]
-            for theta, fl, alpha in variants:
+                variants += [("adaptive", 0.05, gg.GG_RENORM, 4, 0), ("adaptive", 0.05, gg.GG_RENORM, 2, 0),
+                             ("adaptive", 0.0005, gg.GG_INFL_SHARE | gg.GG_RENORM, 4, 0),
+                             ("triggered", 0.0005, gg.GG_INFL_SHARE | gg.GG_RENORM, 8, 0.3)]
+            for policy, theta, fl, alpha, ratio in variants:
                 for sigma in (0.5, 0.9):
-                    r = first_within(app, sigma, "adaptive", theta, 2 * full_iters[app], fl, alpha)
+                    r = first_within(app, sigma, policy, theta, 2 * full_iters[app], fl, alpha, ratio)
                     if r and (best is None or r["ms"] < best["ms"]):
-                        best = {"sigma": sigma, "theta": theta, "alpha": alpha,
+                        best = {"policy": policy, "sigma": sigma, "theta": theta, "alpha": alpha,
+                                **({"trigger_ratio": ratio} if policy == "triggered" else {}),
                                 "flags": [n for n, b in (("GG_INFL_SHARE", gg.GG_INFL_SHARE),
                                                          ("GG_RENORM", gg.GG_RENORM)) if fl & b], **r}
             if best and ex:

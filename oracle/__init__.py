@@ -38,9 +38,11 @@ _lib = None
 
 PAGERANK, SSSP, BFS, CC = 0, 1, 2, 3
 APPS = {"pagerank": PAGERANK, "pr": PAGERANK, "sssp": SSSP, "bfs": BFS, "cc": CC}
-EXACT, NONE, STATIC_SWITCH, ADAPTIVE, TRIGGERED = 0, 1, 2, 3, 4
+EXACT, NONE, STATIC_SWITCH, ADAPTIVE, TRIGGERED, LEARNED = 0, 1, 2, 3, 4, 5
 POLICIES = {"exact": EXACT, "none": NONE, "sp": NONE, "static_switch": STATIC_SWITCH,
-            "sms": STATIC_SWITCH, "adaptive": ADAPTIVE, "gg": ADAPTIVE, "triggered": TRIGGERED}
+            "sms": STATIC_SWITCH, "adaptive": ADAPTIVE, "gg": ADAPTIVE, "triggered": TRIGGERED,
+            "learned": LEARNED}
+MLP_NPARAM = 64 * 8 + 64 + 64 * 64 + 64 + 64 + 1   # W1, b1, W2, b2, w3, b3
 MODE_APPROX, MODE_ACCURATE, MODE_CORRECTION = 0, 1, 2
 STOP_QUIESCE, EST_STRICT, INFL_SHARE, RENORM = 1, 2, 32, 64
 INF = 0xFFFFFFFF
@@ -56,7 +58,12 @@ class _Params(ctypes.Structure):
                 ("nthreads", ctypes.c_int32),
                 ("replay_masks", ctypes.POINTER(ctypes.c_uint8)),
                 ("n_replay", ctypes.c_int32), ("replay_tol", ctypes.c_double),
-                ("trigger_ratio", ctypes.c_double), ("replay_modes", ctypes.POINTER(ctypes.c_int8))]
+                ("trigger_ratio", ctypes.c_double), ("replay_modes", ctypes.POINTER(ctypes.c_int8)),
+                ("mlp", ctypes.POINTER(ctypes.c_float)), ("select_logit", ctypes.c_double),
+                ("fallback_frac", ctypes.c_double), ("replay_select", ctypes.POINTER(ctypes.c_uint8)),
+                ("n_replay_select", ctypes.c_int32), ("replay_select_tol", ctypes.c_double),
+                ("trace_x", ctypes.POINTER(ctypes.c_float)), ("trace_y", ctypes.POINTER(ctypes.c_uint8)),
+                ("trace_cap", ctypes.c_int64), ("label_tol", ctypes.c_double)]
 
 
 class _Out(ctypes.Structure):
@@ -67,9 +74,13 @@ class _Out(ctypes.Structure):
                 ("iter_mode", ctypes.POINTER(ctypes.c_int32)),
                 ("iter_changed", ctypes.POINTER(ctypes.c_int64)),
                 ("iter_sum_delta", ctypes.POINTER(ctypes.c_double)),
+                ("iter_selected", ctypes.POINTER(ctypes.c_int64)),
+                ("logits", ctypes.POINTER(ctypes.c_double)),
                 ("iterations", ctypes.c_int32), ("corrections", ctypes.c_int32),
                 ("replay_mismatch", ctypes.c_int64), ("replay_max_margin", ctypes.c_double),
-                ("replay_violations", ctypes.c_int64)]
+                ("replay_violations", ctypes.c_int64), ("select_mismatch", ctypes.c_int64),
+                ("select_violations", ctypes.c_int64), ("select_max_margin", ctypes.c_double),
+                ("trace_rows", ctypes.c_int64)]
 
 
 def build(force: bool = False) -> str:
@@ -104,6 +115,14 @@ def _load():
                                         ctypes.c_double, ctypes.c_uint64, u8p]
         lib.orc_iteration_mode.restype = ctypes.c_int
         lib.orc_iteration_mode.argtypes = [ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32]
+        f32p, f64p = ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_double)
+        lib.orc_bf16.restype = ctypes.c_float
+        lib.orc_bf16.argtypes = [ctypes.c_float]
+        lib.orc_mlp_forward.restype = None
+        lib.orc_mlp_forward.argtypes = [f32p, f32p, ctypes.c_int64, ctypes.c_int, f64p]
+        lib.orc_mlp_grad.restype = ctypes.c_double
+        lib.orc_mlp_grad.argtypes = [f32p, f32p, u8p, ctypes.POINTER(ctypes.c_int64), ctypes.c_int64,
+                                     ctypes.c_int, f64p]
         lib.orc_run.restype = ctypes.c_int
         lib.orc_run.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, u32p,
                                 ctypes.POINTER(_Params), ctypes.POINTER(_Out)]
@@ -166,7 +185,8 @@ def iteration_mode(policy, alpha: int, i: int) -> int:
 def run(n, rowptr, colidx, weights=None, *, app="pagerank", policy="exact", sigma=1.0,
         seed=0, alpha=4, theta=0.05, max_iters=20, damping=0.85, epsilon=0.0, source=0,
         flags=0, symmetric=False, nthreads=1, replay_masks=None, replay_tol=1e-5,
-        trigger_ratio=0.5, replay_modes=None):
+        trigger_ratio=0.5, replay_modes=None, mlp=None, select_logit=0.0, fallback_frac=1.0,
+        replay_select=None, replay_select_tol=0.05, trace_cap=0, label_tol=1e-3):
     """Run one GraphGuess execution on the CPU; returns a dict with ``values``
     (float64 for PageRank, uint32 otherwise), the final CSC-order ``mask`` and
     per-iteration statistics. ``damping`` and ``theta`` are given as the float32
@@ -178,7 +198,13 @@ def run(n, rowptr, colidx, weights=None, *, app="pagerank", policy="exact", sigm
     ``trigger_ratio`` times the window's first, or after ``alpha`` approximate
     iterations. ``replay_modes`` (int per iteration, MODE_*) makes the run
     follow the given modes instead of its policy's (iterations past the given
-    ones are approximate)."""
+    ones are approximate). ``policy="learned"`` scores every vertex with the
+    MLP ``mlp`` (MLP_NPARAM float32) at each correction and corrects only
+    those with a logit above ``select_logit``; ``replay_select`` (uint8[n] per
+    learned correction) adopts the given selections after checking that every
+    differing one lies within ``replay_select_tol`` of the threshold.
+    ``trace_cap`` > 0 records features / labels of every vertex at each full
+    correction (``trace_x``, ``trace_y``)."""
     a = APPS[app] if isinstance(app, str) else int(app)
     pol = POLICIES[policy] if isinstance(policy, str) else int(policy)
     rowptr = np.ascontiguousarray(rowptr, np.int32)
@@ -194,11 +220,23 @@ def run(n, rowptr, colidx, weights=None, *, app="pagerank", policy="exact", sigm
     if replay_modes is not None:
         modes = np.full(max(max_iters, 1), 0, np.int8)
         modes[:len(replay_modes)] = np.asarray(replay_modes, np.int8)
+    mlp_a = None if mlp is None else np.ascontiguousarray(mlp, np.float32)
+    if mlp_a is not None and mlp_a.shape[0] != MLP_NPARAM:
+        raise ValueError("mlp must hold %d parameters" % MLP_NPARAM)
+    rsel = None
+    n_rsel = 0
+    if replay_select is not None and len(replay_select):
+        rsel = np.ascontiguousarray(np.stack([np.asarray(x, np.uint8) for x in replay_select]))
+        n_rsel = rsel.shape[0]
+    tx = np.zeros((max(trace_cap, 1), 8), np.float32) if trace_cap > 0 else None
+    ty = np.zeros(max(trace_cap, 1), np.uint8) if trace_cap > 0 else None
     prm = _Params(a, pol, float(sigma), seed & 0xFFFFFFFFFFFFFFFF, alpha,
                   float(np.float32(theta)), max_iters, float(np.float32(damping)),
                   float(np.float32(epsilon)), source, flags, int(symmetric), nthreads,
                   _p(rep, ctypes.c_uint8), n_rep, replay_tol, float(np.float32(trigger_ratio)),
-                  _p(modes, ctypes.c_int8))
+                  _p(modes, ctypes.c_int8), _p(mlp_a, ctypes.c_float), float(select_logit),
+                  float(fallback_frac), _p(rsel, ctypes.c_uint8), n_rsel, float(replay_select_tol),
+                  _p(tx, ctypes.c_float), _p(ty, ctypes.c_uint8), int(trace_cap), float(label_tol))
     T = max(max_iters, 1)
     pr = np.empty(n, np.float64) if a == PAGERANK else None
     iv = np.empty(n, np.uint32) if a != PAGERANK else None
@@ -207,9 +245,12 @@ def run(n, rowptr, colidx, weights=None, *, app="pagerank", policy="exact", sigm
     it_mode = np.full(T, -1, np.int32)
     it_changed = np.zeros(T, np.int64)
     it_sum = np.zeros(T, np.float64)
+    it_sel = np.full(T, -1, np.int64)
+    logits = np.full(n, np.nan, np.float64)
     out = _Out(_p(pr, ctypes.c_double), _p(iv, ctypes.c_uint32), _p(mask, ctypes.c_uint8),
                _p(it_arcs, ctypes.c_int64), _p(it_mode, ctypes.c_int32),
-               _p(it_changed, ctypes.c_int64), _p(it_sum, ctypes.c_double), 0, 0, 0, 0.0, 0)
+               _p(it_changed, ctypes.c_int64), _p(it_sum, ctypes.c_double), _p(it_sel, ctypes.c_int64),
+               _p(logits, ctypes.c_double), 0, 0, 0, 0.0, 0, 0, 0, 0.0, 0)
     rc = _load().orc_run(n, m, _p(rowptr, ctypes.c_int32), _p(colidx, ctypes.c_int32),
                          _p(w, ctypes.c_uint32), ctypes.byref(prm), ctypes.byref(out))
     if rc != 0:
@@ -224,7 +265,47 @@ def run(n, rowptr, colidx, weights=None, *, app="pagerank", policy="exact", sigm
         "iter_mode": it_mode[:it],
         "iter_changed": it_changed[:it],
         "iter_sum_delta": it_sum[:it],
+        "iter_selected": it_sel[:it],
+        "logits": logits,
+        "select_mismatch": out.select_mismatch,
+        "select_violations": out.select_violations,
+        "select_max_margin": out.select_max_margin,
+        "trace_x": tx[:out.trace_rows] if tx is not None else None,
+        "trace_y": ty[:out.trace_rows] if ty is not None else None,
         "replay_mismatch": out.replay_mismatch,
         "replay_max_margin": out.replay_max_margin,
         "replay_violations": out.replay_violations,
     }
+
+
+# ------------------------------------------------------------------ scorer --
+
+def bf16(x) -> np.ndarray:
+    """float32 values rounded to bfloat16 (nearest, ties to even), as float32."""
+    x = np.asarray(x, np.float32)
+    lib = _load()
+    return np.array([lib.orc_bf16(float(v)) for v in x.ravel()], np.float32).reshape(x.shape)
+
+
+def mlp_forward(params, x, round_bf16=True) -> np.ndarray:
+    """Logits (float64) of the feature rows x[rows, 8] under the scorer's
+    arithmetic (bfloat16 weights and layer inputs, exact sums)."""
+    P = np.ascontiguousarray(params, np.float32)
+    X = np.ascontiguousarray(x, np.float32).reshape(-1, 8)
+    out = np.empty(X.shape[0], np.float64)
+    _load().orc_mlp_forward(_p(P, ctypes.c_float), _p(X, ctypes.c_float), X.shape[0], int(round_bf16),
+                            _p(out, ctypes.c_double))
+    return out
+
+
+def mlp_grad(params, x, y, idx=None, round_bf16=True):
+    """(gradient float64[MLP_NPARAM], mean logistic loss) over rows idx."""
+    P = np.ascontiguousarray(params, np.float32)
+    X = np.ascontiguousarray(x, np.float32).reshape(-1, 8)
+    Y = np.ascontiguousarray(y, np.uint8)
+    I = np.arange(X.shape[0], dtype=np.int64) if idx is None else np.ascontiguousarray(idx, np.int64)
+    g = np.empty(MLP_NPARAM, np.float64)
+    loss = _load().orc_mlp_grad(_p(P, ctypes.c_float), _p(X, ctypes.c_float), _p(Y, ctypes.c_uint8),
+                                _p(I, ctypes.c_int64), I.shape[0], int(round_bf16), _p(g, ctypes.c_double))
+    return g, float(loss)
+

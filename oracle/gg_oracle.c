@@ -54,6 +54,17 @@
  *    applications, sum |old-new| for PageRank) is at most trigger_ratio times
  *    that of the window's first approximate iteration, or the alpha-th
  *    approximate iteration of the window.
+ *  - ORC_LEARNED (beyond the paper; the scorer is this project's): the
+ *    adaptive schedule, but at a correction a per-vertex MLP scores every
+ *    vertex from 8 features and only the vertices scoring above
+ *    select_logit are corrected (all in-edges gathered, influence and flags
+ *    recomputed); the others keep their value and flags for that iteration.
+ *    A selection holding more than fallback_frac of all arcs runs the full
+ *    correction instead, and so does the correction after a learned one that
+ *    changed no value. Scorer arithmetic: weights and every layer's inputs
+ *    rounded to bfloat16 (nearest even), exact products summed (FP64 here,
+ *    rounded to FP32 before the next rounding), FP32 biases, ReLU after the
+ *    two hidden layers.
  *  - Two PageRank variants beyond the paper (flags): ORC_INFL_SHARE takes
  *    an arc's influence as its share of the row's total (order-free) instead
  *    of the running-prefix form; ORC_RENORM divides a source's rank by its
@@ -69,7 +80,8 @@
 #endif
 
 enum { ORC_PAGERANK = 0, ORC_SSSP = 1, ORC_BFS = 2, ORC_CC = 3 };
-enum { ORC_EXACT = 0, ORC_NONE = 1, ORC_STATIC_SWITCH = 2, ORC_ADAPTIVE = 3, ORC_TRIGGERED = 4 };
+enum { ORC_EXACT = 0, ORC_NONE = 1, ORC_STATIC_SWITCH = 2, ORC_ADAPTIVE = 3, ORC_TRIGGERED = 4,
+       ORC_LEARNED = 5 };
 enum { ORC_MODE_APPROX = 0, ORC_MODE_ACCURATE = 1, ORC_MODE_CORRECTION = 2 };
 #define ORC_STOP_QUIESCE 1u
 #define ORC_EST_STRICT 2u
@@ -95,6 +107,16 @@ typedef struct {
     double replay_tol;
     double trigger_ratio;        /* ORC_TRIGGERED: correct when the window's change falls to this fraction */
     const int8_t *replay_modes;  /* per iteration ORC_MODE_* to follow instead of the trigger, or NULL */
+    const float *mlp;            /* ORC_LEARNED: scorer parameters, ORC_MLP_NPARAM floats */
+    double select_logit;         /* ORC_LEARNED: vertices with a logit above this are corrected */
+    double fallback_frac;        /* ORC_LEARNED: a selection with more arcs than this x m corrects fully */
+    const uint8_t *replay_select;/* n_replay_select x n selections (0/1) to adopt, or NULL */
+    int32_t n_replay_select;
+    double replay_select_tol;    /* a differing selection must have |logit - select_logit| <= this */
+    float *trace_x;              /* features (8 per row) at every full correction, rows c*n+u, or NULL */
+    uint8_t *trace_y;            /* labels of those rows */
+    int64_t trace_cap;           /* rows available in trace_x / trace_y */
+    double label_tol;            /* PageRank label: |new-old| > label_tol * |new| */
 } orc_params;
 
 typedef struct {
@@ -105,11 +127,17 @@ typedef struct {
     int32_t *iter_mode;          /* max_iters: ORC_MODE_* (-1 = skipped) */
     int64_t *iter_changed;       /* max_iters: vertices active after VStatus */
     double *iter_sum_delta;      /* max_iters: sum |old-new| over vertices (nullable) */
+    int64_t *iter_selected;      /* max_iters: vertices a learned correction corrected, else -1 (nullable) */
+    double *logits;              /* n: logits of the last scored correction (nullable) */
     int32_t iterations;          /* iterations counted (skipped no-ops included) */
     int32_t corrections;
     int64_t replay_mismatch;
     double replay_max_margin;
     int64_t replay_violations;
+    int64_t select_mismatch;     /* adopted selections that differ from the oracle's own */
+    int64_t select_violations;   /* ... of which farther than replay_select_tol from the threshold */
+    double select_max_margin;
+    int64_t trace_rows;          /* rows written to the trace */
 } orc_out;
 
 /* SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): the output for a given
@@ -182,6 +210,7 @@ int orc_iteration_mode(int policy, uint32_t alpha, uint32_t i)
         if (i < alpha) return ORC_MODE_APPROX;
         return i == alpha ? ORC_MODE_CORRECTION : ORC_MODE_ACCURATE;
     case ORC_ADAPTIVE:
+    case ORC_LEARNED:
         return (i % (alpha + 1u)) == alpha ? ORC_MODE_CORRECTION : ORC_MODE_APPROX;
     default: return -1;
     }
@@ -193,11 +222,119 @@ static int64_t next_accurate_iteration(int policy, uint32_t alpha, uint32_t i)
 {
     if (policy == ORC_NONE) return -1;
     if (policy == ORC_STATIC_SWITCH) return i < alpha ? (int64_t)alpha : (int64_t)i + 1;
-    if (policy == ORC_ADAPTIVE) {
+    if (policy == ORC_ADAPTIVE || policy == ORC_LEARNED) {
         uint64_t period = (uint64_t)alpha + 1u;
         return (int64_t)(((uint64_t)i / period) * period + alpha);
     }
     return (int64_t)i + 1;   /* EXACT, and TRIGGERED (a quiet window triggers at once) */
+}
+
+/* ------------------------------------------------------------ scorer ----
+ * Parameters (FP32): W1[64][8], b1[64], W2[64][64], b2[64], w3[64], b3. */
+#define ORC_MLP_IN 8
+#define ORC_MLP_H 64
+#define ORC_MLP_NPARAM (ORC_MLP_H * ORC_MLP_IN + ORC_MLP_H + ORC_MLP_H * ORC_MLP_H + ORC_MLP_H + ORC_MLP_H + 1)
+
+/* bfloat16 value of x: round to nearest, ties to even, on the upper 16 bits. */
+float orc_bf16(float x)
+{
+    uint32_t b;
+    memcpy(&b, &x, 4);
+    b += 0x7FFFu + ((b >> 16) & 1u);
+    b &= 0xFFFF0000u;
+    memcpy(&x, &b, 4);
+    return x;
+}
+
+static double rnd(double v, int round) { return round ? (double)orc_bf16((float)v) : v; }
+
+/* Logit of one row; h1 / h2 (64 each) receive the (rounded) hidden
+ * activations and s1 / s2 their pre-activations when not NULL. */
+static double mlp_row(const float *P, const float *x, int round, double *h1, double *h2, double *s1,
+                      double *s2)
+{
+    const float *W1 = P, *b1 = P + 512, *W2 = P + 576, *b2 = P + 4672, *w3 = P + 4736;
+    const float b3 = P[4800];
+    double xb[ORC_MLP_IN], a1[ORC_MLP_H], a2[ORC_MLP_H];
+    for (int f = 0; f < ORC_MLP_IN; ++f) xb[f] = rnd(x[f], round);
+    for (int j = 0; j < ORC_MLP_H; ++j) {
+        double acc = b1[j];
+        for (int f = 0; f < ORC_MLP_IN; ++f) acc += rnd(W1[j * ORC_MLP_IN + f], round) * xb[f];
+        if (s1) s1[j] = acc;
+        a1[j] = acc > 0.0 ? rnd(round ? (double)(float)acc : acc, round) : 0.0;
+        if (h1) h1[j] = a1[j];
+    }
+    for (int j = 0; j < ORC_MLP_H; ++j) {
+        double acc = b2[j];
+        for (int k = 0; k < ORC_MLP_H; ++k) acc += rnd(W2[j * ORC_MLP_H + k], round) * a1[k];
+        if (s2) s2[j] = acc;
+        a2[j] = acc > 0.0 ? rnd(round ? (double)(float)acc : acc, round) : 0.0;
+        if (h2) h2[j] = a2[j];
+    }
+    double z = b3;
+    for (int j = 0; j < ORC_MLP_H; ++j) z += rnd(w3[j], round) * a2[j];
+    return z;
+}
+
+/* Logits of `rows` feature rows (8 floats each). */
+void orc_mlp_forward(const float *P, const float *x, int64_t rows, int round, double *logits)
+{
+    for (int64_t r = 0; r < rows; ++r) logits[r] = mlp_row(P, x + r * ORC_MLP_IN, round, NULL, NULL, NULL, NULL);
+}
+
+/* Gradient of the mean logistic loss over the rows idx[0..b) (labels 0/1)
+ * with respect to the parameters (same layout), the rounding treated as
+ * the identity; returns the loss. */
+double orc_mlp_grad(const float *P, const float *x, const uint8_t *y, const int64_t *idx, int64_t b, int round,
+                    double *grad)
+{
+    const float *W2 = P + 576, *w3 = P + 4736;
+    double *gW1 = grad, *gb1 = grad + 512, *gW2 = grad + 576, *gb2 = grad + 4672, *gw3 = grad + 4736;
+    double h1[ORC_MLP_H], h2[ORC_MLP_H], s1[ORC_MLP_H], s2[ORC_MLP_H], d2[ORC_MLP_H];
+    double loss = 0.0;
+    for (int i = 0; i < ORC_MLP_NPARAM; ++i) grad[i] = 0.0;
+    for (int64_t t = 0; t < b; ++t) {
+        const float *xr = x + idx[t] * ORC_MLP_IN;
+        const double lab = y[idx[t]] ? 1.0 : 0.0;
+        const double z = mlp_row(P, xr, round, h1, h2, s1, s2);
+        loss += (z > 0.0 ? z : 0.0) - z * lab + log1p(exp(-fabs(z)));
+        const double dz = (1.0 / (1.0 + exp(-z)) - lab) / (double)b;
+        grad[4800] += dz;
+        for (int j = 0; j < ORC_MLP_H; ++j) {
+            gw3[j] += dz * h2[j];
+            d2[j] = s2[j] > 0.0 ? dz * rnd(w3[j], round) : 0.0;
+            gb2[j] += d2[j];
+            for (int k = 0; k < ORC_MLP_H; ++k) gW2[j * ORC_MLP_H + k] += d2[j] * h1[k];
+        }
+        for (int k = 0; k < ORC_MLP_H; ++k) {
+            if (!(s1[k] > 0.0)) continue;
+            double d1 = 0.0;
+            for (int j = 0; j < ORC_MLP_H; ++j) d1 += rnd(W2[j * ORC_MLP_H + k], round) * d2[j];
+            gb1[k] += d1;
+            for (int f = 0; f < ORC_MLP_IN; ++f) gW1[k * ORC_MLP_IN + f] += d1 * rnd(xr[f], round);
+        }
+    }
+    return loss / (double)(b > 0 ? b : 1);
+}
+
+/* The scorer's 8 features of vertex u before iteration i (FP32, each from
+ * correctly rounded operations): sqrt(in-degree)/64, sqrt(out-degree)/64,
+ * the change features of the last three executed iterations (newest first),
+ * the active fraction of the in-edges (1 without in-edges), i/64, app id.
+ * hist holds 3 rows of n; executed = iterations executed so far. */
+static void vertex_features(int32_t u, int32_t n, uint32_t i, int app, const int32_t *in_ptr,
+                            const int32_t *outdeg, const uint8_t *mask, const float *hist, uint32_t executed,
+                            float *x)
+{
+    const int32_t indeg = in_ptr[u + 1] - in_ptr[u];
+    int32_t act = 0;
+    for (int32_t k = in_ptr[u]; k < in_ptr[u + 1]; ++k) act += mask[k] ? 1 : 0;
+    x[0] = sqrtf((float)indeg) * 0.015625f;
+    x[1] = sqrtf((float)outdeg[u]) * 0.015625f;
+    for (uint32_t j = 1; j <= 3; ++j) x[1 + j] = hist[(size_t)((executed + 3u - j) % 3u) * (size_t)n + (size_t)u];
+    x[5] = indeg > 0 ? (float)act / (float)indeg : 1.0f;
+    x[6] = (float)i * 0.015625f;
+    x[7] = (float)app;
 }
 
 /* Number of active out-arcs of every vertex under the flags `mask`. */
@@ -232,6 +369,7 @@ int orc_run(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx,
     if (p->app < ORC_PAGERANK || p->app > ORC_CC) return -1;
     if (p->app != ORC_PAGERANK && p->app != ORC_CC && (p->source < 0 || p->source >= n)) return -1;
     if (!(p->sample_ratio > 0.0 && p->sample_ratio <= 1.0)) return -1;
+    if (p->policy == ORC_LEARNED && !p->mlp) return -1;
 #ifdef _OPENMP
     if (p->nthreads > 0) omp_set_num_threads(p->nthreads);
 #endif
@@ -244,6 +382,9 @@ int orc_run(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx,
     double *infl = (double *)malloc((size_t)(m ? m : 1) * sizeof(double));
     int32_t *outdeg = (int32_t *)malloc((size_t)n * sizeof(int32_t));
     int32_t *act = NULL;
+    float *hist = NULL;          /* change features of the last three executed iterations */
+    uint8_t *sel = NULL;         /* vertices a learned correction corrects */
+    double *logit = NULL;
     double *rank = NULL, *rank_next = NULL;
     uint32_t *val = NULL, *val_next = NULL;
     if (!in_ptr || !in_src || !in_w || !mask || !new_mask || !infl || !outdeg) goto done;
@@ -254,6 +395,13 @@ int orc_run(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx,
     const int is_pr = p->app == ORC_PAGERANK;
     const int renorm = is_pr && (p->flags & ORC_RENORM);
     const int share = is_pr && (p->flags & ORC_INFL_SHARE);
+    const int learned_policy = p->policy == ORC_LEARNED;
+    if (learned_policy || p->trace_x) {
+        hist = (float *)calloc((size_t)3 * (size_t)n, sizeof(float));
+        sel = (uint8_t *)malloc((size_t)n);
+        logit = (double *)malloc((size_t)n * sizeof(double));
+        if (!hist || !sel || !logit) goto done;
+    }
     if (renorm) {
         act = (int32_t *)malloc((size_t)n * sizeof(int32_t));
         if (!act) goto done;
@@ -277,6 +425,13 @@ int orc_run(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx,
     o->replay_mismatch = 0;
     o->replay_max_margin = 0.0;
     o->replay_violations = 0;
+    o->select_mismatch = 0;
+    o->select_violations = 0;
+    o->select_max_margin = 0.0;
+    o->trace_rows = 0;
+    uint32_t executed = 0;       /* iterations run (skipped no-ops excluded) */
+    int force_full = 0;          /* the next correction is a full one */
+    int32_t select_next = 0;
     const double d = p->damping;
     const double base = (1.0 - d) / (double)n;
     int32_t replay_next = 0;
@@ -294,10 +449,61 @@ int orc_run(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx,
         const int accurate = mode != ORC_MODE_APPROX;
         const int correcting = mode == ORC_MODE_CORRECTION;
         int64_t arcs = 0, changed = 0;
+        if (o->iter_selected) o->iter_selected[i] = -1;
+
+        /* Learned correction: score every vertex, select, maybe fall back. */
+        int learned = 0;
+        if (correcting && learned_policy && !force_full) {
+            int64_t nsel = 0, sel_arcs = 0;
+            for (int32_t u = 0; u < n; ++u) {
+                float x[ORC_MLP_IN];
+                vertex_features(u, n, i, p->app, in_ptr, outdeg, mask, hist, executed, x);
+                logit[u] = mlp_row(p->mlp, x, 1, NULL, NULL, NULL, NULL);
+                sel[u] = logit[u] > p->select_logit;
+            }
+            if (o->logits) memcpy(o->logits, logit, (size_t)n * sizeof(double));
+            if (p->replay_select && select_next < p->n_replay_select) {
+                const uint8_t *given = p->replay_select + (size_t)select_next * (size_t)n;
+                for (int32_t u = 0; u < n; ++u) {
+                    if ((given[u] != 0) != (sel[u] != 0)) {
+                        const double margin = fabs(logit[u] - p->select_logit);
+                        o->select_mismatch += 1;
+                        if (margin > o->select_max_margin) o->select_max_margin = margin;
+                        if (!(margin <= p->replay_select_tol)) o->select_violations += 1;
+                    }
+                    sel[u] = given[u] ? 1 : 0;
+                }
+                select_next += 1;
+            }
+            for (int32_t u = 0; u < n; ++u) {
+                nsel += sel[u];
+                sel_arcs += sel[u] ? in_ptr[u + 1] - in_ptr[u] : 0;
+            }
+            learned = !((double)sel_arcs > p->fallback_frac * (double)m);
+            if (learned && o->iter_selected) o->iter_selected[i] = nsel;
+        }
+        /* Trace: features before every full correction, labels after it. */
+        const int tracing = correcting && !learned && p->trace_x && o->trace_rows + n <= p->trace_cap;
+        if (tracing) {
+            for (int32_t u = 0; u < n; ++u)
+                vertex_features(u, n, i, p->app, in_ptr, outdeg, mask, hist, executed,
+                                p->trace_x + (size_t)(o->trace_rows + u) * ORC_MLP_IN);
+        }
+        float *hist_out = hist ? hist + (size_t)(executed % 3u) * (size_t)n : NULL;
 
         /* Gather (GG-Gather over in-edges, Alg. 1 / Alg. 2), Apply, VStatus */
 #pragma omp parallel for schedule(dynamic, 256) reduction(+ : arcs, changed, sum_delta)
         for (int32_t u = 0; u < n; ++u) {
+            if (learned && !sel[u]) {   /* not selected: value and flags stay */
+                if (is_pr) rank_next[u] = rank[u];
+                else val_next[u] = val[u];
+                for (int32_t k = in_ptr[u]; k < in_ptr[u + 1]; ++k) {
+                    new_mask[k] = mask[k];
+                    infl[k] = 1e300;
+                }
+                if (hist_out) hist_out[u] = 0.0f;
+                continue;
+            }
             if (is_pr) {
                 double acc = 0.0;
                 for (int32_t k = in_ptr[u]; k < in_ptr[u + 1]; ++k) {
@@ -326,6 +532,7 @@ int orc_run(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx,
                 rank_next[u] = nw;
                 changed += fabs(old - nw) > p->epsilon;
                 sum_delta += fabs(old - nw);
+                if (hist_out) hist_out[u] = (float)((double)n * fabs(old - nw));
             } else {
                 uint32_t acc = ORC_INF;
                 for (int32_t k = in_ptr[u]; k < in_ptr[u + 1]; ++k) {
@@ -357,7 +564,17 @@ int orc_run(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx,
                 uint32_t nw = acc < old ? acc : old;
                 val_next[u] = nw;
                 changed += nw < old;
+                if (hist_out) hist_out[u] = nw < old ? 1.0f : 0.0f;
             }
+        }
+        executed += 1;
+        if (tracing) {
+            for (int32_t u = 0; u < n; ++u) {
+                const int y = is_pr ? fabs(rank_next[u] - rank[u]) > p->label_tol * fabs(rank_next[u])
+                                    : val_next[u] < val[u];
+                p->trace_y[o->trace_rows + u] = (uint8_t)y;
+            }
+            o->trace_rows += n;
         }
         if (!correcting) {
             /* nothing to do for the flags */
@@ -405,8 +622,10 @@ int orc_run(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx,
             }
         }
 
+        if (correcting && learned_policy) force_full = learned && changed == 0;
         int stop_on_quiet = !is_pr || (p->flags & ORC_STOP_QUIESCE);
-        if (stop_on_quiet && changed == 0) {
+        if (stop_on_quiet && changed == 0 && !(accurate && learned)) {
+            /* (a quiet learned correction only makes the next correction full) */
             if (accurate) break;                /* fixed point of the full graph */
             /* An approximate iteration that changed nothing leaves the state
              * as it was, so the approximate iterations until the next
@@ -430,6 +649,6 @@ int orc_run(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx,
     rc = 0;
 done:
     free(in_ptr); free(in_src); free(in_w); free(mask); free(new_mask); free(infl); free(outdeg); free(act);
-    free(rank); free(rank_next); free(val); free(val_next);
+    free(rank); free(rank_next); free(val); free(val_next); free(hist); free(sel); free(logit);
     return rc;
 }
