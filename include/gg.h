@@ -60,13 +60,22 @@ typedef enum {
                                      then accurate to the end (Sec. 5.2) */
     GG_POLICY_ADAPTIVE = 3,       /* GG: a correction after every alpha approximate
                                      iterations (Sec. 3.4) */
-    GG_POLICY_TRIGGERED = 4       /* beyond the paper (which notes the correction points could
+    GG_POLICY_TRIGGERED = 4,      /* beyond the paper (which notes the correction points could
                                      vary, Sec. 3.4): a correction follows the approximate
                                      iteration whose change statistic is at most trigger_ratio
                                      times that of the first approximate iteration since the last
                                      correction, or the alpha-th one. Statistic: vertices changed
                                      (SSSP/BFS/CC, exact) or sum |old-new| (PageRank, the
                                      fixed-point sum of gg_iter_stats.sum_delta) */
+    GG_POLICY_LEARNED = 5         /* beyond the paper: the GG schedule, but at a correction the
+                                     scorer set by gg_set_scorer selects the vertices to correct
+                                     (logit > select_logit): they gather over all in-edges and
+                                     recompute their flags; every other vertex keeps its value and
+                                     flags for that iteration. A selection holding more than
+                                     fallback_frac of the arcs runs the full correction instead,
+                                     and so does the correction after a learned one that changed
+                                     no value (min applications: no vertex decreased; PageRank: no
+                                     |old-new| above epsilon) */
 } gg_policy;
 
 typedef enum {
@@ -79,7 +88,8 @@ typedef enum {
     GG_RESULT_CSC_W = 6,      /* uint32[m]: in-edge weights (graphs loaded with weights) */
     GG_RESULT_SPARSE_PTR = 7, /* int32[n+1]: row pointers of the packed active in-edges */
     GG_RESULT_SPARSE_SRC = 8, /* int32[nnz]: sources of the packed active in-edges */
-    GG_RESULT_OUT_TO_IN = 9   /* int32[m]: CSC position of every CSR arc */
+    GG_RESULT_OUT_TO_IN = 9,  /* int32[m]: CSC position of every CSR arc */
+    GG_RESULT_SCORES = 10     /* float[n]: logits of the last learned correction's scoring */
 } gg_result_kind;
 
 /* gg_load_csr gflags */
@@ -101,6 +111,7 @@ typedef enum {
 
 #define GG_INF 0xFFFFFFFFu
 #define GG_ITER_PUSH 0x100u   /* gg_iter_stats.mode bit: iteration done by the push frontier */
+#define GG_ITER_LEARNED 0x200u /* gg_iter_stats.mode bit: a correction of the selected vertices only */
 
 typedef struct {
     uint32_t alpha;       /* approximate window: approximate iterations between corrections (Sec. 3.4) */
@@ -113,6 +124,9 @@ typedef struct {
     uint32_t flags;       /* GG_* flags above */
     float trigger_ratio;  /* GG_POLICY_TRIGGERED: fraction of the window's first change statistic
                              at or below which a correction follows; finite, >= 0 */
+    float select_logit;   /* GG_POLICY_LEARNED: vertices whose logit exceeds this are corrected */
+    float fallback_frac;  /* GG_POLICY_LEARNED: a selection with more in-edges than this x m runs
+                             the full correction (1 = never; < 0 = always) */
 } gg_params;
 
 typedef struct {
@@ -135,6 +149,8 @@ typedef struct {
     uint32_t n_correct;       /* GG_TIMING: launches counted in ms_correct */
     uint32_t n_push;          /* GG_TIMING: launches counted in ms_push */
     uint32_t kernels_launched;/* kernels this library launched during the last gg_run */
+    uint32_t learned_corrections; /* corrections of the selected vertices only (GG_POLICY_LEARNED) */
+    uint64_t trace_rows;      /* rows written to the trace buffers since gg_set_trace */
 } gg_stats;
 
 typedef struct {
@@ -146,6 +162,7 @@ typedef struct {
     uint64_t sum_delta;       /* sum |old-new|: fixed point 2^-40 (PageRank) or exact integer
                                  over vertices that were reached before */
     uint64_t active_after;    /* active arcs after the iteration */
+    uint64_t selected;        /* learned correction: vertices it corrected (else 0) */
 } gg_iter_stats;
 
 typedef struct gg_graph gg_graph;
@@ -243,6 +260,59 @@ const char *gg_last_error(void);
  * make that first call before any stream capture. Sizes above the limit
  * return GG_ERR_INVALID_ARG. Returns after enqueueing the work.
  */
+/*
+ * Learned correction (beyond the paper). The scorer is a per-vertex MLP
+ * 8 -> 64 -> 64 -> 1 with ReLU after both hidden layers; its parameters are
+ * GG_MLP_NPARAM floats, row-major: W1[64][8], b1[64], W2[64][64], b2[64],
+ * w3[64], b3. Arithmetic: weights and each layer's inputs rounded to
+ * bfloat16 (nearest even), products accumulated in FP32 on the tensor cores,
+ * FP32 biases. Vertex features (FP32, in this order): sqrt(in-degree)/64,
+ * sqrt(out-degree)/64, the change feature of the last three executed
+ * iterations, newest first (PageRank: n |old - new|; SSSP / BFS / CC: 1 if the
+ * value decreased, else 0; 0 before the run's start), the active fraction
+ * of the in-edges (1 without in-edges), iteration / 64, application id.
+ */
+#define GG_MLP_NPARAM 4801
+
+/* gg_set_scorer - copy host params[GG_MLP_NPARAM] into g for GG_POLICY_LEARNED. */
+gg_status gg_set_scorer(gg_graph *g, const float *params);
+
+/*
+ * gg_set_trace - record training rows during later runs of g: at every full
+ * correction, the features of all n vertices (device features[cap_rows][8])
+ * before it and their labels (device labels[cap_rows], 0/1) after it: a
+ * PageRank vertex is labelled 1 if |new - old| > label_tol * |new| (FP32), a
+ * min-application vertex if its value decreased. Rows are appended (c*n + u)
+ * across runs while cap_rows has room for all n; the count is
+ * gg_stats.trace_rows. The buffers stay the caller's; features = NULL stops
+ * recording.
+ */
+gg_status gg_set_trace(gg_graph *g, float *features, uint8_t *labels, uint64_t cap_rows, float label_tol);
+
+/*
+ * gg_mlp_score - logits of rows feature rows (device features[rows][8], 8-byte
+ * aligned) into device logits[rows], with device params[GG_MLP_NPARAM].
+ * Enqueued on stream (NULL = legacy default stream).
+ */
+gg_status gg_mlp_score(const float *features, uint64_t rows, const float *params, float *logits, void *stream);
+
+/*
+ * gg_mlp_train - `steps` steps of minibatch SGD on the mean logistic loss,
+ * in one block: step s uses rows ((start + s*batch + j) mod rows) * stride
+ * mod rows, j < batch (stride coprime to rows makes this a permutation).
+ * Forward in the scorer's arithmetic; gradients in FP32 with the bfloat16
+ * rounding treated as the identity, summed in row order (deterministic).
+ *   features  device float[rows][8]; labels device uint8[rows] (0 / 1)
+ *   rows      1 .. 2^32-1; stride < rows
+ *   params    device float[GG_MLP_NPARAM], updated in place (FP32 masters)
+ *   batch     1 .. 128
+ *   losses    device float[steps] (nullable): each step's mean loss
+ *   grad_last device float[GG_MLP_NPARAM] (nullable): the last step's gradient
+ */
+gg_status gg_mlp_train(const float *features, const uint8_t *labels, uint64_t rows, float *params,
+                       uint32_t batch, uint32_t steps, float lr, uint64_t stride, uint64_t start,
+                       float *losses, float *grad_last, void *stream);
+
 #define GG_NOALLOC_MAX_ITEMS (1u << 24)
 gg_status gg_sample_csc_noalloc(int32_t n, int64_t m, const int32_t *in_ptr, const int32_t *in_src,
                                 double sample_ratio, uint64_t seed, int symmetric, uint32_t *mask,

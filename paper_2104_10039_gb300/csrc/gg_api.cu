@@ -63,7 +63,9 @@ static int policy_mode(gg_policy p, uint32_t alpha, uint32_t i)
     case GG_POLICY_NONE: return MODE_APPROX;
     case GG_POLICY_STATIC_SWITCH:
         return i < alpha ? MODE_APPROX : (i == alpha ? MODE_CORRECTION : MODE_ACCURATE);
-    case GG_POLICY_ADAPTIVE: return (i % (alpha + 1u)) == alpha ? MODE_CORRECTION : MODE_APPROX;
+    case GG_POLICY_ADAPTIVE:
+    case GG_POLICY_LEARNED: return (i % (alpha + 1u)) == alpha ? MODE_CORRECTION : MODE_APPROX;
+    default: break;
     }
     return MODE_ACCURATE;
 }
@@ -74,7 +76,7 @@ static int64_t next_accurate(gg_policy p, uint32_t alpha, uint32_t i)
 {
     if (p == GG_POLICY_NONE) return -1;
     if (p == GG_POLICY_STATIC_SWITCH) return i < alpha ? (int64_t)alpha : (int64_t)i + 1;
-    if (p == GG_POLICY_ADAPTIVE) {
+    if (p == GG_POLICY_ADAPTIVE || p == GG_POLICY_LEARNED) {
         const uint64_t period = (uint64_t)alpha + 1u;
         return (int64_t)(((uint64_t)i / period) * period + alpha);
     }
@@ -247,10 +249,177 @@ static gg_status refresh_active_outdeg(gg_graph *g)
     return GG_OK;
 }
 
+#define GG_ALLOC_BUF(buf, bytes)                                  \
+    do {                                                          \
+        const gg_status s_ = (buf).alloc((bytes), g->stream);     \
+        if (s_ != GG_OK) return s_;                               \
+    } while (0)
+
+// Read a device scalar (synchronises the stream).
+static gg_status read_u32(gg_graph *g, const uint32_t *d, uint32_t *h)
+{
+    GG_CUDA(cudaMemcpyAsync(h, d, sizeof(uint32_t), cudaMemcpyDeviceToHost, g->stream));
+    GG_CUDA(cudaStreamSynchronize(g->stream));
+    return GG_OK;
+}
+
+// ---------------------------------------------- learned correction, traces --
+static gg_status ensure_hist(gg_graph *g)
+{
+    if (!g->hist) {
+        GG_ALLOC_BUF(g->b_hist, 4 * 3 * (size_t)g->n);
+        g->hist = g->b_hist.f32();
+    }
+    GG_CUDA(cudaMemsetAsync(g->hist, 0, 4 * 3 * (size_t)g->n, g->stream));
+    return GG_OK;
+}
+
+static gg_status ensure_learned(gg_graph *g)
+{
+    if (g->sel_flag) return GG_OK;
+    const size_t n = (size_t)g->n, m = (size_t)g->m;
+    GG_ALLOC_BUF(g->b_sel, 4 * (6 * n + 8));
+    GG_ALLOC_BUF(g->b_sub, 4 * (3 * m + m / 32 + 4));
+    GG_ALLOC_BUF(g->b_sub_tiles, 4 * ((size_t)g->max_tiles + 4));
+    uint32_t *s = g->b_sel.u32();
+    g->sel_flag = s;
+    g->sel_pos = s + n;               // n + 1
+    g->sel_off = s + 2 * n + 1;       // n + 1
+    g->sel_rows = (int32_t *)(s + 3 * n + 2);
+    g->sub_ptr = (int32_t *)(s + 4 * n + 2);   // n + 1
+    g->logits = (float *)(s + 5 * n + 3);
+    g->sel_counts = s + 6 * n + 4;    // 2
+    uint32_t *b = g->b_sub.u32();
+    g->sub_src = (int32_t *)b;
+    g->sub_w = b + m;
+    g->sub_pos = (int32_t *)(b + 2 * m);
+    g->sub_mask = b + 3 * m;
+    g->sub_tile_info = g->b_sub_tiles.i32();
+    g->sub_num_tiles = g->b_sub_tiles.u32() + g->max_tiles + 2;
+    return GG_OK;
+}
+
+// Change-feature slot of the iteration about to execute (or nullptr).
+static float *hist_slot(gg_graph *g)
+{
+    return g->keep_hist ? g->hist + (size_t)(g->executed % 3u) * (size_t)g->n : nullptr;
+}
+
+static FeatArgs feat_args(gg_graph *g, gg_app app, uint32_t i)
+{
+    FeatArgs fa{};
+    fa.n = g->n;
+    fa.in_ptr = g->in_ptr;
+    fa.out_ptr = g->out_ptr;
+    fa.sp_ptr = g->sp_ptr;
+    const uint32_t e = g->executed;
+    fa.hist1 = g->hist + (size_t)((e + 2u) % 3u) * (size_t)g->n;
+    fa.hist2 = g->hist + (size_t)((e + 1u) % 3u) * (size_t)g->n;
+    fa.hist3 = g->hist + (size_t)(e % 3u) * (size_t)g->n;
+    fa.iter_f = (float)i * 0.015625f;
+    fa.app_f = (float)app;
+    return fa;
+}
+
+// Trace rows of a full correction: features now (before it runs).
+static gg_status trace_features(gg_graph *g, gg_app app, uint32_t i, bool *tracing)
+{
+    *tracing = g->trace_x && g->trace_rows + (uint64_t)g->n <= g->trace_cap;
+    if (!*tracing) return GG_OK;
+    GG_CUDA(launch_trace_features(feat_args(g, app, i), g->trace_x + g->trace_rows * 8, g->num_sms, g->stream));
+    g->launches += 1;
+    return GG_OK;
+}
+
+// ... and labels once the correction has produced the next values.
+static gg_status trace_labels(gg_graph *g, bool pr)
+{
+    const int c = g->cur, nx = g->cur ^ 1;
+    GG_CUDA(launch_trace_labels(g->n, pr ? g->rank[c] : nullptr, pr ? g->rank[nx] : nullptr, pr ? nullptr : g->val[c],
+                                pr ? nullptr : g->val[nx], g->label_tol, g->trace_y + g->trace_rows, g->num_sms,
+                                g->stream));
+    g->launches += 1;
+    g->trace_rows += (uint64_t)g->n;
+    return GG_OK;
+}
+
+// Learned correction, selection: score every vertex, compact the selected
+// rows and their in-edge offsets; *learned = the selection is small enough
+// (else the full correction runs).
+static gg_status learned_select(gg_graph *g, gg_app app, const gg_params *p, uint32_t i, bool *learned,
+                                uint32_t *nsel, uint32_t *total)
+{
+    *learned = false;
+    GG_CUDA(launch_mlp_select(feat_args(g, app, i), g->mlp, p->select_logit, g->sel_flag, g->sel_off, g->logits,
+                              g->num_sms, g->stream));
+    GG_CUDA(launch_scan_u32(g->sel_flag, g->sel_pos, (size_t)g->n, g->scan_tmp, g->stream));
+    GG_CUDA(launch_scan_u32(g->sel_off, g->sel_off, (size_t)g->n, g->scan_tmp, g->stream));
+    GG_CUDA(launch_sel_compact(g->n, g->sel_flag, g->sel_pos, g->sel_off, g->sel_rows, g->sub_ptr, g->sel_counts,
+                               g->num_sms, g->stream));
+    g->launches += 8;
+    g->logits_valid = true;
+    uint32_t counts[2] = {0, 0};
+    GG_CUDA(cudaMemcpyAsync(counts, g->sel_counts, sizeof counts, cudaMemcpyDeviceToHost, g->stream));
+    GG_CUDA(cudaStreamSynchronize(g->stream));
+    *nsel = counts[0];
+    *total = counts[1];
+    *learned = !((double)counts[1] > (double)p->fallback_frac * (double)g->m);
+    return GG_OK;
+}
+
+// Learned correction, the corrected rows: every vertex keeps its value, then
+// the correction kernels walk the selected rows' sub-list and overwrite
+// theirs; the new flags go back to the full bitmap, whose tile counts are
+// recounted for the pack. `a` carries the application's fields.
+static gg_status learned_correct(gg_graph *g, gg_app app, TileArgs a, uint32_t nsel, uint32_t total)
+{
+    const bool pr = app == GG_APP_PAGERANK;
+    const bool weighted = app == GG_APP_SSSP && g->has_w;
+    GG_CUDA(launch_sub_copy(g->sub_ptr, (int32_t)nsel, total, g->sel_rows, g->in_ptr, g->in_src,
+                            weighted ? g->in_w : nullptr, g->mask, g->sub_src, g->sub_w, g->sub_pos, g->sub_mask,
+                            g->stream));
+    const uint32_t sub_tiles = (uint32_t)(((uint64_t)nsel + total + kWT - 1) / kWT) + 1;
+    GG_CUDA(launch_partition(g->sub_ptr, (int32_t)nsel, g->sel_counts + 1, sub_tiles, g->sub_tile_info,
+                             g->sub_num_tiles, g->stream));
+    float *hs = hist_slot(g);
+    const int c = g->cur, nx = g->cur ^ 1;
+    GG_CUDA(launch_keep_values(g->n, pr ? g->rank[c] : nullptr, pr ? g->rank[nx] : nullptr,
+                               pr ? g->contrib[c] : nullptr, pr ? g->contrib[nx] : nullptr,
+                               pr ? nullptr : g->val[c], pr ? nullptr : g->val[nx], hs, g->num_sms, g->stream));
+    a.row_ptr = g->sub_ptr;
+    a.arc_src = g->sub_src;
+    a.arc_w = weighted ? g->sub_w : nullptr;
+    a.n = (int32_t)nsel;
+    a.list_nnz = g->sel_counts + 1;
+    a.tile_info = g->sub_tile_info;
+    a.num_tiles = g->sub_num_tiles;
+    a.row_vtx = g->sel_rows;
+    a.mask = g->sub_mask;
+    a.sp_ptr = nullptr;
+    a.tile_cnt = nullptr;
+    a.hist_out = hs;
+    a.epoch = next_epoch(g);
+    if (nsel > 0) {
+        if (pr) GG_CUDA(launch_tile_pr(K_CORRECT, a, (int)sub_tiles, g->num_sms, g->stream));
+        else GG_CUDA(launch_tile_min((int)app, K_CORRECT, a, (int)sub_tiles, g->num_sms, g->stream));
+    }
+    GG_CUDA(launch_scatter_flags(g->sub_pos, g->sub_mask, total, g->mask, g->num_sms, g->stream));
+    TileArgs r{};
+    fill_list(g, false, r);
+    r.mask = g->mask;
+    r.sp_ptr = g->sp_ptr;
+    r.epoch = next_epoch(g);
+    GG_CUDA(launch_tile_recount(r, (int)g->max_tiles, g->num_sms, g->stream));
+    g->launches += 8;
+    g->stats.learned_corrections += 1;
+    return GG_OK;
+}
+
 static gg_status run_pagerank(gg_graph *g, gg_policy policy, const gg_params *p)
 {
     const bool timing = (p->flags & GG_TIMING) != 0;
     const bool renorm = (p->flags & GG_RENORM) != 0 && policy != GG_POLICY_EXACT;
+    const bool learned_policy = policy == GG_POLICY_LEARNED;
     Trigger trig(policy, p);
     g->cur = 0;
     GG_CUDA(launch_init_pr(g->n, g->out_ptr, g->rank[0], g->contrib[0], g->num_sms, g->stream));
@@ -283,18 +452,44 @@ static gg_status run_pagerank(gg_graph *g, gg_policy policy, const gg_params *p)
         a.epsilon = p->epsilon;
         a.epoch = next_epoch(g);
         a.stats = g->iter_stats + i;
+        a.hist_out = hist_slot(g);
+        a.n_f = (float)g->n;
         if (kind == K_CORRECT) {
             a.mask = g->mask;
             a.sp_ptr = g->sp_ptr;
             a.theta = p->theta;
         }
-        GG_CUDA(launch_iter_header(a.stats, (uint32_t)mode, a.list_nnz, 0, g->stream));
+        bool learned = false;
+        uint32_t nsel = 0, sel_arcs = 0;
+        if (kind == K_CORRECT && learned_policy && !g->force_full) {
+            gg_status st = learned_select(g, GG_APP_PAGERANK, p, i, &learned, &nsel, &sel_arcs);
+            if (st != GG_OK) return st;
+        }
         size_t slot;
-        timed_begin(g, timing, kind == K_CORRECT ? 1 : 0, &slot);
-        GG_CUDA(launch_tile_pr(kind, a, (int)g->max_tiles, g->num_sms, g->stream));
-        if (kind == K_GATHER) GG_CUDA(launch_fixup(GG_APP_PAGERANK, a, (int)g->max_tiles, g->num_sms, g->stream));
-        timed_end(g, slot);
-        g->launches += 3;
+        if (learned) {
+            GG_CUDA(launch_iter_header(a.stats, (uint32_t)mode | GG_ITER_LEARNED, nullptr, sel_arcs, g->stream, nsel));
+            timed_begin(g, timing, 1, &slot);
+            gg_status st = learned_correct(g, GG_APP_PAGERANK, a, nsel, sel_arcs);
+            if (st != GG_OK) return st;
+            timed_end(g, slot);
+            g->launches += 1;
+        } else {
+            bool tracing = false;
+            if (kind == K_CORRECT) {
+                gg_status st = trace_features(g, GG_APP_PAGERANK, i, &tracing);
+                if (st != GG_OK) return st;
+            }
+            GG_CUDA(launch_iter_header(a.stats, (uint32_t)mode, a.list_nnz, 0, g->stream));
+            timed_begin(g, timing, kind == K_CORRECT ? 1 : 0, &slot);
+            GG_CUDA(launch_tile_pr(kind, a, (int)g->max_tiles, g->num_sms, g->stream));
+            if (kind == K_GATHER) GG_CUDA(launch_fixup(GG_APP_PAGERANK, a, (int)g->max_tiles, g->num_sms, g->stream));
+            timed_end(g, slot);
+            g->launches += 3;
+            if (tracing) {
+                gg_status st = trace_labels(g, true);
+                if (st != GG_OK) return st;
+            }
+        }
         if (kind == K_CORRECT) {
             gg_status st = finish_pack(g, false, a.stats);
             if (st != GG_OK) return st;
@@ -309,10 +504,21 @@ static gg_status run_pagerank(gg_graph *g, gg_policy policy, const gg_params *p)
                     g->launches += 1;
                 }
             }
+            if (learned_policy) {
+                // a learned correction that changed no value makes the next one full
+                unsigned long long changed = 0;
+                if (learned) {
+                    GG_CUDA(cudaMemcpyAsync(&changed, &g->iter_stats[i].changed, sizeof changed,
+                                            cudaMemcpyDeviceToHost, g->stream));
+                    GG_CUDA(cudaStreamSynchronize(g->stream));
+                }
+                g->force_full = learned && changed == 0;
+            }
         }
         g->stats.pull_iterations += 1;
         g->cur ^= 1;
         g->iterations = i + 1;
+        g->executed += 1;
         if (trig.on) {
             double metric = 0.0;
             if (mode == MODE_APPROX) {
@@ -331,7 +537,7 @@ static gg_status run_pagerank(gg_graph *g, gg_policy policy, const gg_params *p)
                 g->launches += 1;
             }
         }
-        if ((p->flags & GG_STOP_QUIESCE) && mode != MODE_APPROX) {
+        if ((p->flags & GG_STOP_QUIESCE) && mode != MODE_APPROX && !learned) {
             unsigned long long changed = 0;
             GG_CUDA(cudaMemcpyAsync(&changed, &g->iter_stats[i].changed, sizeof changed, cudaMemcpyDeviceToHost,
                                     g->stream));
@@ -339,14 +545,6 @@ static gg_status run_pagerank(gg_graph *g, gg_policy policy, const gg_params *p)
             if (changed == 0) break;
         }
     }
-    return GG_OK;
-}
-
-// Read a device scalar (synchronises the stream).
-static gg_status read_u32(gg_graph *g, const uint32_t *d, uint32_t *h)
-{
-    GG_CUDA(cudaMemcpyAsync(h, d, sizeof(uint32_t), cudaMemcpyDeviceToHost, g->stream));
-    GG_CUDA(cudaStreamSynchronize(g->stream));
     return GG_OK;
 }
 
@@ -367,6 +565,7 @@ static gg_status frontier_degrees(gg_graph *g, int qc, uint32_t qlen, uint64_t *
 static gg_status run_min(gg_graph *g, gg_app app, gg_policy policy, const gg_params *p)
 {
     const bool timing = (p->flags & GG_TIMING) != 0;
+    const bool learned_policy = policy == GG_POLICY_LEARNED;
     g->cur = 0;
     int qc = 0;
     GG_CUDA(launch_init_min(g->n, (int)app, p->source, g->val[0], g->q[0], g->q_val[0], &g->q_len[0], g->num_sms,
@@ -396,14 +595,16 @@ static gg_status run_min(gg_graph *g, gg_app app, gg_policy policy, const gg_par
         bool push = mode != MODE_CORRECTION && !(p->flags & GG_FORCE_PULL) &&
                     ((p->flags & GG_FORCE_PUSH) || front_arcs * kPushFactor < list_nnz);
         IterStatsDev *sti = g->iter_stats + i;
-        GG_CUDA(launch_iter_header(sti, (uint32_t)mode | (push ? GG_ITER_PUSH : 0u), nullptr, list_nnz,
-                                   g->stream));
-        g->launches += 1;
+        float *hs = hist_slot(g);
+        bool learned = false;
         if (push) {
+            GG_CUDA(launch_iter_header(sti, (uint32_t)mode | GG_ITER_PUSH, nullptr, list_nnz, g->stream));
+            g->launches += 1;
             if (++g->stamp_tag == 0) {
                 GG_CUDA(cudaMemsetAsync(g->stamp, 0, sizeof(uint32_t) * g->n, g->stream));
                 g->stamp_tag = 1;
             }
+            if (hs) GG_CUDA(cudaMemsetAsync(hs, 0, sizeof(float) * g->n, g->stream));
             PushArgs pa{};
             pa.q = g->q[qc];
             pa.q_val = g->q_val[qc];
@@ -426,7 +627,7 @@ static gg_status run_min(gg_graph *g, gg_app app, gg_policy policy, const gg_par
             timed_begin(g, timing, 2, &slot);
             GG_CUDA(launch_push(pa, (uint32_t)front_arcs, g->num_sms * 8, g->stream));
             timed_end(g, slot);
-            GG_CUDA(launch_snapshot(g->q[nq], &g->q_len[nq], g->val[g->cur], g->q_val[nq], (uint32_t)g->n,
+            GG_CUDA(launch_snapshot(g->q[nq], &g->q_len[nq], g->val[g->cur], g->q_val[nq], hs, (uint32_t)g->n,
                                     g->num_sms, g->stream));
             GG_CUDA(launch_iter_changed(sti, &g->q_len[nq], g->stream));
             g->launches += 3;
@@ -442,6 +643,7 @@ static gg_status run_min(gg_graph *g, gg_app app, gg_policy policy, const gg_par
             a.q_out = g->q[nq];
             a.q_out_val = g->q_val[nq];
             a.q_out_len = &g->q_len[nq];
+            a.hist_out = hs;
             if (app != GG_APP_SSSP) a.arc_w = nullptr;
             if (kind == K_CORRECT) {
                 a.mask = g->mask;
@@ -450,12 +652,37 @@ static gg_status run_min(gg_graph *g, gg_app app, gg_policy policy, const gg_par
                 a.theta_fx = theta_fx;
                 a.est_strict = (p->flags & GG_EST_STRICT) ? 1 : 0;
             }
+            uint32_t nsel = 0, sel_arcs = 0;
+            if (kind == K_CORRECT && learned_policy && !g->force_full) {
+                st = learned_select(g, app, p, i, &learned, &nsel, &sel_arcs);
+                if (st != GG_OK) return st;
+            }
             size_t slot;
-            timed_begin(g, timing, kind == K_CORRECT ? 1 : 0, &slot);
-            GG_CUDA(launch_tile_min((int)app, kind, a, (int)g->max_tiles, g->num_sms, g->stream));
-            if (kind == K_GATHER) GG_CUDA(launch_fixup((int)app, a, (int)g->max_tiles, g->num_sms, g->stream));
-            timed_end(g, slot);
-            g->launches += 2;
+            if (learned) {
+                GG_CUDA(launch_iter_header(sti, (uint32_t)mode | GG_ITER_LEARNED, nullptr, sel_arcs, g->stream,
+                                           nsel));
+                timed_begin(g, timing, 1, &slot);
+                st = learned_correct(g, app, a, nsel, sel_arcs);
+                if (st != GG_OK) return st;
+                timed_end(g, slot);
+                g->launches += 1;
+            } else {
+                bool tracing = false;
+                if (kind == K_CORRECT) {
+                    st = trace_features(g, app, i, &tracing);
+                    if (st != GG_OK) return st;
+                }
+                GG_CUDA(launch_iter_header(sti, (uint32_t)mode, nullptr, list_nnz, g->stream));
+                timed_begin(g, timing, kind == K_CORRECT ? 1 : 0, &slot);
+                GG_CUDA(launch_tile_min((int)app, kind, a, (int)g->max_tiles, g->num_sms, g->stream));
+                if (kind == K_GATHER) GG_CUDA(launch_fixup((int)app, a, (int)g->max_tiles, g->num_sms, g->stream));
+                timed_end(g, slot);
+                g->launches += 3;
+                if (tracing) {
+                    st = trace_labels(g, false);
+                    if (st != GG_OK) return st;
+                }
+            }
             if (kind == K_CORRECT) {
                 st = finish_pack(g, app == GG_APP_SSSP && g->has_w, sti);
                 if (st != GG_OK) return st;
@@ -467,12 +694,25 @@ static gg_status run_min(gg_graph *g, gg_app app, gg_policy policy, const gg_par
             g->cur ^= 1;
             g->stats.pull_iterations += 1;
         }
+        const uint32_t prev_qlen = qlen;
+        const int prev_qc = qc;
         qc = nq;
         st = read_u32(g, &g->q_len[qc], &qlen);
         if (st != GG_OK) return st;
         g->iterations = i + 1;
+        g->executed += 1;
         trig.after(mode == MODE_CORRECTION, (double)qlen);
-        if (qlen == 0) {
+        if (learned_policy && mode == MODE_CORRECTION) g->force_full = learned && qlen == 0;
+        if (learned && prev_qlen > 0) {
+            // the rows left alone did not gather the previous iteration's
+            // changes: the next frontier takes those vertices too
+            GG_CUDA(launch_append_frontier(g->q[prev_qc], prev_qlen, hs, g->val[g->cur], g->q[qc], g->q_val[qc],
+                                           &g->q_len[qc], g->num_sms, g->stream));
+            g->launches += 1;
+            st = read_u32(g, &g->q_len[qc], &qlen);
+            if (st != GG_OK) return st;
+        }
+        if (qlen == 0 && !learned) {
             // Quiet iteration: an accurate one means a fixed point of the full
             // graph; an approximate one makes every approximate iteration up to
             // the next accurate one a no-op (skipped, still counted).
@@ -506,7 +746,14 @@ gg_status run(gg_graph *g, gg_app app, double ratio, gg_policy policy, const gg_
 {
     if (!p) { set_error("gg_run: params is NULL"); return GG_ERR_INVALID_ARG; }
     if ((int)app < GG_APP_PAGERANK || (int)app > GG_APP_CC) { set_error("gg_run: unknown app %d", (int)app); return GG_ERR_INVALID_ARG; }
-    if ((int)policy < GG_POLICY_EXACT || (int)policy > GG_POLICY_TRIGGERED) { set_error("gg_run: unknown policy %d", (int)policy); return GG_ERR_INVALID_ARG; }
+    if ((int)policy < GG_POLICY_EXACT || (int)policy > GG_POLICY_LEARNED) { set_error("gg_run: unknown policy %d", (int)policy); return GG_ERR_INVALID_ARG; }
+    if (policy == GG_POLICY_LEARNED) {
+        if (!g->has_scorer) { set_error("gg_run: GG_POLICY_LEARNED needs a scorer (gg_set_scorer)"); return GG_ERR_STATE; }
+        if (p->fallback_frac != p->fallback_frac || p->select_logit != p->select_logit) {
+            set_error("gg_run: select_logit / fallback_frac is NaN");
+            return GG_ERR_INVALID_ARG;
+        }
+    }
     if (policy == GG_POLICY_TRIGGERED && !(p->trigger_ratio >= 0.0f && p->trigger_ratio <= 3.0e38f)) {
         set_error("gg_run: trigger_ratio must be finite and >= 0");
         return GG_ERR_INVALID_ARG;
@@ -539,6 +786,17 @@ gg_status run(gg_graph *g, gg_app app, double ratio, gg_policy policy, const gg_
     g->launches = 0;
     g->iterations = 0;
     g->last_app = -1;
+    g->executed = 0;
+    g->force_full = false;
+    g->keep_hist = policy == GG_POLICY_LEARNED || g->trace_x != nullptr;
+    if (g->keep_hist) {
+        st = ensure_hist(g);
+        if (st != GG_OK) return st;
+    }
+    if (policy == GG_POLICY_LEARNED) {
+        st = ensure_learned(g);
+        if (st != GG_OK) return st;
+    }
     GG_CUDA(cudaMemsetAsync(g->dev_err, 0, sizeof(uint32_t), g->stream));
     GG_CUDA(cudaEventRecord(g->ev_run0, g->stream));
     if (policy != GG_POLICY_EXACT &&
@@ -768,6 +1026,7 @@ static size_t result_size(gg_graph *g, gg_result_kind kind, const void **src)
         *src = g->sp_src;
         return 4 * (size_t)g->sp_nnz_host;
     case GG_RESULT_OUT_TO_IN: *src = g->out_to_in; return 4 * m;
+    case GG_RESULT_SCORES: if (!g->logits_valid) return 0; *src = g->logits; return 4 * n;
     }
     return 0;
 }
@@ -798,6 +1057,7 @@ static gg_status fill_stats(gg_graph *g)
     if (g->sampled && !g->sample_clean) cudaMemcpy(&nnz, g->sp_nnz, 4, cudaMemcpyDeviceToHost);
     else if (g->sampled) cudaMemcpy(&nnz, g->sp_nnz, 4, cudaMemcpyDeviceToHost);
     s.active_arcs = nnz;
+    s.trace_rows = g->trace_rows;
     uint32_t err = 0;
     cudaMemcpy(&err, g->dev_err, 4, cudaMemcpyDeviceToHost);
     s.device_error = err;
@@ -827,7 +1087,7 @@ gg_status gg_result(gg_graph *g, gg_result_kind kind, void *dst, size_t bytes, i
             return GG_ERR_TIMEOUT;
         }
     }
-    if ((int)kind < GG_RESULT_VALUES || (int)kind > GG_RESULT_OUT_TO_IN) {
+    if ((int)kind < GG_RESULT_VALUES || (int)kind > GG_RESULT_SCORES) {
         set_error("gg_result: unknown kind %d", (int)kind);
         return GG_ERR_INVALID_ARG;
     }
@@ -876,5 +1136,64 @@ void gg_free_graph(gg_graph *g)
 }
 
 const char *gg_last_error(void) { return g_err; }
+
+gg_status gg_set_scorer(gg_graph *g, const float *params)
+{
+    if (!g || !params) { set_error("gg_set_scorer: graph or params is NULL"); return GG_ERR_INVALID_ARG; }
+    if (!g->mlp) {
+        GG_ALLOC_BUF(g->b_mlp, 4 * (size_t)GG_MLP_NPARAM);
+        g->mlp = g->b_mlp.f32();
+    }
+    GG_CUDA(cudaMemcpyAsync(g->mlp, params, 4 * (size_t)GG_MLP_NPARAM, cudaMemcpyHostToDevice, g->stream));
+    GG_CUDA(cudaStreamSynchronize(g->stream));
+    g->has_scorer = true;
+    return GG_OK;
+}
+
+gg_status gg_set_trace(gg_graph *g, float *features, uint8_t *labels, uint64_t cap_rows, float label_tol)
+{
+    if (!g) { set_error("gg_set_trace: graph is NULL"); return GG_ERR_INVALID_ARG; }
+    if (features && !labels) { set_error("gg_set_trace: labels is NULL"); return GG_ERR_INVALID_ARG; }
+    if (!(label_tol >= 0.0f && label_tol <= 3.0e38f)) {
+        set_error("gg_set_trace: label_tol must be finite and >= 0");
+        return GG_ERR_INVALID_ARG;
+    }
+    if (features && (((uintptr_t)features) & 7u)) { set_error("gg_set_trace: features must be 8-byte aligned"); return GG_ERR_INVALID_ARG; }
+    g->trace_x = features;
+    g->trace_y = features ? labels : nullptr;
+    g->trace_cap = features ? cap_rows : 0;
+    g->trace_rows = 0;
+    g->label_tol = label_tol;
+    return GG_OK;
+}
+
+gg_status gg_mlp_score(const float *features, uint64_t rows, const float *params, float *logits, void *stream)
+{
+    if (rows == 0) return GG_OK;
+    if (!features || !params || !logits) { set_error("gg_mlp_score: NULL argument"); return GG_ERR_INVALID_ARG; }
+    if (((uintptr_t)features) & 7u) { set_error("gg_mlp_score: features must be 8-byte aligned"); return GG_ERR_INVALID_ARG; }
+    if (rows > ((uint64_t)1 << 40)) { set_error("gg_mlp_score: too many rows"); return GG_ERR_INVALID_ARG; }
+    int dev = 0, sms = 0;
+    GG_CUDA(cudaGetDevice(&dev));
+    GG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    GG_CUDA(launch_mlp_score(features, (long long)rows, params, logits, sms, (cudaStream_t)stream));
+    return GG_OK;
+}
+
+gg_status gg_mlp_train(const float *features, const uint8_t *labels, uint64_t rows, float *params, uint32_t batch,
+                       uint32_t steps, float lr, uint64_t stride, uint64_t start, float *losses, float *grad_last,
+                       void *stream)
+{
+    if (!features || !labels || !params) { set_error("gg_mlp_train: NULL argument"); return GG_ERR_INVALID_ARG; }
+    if (rows < 1 || rows > 0xFFFFFFFFull) { set_error("gg_mlp_train: rows must be in [1, 2^32)"); return GG_ERR_INVALID_ARG; }
+    if (batch < 1 || batch > 128) { set_error("gg_mlp_train: batch must be in [1, 128]"); return GG_ERR_INVALID_ARG; }
+    if (stride >= rows && rows > 1) { set_error("gg_mlp_train: stride must be < rows"); return GG_ERR_INVALID_ARG; }
+    if (!(lr == lr)) { set_error("gg_mlp_train: lr is NaN"); return GG_ERR_INVALID_ARG; }
+    if (((uintptr_t)features) & 7u) { set_error("gg_mlp_train: features must be 8-byte aligned"); return GG_ERR_INVALID_ARG; }
+    if (steps == 0) return GG_OK;
+    GG_CUDA(launch_mlp_train(features, labels, rows, params, (int)batch, (int)steps, lr, rows > 1 ? stride : 0,
+                             start, losses, grad_last, (cudaStream_t)stream));
+    return GG_OK;
+}
 
 }  // extern "C"

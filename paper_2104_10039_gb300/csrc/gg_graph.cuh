@@ -130,6 +130,28 @@ struct gg_graph {
     size_t timed_used = 0;
     uint32_t launches = 0;
     uint32_t load_launches = 0;
+    // learned correction: scorer, change features of the last three executed
+    // iterations, selection and the selected rows' sub-list
+    gg::DevBuf b_mlp, b_hist, b_sel, b_sub, b_sub_tiles;
+    float *mlp = nullptr;
+    bool has_scorer = false;
+    float *hist = nullptr;           // 3 x n
+    bool keep_hist = false;          // this run keeps change features
+    uint32_t executed = 0;           // iterations executed in this run
+    bool force_full = false;         // the next correction is a full one
+    uint32_t *sel_flag = nullptr, *sel_pos = nullptr, *sel_off = nullptr, *sel_counts = nullptr;
+    int32_t *sel_rows = nullptr, *sub_ptr = nullptr;
+    float *logits = nullptr;
+    bool logits_valid = false;
+    int32_t *sub_src = nullptr, *sub_pos = nullptr;
+    uint32_t *sub_w = nullptr, *sub_mask = nullptr;
+    int32_t *sub_tile_info = nullptr;
+    uint32_t *sub_num_tiles = nullptr;
+    // training trace (caller-owned device buffers)
+    float *trace_x = nullptr;
+    uint8_t *trace_y = nullptr;
+    uint64_t trace_cap = 0, trace_rows = 0;
+    float label_tol = 0.0f;
 };
 
 namespace gg {

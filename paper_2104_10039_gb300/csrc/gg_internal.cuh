@@ -50,6 +50,7 @@ struct IterStatsDev {
     unsigned long long changed;
     unsigned long long sum_delta;
     unsigned long long active_after;
+    unsigned long long selected;
 };
 static_assert(sizeof(IterStatsDev) == sizeof(gg_iter_stats), "stats layout");
 
@@ -107,11 +108,31 @@ struct TileArgs {
     int32_t *q_out;
     uint32_t *q_out_val;
     uint32_t *q_out_len;
+    // learned correction: the vertex of every list row (nullptr: row = vertex),
+    // and the change feature of every applied vertex (nullptr: not kept)
+    const int32_t *row_vtx;
+    float *hist_out;
+    float n_f;                  // vertex count (PageRank change feature = n |old - new|)
 };
 
 // K_GATHER: approximate / accurate pull iteration. K_STASH + K_CORRECT: the
 // two launches of a correction iteration. K_SAMPLE: sparsification.
-enum TileKind { K_GATHER = 0, K_CORRECT = 1, K_SAMPLE = 2, K_STASH = 3 };
+// K_RECOUNT: tile counts and tile-local row ends of the flags already in the
+// bitmap (after a learned correction rewrote some rows' flags).
+enum TileKind { K_GATHER = 0, K_CORRECT = 1, K_SAMPLE = 2, K_STASH = 3, K_RECOUNT = 4 };
+
+// Inputs of the learned correction's vertex features.
+struct FeatArgs {
+    int32_t n;
+    const int32_t *in_ptr;
+    const int32_t *out_ptr;
+    const int32_t *sp_ptr;      // packed active in-edges (current flags)
+    const float *hist1;         // change features of the last three executed iterations, newest first
+    const float *hist2;
+    const float *hist3;
+    float iter_f;               // iteration / 64
+    float app_f;                // application id
+};
 
 struct PushArgs {
     const int32_t *q;           // frontier vertices
@@ -227,6 +248,7 @@ cudaError_t launch_pack(const int32_t *tile_info, const uint32_t *tile_off, uint
 cudaError_t launch_tile_pr(int kind, const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s);
 cudaError_t launch_tile_min(int app, int kind, const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s);
 cudaError_t launch_tile_sample(const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s);
+cudaError_t launch_tile_recount(const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s);
 // Rows a gather left open at tile starts (one launch after every gather).
 cudaError_t launch_fixup(int app, const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s);
 cudaError_t launch_push(const PushArgs &a, uint32_t max_arcs, int grid, cudaStream_t s);
@@ -235,13 +257,16 @@ size_t scan_tmp_words(size_t n);
 cudaError_t launch_qdeg(const int32_t *q, const uint32_t *q_len, const int32_t *out_ptr, uint32_t *deg,
                         uint32_t max_n, int num_sms, cudaStream_t s);
 cudaError_t launch_snapshot(const int32_t *q, const uint32_t *q_len, const uint32_t *val, uint32_t *q_val,
-                            uint32_t max_n, int num_sms, cudaStream_t s);
+                            float *hist, uint32_t max_n, int num_sms, cudaStream_t s);
 cudaError_t launch_init_pr(int32_t n, const int32_t *out_ptr, float *rank, float *contrib, int num_sms,
                            cudaStream_t s);
 cudaError_t launch_init_min(int32_t n, int app, int32_t source, uint32_t *val, int32_t *q, uint32_t *q_val,
                             uint32_t *q_len, int num_sms, cudaStream_t s);
 cudaError_t launch_iter_header(IterStatsDev *st, uint32_t mode, const uint32_t *arcs_dev,
-                               unsigned long long arcs, cudaStream_t s);
+                               unsigned long long arcs, cudaStream_t s, unsigned long long selected = 0);
+cudaError_t launch_append_frontier(const int32_t *q_src, uint32_t len, const float *hist_now, const uint32_t *val,
+                                   int32_t *q_dst, uint32_t *q_dst_val, uint32_t *q_dst_len, int num_sms,
+                                   cudaStream_t s);
 cudaError_t launch_iter_changed(IterStatsDev *st, const uint32_t *q_len, cudaStream_t s);
 // Active out-degree of every vertex from the packed active in-edges.
 cudaError_t launch_active_outdeg(const int32_t *sp_src, const uint32_t *sp_nnz, uint32_t max_arcs, int32_t n,
@@ -249,5 +274,28 @@ cudaError_t launch_active_outdeg(const int32_t *sp_src, const uint32_t *sp_nnz, 
 // contrib[u] = rank[u] / deg[u], or / the full out-degree when deg is null (0 when the degree is 0).
 cudaError_t launch_contrib(int32_t n, const float *rank, const int32_t *deg, const int32_t *out_ptr,
                            float *contrib, int num_sms, cudaStream_t s);
+
+// Scorer (gg_mlp.cu).
+cudaError_t launch_mlp_score(const float *x, long long rows, const float *P, float *logits, int num_sms,
+                             cudaStream_t s);
+cudaError_t launch_mlp_select(const FeatArgs &fa, const float *P, float tau, uint32_t *sel_flag, uint32_t *sel_deg,
+                              float *logits, int num_sms, cudaStream_t s);
+cudaError_t launch_trace_features(const FeatArgs &fa, float *out, int num_sms, cudaStream_t s);
+cudaError_t launch_trace_labels(int32_t n, const float *rc, const float *rn, const uint32_t *vc, const uint32_t *vn,
+                                float tol, uint8_t *y, int num_sms, cudaStream_t s);
+cudaError_t launch_mlp_train(const float *x, const uint8_t *y, unsigned long long rows, float *params, int B,
+                             int steps, float lr, unsigned long long stride, unsigned long long start, float *losses,
+                             float *grad_last, cudaStream_t s);
+// Learned correction plumbing (gg_learned.cu).
+cudaError_t launch_sel_compact(int32_t n, const uint32_t *sel_flag, const uint32_t *sel_pos, const uint32_t *sel_off,
+                               int32_t *rows, int32_t *sub_ptr, uint32_t *counts, int num_sms, cudaStream_t s);
+cudaError_t launch_sub_copy(const int32_t *sub_ptr, int32_t nsel, uint32_t total, const int32_t *rows,
+                            const int32_t *in_ptr, const int32_t *in_src, const uint32_t *in_w, const uint32_t *mask,
+                            int32_t *sub_src, uint32_t *sub_w, int32_t *sub_pos, uint32_t *sub_mask, cudaStream_t s);
+cudaError_t launch_keep_values(int32_t n, const float *rank_cur, float *rank_next, const float *contrib_cur,
+                               float *contrib_next, const uint32_t *val_cur, uint32_t *val_next, float *hist,
+                               int num_sms, cudaStream_t s);
+cudaError_t launch_scatter_flags(const int32_t *sub_pos, const uint32_t *sub_mask, uint32_t total, uint32_t *mask,
+                                 int num_sms, cudaStream_t s);
 
 }  // namespace gg

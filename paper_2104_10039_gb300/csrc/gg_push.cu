@@ -93,13 +93,17 @@ __global__ void k_qdeg(const int32_t *__restrict__ q, const uint32_t *__restrict
     }
 }
 
-// Values of the frontier vertices at the end of a push iteration.
+// Values of the frontier vertices at the end of a push iteration; with hist,
+// also their change feature (1: the value decreased; the slot was zeroed).
 __global__ void k_snapshot(const int32_t *__restrict__ q, const uint32_t *__restrict__ q_len,
-                           const uint32_t *__restrict__ val, uint32_t *__restrict__ q_val)
+                           const uint32_t *__restrict__ val, uint32_t *__restrict__ q_val, float *__restrict__ hist)
 {
     const uint32_t qn = *q_len;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < qn; i += gridDim.x * blockDim.x)
-        q_val[i] = val[q[i]];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < qn; i += gridDim.x * blockDim.x) {
+        const int32_t u = q[i];
+        q_val[i] = val[u];
+        if (hist) hist[u] = 1.0f;
+    }
 }
 
 // GG-Apply's starting point for PageRank: rank 1/N, contribution rank/outdeg.
@@ -139,10 +143,53 @@ __global__ void k_init_min(int32_t n, int app, int32_t source, uint32_t *__restr
     }
 }
 
-__global__ void k_iter_header(IterStatsDev *s, uint32_t mode, const uint32_t *arcs_dev, unsigned long long arcs)
+__global__ void k_iter_header(IterStatsDev *s, uint32_t mode, const uint32_t *arcs_dev, unsigned long long arcs,
+                              unsigned long long selected)
 {
     s->mode = mode;
     s->arcs = arcs_dev ? (unsigned long long)*arcs_dev : arcs;
+    s->selected = selected;
+}
+
+// After a learned correction: the frontier of the next push iteration also
+// takes the vertices that changed in the iteration before it (the rows the
+// correction left alone did not gather them), unless already in it.
+__global__ void k_append_frontier(const int32_t *__restrict__ q_src, uint32_t len, const float *__restrict__ hist_now,
+                                  const uint32_t *__restrict__ val, int32_t *__restrict__ q_dst,
+                                  uint32_t *__restrict__ q_dst_val, uint32_t *__restrict__ q_dst_len)
+{
+    const uint32_t lane = lane_id();
+    const uint32_t lt = (1u << lane) - 1u;
+    for (uint32_t i0 = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; i0 < len; i0 += gridDim.x * blockDim.x) {
+        const uint32_t i = i0 + lane;
+        int32_t u = 0;
+        bool want = false;
+        if (i < len) {
+            u = q_src[i];
+            want = hist_now[u] == 0.0f;
+        }
+        const uint32_t b = __ballot_sync(0xFFFFFFFFu, want);
+        if (b) {
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(q_dst_len, (uint32_t)__popc(b));
+            base = __shfl_sync(0xFFFFFFFFu, base, 0);
+            if (want) {
+                q_dst[base + __popc(b & lt)] = u;
+                q_dst_val[base + __popc(b & lt)] = val[u];
+            }
+        }
+    }
+}
+
+cudaError_t launch_append_frontier(const int32_t *q_src, uint32_t len, const float *hist_now, const uint32_t *val,
+                                   int32_t *q_dst, uint32_t *q_dst_val, uint32_t *q_dst_len, int num_sms,
+                                   cudaStream_t s)
+{
+    if (len == 0) return cudaSuccess;
+    int blocks = (int)((len + 255) / 256);
+    if (blocks > num_sms * 8) blocks = num_sms * 8;
+    k_append_frontier<<<blocks, 256, 0, s>>>(q_src, len, hist_now, val, q_dst, q_dst_val, q_dst_len);
+    return cudaGetLastError();
 }
 
 __global__ void k_iter_changed(IterStatsDev *s, const uint32_t *q_len) { s->changed = *q_len; }
@@ -158,12 +205,12 @@ cudaError_t launch_qdeg(const int32_t *q, const uint32_t *q_len, const int32_t *
 }
 
 cudaError_t launch_snapshot(const int32_t *q, const uint32_t *q_len, const uint32_t *val, uint32_t *q_val,
-                            uint32_t max_n, int num_sms, cudaStream_t s)
+                            float *hist, uint32_t max_n, int num_sms, cudaStream_t s)
 {
     int blocks = (int)((max_n + 255) / 256);
     if (blocks > num_sms * 8) blocks = num_sms * 8;
     if (blocks < 1) blocks = 1;
-    k_snapshot<<<blocks, 256, 0, s>>>(q, q_len, val, q_val);
+    k_snapshot<<<blocks, 256, 0, s>>>(q, q_len, val, q_val, hist);
     return cudaGetLastError();
 }
 
@@ -182,9 +229,9 @@ cudaError_t launch_init_min(int32_t n, int app, int32_t source, uint32_t *val, i
 }
 
 cudaError_t launch_iter_header(IterStatsDev *st, uint32_t mode, const uint32_t *arcs_dev,
-                               unsigned long long arcs, cudaStream_t s)
+                               unsigned long long arcs, cudaStream_t s, unsigned long long selected)
 {
-    k_iter_header<<<1, 1, 0, s>>>(st, mode, arcs_dev, arcs);
+    k_iter_header<<<1, 1, 0, s>>>(st, mode, arcs_dev, arcs, selected);
     return cudaGetLastError();
 }
 

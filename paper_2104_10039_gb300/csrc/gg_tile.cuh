@@ -179,6 +179,7 @@ __device__ __forceinline__ void apply_pr(const TileArgs &a, int32_t u, float acc
     const float delta = fabsf(__fsub_rn(nw, old));
     a.rank_next[u] = nw;
     a.contrib_next[u] = deg > 0 ? __fdiv_rn(nw, (float)deg) : 0.0f;
+    if (a.hist_out) a.hist_out[u] = __fmul_rn(a.n_f, delta);
     st.changed += delta > a.epsilon ? 1ull : 0ull;
     st.sum += __float2ull_rz(delta * 1099511627776.0f);   // fixed point 2^-40
     const uint32_t db = __float_as_uint(delta);
@@ -192,6 +193,7 @@ __device__ __forceinline__ uint32_t apply_min(const TileArgs &a, int32_t u, uint
     const uint32_t nw = acc < old ? acc : old;
     a.val_next[u] = nw;
     *changed = nw < old;
+    if (a.hist_out) a.hist_out[u] = nw < old ? 1.0f : 0.0f;
     if (nw < old) {
         st.changed += 1;
         if (old != kInf) {
@@ -241,8 +243,8 @@ template <int APP, int KIND>
 struct WarpSmem {
     int32_t rowend[kWT + 1];
     uint32_t val[kPadded];   // arc values (bits of T), or arc sources when sampling
-    uint32_t vtx[(KIND == K_SAMPLE || KIND == K_STASH) ? 1 : kWT];   // rows' current value
-    int32_t deg[(KIND != K_SAMPLE && KIND != K_STASH && APP == GG_APP_PAGERANK) ? kWT : 1];  // rows' out-degree
+    uint32_t vtx[(KIND == K_SAMPLE || KIND == K_STASH || KIND == K_RECOUNT) ? 1 : kWT];   // rows' current value
+    int32_t deg[(KIND == K_GATHER || KIND == K_CORRECT) && APP == GG_APP_PAGERANK ? kWT : 1];  // rows' out-degree
     uint32_t bits[(KIND == K_GATHER) ? 1 : (kWT / 32 + 2)];
     uint32_t oldw[(KIND == K_CORRECT && APP != GG_APP_PAGERANK) ? (kWT / 32 + 2) : 1];
     float rowtot[(KIND == K_CORRECT && APP == GG_APP_PAGERANK) ? kWT + 1 : 1];   // influence share
@@ -254,7 +256,8 @@ k_tile(TileArgs a)
 {
     using T = typename Acc<APP>::T;
     using A = Acc<APP>;
-    constexpr bool kPack = KIND == K_CORRECT || KIND == K_SAMPLE;
+    constexpr bool kPack = KIND == K_CORRECT || KIND == K_SAMPLE || KIND == K_RECOUNT;
+    constexpr bool kNoGather = KIND == K_SAMPLE || KIND == K_RECOUNT;   // flags only, no values
     constexpr bool kMin = APP != GG_APP_PAGERANK;
     constexpr bool kWeighted = APP == GG_APP_SSSP && (KIND == K_GATHER || KIND == K_STASH);
     constexpr bool kApply = KIND == K_GATHER || KIND == K_CORRECT;
@@ -289,7 +292,8 @@ k_tile(TileArgs a)
         for (int i = 0; i < kIPT; ++i) {
             const int k = (int)lane + 32 * i;
             const bool ok = live && k < b1 - b0;
-            if constexpr (kStashed) srcv[i] = ok ? (int32_t)__ldcs(a.stash + b0 + k) : 0;
+            if constexpr (KIND == K_RECOUNT) srcv[i] = 0;
+            else if constexpr (kStashed) srcv[i] = ok ? (int32_t)__ldcs(a.stash + b0 + k) : 0;
             else srcv[i] = ok ? __ldg(a.arc_src + b0 + k) : 0;
             if constexpr (kWeighted) wv[i] = (ok && load_w) ? __ldg(a.arc_w + b0 + k) : 1u;
         }
@@ -313,7 +317,7 @@ k_tile(TileArgs a)
 #pragma unroll
         for (int i = 0; i < kIPT; ++i) {
             const int k = (int)lane + 32 * i;
-            if constexpr (KIND == K_SAMPLE || kStashed) {
+            if constexpr (kNoGather || kStashed) {
                 gv[i] = (uint32_t)src_cur[i];
             } else if constexpr (APP == GG_APP_PAGERANK) {
                 gv[i] = k < narcs ? __float_as_uint(__ldg(a.contrib_cur + src_cur[i])) : 0u;
@@ -328,11 +332,12 @@ k_tile(TileArgs a)
         for (int i = (int)lane; i < nrows; i += 32) {
             s.rowend[i] = a.row_ptr[r0 + i + 1];
             if constexpr (kApply) {
+                const int32_t v = a.row_vtx ? a.row_vtx[r0 + i] : r0 + i;
                 if constexpr (APP == GG_APP_PAGERANK) {
-                    s.vtx[i] = __float_as_uint(a.rank_cur[r0 + i]);
-                    s.deg[i] = a.deg_apply ? a.deg_apply[r0 + i] : a.out_ptr[r0 + i + 1] - a.out_ptr[r0 + i];
+                    s.vtx[i] = __float_as_uint(a.rank_cur[v]);
+                    s.deg[i] = a.deg_apply ? a.deg_apply[v] : a.out_ptr[v + 1] - a.out_ptr[v];
                 } else {
-                    s.vtx[i] = a.val_cur[r0 + i];
+                    s.vtx[i] = a.val_cur[v];
                 }
             }
         }
@@ -407,7 +412,7 @@ k_tile(TileArgs a)
         // ---- fold + warp segmented scan --------------------------------------
         T carry_in = A::id();
         bool defer_first = false;   // gather: the tile's first row end waits for k_fixup
-        if constexpr (KIND != K_SAMPLE) {
+        if constexpr (!kNoGather) {
             T v = A::id(), head = A::id();
             uint32_t f = 0;
 #pragma unroll
@@ -469,6 +474,11 @@ k_tile(TileArgs a)
                         const uint32_t fl = sampled_flag((int32_t)item_v[i], r0 + x, a.symmetric, a.seed, a.thr);
                         my_flags |= fl << i;
                         my_active += fl;
+                    } else if constexpr (KIND == K_RECOUNT) {
+                        const int k = a0 + y;
+                        const uint32_t fl = (__ldg(a.mask + (k >> 5)) >> (k & 31)) & 1u;
+                        my_flags |= fl << i;
+                        my_active += fl;
                     } else {
                         const T v = A::from_bits(item_v[i]);
                         if constexpr (KIND == K_CORRECT) {
@@ -506,7 +516,7 @@ k_tile(TileArgs a)
                         if (defer_first) {
                             defer_first = false;   // completed by k_fixup
                         } else {
-                            const int32_t u = r0 + x;
+                            const int32_t u = a.row_vtx ? a.row_vtx[r0 + x] : r0 + x;
                             if constexpr (APP == GG_APP_PAGERANK) {
                                 apply_pr(a, u, acc, __uint_as_float(s.vtx[x]), s.deg[x], st);
                             } else {
@@ -558,7 +568,7 @@ k_tile(TileArgs a)
         // ---- new flags into the bitmap; tile count and tile-local row ends --
         if constexpr (kPack) {
             const uint32_t incl = warp_incl_sum_u32(my_active);
-            if (lane == 31) a.tile_cnt[t] = incl;
+            if (lane == 31 && a.tile_cnt) a.tile_cnt[t] = incl;
             uint32_t off = incl - my_active;   // active arcs of the tile before this lane's items
             {
                 int x = lx, y = ly;
@@ -572,13 +582,13 @@ k_tile(TileArgs a)
                         }
                         ++y;
                     } else if ((endmask >> i) & 1u) {
-                        a.sp_ptr[r0 + x + 1] = (int32_t)off;   // tile-local; k_pack adds the tile offset
+                        if (a.sp_ptr) a.sp_ptr[r0 + x + 1] = (int32_t)off;   // tile-local; k_pack adds the tile offset
                         ++x;
                     }
                 }
             }
             __syncwarp();
-            for (int i = (int)lane; i < nwords; i += 32) {
+            for (int i = (int)lane; KIND != K_RECOUNT && i < nwords; i += 32) {
                 const int w = w0 + i;
                 const int lo = a0 > w * 32 ? a0 : w * 32;
                 const int hi = a1 < w * 32 + 32 ? a1 : w * 32 + 32;
@@ -636,7 +646,8 @@ k_fixup(TileArgs a)
                 T acc = A::from_bits(a.part[j].y);
                 for (long long k = j + 1; k < t; ++k) acc = A::op(acc, A::from_bits(a.part[k].y));
                 acc = A::op(acc, A::from_bits(a.part_head[t]));
-                const int32_t u = (int32_t)(info & 0x7FFFFFFFu);
+                const int32_t r = (int32_t)(info & 0x7FFFFFFFu);
+                const int32_t u = a.row_vtx ? a.row_vtx[r] : r;
                 if constexpr (APP == GG_APP_PAGERANK) {
                     apply_pr(a, u, acc, a.rank_cur[u],
                              a.deg_apply ? a.deg_apply[u] : a.out_ptr[u + 1] - a.out_ptr[u], st);

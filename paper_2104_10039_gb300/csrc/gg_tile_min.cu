@@ -25,6 +25,13 @@ cudaError_t launch_tile_sample(const TileArgs &a, int max_tiles, int num_sms, cu
     return launch_tiles<GG_APP_CC, K_SAMPLE>(a, max_tiles, num_sms, s);
 }
 
+// Tile counts and tile-local row ends of the flags in the bitmap (no hash,
+// no gather): after a learned correction rewrote the flags of some rows.
+cudaError_t launch_tile_recount(const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s)
+{
+    return launch_tiles<GG_APP_CC, K_RECOUNT>(a, max_tiles, num_sms, s);
+}
+
 cudaError_t launch_fixup_pr(const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s);
 
 cudaError_t launch_fixup(int app, const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s)

@@ -27,22 +27,24 @@ _lib = ctypes.CDLL(LIB_PATH)
 GG_OK, GG_ERR_INVALID_ARG, GG_ERR_BAD_GRAPH, GG_ERR_OOM, GG_ERR_CUDA, GG_ERR_STATE, \
     GG_ERR_TIMEOUT, GG_ERR_UNSUPPORTED = range(8)
 GG_APP_PAGERANK, GG_APP_SSSP, GG_APP_BFS, GG_APP_CC = range(4)
-GG_POLICY_EXACT, GG_POLICY_NONE, GG_POLICY_STATIC_SWITCH, GG_POLICY_ADAPTIVE, GG_POLICY_TRIGGERED = range(5)
+GG_POLICY_EXACT, GG_POLICY_NONE, GG_POLICY_STATIC_SWITCH, GG_POLICY_ADAPTIVE, GG_POLICY_TRIGGERED, \
+    GG_POLICY_LEARNED = range(6)
 (GG_RESULT_VALUES, GG_RESULT_MASK, GG_RESULT_STATS, GG_RESULT_ITER_STATS, GG_RESULT_CSC_PTR,
  GG_RESULT_CSC_SRC, GG_RESULT_CSC_W, GG_RESULT_SPARSE_PTR, GG_RESULT_SPARSE_SRC,
- GG_RESULT_OUT_TO_IN) = range(10)
+ GG_RESULT_OUT_TO_IN, GG_RESULT_SCORES) = range(11)
 GG_DIRECTED, GG_SYMMETRIC, GG_DEVICE_PTRS = 0, 1, 2
 GG_STOP_QUIESCE, GG_EST_STRICT, GG_FORCE_PULL, GG_FORCE_PUSH, GG_TIMING = 1, 2, 4, 8, 16
 GG_INFL_SHARE, GG_RENORM = 32, 64
 GG_INF = 0xFFFFFFFF
 GG_ITER_PUSH = 0x100
+GG_ITER_LEARNED = 0x200
 
 APPS = {"pagerank": GG_APP_PAGERANK, "pr": GG_APP_PAGERANK, "sssp": GG_APP_SSSP,
         "bfs": GG_APP_BFS, "cc": GG_APP_CC}
 POLICIES = {"exact": GG_POLICY_EXACT, "none": GG_POLICY_NONE, "sp": GG_POLICY_NONE,
             "static_switch": GG_POLICY_STATIC_SWITCH, "sms": GG_POLICY_STATIC_SWITCH,
             "adaptive": GG_POLICY_ADAPTIVE, "gg": GG_POLICY_ADAPTIVE,
-            "triggered": GG_POLICY_TRIGGERED}
+            "triggered": GG_POLICY_TRIGGERED, "learned": GG_POLICY_LEARNED}
 
 
 class gg_params(ctypes.Structure):
@@ -50,7 +52,8 @@ class gg_params(ctypes.Structure):
                 ("max_iters", ctypes.c_uint32), ("damping", ctypes.c_float),
                 ("epsilon", ctypes.c_float), ("source", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("flags", ctypes.c_uint32),
-                ("trigger_ratio", ctypes.c_float)]
+                ("trigger_ratio", ctypes.c_float), ("select_logit", ctypes.c_float),
+                ("fallback_frac", ctypes.c_float)]
 
 
 class gg_stats(ctypes.Structure):
@@ -63,12 +66,14 @@ class gg_stats(ctypes.Structure):
                 ("ms_gather", ctypes.c_float), ("ms_correct", ctypes.c_float),
                 ("ms_push", ctypes.c_float), ("n_gather", ctypes.c_uint32),
                 ("n_correct", ctypes.c_uint32), ("n_push", ctypes.c_uint32),
-                ("kernels_launched", ctypes.c_uint32)]
+                ("kernels_launched", ctypes.c_uint32), ("learned_corrections", ctypes.c_uint32),
+                ("trace_rows", ctypes.c_uint64)]
 
 
 ITER_STATS_DTYPE = np.dtype([("mode", np.uint32), ("max_delta_bits", np.uint32),
                              ("arcs", np.uint64), ("changed", np.uint64),
-                             ("sum_delta", np.uint64), ("active_after", np.uint64)])
+                             ("sum_delta", np.uint64), ("active_after", np.uint64),
+                             ("selected", np.uint64)])
 
 _vp = ctypes.c_void_p
 _lib.gg_load_csr.restype = ctypes.c_int
@@ -92,6 +97,16 @@ _lib.gg_sample_csc_noalloc.restype = ctypes.c_int
 _lib.gg_sample_csc_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int64, _vp, _vp, ctypes.c_double,
                                        ctypes.c_uint64, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
 GG_NOALLOC_MAX_ITEMS = 1 << 24
+_lib.gg_set_scorer.restype = ctypes.c_int
+_lib.gg_set_scorer.argtypes = [_vp, _vp]
+_lib.gg_set_trace.restype = ctypes.c_int
+_lib.gg_set_trace.argtypes = [_vp, _vp, _vp, ctypes.c_uint64, ctypes.c_float]
+_lib.gg_mlp_score.restype = ctypes.c_int
+_lib.gg_mlp_score.argtypes = [_vp, ctypes.c_uint64, _vp, _vp, _vp]
+_lib.gg_mlp_train.restype = ctypes.c_int
+_lib.gg_mlp_train.argtypes = [_vp, _vp, ctypes.c_uint64, _vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_float,
+                              ctypes.c_uint64, ctypes.c_uint64, _vp, _vp, _vp]
+GG_MLP_NPARAM = 4801
 
 
 class GGError(RuntimeError):
@@ -136,9 +151,9 @@ def gg_sample_edges(g: int, sample_ratio: float, seed: int):
 
 
 def make_params(alpha=4, theta=0.05, max_iters=20, damping=0.85, epsilon=0.0, source=0, seed=0,
-                flags=0, trigger_ratio=0.5) -> gg_params:
+                flags=0, trigger_ratio=0.5, select_logit=0.0, fallback_frac=1.0) -> gg_params:
     return gg_params(alpha, theta, max_iters, damping, epsilon, source,
-                     seed & 0xFFFFFFFFFFFFFFFF, flags, trigger_ratio)
+                     seed & 0xFFFFFFFFFFFFFFFF, flags, trigger_ratio, select_logit, fallback_frac)
 
 
 def gg_run(g: int, app, sample_ratio: float, policy, params: gg_params):
@@ -179,7 +194,7 @@ def gg_sample_csc_noalloc(n: int, m: int, in_ptr, in_src, sample_ratio: float, s
 _RESULT_DTYPES = {GG_RESULT_MASK: np.uint32, GG_RESULT_CSC_PTR: np.int32,
                   GG_RESULT_CSC_SRC: np.int32, GG_RESULT_CSC_W: np.uint32,
                   GG_RESULT_SPARSE_PTR: np.int32, GG_RESULT_SPARSE_SRC: np.int32,
-                  GG_RESULT_OUT_TO_IN: np.int32}
+                  GG_RESULT_OUT_TO_IN: np.int32, GG_RESULT_SCORES: np.float32}
 
 
 def result_array(g: int, kind: int, dtype=None) -> np.ndarray:
@@ -211,3 +226,32 @@ def mask_bits(g: int, m: int) -> np.ndarray:
     words = result_array(g, GG_RESULT_MASK)
     bits = np.unpackbits(words.view(np.uint8), bitorder="little")
     return bits[:m].astype(np.uint8)
+
+
+def gg_set_scorer(g: int, params: np.ndarray):
+    """Scorer parameters (host float32[GG_MLP_NPARAM]) for GG_POLICY_LEARNED."""
+    P = np.ascontiguousarray(params, np.float32)
+    if P.shape != (GG_MLP_NPARAM,):
+        raise ValueError(f"params must hold {GG_MLP_NPARAM} float32 values")
+    _check(_lib.gg_set_scorer(g, P.ctypes.data), "gg_set_scorer")
+
+
+def gg_set_trace(g: int, features, labels, cap_rows: int, label_tol: float = 1e-3):
+    """Record training rows into device buffers features[cap_rows][8] (float32)
+    and labels[cap_rows] (uint8); features=None stops recording."""
+    _check(_lib.gg_set_trace(g, _addr(features), _addr(labels), int(cap_rows), float(label_tol)),
+           "gg_set_trace")
+
+
+def gg_mlp_score(features, rows: int, params, logits, stream=None):
+    """Logits of device feature rows (float32[rows][8]) into device logits[rows]."""
+    _check(_lib.gg_mlp_score(_addr(features), int(rows), _addr(params), _addr(logits), _addr(stream)),
+           "gg_mlp_score")
+
+
+def gg_mlp_train(features, labels, rows: int, params, batch: int, steps: int, lr: float, stride: int,
+                 start: int = 0, losses=None, grad_last=None, stream=None):
+    """Minibatch SGD on the scorer's device parameters (updated in place)."""
+    _check(_lib.gg_mlp_train(_addr(features), _addr(labels), int(rows), _addr(params), int(batch), int(steps),
+                             float(lr), int(stride), int(start), _addr(losses), _addr(grad_last), _addr(stream)),
+           "gg_mlp_train")
