@@ -418,6 +418,25 @@ def accuracy_table(g, source, collected):
             "reference_iters": full_iters, "time_to_target": tta, "timed_runs": timed}
 
 
+def learned_section(g, source):
+    """Learned correction (beyond the paper): the scorer is trained on the
+    traces of plain adaptive runs on R-MAT scale 12 and on this graph, then
+    GG_POLICY_LEARNED is compared with plain adaptive correction on this
+    graph (device time and error at equal iteration counts, time to 1 %)."""
+    import torch
+
+    import graphgen
+    from paper_2104_10039_gb300 import gg, learned_eval
+    g12 = graphgen.add_weights(graphgen.rmat(12, EDGEFACTOR, seed=GRAPH_SEED), seed=WEIGHT_SEED)
+    s12 = int(graphgen.sources(g12, 1, seed=SOURCE_SEED)[0])
+    X, Y = learned_eval.collect_traces(gg, torch, [(g12, s12), (g, source)])
+    P, tr = learned_eval.train(gg, torch, X, Y)
+    del X, Y
+    torch.cuda.empty_cache()
+    return {"training": tr, "alpha": learned_eval.ALPHA, "theta": learned_eval.THETA,
+            "results": learned_eval.compare(gg, g, source, P, sigmas=(0.5,))}
+
+
 # ------------------------------------------------------------- oracle (CPU) --
 def cpu_sample(g):
     """The oracle as it stands on the host cores: one adaptive-correction
@@ -477,6 +496,7 @@ def main():
     out, g, source, collected = res
     if not a.no_accuracy:
         out["time_to_accuracy"] = accuracy_table(g, source, collected)
+        out["learned_correction"] = learned_section(g, source)
     if not a.no_cpu_baseline and world >= 1:
         arcs, secs = cpu_sample(g)
         out["cpu_baseline"] = {"value": round(arcs / secs / 1e9, 4), "unit": "GTEPS",
