@@ -36,8 +36,8 @@ _SRC = os.path.join(_HERE, "gg_oracle.c")
 _LIB = os.path.join(_HERE, "libggoracle.so")
 _lib = None
 
-PAGERANK, SSSP, BFS, CC = 0, 1, 2, 3
-APPS = {"pagerank": PAGERANK, "pr": PAGERANK, "sssp": SSSP, "bfs": BFS, "cc": CC}
+PAGERANK, SSSP, BFS, CC, PPR = 0, 1, 2, 3, 4
+APPS = {"pagerank": PAGERANK, "pr": PAGERANK, "sssp": SSSP, "bfs": BFS, "cc": CC, "ppr": PPR}
 EXACT, NONE, STATIC_SWITCH, ADAPTIVE, TRIGGERED, LEARNED = 0, 1, 2, 3, 4, 5
 POLICIES = {"exact": EXACT, "none": NONE, "sp": NONE, "static_switch": STATIC_SWITCH,
             "sms": STATIC_SWITCH, "adaptive": ADAPTIVE, "gg": ADAPTIVE, "triggered": TRIGGERED,
@@ -238,8 +238,8 @@ def run(n, rowptr, colidx, weights=None, *, app="pagerank", policy="exact", sigm
                   float(fallback_frac), _p(rsel, ctypes.c_uint8), n_rsel, float(replay_select_tol),
                   _p(tx, ctypes.c_float), _p(ty, ctypes.c_uint8), int(trace_cap), float(label_tol))
     T = max(max_iters, 1)
-    pr = np.empty(n, np.float64) if a == PAGERANK else None
-    iv = np.empty(n, np.uint32) if a != PAGERANK else None
+    pr = np.empty(n, np.float64) if a in (PAGERANK, PPR) else None
+    iv = np.empty(n, np.uint32) if a not in (PAGERANK, PPR) else None
     mask = np.empty(max(m, 1), np.uint8)
     it_arcs = np.zeros(T, np.int64)
     it_mode = np.full(T, -1, np.int32)
@@ -257,7 +257,7 @@ def run(n, rowptr, colidx, weights=None, *, app="pagerank", policy="exact", sigm
         raise ValueError("oracle rejected its arguments")
     it = out.iterations
     return {
-        "values": pr if a == PAGERANK else iv,
+        "values": pr if a in (PAGERANK, PPR) else iv,
         "mask": mask[:m],
         "iterations": it,
         "corrections": out.corrections,

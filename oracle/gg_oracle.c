@@ -65,6 +65,9 @@
  *    rounded to bfloat16 (nearest even), exact products summed (FP64 here,
  *    rounded to FP32 before the next rounding), FP32 biases, ReLU after the
  *    two hidden layers.
+ *  - ORC_PPR (beyond the paper): personalized PageRank from `source`, the
+ *    same gather with the restart mass on the source only: rank_0 = e_s,
+ *    rank' = (1-d) e_s + d * sum over in-edges of rank(v) / outdeg(v).
  *  - Two PageRank variants beyond the paper (flags): ORC_INFL_SHARE takes
  *    an arc's influence as its share of the row's total (order-free) instead
  *    of the running-prefix form; ORC_RENORM divides a source's rank by its
@@ -79,7 +82,7 @@
 #include <omp.h>
 #endif
 
-enum { ORC_PAGERANK = 0, ORC_SSSP = 1, ORC_BFS = 2, ORC_CC = 3 };
+enum { ORC_PAGERANK = 0, ORC_SSSP = 1, ORC_BFS = 2, ORC_CC = 3, ORC_PPR = 4 };
 enum { ORC_EXACT = 0, ORC_NONE = 1, ORC_STATIC_SWITCH = 2, ORC_ADAPTIVE = 3, ORC_TRIGGERED = 4,
        ORC_LEARNED = 5 };
 enum { ORC_MODE_APPROX = 0, ORC_MODE_ACCURATE = 1, ORC_MODE_CORRECTION = 2 };
@@ -366,7 +369,7 @@ int orc_run(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx,
             const uint32_t *weights, const orc_params *p, orc_out *o)
 {
     if (n <= 0 || m < 0 || !p || !o) return -1;
-    if (p->app < ORC_PAGERANK || p->app > ORC_CC) return -1;
+    if (p->app < ORC_PAGERANK || p->app > ORC_PPR) return -1;
     if (p->app != ORC_PAGERANK && p->app != ORC_CC && (p->source < 0 || p->source >= n)) return -1;
     if (!(p->sample_ratio > 0.0 && p->sample_ratio <= 1.0)) return -1;
     if (p->policy == ORC_LEARNED && !p->mlp) return -1;
@@ -392,7 +395,8 @@ int orc_run(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx,
     for (int32_t v = 0; v < n; ++v) outdeg[v] = rowptr[v + 1] - rowptr[v];
     orc_sample_mask(n, in_ptr, in_src, p->symmetric, p->sample_ratio, p->seed, mask);
 
-    const int is_pr = p->app == ORC_PAGERANK;
+    const int is_pr = p->app == ORC_PAGERANK || p->app == ORC_PPR;
+    const int ppr = p->app == ORC_PPR;
     const int renorm = is_pr && (p->flags & ORC_RENORM);
     const int share = is_pr && (p->flags & ORC_INFL_SHARE);
     const int learned_policy = p->policy == ORC_LEARNED;
@@ -411,7 +415,7 @@ int orc_run(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx,
         rank = (double *)malloc((size_t)n * sizeof(double));
         rank_next = (double *)malloc((size_t)n * sizeof(double));
         if (!rank || !rank_next) goto done;
-        for (int32_t u = 0; u < n; ++u) rank[u] = 1.0 / (double)n;
+        for (int32_t u = 0; u < n; ++u) rank[u] = ppr ? (u == p->source ? 1.0 : 0.0) : 1.0 / (double)n;
     } else {
         val = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
         val_next = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
@@ -528,7 +532,7 @@ int orc_run(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx,
                     }
                 }
                 double old = rank[u];
-                double nw = base + d * acc;
+                double nw = (ppr ? (u == p->source ? 1.0 - d : 0.0) : base) + d * acc;
                 rank_next[u] = nw;
                 changed += fabs(old - nw) > p->epsilon;
                 sum_delta += fabs(old - nw);

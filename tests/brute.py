@@ -96,3 +96,23 @@ def pagerank_dense(g, damping, iters):
     for _ in range(iters):
         x = (1.0 - d) / n + d * (P.T @ x)
     return x
+
+
+def ppr_dense(g, damping, iters, source):
+    """Personalized PageRank by dense power iteration:
+    x_0 = e_s, x_{t+1} = (1-d) e_s + d * A^T D^-1 x_t."""
+    n = g.n
+    d = float(np.float32(damping))
+    A = np.zeros((n, n), np.float64)
+    for s, t, _ in arcs_of(g):
+        A[s, t] += 1.0
+    outdeg = A.sum(axis=1)
+    P = np.zeros_like(A)
+    nz = outdeg > 0
+    P[nz] = A[nz] / outdeg[nz, None]
+    e = np.zeros(n)
+    e[source] = 1.0
+    x = e.copy()
+    for _ in range(iters):
+        x = (1.0 - d) * e + d * (P.T @ x)
+    return x

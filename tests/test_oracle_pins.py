@@ -455,3 +455,40 @@ def test_replayed_modes_reproduce_the_run():
                         theta=0.05, trigger_ratio=0.0, max_iters=14, replay_modes=r["iter_mode"])
         assert np.array_equal(rr["iter_mode"], r["iter_mode"])
         assert np.array_equal(rr["values"], r["values"]) and np.array_equal(rr["mask"], r["mask"])
+
+
+# ------------------------------------------------- personalized PageRank --
+
+def test_ppr_matches_dense_power_iteration():
+    for g in _small_graphs()[:4]:
+        for s in (0, g.n - 1):
+            for T in (1, 3, 12):
+                r = oracle.run(g.n, g.rowptr, g.colidx, app="ppr", source=s, max_iters=T)
+                ref = brute.ppr_dense(g, 0.85, T, s)
+                assert np.abs(r["values"] - ref).sum() <= 1e-13 * max(np.abs(ref).sum(), 1e-300)
+
+
+def test_ppr_path_closed_form():
+    g = graphgen.from_arcs(4, [(0, 1), (1, 2), (2, 3)])
+    d = float(np.float32(0.85))
+    r = oracle.run(g.n, g.rowptr, g.colidx, app="ppr", source=0, max_iters=2)
+    assert np.allclose(r["values"], [1 - d, d * (1 - d), d * d, 0.0], rtol=0, atol=1e-15)
+    # T = 3 puts d^3 on vertex 3, which has no out-arcs: that mass leaves
+    # (no dangling redistribution), so T = 4 holds d^3 (1-d) there
+    r = oracle.run(g.n, g.rowptr, g.colidx, app="ppr", source=0, max_iters=3)
+    assert np.allclose(r["values"], [1 - d, d * (1 - d), d * d * (1 - d), d ** 3], rtol=0, atol=1e-15)
+    r = oracle.run(g.n, g.rowptr, g.colidx, app="ppr", source=0, max_iters=4)
+    assert np.allclose(r["values"], [1 - d, d * (1 - d), d * d * (1 - d), d ** 3 * (1 - d)], rtol=0, atol=1e-15)
+
+
+def test_ppr_averaged_over_sources_is_pagerank():
+    # rank_t is linear in the restart and starting vectors: the mean of the
+    # personalized vectors over every source is the global PageRank
+    g = graphgen.rmat(6, edgefactor=4, seed=2)
+    for T in (1, 4, 10):
+        mean = np.zeros(g.n)
+        for s in range(g.n):
+            mean += oracle.run(g.n, g.rowptr, g.colidx, app="ppr", source=s, max_iters=T)["values"]
+        mean /= g.n
+        pr = oracle.run(g.n, g.rowptr, g.colidx, app="pagerank", max_iters=T)["values"]
+        assert np.abs(mean - pr).sum() <= 1e-13
