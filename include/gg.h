@@ -50,7 +50,9 @@ typedef enum {
     GG_APP_PAGERANK = 0,      /* Alg. 2: pull PageRank, FP32 ranks */
     GG_APP_SSSP = 1,          /* Sec. 4.1: single-source shortest paths, uint32 weights */
     GG_APP_BFS = 2,           /* unit-weight SSSP: levels */
-    GG_APP_CC = 3             /* Sec. 4.1 WCC: min-label propagation (symmetric graphs) */
+    GG_APP_CC = 3,            /* Sec. 4.1 WCC: min-label propagation (symmetric graphs) */
+    GG_APP_PPR = 4            /* beyond the paper: personalized PageRank from the source,
+                                 rank_0 = e_s, rank' = (1-d) e_s + d * sum rank(v)/outdeg(v) */
 } gg_app;
 
 typedef enum {
@@ -312,6 +314,57 @@ gg_status gg_mlp_score(const float *features, uint64_t rows, const float *params
 gg_status gg_mlp_train(const float *features, const uint8_t *labels, uint64_t rows, float *params,
                        uint32_t batch, uint32_t steps, float lr, uint64_t stride, uint64_t start,
                        float *losses, float *grad_last, void *stream);
+
+/*
+ * Batched serving (beyond the paper): many BFS / SSSP / personalized-
+ * PageRank queries over loaded graphs of uneven size in one persistent
+ * launch, replayed as a captured CUDA graph. Queries on graphs with at least
+ * big_arcs arcs are served by a whole thread-block cluster of `cluster`
+ * CTAs (meeting at the cluster barrier between iterations), the others by
+ * single CTAs; each team claims its next query (most estimated work first)
+ * with one atomic, so no team waits on another. Vertices are binned by
+ * degree: below warp_deg one thread handles a vertex, below cta_deg a warp,
+ * else the whole CTA. BFS / SSSP run exactly to the fixed point (push
+ * frontier); personalized PageRank runs `iters` pull iterations. The batch
+ * reads the graphs' device arrays: the graphs must outlive it.
+ */
+typedef struct {
+    int32_t graph;        /* index into the graphs given to gg_batch_create */
+    int32_t app;          /* GG_APP_BFS, GG_APP_SSSP (weighted graph) or GG_APP_PPR */
+    int32_t source;
+    uint32_t iters;       /* GG_APP_PPR: iterations */
+    float damping;        /* GG_APP_PPR: d in [0, 1] */
+} gg_query;
+
+typedef struct {
+    int32_t cluster;      /* CTAs per cluster team: 1 (no cluster teams), 2, 4 or 8 */
+    int32_t warp_deg;     /* degree from which a warp handles a vertex (>= 1) */
+    int32_t cta_deg;      /* degree from which the whole CTA does (>= warp_deg) */
+    int32_t reserved;
+    int64_t big_arcs;     /* graphs with at least this many arcs get cluster teams */
+} gg_batch_config;
+
+typedef struct {
+    uint64_t latency_ns;  /* from the launch's start to the query's completion */
+    uint64_t service_ns;  /* from the query's claim to its completion */
+    uint64_t arcs;        /* arcs the query traversed (pushes, or iters x m pulls) */
+    uint32_t iterations;
+    uint32_t team;        /* CTAs that served it */
+} gg_query_stats;
+
+typedef struct gg_batch gg_batch;
+
+/* Validate queries, lay out their state in one device arena, plan the teams. */
+gg_status gg_batch_create(gg_graph *const *graphs, int32_t n_graphs, const gg_query *queries, int32_t n_queries,
+                          const gg_batch_config *cfg, gg_batch **out);
+/* Serve every query (one persistent launch; captured as a CUDA graph on the
+ * first call, replayed afterwards); *ms = device time of the launch. */
+gg_status gg_batch_run(gg_batch *b, float *ms);
+/* Per-query latency, service time, arcs and iterations of the last run. */
+gg_status gg_batch_query_stats(gg_batch *b, gg_query_stats *out, int32_t n);
+/* Values of query q (uint32 distances / levels, or float ranks) into host dst. */
+gg_status gg_batch_result(gg_batch *b, int32_t q, void *dst, size_t bytes);
+void gg_batch_free(gg_batch *b);
 
 #define GG_NOALLOC_MAX_ITEMS (1u << 24)
 gg_status gg_sample_csc_noalloc(int32_t n, int64_t m, const int32_t *in_ptr, const int32_t *in_src,

@@ -26,7 +26,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 # ---- enums and flags (gg.h) ---------------------------------------------
 GG_OK, GG_ERR_INVALID_ARG, GG_ERR_BAD_GRAPH, GG_ERR_OOM, GG_ERR_CUDA, GG_ERR_STATE, \
     GG_ERR_TIMEOUT, GG_ERR_UNSUPPORTED = range(8)
-GG_APP_PAGERANK, GG_APP_SSSP, GG_APP_BFS, GG_APP_CC = range(4)
+GG_APP_PAGERANK, GG_APP_SSSP, GG_APP_BFS, GG_APP_CC, GG_APP_PPR = range(5)
 GG_POLICY_EXACT, GG_POLICY_NONE, GG_POLICY_STATIC_SWITCH, GG_POLICY_ADAPTIVE, GG_POLICY_TRIGGERED, \
     GG_POLICY_LEARNED = range(6)
 (GG_RESULT_VALUES, GG_RESULT_MASK, GG_RESULT_STATS, GG_RESULT_ITER_STATS, GG_RESULT_CSC_PTR,
@@ -40,7 +40,7 @@ GG_ITER_PUSH = 0x100
 GG_ITER_LEARNED = 0x200
 
 APPS = {"pagerank": GG_APP_PAGERANK, "pr": GG_APP_PAGERANK, "sssp": GG_APP_SSSP,
-        "bfs": GG_APP_BFS, "cc": GG_APP_CC}
+        "bfs": GG_APP_BFS, "cc": GG_APP_CC, "ppr": GG_APP_PPR}
 POLICIES = {"exact": GG_POLICY_EXACT, "none": GG_POLICY_NONE, "sp": GG_POLICY_NONE,
             "static_switch": GG_POLICY_STATIC_SWITCH, "sms": GG_POLICY_STATIC_SWITCH,
             "adaptive": GG_POLICY_ADAPTIVE, "gg": GG_POLICY_ADAPTIVE,
@@ -255,3 +255,74 @@ def gg_mlp_train(features, labels, rows: int, params, batch: int, steps: int, lr
     _check(_lib.gg_mlp_train(_addr(features), _addr(labels), int(rows), _addr(params), int(batch), int(steps),
                              float(lr), int(stride), int(start), _addr(losses), _addr(grad_last), _addr(stream)),
            "gg_mlp_train")
+
+
+# ------------------------------------------------------- batched serving --
+class gg_query(ctypes.Structure):
+    _fields_ = [("graph", ctypes.c_int32), ("app", ctypes.c_int32), ("source", ctypes.c_int32),
+                ("iters", ctypes.c_uint32), ("damping", ctypes.c_float)]
+
+
+class gg_batch_config(ctypes.Structure):
+    _fields_ = [("cluster", ctypes.c_int32), ("warp_deg", ctypes.c_int32), ("cta_deg", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("big_arcs", ctypes.c_int64)]
+
+
+class gg_query_stats(ctypes.Structure):
+    _fields_ = [("latency_ns", ctypes.c_uint64), ("service_ns", ctypes.c_uint64), ("arcs", ctypes.c_uint64),
+                ("iterations", ctypes.c_uint32), ("team", ctypes.c_uint32)]
+
+
+_lib.gg_batch_create.restype = ctypes.c_int
+_lib.gg_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int32, ctypes.POINTER(gg_query), ctypes.c_int32,
+                                 ctypes.POINTER(gg_batch_config), ctypes.POINTER(_vp)]
+_lib.gg_batch_run.restype = ctypes.c_int
+_lib.gg_batch_run.argtypes = [_vp, ctypes.POINTER(ctypes.c_float)]
+_lib.gg_batch_query_stats.restype = ctypes.c_int
+_lib.gg_batch_query_stats.argtypes = [_vp, ctypes.POINTER(gg_query_stats), ctypes.c_int32]
+_lib.gg_batch_result.restype = ctypes.c_int
+_lib.gg_batch_result.argtypes = [_vp, ctypes.c_int32, _vp, ctypes.c_size_t]
+_lib.gg_batch_free.restype = None
+_lib.gg_batch_free.argtypes = [_vp]
+
+
+def make_query(graph: int, app, source: int, iters: int = 20, damping: float = 0.85) -> gg_query:
+    a = APPS[app] if isinstance(app, str) else int(app)
+    return gg_query(graph, a, source, iters, damping)
+
+
+def gg_batch_create(graphs, queries, cluster=4, warp_deg=32, cta_deg=1024, big_arcs=1 << 22) -> int:
+    """Plan a batch over loaded graph handles; returns the batch handle."""
+    ga = (_vp * len(graphs))(*graphs)
+    qa = (gg_query * len(queries))(*queries)
+    cfg = gg_batch_config(cluster, warp_deg, cta_deg, 0, big_arcs)
+    h = _vp()
+    _check(_lib.gg_batch_create(ga, len(graphs), qa, len(queries), ctypes.byref(cfg), ctypes.byref(h)),
+           "gg_batch_create")
+    return h.value
+
+
+def gg_batch_run(b: int) -> float:
+    """Serve every query; returns the launch's device time in ms."""
+    ms = ctypes.c_float(0.0)
+    _check(_lib.gg_batch_run(b, ctypes.byref(ms)), "gg_batch_run")
+    return ms.value
+
+
+def gg_batch_query_stats(b: int, n: int) -> np.ndarray:
+    out = (gg_query_stats * n)()
+    _check(_lib.gg_batch_query_stats(b, out, n), "gg_batch_query_stats")
+    return np.array([(s.latency_ns, s.service_ns, s.arcs, s.iterations, s.team) for s in out],
+                    dtype=[("latency_ns", np.uint64), ("service_ns", np.uint64), ("arcs", np.uint64),
+                           ("iterations", np.uint32), ("team", np.uint32)])
+
+
+def gg_batch_result(b: int, q: int, n: int, app) -> np.ndarray:
+    a = APPS[app] if isinstance(app, str) else int(app)
+    out = np.empty(n, np.float32 if a == GG_APP_PPR else np.uint32)
+    _check(_lib.gg_batch_result(b, q, out.ctypes.data, out.nbytes), "gg_batch_result")
+    return out
+
+
+def gg_batch_free(b: int):
+    _lib.gg_batch_free(b)

@@ -38,7 +38,8 @@ def test_binding_layouts_match_the_header():
     import subprocess
     import tempfile
     from paper_2104_10039_gb300 import gg
-    structs = {"gg_params": gg.gg_params, "gg_stats": gg.gg_stats}
+    structs = {"gg_params": gg.gg_params, "gg_stats": gg.gg_stats, "gg_query": gg.gg_query,
+               "gg_batch_config": gg.gg_batch_config, "gg_query_stats": gg.gg_query_stats}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gg.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
