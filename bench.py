@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--scale", type=int, default=SCALE, help="R-MAT scale (the workload is 22)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     return ap.parse_args()
 
 
@@ -497,6 +498,10 @@ def main():
     if not a.no_accuracy:
         out["time_to_accuracy"] = accuracy_table(g, source, collected)
         out["learned_correction"] = learned_section(g, source)
+    if not a.no_serving:
+        from paper_2104_10039_gb300 import gg, serve
+        graphs, queries, scales = serve.make_workload()
+        out["serving"] = serve.measure(gg, graphs, queries, scales)
     if not a.no_cpu_baseline and world >= 1:
         arcs, secs = cpu_sample(g)
         out["cpu_baseline"] = {"value": round(arcs / secs / 1e9, 4), "unit": "GTEPS",

@@ -337,11 +337,15 @@ typedef struct {
 } gg_query;
 
 typedef struct {
-    int32_t cluster;      /* CTAs per cluster team: 1 (no cluster teams), 2, 4 or 8 */
+    int32_t cluster;      /* CTAs per cluster team: 1 (no cluster teams), 2, 4, 8 or 16 (16 is a
+                             non-portable size: GG_ERR_CUDA where the device cannot place it) */
     int32_t warp_deg;     /* degree from which a warp handles a vertex (>= 1) */
     int32_t cta_deg;      /* degree from which the whole CTA does (>= warp_deg) */
-    int32_t reserved;
+    int32_t threads;      /* threads per CTA: 256, 512 or 1024 (0 = 256) */
     int64_t big_arcs;     /* graphs with at least this many arcs get cluster teams */
+    int32_t small_first;  /* every small_first-th cluster serves the single-CTA queries first,
+                             the rest start with the cluster-team queries (0: all start there) */
+    int32_t reserved;     /* 0 */
 } gg_batch_config;
 
 typedef struct {

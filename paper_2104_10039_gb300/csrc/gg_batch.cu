@@ -20,6 +20,12 @@
 // Personalized PageRank pulls over the in-edges for a fixed number of
 // iterations: rank_0 = e_s, rank' = (1-d) e_s + d * sum rank(v) / outdeg(v),
 // summed per row in a fixed order.
+//
+// Visibility: the team barrier orders each iteration's writes before the
+// next iteration's reads (__syncthreads within a CTA; the cluster barrier
+// has release / acquire semantics at cluster scope), so the rank arrays use
+// plain, L1-cached loads; BFS / SSSP values, which other CTAs lower with
+// atomics during an iteration, are read from L2.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -73,10 +79,11 @@ struct BatchArgs {
     unsigned long long *t0;
     int32_t warp_deg, cta_deg;
     int32_t cluster;
+    int32_t small_first;          // every small_first-th cluster serves small queries first (0: none)
 };
 
-constexpr int kBT = 256;          // threads per CTA
-constexpr int kHubList = 256;     // CTA-binned vertices staged per pass
+// BT = threads per CTA (256, 512 or 1024: an autotuned size); at most BT
+// CTA-binned vertices are staged per pass.
 
 __device__ __forceinline__ unsigned long long globaltimer()
 {
@@ -98,12 +105,13 @@ struct ClusterTeam {
     __device__ void sync() const { cl.sync(); }
 };
 
+template <int BT>
 struct Shared {
-    int32_t hub[kHubList];
+    int32_t hub[BT];
     int32_t hub_n;
     int32_t claim;
     unsigned long long arcs;
-    float red[kBT / 32];
+    float red[BT / 32];
 };
 
 // Relax arc (v -> u) with candidate cand (BFS / SSSP push).
@@ -126,9 +134,9 @@ __device__ __forceinline__ uint32_t cand_of(uint32_t vv, int app, const uint32_t
 }
 
 // ---------------------------------------------------------- BFS / SSSP --
-template <class Team>
+template <int BT, class Team>
 __device__ void serve_push(const BatchArgs &A, const BatchQuery &Q, const BatchGraph &G, const Team &team,
-                           Shared &sh, QueryStatsDev *qs)
+                           Shared<BT> &sh, QueryStatsDev *qs)
 {
     const int32_t n = G.n;
     uint32_t *val = A.arena + Q.off;
@@ -138,7 +146,7 @@ __device__ void serve_push(const BatchArgs &A, const BatchQuery &Q, const BatchG
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tr = team.rank(), ts = team.size();
     // init
-    for (int32_t u = tr * kBT + tid; u < n; u += ts * kBT) {
+    for (int32_t u = tr * BT + tid; u < n; u += ts * BT) {
         __stcg(val + u, u == Q.source ? 0u : kInf);
         __stcg(stamp + u, 0u);
     }
@@ -162,7 +170,7 @@ __device__ void serve_push(const BatchArgs &A, const BatchQuery &Q, const BatchG
         const uint32_t lo = (uint32_t)(((unsigned long long)len * tr) / ts);
         const uint32_t hi = (uint32_t)(((unsigned long long)len * (tr + 1)) / ts);
         unsigned long long my_arcs = 0;
-        for (uint32_t b0 = lo; b0 < hi; b0 += kBT) {
+        for (uint32_t b0 = lo; b0 < hi; b0 += BT) {
             const uint32_t i = b0 + tid;
             int32_t v = -1, e0 = 0, deg = 0;
             if (i < hi) {
@@ -201,7 +209,7 @@ __device__ void serve_push(const BatchArgs &A, const BatchQuery &Q, const BatchG
                 const int32_t he0 = __ldg(G.out_ptr + hv);
                 const int32_t hdeg = __ldg(G.out_ptr + hv + 1) - he0;
                 const uint32_t vv = __ldcg(val + hv);
-                for (int32_t k = tid; k < hdeg; k += kBT) {
+                for (int32_t k = tid; k < hdeg; k += BT) {
                     const int32_t e = he0 + k;
                     relax(val, stamp, tag, qn, ln, __ldg(G.out_dst + e), cand_of(vv, Q.app, G.out_w, e));
                 }
@@ -218,9 +226,9 @@ __device__ void serve_push(const BatchArgs &A, const BatchQuery &Q, const BatchG
 }
 
 // ------------------------------------------------ personalized PageRank --
-template <class Team>
+template <int BT, class Team>
 __device__ void serve_ppr(const BatchArgs &A, const BatchQuery &Q, const BatchGraph &G, const Team &team,
-                          Shared &sh, QueryStatsDev *qs)
+                          Shared<BT> &sh, QueryStatsDev *qs)
 {
     const int32_t n = G.n;
     float *rank[2] = {(float *)(A.arena + Q.off), (float *)(A.arena + Q.off + (size_t)n)};
@@ -228,11 +236,11 @@ __device__ void serve_ppr(const BatchArgs &A, const BatchQuery &Q, const BatchGr
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tr = team.rank(), ts = team.size();
     const float d = Q.damping, restart = 1.0f - Q.damping;
-    for (int32_t u = tr * kBT + tid; u < n; u += ts * kBT) {
+    for (int32_t u = tr * BT + tid; u < n; u += ts * BT) {
         const int32_t od = __ldg(G.out_ptr + u + 1) - __ldg(G.out_ptr + u);
         const float r = u == Q.source ? 1.0f : 0.0f;
-        __stcg(rank[0] + u, r);
-        __stcg(contrib[0] + u, od > 0 ? __fdiv_rn(r, (float)od) : 0.0f);
+        rank[0][u] = r;
+        contrib[0][u] = od > 0 ? __fdiv_rn(r, (float)od) : 0.0f;
     }
     team.sync();
     const int32_t lo = (int32_t)(((long long)n * tr) / ts), hi = (int32_t)(((long long)n * (tr + 1)) / ts);
@@ -243,10 +251,10 @@ __device__ void serve_ppr(const BatchArgs &A, const BatchQuery &Q, const BatchGr
         auto apply = [&](int32_t u, float acc) {
             const float nw = __fmaf_rn(d, acc, u == Q.source ? restart : 0.0f);
             const int32_t od = __ldg(G.out_ptr + u + 1) - __ldg(G.out_ptr + u);
-            __stcg(rn + u, nw);
-            __stcg(cn + u, od > 0 ? __fdiv_rn(nw, (float)od) : 0.0f);
+            rn[u] = nw;
+            cn[u] = od > 0 ? __fdiv_rn(nw, (float)od) : 0.0f;
         };
-        for (int32_t b0 = lo; b0 < hi; b0 += kBT) {
+        for (int32_t b0 = lo; b0 < hi; b0 += BT) {
             const int32_t u = b0 + tid;
             int32_t k0 = 0, deg = -1;
             if (u < hi) {
@@ -256,8 +264,16 @@ __device__ void serve_ppr(const BatchArgs &A, const BatchQuery &Q, const BatchGr
             if (tid == 0) sh.hub_n = 0;
             __syncthreads();
             if (deg >= 0 && deg < A.warp_deg) {
+                // four independent gathers in flight, summed in arc order
                 float acc = 0.0f;
-                for (int32_t k = k0; k < k0 + deg; ++k) acc = __fadd_rn(acc, __ldcg(cc + __ldg(G.in_src + k)));
+                int32_t k = k0;
+                for (; k + 4 <= k0 + deg; k += 4) {
+                    const int32_t s0 = __ldg(G.in_src + k), s1 = __ldg(G.in_src + k + 1);
+                    const int32_t s2 = __ldg(G.in_src + k + 2), s3 = __ldg(G.in_src + k + 3);
+                    const float c0 = cc[s0], c1 = cc[s1], c2 = cc[s2], c3 = cc[s3];
+                    acc = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(acc, c0), c1), c2), c3);
+                }
+                for (; k < k0 + deg; ++k) acc = __fadd_rn(acc, cc[__ldg(G.in_src + k)]);
                 apply(u, acc);
             }
             unsigned mb = __ballot_sync(0xFFFFFFFFu, deg >= A.warp_deg && deg < A.cta_deg);
@@ -268,7 +284,7 @@ __device__ void serve_ppr(const BatchArgs &A, const BatchQuery &Q, const BatchGr
                 const int32_t wk0 = __shfl_sync(0xFFFFFFFFu, k0, src);
                 const int32_t wdeg = __shfl_sync(0xFFFFFFFFu, deg, src);
                 float acc = 0.0f;
-                for (int32_t k = lane; k < wdeg; k += 32) acc = __fadd_rn(acc, __ldcg(cc + __ldg(G.in_src + wk0 + k)));
+                for (int32_t k = lane; k < wdeg; k += 32) acc = __fadd_rn(acc, cc[__ldg(G.in_src + wk0 + k)]);
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) acc = __fadd_rn(acc, __shfl_xor_sync(0xFFFFFFFFu, acc, o));
                 if (lane == src) apply(wu, acc);
@@ -280,14 +296,14 @@ __device__ void serve_ppr(const BatchArgs &A, const BatchQuery &Q, const BatchGr
                 const int32_t hk0 = __ldg(G.in_ptr + hu);
                 const int32_t hdeg = __ldg(G.in_ptr + hu + 1) - hk0;
                 float acc = 0.0f;
-                for (int32_t k = tid; k < hdeg; k += kBT) acc = __fadd_rn(acc, __ldcg(cc + __ldg(G.in_src + hk0 + k)));
+                for (int32_t k = tid; k < hdeg; k += BT) acc = __fadd_rn(acc, cc[__ldg(G.in_src + hk0 + k)]);
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) acc = __fadd_rn(acc, __shfl_xor_sync(0xFFFFFFFFu, acc, o));
                 if (lane == 0) sh.red[warp] = acc;
                 __syncthreads();
                 if (tid == 0) {
                     float t = 0.0f;
-                    for (int w = 0; w < kBT / 32; ++w) t = __fadd_rn(t, sh.red[w]);
+                    for (int w = 0; w < BT / 32; ++w) t = __fadd_rn(t, sh.red[w]);
                     apply(hu, t);
                 }
                 __syncthreads();
@@ -302,8 +318,8 @@ __device__ void serve_ppr(const BatchArgs &A, const BatchQuery &Q, const BatchGr
     }
 }
 
-template <class Team>
-__device__ void serve(const BatchArgs &A, int32_t q, const Team &team, Shared &sh)
+template <int BT, class Team>
+__device__ void serve(const BatchArgs &A, int32_t q, const Team &team, Shared<BT> &sh)
 {
     const BatchQuery Q = A.queries[q];
     const BatchGraph G = A.graphs[Q.graph];
@@ -312,35 +328,45 @@ __device__ void serve(const BatchArgs &A, int32_t q, const Team &team, Shared &s
         qs->t_start = globaltimer();
         qs->team = (uint32_t)team.size();
     }
-    if (Q.app == GG_APP_PPR) serve_ppr(A, Q, G, team, sh, qs);
-    else serve_push(A, Q, G, team, sh, qs);
+    if (Q.app == GG_APP_PPR) serve_ppr<BT>(A, Q, G, team, sh, qs);
+    else serve_push<BT>(A, Q, G, team, sh, qs);
     team.sync();
     if (team.rank() == 0 && threadIdx.x == 0) qs->t_end = globaltimer();
 }
 
-__global__ void __launch_bounds__(kBT) k_batch(BatchArgs A)
+template <int BT>
+__global__ void __launch_bounds__(BT) k_batch(BatchArgs A)
 {
-    __shared__ Shared sh;
+    __shared__ Shared<BT> sh;
     if (threadIdx.x == 0) atomicMin(A.t0, globaltimer());
-    if (A.cluster > 1) {
-        ClusterTeam team{cg::this_cluster()};
-        for (;;) {
-            if (team.rank() == 0 && threadIdx.x == 0) sh.claim = (int32_t)atomicAdd(&A.counters[0], 1u);
-            team.sync();
-            const int32_t idx = *team.cl.map_shared_rank(&sh.claim, 0);
-            team.sync();
-            if (idx >= A.n_big) break;
-            serve(A, A.order_big[idx], team, sh);
+    // Some clusters start with the small queries (so short queries do not
+    // queue behind every large one), the others with the large ones; each
+    // then serves the other kind until none is left.
+    const int cid = (int)(blockIdx.x / (unsigned)(A.cluster > 1 ? A.cluster : 1));
+    const bool small_first = A.cluster > 1 && A.small_first > 0 && cid % A.small_first == 0;
+    for (int phase = 0; phase < 2; ++phase) {
+        if ((phase == 0) != small_first) {
+            if (A.cluster <= 1) continue;
+            ClusterTeam team{cg::this_cluster()};
+            for (;;) {
+                if (team.rank() == 0 && threadIdx.x == 0) sh.claim = (int32_t)atomicAdd(&A.counters[0], 1u);
+                team.sync();
+                const int32_t idx = *team.cl.map_shared_rank(&sh.claim, 0);
+                team.sync();
+                if (idx >= A.n_big) break;
+                serve<BT>(A, A.order_big[idx], team, sh);
+            }
+        } else {
+            CtaTeam solo;
+            for (;;) {
+                if (threadIdx.x == 0) sh.claim = (int32_t)atomicAdd(&A.counters[1], 1u);
+                __syncthreads();
+                const int32_t idx = sh.claim;
+                __syncthreads();
+                if (idx >= A.n_small) break;
+                serve<BT>(A, A.order_small[idx], solo, sh);
+            }
         }
-    }
-    CtaTeam solo;
-    for (;;) {
-        if (threadIdx.x == 0) sh.claim = (int32_t)atomicAdd(&A.counters[1], 1u);
-        __syncthreads();
-        const int32_t idx = sh.claim;
-        __syncthreads();
-        if (idx >= A.n_small) break;
-        serve(A, A.order_small[idx], solo, sh);
     }
 }
 
@@ -359,6 +385,7 @@ struct gg_batch {
     gg::DevBuf b_graphs, b_queries, b_order, b_counters, b_arena, b_qs;
     gg::BatchArgs args{};
     int grid = 0;
+    int threads = 256;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -366,11 +393,20 @@ struct gg_batch {
 
 using namespace gg;
 
+static const void *batch_kernel(int threads)
+{
+    switch (threads) {
+    case 512: return (const void *)k_batch<512>;
+    case 1024: return (const void *)k_batch<1024>;
+    default: return (const void *)k_batch<256>;
+    }
+}
+
 static cudaError_t launch_batch(gg_batch *b)
 {
     cudaLaunchConfig_t lc{};
     lc.gridDim = dim3((unsigned)b->grid);
-    lc.blockDim = dim3(kBT);
+    lc.blockDim = dim3((unsigned)b->threads);
     lc.dynamicSmemBytes = 0;
     lc.stream = b->stream;
     cudaLaunchAttribute at[1];
@@ -380,7 +416,8 @@ static cudaError_t launch_batch(gg_batch *b)
     at[0].val.clusterDim.z = 1;
     lc.attrs = at;
     lc.numAttrs = 1;
-    return cudaLaunchKernelEx(&lc, k_batch, b->args);
+    void *args[] = {&b->args};
+    return cudaLaunchKernelExC(&lc, batch_kernel(b->threads), args);
 }
 
 extern "C" {
@@ -394,8 +431,13 @@ gg_status gg_batch_create(gg_graph *const *graphs, int32_t n_graphs, const gg_qu
         set_error("gg_batch_create: empty or NULL graphs / queries / cfg");
         return GG_ERR_INVALID_ARG;
     }
-    if (!(cfg->cluster == 1 || cfg->cluster == 2 || cfg->cluster == 4 || cfg->cluster == 8)) {
-        set_error("gg_batch_create: cluster must be 1, 2, 4 or 8");
+    if (!(cfg->cluster == 1 || cfg->cluster == 2 || cfg->cluster == 4 || cfg->cluster == 8 || cfg->cluster == 16)) {
+        set_error("gg_batch_create: cluster must be 1, 2, 4, 8 or 16");
+        return GG_ERR_INVALID_ARG;
+    }
+    if (cfg->small_first < 0) { set_error("gg_batch_create: small_first must be >= 0"); return GG_ERR_INVALID_ARG; }
+    if (!(cfg->threads == 0 || cfg->threads == 256 || cfg->threads == 512 || cfg->threads == 1024)) {
+        set_error("gg_batch_create: threads must be 0 (256), 256, 512 or 1024");
         return GG_ERR_INVALID_ARG;
     }
     if (cfg->warp_deg < 1 || cfg->cta_deg < cfg->warp_deg) {
@@ -407,6 +449,7 @@ gg_status gg_batch_create(gg_graph *const *graphs, int32_t n_graphs, const gg_qu
     gg_batch *b = new (std::nothrow) gg_batch();
     if (!b) { set_error("gg_batch_create: host allocation failed"); return GG_ERR_OOM; }
     b->cfg = *cfg;
+    b->threads = cfg->threads ? cfg->threads : 256;
     b->n_queries = n_queries;
     gg_status st = GG_OK;
     cudaError_t e;
@@ -480,9 +523,16 @@ gg_status gg_batch_create(gg_graph *const *graphs, int32_t n_graphs, const gg_qu
         A.warp_deg = cfg->warp_deg;
         A.cta_deg = cfg->cta_deg;
         A.cluster = cfg->cluster;
+        A.small_first = cfg->small_first;
         // persistent grid: as many clusters (or CTAs) as fit at once
+        const void *fn = batch_kernel(b->threads);
+        if (cfg->cluster > 8 &&
+            (e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) {
+            st = cuda_fail(e, "cluster size 16 (non-portable)");
+            break;
+        }
         cudaLaunchConfig_t lc{};
-        lc.blockDim = dim3(kBT);
+        lc.blockDim = dim3((unsigned)b->threads);
         lc.gridDim = dim3((unsigned)(b->num_sms * cfg->cluster));
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;
@@ -492,7 +542,7 @@ gg_status gg_batch_create(gg_graph *const *graphs, int32_t n_graphs, const gg_qu
         lc.attrs = at;
         lc.numAttrs = 1;
         int clusters = 0;
-        if ((e = cudaOccupancyMaxActiveClusters(&clusters, k_batch, &lc)) != cudaSuccess || clusters < 1) {
+        if ((e = cudaOccupancyMaxActiveClusters(&clusters, fn, &lc)) != cudaSuccess || clusters < 1) {
             if (e == cudaSuccess) e = cudaErrorInvalidConfiguration;
             st = cuda_fail(e, "cudaOccupancyMaxActiveClusters");
             break;

@@ -265,7 +265,8 @@ class gg_query(ctypes.Structure):
 
 class gg_batch_config(ctypes.Structure):
     _fields_ = [("cluster", ctypes.c_int32), ("warp_deg", ctypes.c_int32), ("cta_deg", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("big_arcs", ctypes.c_int64)]
+                ("threads", ctypes.c_int32), ("big_arcs", ctypes.c_int64), ("small_first", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class gg_query_stats(ctypes.Structure):
@@ -291,11 +292,12 @@ def make_query(graph: int, app, source: int, iters: int = 20, damping: float = 0
     return gg_query(graph, a, source, iters, damping)
 
 
-def gg_batch_create(graphs, queries, cluster=4, warp_deg=32, cta_deg=1024, big_arcs=1 << 22) -> int:
+def gg_batch_create(graphs, queries, cluster=4, warp_deg=32, cta_deg=1024, big_arcs=1 << 22, threads=256,
+                    small_first=0) -> int:
     """Plan a batch over loaded graph handles; returns the batch handle."""
     ga = (_vp * len(graphs))(*graphs)
     qa = (gg_query * len(queries))(*queries)
-    cfg = gg_batch_config(cluster, warp_deg, cta_deg, 0, big_arcs)
+    cfg = gg_batch_config(cluster, warp_deg, cta_deg, threads, big_arcs, small_first, 0)
     h = _vp()
     _check(_lib.gg_batch_create(ga, len(graphs), qa, len(queries), ctypes.byref(cfg), ctypes.byref(h)),
            "gg_batch_create")

@@ -52,16 +52,18 @@ def _oracle(g, app, src, iters):
                       nthreads=0)["values"]
 
 
-@pytest.mark.parametrize("cluster,warp_deg,cta_deg,big_arcs", [
-    (1, 32, 1024, 0), (4, 8, 64, 20000), (8, 2, 16, 0), (2, 1, 1, 40000), (4, 1000000, 1000000, 0)])
-def test_batch_matches_oracle(gg, cluster, warp_deg, cta_deg, big_arcs):
+@pytest.mark.parametrize("cluster,warp_deg,cta_deg,big_arcs,threads,small_first", [
+    (1, 32, 1024, 0, 256, 0), (4, 8, 64, 20000, 256, 0), (8, 2, 16, 0, 512, 0), (2, 1, 1, 40000, 1024, 1),
+    (4, 1000000, 1000000, 0, 256, 0), (8, 16, 128, 30000, 1024, 0), (4, 8, 64, 30000, 512, 2)])
+def test_batch_matches_oracle(gg, cluster, warp_deg, cta_deg, big_arcs, threads, small_first):
     gs = _graphs()
     hs = [gc.load(gg, g) for g in gs]
     b = None
     try:
         qs = _queries(gg, gs, 40, seed=cluster * 7 + warp_deg)
         b = gg.gg_batch_create(hs, [gg.make_query(gi, app, s, it) for gi, app, s, it in qs], cluster=cluster,
-                               warp_deg=warp_deg, cta_deg=cta_deg, big_arcs=big_arcs)
+                               warp_deg=warp_deg, cta_deg=cta_deg, big_arcs=big_arcs, threads=threads,
+                               small_first=small_first)
         for rep in range(2):          # first run captures the graph, the second replays it
             gg.gg_batch_run(b)
             st = gg.gg_batch_query_stats(b, len(qs))
@@ -88,7 +90,8 @@ def test_batch_errors(gg):
     h = gc.load(gg, g)
     try:
         for q, kw in (((0, "sssp", 0), {}), ((1, "bfs", 0), {}), ((0, "bfs", g.n), {}), ((0, "cc", 0), {}),
-                      ((0, "bfs", 0), {"cluster": 3}), ((0, "bfs", 0), {"warp_deg": 8, "cta_deg": 4})):
+                      ((0, "bfs", 0), {"cluster": 3}), ((0, "bfs", 0), {"warp_deg": 8, "cta_deg": 4}),
+                      ((0, "bfs", 0), {"threads": 128})):
             with pytest.raises(gg.GGError) as e:
                 gg.gg_batch_create([h], [gg.make_query(*q)], **kw)
             assert e.value.status == gg.GG_ERR_INVALID_ARG
