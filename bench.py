@@ -21,7 +21,6 @@ on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
-import hashlib
 import json
 import os
 import statistics
@@ -179,27 +178,20 @@ def peak_hbm():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_hash():
-    h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2104_10039_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(fh.read())
-    return h.hexdigest()[:16]
-
-
-def recorded_traffic(cls):
-    """DRAM bytes per launch of a kernel class from the committed ncu summary,
-    if it was taken on the current kernel sources."""
+def recorded_traffic(cls, algorithmic_bytes):
+    """DRAM bytes per launch of a kernel class: the committed ncu capture's
+    traffic / algorithmic-bytes ratio times this launch's algorithmic bytes,
+    if the capture was taken on the current tile-engine sources."""
+    from paper_2104_10039_gb300 import profile_traffic
     try:
         with open(TRAFFIC) as f:
             t = json.load(f)
     except (OSError, ValueError):
         return None
-    if t.get("kernel_hash") != kernel_hash():
+    if t.get("kernel_hash") != profile_traffic.kernel_hash():
         return None
-    return t.get("bytes_per_launch", {}).get(cls)
+    c = t.get("classes", {}).get(cls)
+    return int(c["ratio"] * algorithmic_bytes) if c else None
 
 
 # ------------------------------------------------------------------ our arm --
@@ -319,7 +311,7 @@ def bench_ours(a, rank, world, local):
                 "correct": "k_tile<{a}, K_STASH> + k_tile<{a}, K_CORRECT>"}[dom[1]].format(a=dom[0])
         roof = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
-                "traffic": recorded_traffic(f"{dom[0]}/{dom[1]}"),
+                "traffic": recorded_traffic(f"{dom[0]}/{dom[1]}", bytes_per),
                 "algorithmic_bytes_per_launch": int(bytes_per),
                 "avg_launch_ms": round(classes[dom][0] / classes[dom][1], 4),
                 "ms_last_step": {f"{k[0]}/{k[1]}": round(v[0], 3) for k, v in classes.items()}}

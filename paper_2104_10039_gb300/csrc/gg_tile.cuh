@@ -484,11 +484,14 @@ k_tile(TileArgs a)
                         if constexpr (KIND == K_CORRECT) {
                             uint32_t fl;
                             if constexpr (APP == GG_APP_PAGERANK) {
-                                // GG-Gather's returned influence (Alg. 2): (new - old) / new;
-                                // with the share variant, decided after the row totals
+                                // GG-Gather's returned influence (Alg. 2): (new - old) / new
+                                // > theta, tested without the division as (new - old) >
+                                // theta * new (new >= 0); with the share variant, decided
+                                // after the row totals
                                 const float after = __fadd_rn(acc, v);
-                                const float infl = after != 0.0f ? __fdiv_rn(__fsub_rn(after, acc), after) : 0.0f;
-                                fl = (!a.infl_share && infl > a.theta) ? 1u : 0u;
+                                const bool hit = after != 0.0f ? __fsub_rn(after, acc) > __fmul_rn(a.theta, after)
+                                                               : 0.0f > a.theta;
+                                fl = (!a.infl_share && hit) ? 1u : 0u;
                             } else {
                                 if (v == kInf) {   // no candidate: the arc keeps its flag
                                     const int k = a0 + y;
@@ -550,9 +553,10 @@ k_tile(TileArgs a)
 #pragma unroll
                 for (int i = 0; i < kIPT; ++i) {
                     if ((arcmask >> i) & 1u) {
-                        const float tot = s.rowtot[x];
-                        const float infl = tot != 0.0f ? __fdiv_rn(__uint_as_float(item_v[i]), tot) : 0.0f;
-                        const uint32_t fl = infl > a.theta ? 1u : 0u;
+                        const float tot = s.rowtot[x];   // share c / tot > theta as c > theta * tot
+                        const bool hit = tot != 0.0f ? __uint_as_float(item_v[i]) > __fmul_rn(a.theta, tot)
+                                                     : 0.0f > a.theta;
+                        const uint32_t fl = hit ? 1u : 0u;
                         my_flags |= fl << i;
                         my_active += fl;
                     } else if ((endmask >> i) & 1u) {
@@ -571,20 +575,29 @@ k_tile(TileArgs a)
             if (lane == 31 && a.tile_cnt) a.tile_cnt[t] = incl;
             uint32_t off = incl - my_active;   // active arcs of the tile before this lane's items
             {
-                int x = lx, y = ly;
+                // this lane's arcs are the consecutive list positions a0+ly ..,
+                // so its flags form one run of at most kIPT bits: at most two
+                // shared-memory ORs per lane
+                uint32_t run = 0;
+                int na = 0, x = lx;
 #pragma unroll
                 for (int i = 0; i < kIPT; ++i) {
                     if ((arcmask >> i) & 1u) {
                         if ((my_flags >> i) & 1u) {
-                            const int k = a0 + y;
-                            atomicOr(&s.bits[(k >> 5) - w0], 1u << (k & 31));
+                            run |= 1u << na;
                             ++off;
                         }
-                        ++y;
+                        ++na;
                     } else if ((endmask >> i) & 1u) {
                         if (a.sp_ptr) a.sp_ptr[r0 + x + 1] = (int32_t)off;   // tile-local; k_pack adds the tile offset
                         ++x;
                     }
+                }
+                if (run) {
+                    const int k0 = a0 + ly;
+                    const int sh = k0 & 31, wi = (k0 >> 5) - w0;
+                    atomicOr(&s.bits[wi], run << sh);
+                    if (sh + na > 32) atomicOr(&s.bits[wi + 1], run >> (32 - sh));
                 }
             }
             __syncwarp();
