@@ -459,6 +459,7 @@ int orc_run(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx,
         int learned = 0;
         if (correcting && learned_policy && !force_full) {
             int64_t nsel = 0, sel_arcs = 0;
+#pragma omp parallel for schedule(dynamic, 1024)
             for (int32_t u = 0; u < n; ++u) {
                 float x[ORC_MLP_IN];
                 vertex_features(u, n, i, p->app, in_ptr, outdeg, mask, hist, executed, x);
@@ -489,6 +490,7 @@ int orc_run(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx,
         /* Trace: features before every full correction, labels after it. */
         const int tracing = correcting && !learned && p->trace_x && o->trace_rows + n <= p->trace_cap;
         if (tracing) {
+#pragma omp parallel for schedule(static)
             for (int32_t u = 0; u < n; ++u)
                 vertex_features(u, n, i, p->app, in_ptr, outdeg, mask, hist, executed,
                                 p->trace_x + (size_t)(o->trace_rows + u) * ORC_MLP_IN);

@@ -68,15 +68,37 @@ __global__ void k_pack(const int32_t *__restrict__ tile_info, const uint32_t *__
         const int32_t r0 = tile_info[t] & 0x7FFFFFFF, r1 = tile_info[t + 1] & 0x7FFFFFFF;
         const long long d1 = (t + 1) * kWT < total_items ? (t + 1) * kWT : total_items;
         const int32_t a0 = (int32_t)(t * kWT - r0), a1 = (int32_t)(d1 - r1);
+        // the tile's flag words (at most kWords) in one load per lane, then
+        // every chunk's source loads issued before any store
+        constexpr int kWords = kWT / 32 + 1;
+        const int32_t wb = a0 >> 5;
+        const int nw = a1 > a0 ? ((a1 - 1) >> 5) - wb + 1 : 0;
+        const uint32_t myw = (int)lane < nw ? mask[wb + (int)lane] : 0u;
+        int32_t sv[kWords];
+        uint32_t wv[kWords];
+        uint32_t onbits = 0;
+#pragma unroll
+        for (int c = 0; c < kWords; ++c) {
+            sv[c] = 0;
+            wv[c] = 0;
+            const uint32_t word = __shfl_sync(0xFFFFFFFFu, myw, c);
+            const int32_t k = (wb + c) * 32 + (int32_t)lane;
+            const bool on = c < nw && k >= a0 && k < a1 && ((word >> lane) & 1u);
+            if (on) {
+                sv[c] = __ldg(in_src + k);
+                if (sp_w) wv[c] = __ldg(in_w + k);
+                onbits |= 1u << c;
+            }
+        }
         uint32_t pos = tile_off[t];
-        for (int32_t base = a0; base < a1; base += 32) {
-            const int32_t k = base + (int32_t)lane;
-            const bool on = k < a1 && ((mask[k >> 5] >> (k & 31)) & 1u);
+#pragma unroll
+        for (int c = 0; c < kWords; ++c) {
+            const bool on = (onbits >> c) & 1u;
             const uint32_t b = __ballot_sync(0xFFFFFFFFu, on);
             if (on) {
                 const uint32_t q = pos + __popc(b & lt);
-                sp_src[q] = in_src[k];
-                if (sp_w) sp_w[q] = in_w[k];
+                sp_src[q] = sv[c];
+                if (sp_w) sp_w[q] = wv[c];
             }
             pos += __popc(b);
         }

@@ -80,10 +80,15 @@ def _error(app, vals, ref, source):
     return metrics.stretch_error(vals, ref, source)["error"]
 
 
+POLICIES = (("adaptive", "adaptive", 1.0), ("learned", "learned", 1.0), ("learned_fallback_0.5", "learned", 0.5))
+
+
 def compare(gg, g, source, P, apps=("pagerank", "sssp"), sigmas=(0.5, 0.9), select_logit=0.0, target=0.01):
-    """Plain adaptive vs learned correction on g: per app and sigma, device
-    time and error at the exact run's iteration count, and the time to reach
-    `target` error (fewest iterations)."""
+    """Plain adaptive vs learned correction (without fallback, and falling
+    back to the full correction when the selection holds more than half the
+    arcs) on g: per app and sigma, device time and error at the exact run's
+    iteration count, and the time to reach `target` error (fewest
+    iterations)."""
     h = gg.gg_load_csr(g.n, g.m, g.rowptr, g.colidx, g.weights, gg.GG_DIRECTED)
     out = {}
     try:
@@ -95,20 +100,20 @@ def compare(gg, g, source, P, apps=("pagerank", "sssp"), sigmas=(0.5, 0.9), sele
             ex_ms = gg.stats(h).ms_run
             res = {"exact": {"iters": full_iters, "ms": round(ex_ms, 3)}}
 
-            def run(policy, sigma, iters):
+            def run(policy, sigma, iters, frac):
                 gg.gg_run(h, app, sigma, policy, _params(gg, app, source, iters,
-                                                         {"select_logit": select_logit}))
+                                                         {"select_logit": select_logit, "fallback_frac": frac}))
                 st = gg.stats(h)
                 return gg.values(h, app), st
 
             for sigma in sigmas:
                 row = {}
-                for policy in ("adaptive", "learned"):
-                    run(policy, sigma, full_iters)   # warm
-                    vals, st = run(policy, sigma, full_iters)
+                for label, policy, frac in POLICIES:
+                    run(policy, sigma, full_iters, frac)   # warm
+                    vals, st = run(policy, sigma, full_iters, frac)
                     it = gg.result_array(h, gg.GG_RESULT_ITER_STATS)
                     lm = (it["mode"] & gg.GG_ITER_LEARNED) != 0
-                    row[policy] = {"ms": round(st.ms_run, 3), "error": round(_error(app, vals, ref, source), 5),
+                    row[label] = {"ms": round(st.ms_run, 3), "error": round(_error(app, vals, ref, source), 5),
                                    "corrections": st.corrections, "learned_corrections": st.learned_corrections,
                                    "selected_frac": round(float(it["selected"][lm].mean() / g.n), 4) if lm.any()
                                    else None,
@@ -116,14 +121,15 @@ def compare(gg, g, source, P, apps=("pagerank", "sssp"), sigmas=(0.5, 0.9), sele
                                    if lm.any() else None}
                     ttt = None
                     for t in range(1, 2 * full_iters + 1):
-                        v, s2 = run(policy, sigma, t)
+                        v, s2 = run(policy, sigma, t, frac)
                         if _error(app, v, ref, source) <= target:
                             ttt = {"iters": t, "ms": round(s2.ms_run, 3)}
                             break
-                    row[policy]["time_to_target"] = ttt
-                a, b = row["adaptive"]["time_to_target"], row["learned"]["time_to_target"]
-                row["learned_speedup_at_target"] = round(a["ms"] / b["ms"], 3) if a and b else None
-                row["learned_speedup_equal_iters"] = round(row["adaptive"]["ms"] / row["learned"]["ms"], 3)
+                    row[label]["time_to_target"] = ttt
+                for label, _, _ in POLICIES[1:]:
+                    a, b = row["adaptive"]["time_to_target"], row[label]["time_to_target"]
+                    row[label]["speedup_at_target"] = round(a["ms"] / b["ms"], 3) if a and b else None
+                    row[label]["speedup_equal_iters"] = round(row["adaptive"]["ms"] / row[label]["ms"], 3)
                 res[f"sigma_{sigma}"] = row
             out[app] = res
     finally:

@@ -115,3 +115,67 @@ def test_scale24_symmetric_bit_exact(gg, sym24, app):
         assert st.iterations == ref["iterations"]
     finally:
         gg.gg_free_graph(h)
+
+
+def test_rmat22_learned_and_triggered_sssp_bit_exact(gg, rmat22):
+    """The learned correction (a scorer whose selection is decided exactly:
+    logit = bfloat16(sqrt(in-degree)/64) - t) and the triggered policy at the
+    bench's size, against the oracle."""
+    from paper_2104_10039_gb300 import scorer
+    g, s = rmat22
+    lo, hi = (float(oracle.bf16(np.float32(np.sqrt(np.float32(k)) / np.float32(64)))) for k in (40, 41))
+    P = np.zeros(scorer.N_PARAM, np.float32)
+    P[scorer.OFF_W1] = P[scorer.OFF_W2] = P[scorer.OFF_W3] = 1.0
+    P[scorer.OFF_B3] = -(lo + hi) / 2
+    h = gc.load(gg, g)
+    try:
+        gg.gg_set_scorer(h, P)
+        p = gg.make_params(alpha=ALPHA, theta=THETA, max_iters=BIG, source=s, seed=1)
+        gg.gg_run(h, "sssp", 0.3, "learned", p)
+        got, mask = gg.values(h, "sssp"), gg.mask_bits(h, g.m)
+        assert gg.stats(h).learned_corrections >= 1
+        ref = oracle.run(g.n, g.rowptr, g.colidx, g.weights, app="sssp", policy="learned", mlp=P, sigma=0.3,
+                         seed=1, alpha=ALPHA, theta=THETA, source=s, max_iters=BIG, nthreads=0)
+        assert np.array_equal(got, ref["values"]) and np.array_equal(mask, ref["mask"])
+        p = gg.make_params(alpha=8, theta=THETA, max_iters=BIG, source=s, seed=1, trigger_ratio=0.2)
+        gg.gg_run(h, "sssp", 0.3, "triggered", p)
+        ref = oracle.run(g.n, g.rowptr, g.colidx, g.weights, app="sssp", policy="triggered", sigma=0.3, seed=1,
+                         alpha=8, theta=THETA, trigger_ratio=0.2, source=s, max_iters=BIG, nthreads=0)
+        assert np.array_equal(gg.values(h, "sssp"), ref["values"])
+        assert np.array_equal(gg.mask_bits(h, g.m), ref["mask"])
+    finally:
+        gg.gg_free_graph(h)
+
+
+def test_serving_workload_sample(gg):
+    """Queries of the serving workload (64 R-MAT graphs, scales 14-20) in the
+    configuration its autotuner picks on GB300, against the oracle: the
+    largest graphs' queries (cluster teams) and a few small ones."""
+    from paper_2104_10039_gb300 import serve
+    graphs, queries, scales = serve.make_workload()
+    order = sorted(range(len(queries)), key=lambda q: -graphs[queries[q][0]].m)
+    pick = order[:9] + order[-3:]
+    used = sorted({queries[q][0] for q in pick})
+    remap = {gi: i for i, gi in enumerate(used)}
+    hs = [gc.load(gg, graphs[gi]) for gi in used]
+    b = None
+    try:
+        qs = [queries[q] for q in pick]
+        b = gg.gg_batch_create(hs, [gg.make_query(remap[gi], app, src, it) for gi, app, src, it in qs], cluster=8,
+                               warp_deg=32, cta_deg=1024, big_arcs=1 << 21, threads=1024, small_first=4)
+        gg.gg_batch_run(b)
+        for q, (gi, app, src, it) in enumerate(qs):
+            g = graphs[gi]
+            got = gg.gg_batch_result(b, q, g.n, app)
+            if app == "ppr":
+                want = oracle.run(g.n, g.rowptr, g.colidx, app="ppr", source=src, max_iters=it, nthreads=0)["values"]
+                assert gc.rel_l1(got, want) <= 1e-5, (q, gi)
+            else:
+                want = oracle.run(g.n, g.rowptr, g.colidx, g.weights, app=app, source=src, max_iters=BIG,
+                                  nthreads=0)["values"]
+                assert np.array_equal(got, want), (q, gi, app)
+    finally:
+        if b:
+            gg.gg_batch_free(b)
+        for h in hs:
+            gg.gg_free_graph(h)
