@@ -334,6 +334,8 @@ typedef struct {
     int32_t source;
     uint32_t iters;       /* GG_APP_PPR: iterations */
     float damping;        /* GG_APP_PPR: d in [0, 1] */
+    int32_t warp_deg;     /* this query's degree bins (see gg_batch_config); 0, 0 = the batch's */
+    int32_t cta_deg;
 } gg_query;
 
 typedef struct {

@@ -12,7 +12,8 @@
 //
 // Work inside a CTA is binned by degree: a vertex below warp_deg is handled
 // by one thread, up to cta_deg by a warp (lanes over its arcs), above by the
-// whole CTA (threads over its arcs, staged through shared memory).
+// whole CTA (threads over its arcs, staged through shared memory). The bins
+// are per query (the autotuner picks them per graph scale).
 //
 // BFS / SSSP push over a frontier (atomicMin relaxations, per-iteration
 // stamps so a vertex enters the next frontier once); they run until the
@@ -57,6 +58,8 @@ struct BatchQuery {
     int32_t source;
     uint32_t iters;
     float damping;
+    int32_t warp_deg;          // degree bins of this query
+    int32_t cta_deg;
     uint32_t pad;
     unsigned long long off;    // first word of the query's state in the arena
 };
@@ -182,13 +185,13 @@ __device__ void serve_push(const BatchArgs &A, const BatchQuery &Q, const BatchG
             if (tid == 0) sh.hub_n = 0;
             __syncthreads();
             // thread bin
-            if (v >= 0 && deg < A.warp_deg) {
+            if (v >= 0 && deg < Q.warp_deg) {
                 const uint32_t vv = __ldcg(val + v);
                 for (int32_t e = e0; e < e0 + deg; ++e)
                     relax(val, stamp, tag, qn, ln, __ldg(G.out_dst + e), cand_of(vv, Q.app, G.out_w, e));
             }
             // warp bin
-            unsigned mb = __ballot_sync(0xFFFFFFFFu, v >= 0 && deg >= A.warp_deg && deg < A.cta_deg);
+            unsigned mb = __ballot_sync(0xFFFFFFFFu, v >= 0 && deg >= Q.warp_deg && deg < Q.cta_deg);
             while (mb) {
                 const int src = __ffs(mb) - 1;
                 mb &= mb - 1;
@@ -202,7 +205,7 @@ __device__ void serve_push(const BatchArgs &A, const BatchQuery &Q, const BatchG
                 }
             }
             // CTA bin
-            if (v >= 0 && deg >= A.cta_deg) sh.hub[atomicAdd(&sh.hub_n, 1)] = i;
+            if (v >= 0 && deg >= Q.cta_deg) sh.hub[atomicAdd(&sh.hub_n, 1)] = i;
             __syncthreads();
             for (int h = 0; h < sh.hub_n; ++h) {
                 const int32_t hv = __ldcg(q + sh.hub[h]);
@@ -263,7 +266,7 @@ __device__ void serve_ppr(const BatchArgs &A, const BatchQuery &Q, const BatchGr
             }
             if (tid == 0) sh.hub_n = 0;
             __syncthreads();
-            if (deg >= 0 && deg < A.warp_deg) {
+            if (deg >= 0 && deg < Q.warp_deg) {
                 // four independent gathers in flight, summed in arc order
                 float acc = 0.0f;
                 int32_t k = k0;
@@ -276,7 +279,7 @@ __device__ void serve_ppr(const BatchArgs &A, const BatchQuery &Q, const BatchGr
                 for (; k < k0 + deg; ++k) acc = __fadd_rn(acc, cc[__ldg(G.in_src + k)]);
                 apply(u, acc);
             }
-            unsigned mb = __ballot_sync(0xFFFFFFFFu, deg >= A.warp_deg && deg < A.cta_deg);
+            unsigned mb = __ballot_sync(0xFFFFFFFFu, deg >= Q.warp_deg && deg < Q.cta_deg);
             while (mb) {
                 const int src = __ffs(mb) - 1;
                 mb &= mb - 1;
@@ -289,7 +292,7 @@ __device__ void serve_ppr(const BatchArgs &A, const BatchQuery &Q, const BatchGr
                 for (int o = 16; o > 0; o >>= 1) acc = __fadd_rn(acc, __shfl_xor_sync(0xFFFFFFFFu, acc, o));
                 if (lane == src) apply(wu, acc);
             }
-            if (deg >= A.cta_deg) sh.hub[atomicAdd(&sh.hub_n, 1)] = u;
+            if (deg >= Q.cta_deg) sh.hub[atomicAdd(&sh.hub_n, 1)] = u;
             __syncthreads();
             for (int h = 0; h < sh.hub_n; ++h) {
                 const int32_t hu = sh.hub[h];
@@ -480,7 +483,13 @@ gg_status gg_batch_create(gg_graph *const *graphs, int32_t n_graphs, const gg_qu
             if (Q.source < 0 || Q.source >= g->n) { set_error("query %d: source %d outside [0, %d)", q, Q.source, g->n); st = GG_ERR_INVALID_ARG; break; }
             if (Q.app == GG_APP_SSSP && !g->has_w) { set_error("query %d: SSSP needs a weighted graph", q); st = GG_ERR_INVALID_ARG; break; }
             if (Q.app == GG_APP_PPR && !(Q.damping >= 0.0f && Q.damping <= 1.0f)) { set_error("query %d: damping must be in [0, 1]", q); st = GG_ERR_INVALID_ARG; break; }
-            BatchQuery bq{Q.graph, Q.app, Q.source, Q.iters, Q.damping, 0u, words};
+            if ((Q.warp_deg != 0 || Q.cta_deg != 0) && !(Q.warp_deg >= 1 && Q.cta_deg >= Q.warp_deg)) {
+                set_error("query %d: need 1 <= warp_deg <= cta_deg (or both 0)", q);
+                st = GG_ERR_INVALID_ARG;
+                break;
+            }
+            const int32_t wd = Q.warp_deg ? Q.warp_deg : cfg->warp_deg, cd = Q.warp_deg ? Q.cta_deg : cfg->cta_deg;
+            BatchQuery bq{Q.graph, Q.app, Q.source, Q.iters, Q.damping, wd, cd, 0u, words};
             b->hq[q] = bq;
             b->hn[q] = g->n;
             words += 4ull * (unsigned long long)g->n + 8ull;

@@ -260,7 +260,8 @@ def gg_mlp_train(features, labels, rows: int, params, batch: int, steps: int, lr
 # ------------------------------------------------------- batched serving --
 class gg_query(ctypes.Structure):
     _fields_ = [("graph", ctypes.c_int32), ("app", ctypes.c_int32), ("source", ctypes.c_int32),
-                ("iters", ctypes.c_uint32), ("damping", ctypes.c_float)]
+                ("iters", ctypes.c_uint32), ("damping", ctypes.c_float), ("warp_deg", ctypes.c_int32),
+                ("cta_deg", ctypes.c_int32)]
 
 
 class gg_batch_config(ctypes.Structure):
@@ -287,9 +288,10 @@ _lib.gg_batch_free.restype = None
 _lib.gg_batch_free.argtypes = [_vp]
 
 
-def make_query(graph: int, app, source: int, iters: int = 20, damping: float = 0.85) -> gg_query:
+def make_query(graph: int, app, source: int, iters: int = 20, damping: float = 0.85, warp_deg: int = 0,
+               cta_deg: int = 0) -> gg_query:
     a = APPS[app] if isinstance(app, str) else int(app)
-    return gg_query(graph, a, source, iters, damping)
+    return gg_query(graph, a, source, iters, damping, warp_deg, cta_deg)
 
 
 def gg_batch_create(graphs, queries, cluster=4, warp_deg=32, cta_deg=1024, big_arcs=1 << 22, threads=256,

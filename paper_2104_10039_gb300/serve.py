@@ -6,9 +6,11 @@ out-arcs, over `n_graphs` directed R-MAT graphs whose scales are drawn
 unevenly from [scale_lo, scale_hi] (small graphs are more frequent: scale =
 lo + floor((hi - lo + 1) * u^2)).
 
-Autotuner: times candidate team / bin configurations (cluster size, the arc
-count from which a graph's queries get a cluster team, the warp and CTA
-degree bins) on a calibration subset of the queries and keeps the fastest.
+Autotuner: first the team shape (threads per CTA, cluster size, the arc
+count from which a graph's queries get a cluster team, small-first
+clusters) on a calibration subset of the queries, then, for every graph
+scale, the warp and CTA degree bins on that scale's queries; each query
+then runs with its graph scale's bins.
 Every timed run is the library's persistent launch replayed from its
 captured CUDA graph; this module only arranges calls and reduces results.
 """
@@ -41,8 +43,12 @@ def make_workload(n_graphs=64, n_queries=512, scale_lo=14, scale_hi=20, edgefact
     return graphs, queries, scales
 
 
-def _run(gg, handles, queries, cfg, reps=3, warm=1):
-    b = gg.gg_batch_create(handles, [gg.make_query(gi, app, s, it) for gi, app, s, it in queries], **cfg)
+def _run(gg, handles, queries, cfg, reps=3, warm=1, bins=None):
+    """Create the batch (queries: (graph, app, source, iters); bins: per-query
+    (warp_deg, cta_deg) or None), run warm-up and timed launches."""
+    qs = [gg.make_query(gi, app, s, it, warp_deg=bins[i][0] if bins else 0, cta_deg=bins[i][1] if bins else 0)
+          for i, (gi, app, s, it) in enumerate(queries)]
+    b = gg.gg_batch_create(handles, qs, **cfg)
     try:
         for _ in range(warm):
             gg.gg_batch_run(b)
@@ -54,35 +60,56 @@ def _run(gg, handles, queries, cfg, reps=3, warm=1):
         raise
 
 
-def candidates(scale_hi=20, edgefactor=16):
-    """Team sizes (threads per CTA x CTAs per cluster), the graph size from
-    which a query gets a cluster team, and the degree bins."""
+BIN_CANDIDATES = ((8, 256), (16, 1024), (32, 1024), (64, 4096))
+
+
+def team_candidates(scale_hi=20, edgefactor=16):
+    """Team shapes: threads per CTA, CTAs per cluster, the graph size from
+    which a query gets a cluster team, and small-first clusters."""
     out = []
     for threads in (256, 1024):
-        for warp_deg, cta_deg in ((8, 256), (32, 1024)):
-            out.append(dict(cluster=1, warp_deg=warp_deg, cta_deg=cta_deg, big_arcs=1 << 62, threads=threads))
-            for cluster, big_scale in itertools.product((8, 16), (scale_hi - 3, scale_hi - 1)):
-                out.append(dict(cluster=cluster, warp_deg=warp_deg, cta_deg=cta_deg,
-                                big_arcs=edgefactor << big_scale, threads=threads, small_first=4))
+        out.append(dict(cluster=1, warp_deg=32, cta_deg=1024, big_arcs=1 << 62, threads=threads, small_first=0))
+        for cluster, big_scale in itertools.product((8, 16), (scale_hi - 3, scale_hi - 1)):
+            out.append(dict(cluster=cluster, warp_deg=32, cta_deg=1024, big_arcs=edgefactor << big_scale,
+                            threads=threads, small_first=4))
     return out
 
 
-def autotune(gg, handles, queries, cands, calib=128, seed=5):
-    """Fastest candidate on a calibration subset; returns (best, table)."""
+def _timed(gg, handles, queries, cfg, bins=None):
+    try:
+        b, times, _ = _run(gg, handles, queries, cfg, reps=2, warm=1, bins=bins)
+    except gg.GGError as e:   # e.g. a cluster size the device cannot place
+        return None, str(e)[:80]
+    gg.gg_batch_free(b)
+    return round(min(times), 3), None
+
+
+def autotune(gg, handles, queries, graph_scales, calib=128, per_scale=48, seed=5):
+    """(1) the team shape on a calibration subset of the queries with the
+    default bins; (2) for every graph scale, the degree bins on that scale's
+    queries under the chosen team shape. Returns (config, bins by scale,
+    tables)."""
     rng = np.random.default_rng(seed)
     sub = [queries[i] for i in sorted(rng.choice(len(queries), min(calib, len(queries)), replace=False))]
-    table = []
-    for cfg in cands:
-        try:
-            b, times, _ = _run(gg, handles, sub, cfg, reps=2, warm=1)
-        except gg.GGError as e:   # e.g. a cluster size the device cannot place
-            table.append({**{k: int(v) for k, v in cfg.items()}, "ms": None, "error": str(e)[:80]})
+    teams = []
+    for cfg in team_candidates():
+        ms, err = _timed(gg, handles, sub, cfg)
+        teams.append({**{k: int(v) for k, v in cfg.items()}, "ms": ms, **({"error": err} if err else {})})
+    best = min((r for r in teams if r["ms"] is not None), key=lambda r: r["ms"])
+    cfg = {k: best[k] for k in ("cluster", "warp_deg", "cta_deg", "big_arcs", "threads", "small_first")}
+    bins_by_scale, bin_table = {}, []
+    for sc in sorted(set(graph_scales)):
+        qs = [q for q in queries if graph_scales[q[0]] == sc][:per_scale]
+        if not qs:
             continue
-        gg.gg_batch_free(b)
-        table.append({**{k: int(v) for k, v in cfg.items()}, "ms": round(min(times), 3)})
-    best = min((r for r in table if r["ms"] is not None), key=lambda r: r["ms"])
-    return {k: best[k] for k in ("cluster", "warp_deg", "cta_deg", "big_arcs", "threads", "small_first")
-            if k in best}, table
+        row = {"scale": int(sc), "queries": len(qs)}
+        for wd, cd in BIN_CANDIDATES:
+            ms, _ = _timed(gg, handles, qs, cfg, bins=[(wd, cd)] * len(qs))
+            row[f"{wd}/{cd}"] = ms
+        bins_by_scale[int(sc)] = min(BIN_CANDIDATES, key=lambda b: row[f"{b[0]}/{b[1]}"] or float("inf"))
+        bin_table.append(row)
+    return cfg, bins_by_scale, {"teams": sorted((r for r in teams if r["ms"] is not None), key=lambda r: r["ms"])[:6],
+                                "team_candidates": len(teams), "bins_by_scale_ms": bin_table}
 
 
 def measure(gg, graphs, queries, scales, tune=True, reps=5, ppr_iters=20):
@@ -92,12 +119,12 @@ def measure(gg, graphs, queries, scales, tune=True, reps=5, ppr_iters=20):
     handles = [gg.gg_load_csr(g.n, g.m, g.rowptr, g.colidx, g.weights, gg.GG_DIRECTED) for g in graphs]
     t_load = time.perf_counter() - t0
     try:
-        cands = candidates()
         if tune:
-            best, table = autotune(gg, handles, queries, cands)
+            cfg, bins_by_scale, table = autotune(gg, handles, queries, scales)
         else:
-            best, table = cands[0], []
-        b, times, st = _run(gg, handles, queries, best, reps=reps, warm=1)
+            cfg, bins_by_scale, table = team_candidates()[0], {}, {}
+        bins = [bins_by_scale.get(int(scales[gi]), (cfg["warp_deg"], cfg["cta_deg"])) for gi, _, _, _ in queries]
+        b, times, st = _run(gg, handles, queries, cfg, reps=reps, warm=1, bins=bins)
         gg.gg_batch_free(b)
     finally:
         for h in handles:
@@ -118,8 +145,7 @@ def measure(gg, graphs, queries, scales, tune=True, reps=5, ppr_iters=20):
                     f"{int(max(scales))} (ef 16, weights 1..255)",
         "graphs_by_scale": {int(s): int((scales == s).sum()) for s in sorted(set(scales.tolist()))},
         "total_arcs_in_graphs": int(sum(g.m for g in graphs)),
-        "config": best, "autotune": sorted((r for r in table if r["ms"] is not None), key=lambda r: r["ms"])[:6],
-        "autotune_candidates": len(table),
+        "config": cfg, "bins_by_scale": {str(k): list(v) for k, v in bins_by_scale.items()}, "autotune": table,
         "makespan_ms": round(ms, 3), "makespan_ms_runs": [round(t, 3) for t in times],
         "gteps": round(arcs / (ms * 1e-3) / 1e9, 3), "arcs_traversed": arcs,
         "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3), "p99": round(float(np.percentile(lat, 99)), 3),

@@ -97,3 +97,33 @@ def test_batch_errors(gg):
             assert e.value.status == gg.GG_ERR_INVALID_ARG
     finally:
         gg.gg_free_graph(h)
+
+
+def test_batch_per_query_bins(gg):
+    """Queries of one batch with different degree bins (as the autotuner sets
+    them per graph scale)."""
+    gs = _graphs()
+    hs = [gc.load(gg, g) for g in gs]
+    b = None
+    try:
+        qs = _queries(gg, gs, 30, seed=99)
+        rng = np.random.default_rng(4)
+        bins = [((1, 1), (2, 16), (8, 256), (32, 1024), (0, 0))[int(rng.integers(0, 5))] for _ in qs]
+        b = gg.gg_batch_create(hs, [gg.make_query(gi, app, s, it, warp_deg=bn[0], cta_deg=bn[1]) for (gi, app, s, it), bn in zip(qs, bins)],
+                               cluster=4, big_arcs=30000, threads=512, small_first=2)
+        gg.gg_batch_run(b)
+        for q, (gi, app, s, it) in enumerate(qs):
+            g = gs[gi]
+            got = gg.gg_batch_result(b, q, g.n, app)
+            want = _oracle(g, app, s, it)
+            if app == "ppr":
+                assert gc.rel_l1(got, want) <= 1e-5, (q, bins[q])
+            else:
+                assert np.array_equal(got, want), (q, app, bins[q])
+        with pytest.raises(gg.GGError):
+            gg.gg_batch_create(hs, [gg.make_query(0, "bfs", 0, 0, 0.85, 8, 4)])
+    finally:
+        if b:
+            gg.gg_batch_free(b)
+        for h in hs:
+            gg.gg_free_graph(h)
