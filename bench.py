@@ -236,7 +236,7 @@ def bench_ours(a, rank, world, local):
             h = gg.gg_load_csr(n, m, d_rowptr, d_colidx, d_w, gg.GG_DIRECTED | gg.GG_DEVICE_PTRS)
         arcs = 0
         launches = gg.stats(h).kernels_load
-        per = {"load_ms": gg.stats(h).ms_load}
+        per = {"load_ms": gg.stats(h).ms_load, "exact_equivalent_arcs": 0}
         sssp_iters = None
         try:
             for app, sigma, policy in runs:
@@ -246,6 +246,7 @@ def bench_ours(a, rank, world, local):
                 if app == "sssp" and policy == "exact":
                     sssp_iters = st.iterations
                 arcs += st.arcs_processed
+                per["exact_equivalent_arcs"] += st.iterations * m
                 launches += st.kernels_launched
                 if e2e:
                     gg.gg_result(h, gg.GG_RESULT_VALUES, out_host, 4 * n)
@@ -269,16 +270,18 @@ def bench_ours(a, rank, world, local):
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    arcs_total, launches_total = 0, 0
+    arcs_total, launches_total, eq_total = 0, 0, 0
     for k in range(a.steps):
-        arcs, launches, _ = step(collect=collected if k == a.steps - 1 else None)
+        arcs, launches, per = step(collect=collected if k == a.steps - 1 else None)
         arcs_total += arcs
         launches_total += launches
+        eq_total += per["exact_equivalent_arcs"]
     ev1.record(stream)
     barrier()
     clocks = clocks_summary(clk, local) if rank == 0 else None
     ms, arcs_all = aggregate(ev0.elapsed_time(ev1), arcs_total, world, "cuda")
     value = arcs_all / (ms * 1e-3) / 1e9
+    _, eq_all = aggregate(ev0.elapsed_time(ev1), eq_total, world, "cuda")
 
     # ---- end to end: host buffers, copies inside ---------------------------
     for _ in range(1):
@@ -339,6 +342,7 @@ def bench_ours(a, rank, world, local):
                 "h2d_bytes_per_step": int(4 * (n + 1) + 8 * m),
                 "d2h_bytes_per_step": int(4 * n * len(runs))},
         "gpu_launches": int(launches_total),
+        "exact_equivalent_gteps": round(eq_all / (ms * 1e-3) / 1e9, 3),
         "clocks": clocks,
     }
     return out, g, source, collected
@@ -417,6 +421,62 @@ def accuracy_table(g, source, collected):
             "reference_iters": full_iters, "time_to_target": tta, "timed_runs": timed}
 
 
+def sweep_table(g, source, thetas=(0.05, 0.2, 0.5, 0.8), alphas=(2, 4, 8)):
+    """The scope's parameter sweep: adaptive correction over sigma x theta x
+    alpha for PageRank (20 iterations) and SSSP (the exact run's iteration
+    count); device time of each run and its error against the exact result
+    (top-100 / mean stretch). Rows: [sigma, theta, alpha, ms, error]."""
+    from paper_2104_10039_gb300 import gg, metrics
+    h = gg.gg_load_csr(g.n, g.m, g.rowptr, g.colidx, g.weights, gg.GG_DIRECTED)
+    out = {}
+    try:
+        for app in ("pagerank", "sssp"):
+            gg.gg_run(h, app, 1.0, "exact", params(gg, app, source, timing=False))
+            ref, iters, ex_ms = gg.values(h, app), gg.stats(h).iterations, gg.stats(h).ms_run
+            rows = []
+            for sigma in SIGMAS:
+                for theta in thetas:
+                    for alpha in alphas:
+                        p = gg.make_params(alpha=alpha, theta=theta, max_iters=iters, damping=DAMPING, source=source,
+                                           seed=SAMPLE_SEED)
+                        gg.gg_run(h, app, sigma, "adaptive", p)
+                        v = gg.values(h, app)
+                        err = (metrics.top_k_error(v, ref, 100) if app == "pagerank"
+                               else metrics.stretch_error(v, ref, source)["error"])
+                        rows.append([sigma, theta, alpha, round(gg.stats(h).ms_run, 3), round(err, 4)])
+            out[app] = {"exact": {"iters": iters, "ms": round(ex_ms, 3)}, "metric": "top-100 error"
+                        if app == "pagerank" else "mean stretch error",
+                        "columns": ["sigma", "theta", "alpha", "ms", "error"], "rows": rows}
+    finally:
+        gg.gg_free_graph(h)
+    return out
+
+
+def sssp_sources(g, k=16, sigma=0.5):
+    """SSSP from 16 random sources with out-arcs (seed 2): exact and adaptive
+    (alpha 4, theta 0.05, the exact run's iteration count) device time and the
+    adaptive run's mean-stretch error; means over the sources."""
+    import graphgen
+    from paper_2104_10039_gb300 import gg, metrics
+    srcs = graphgen.sources(g, k, seed=SOURCE_SEED)
+    h = gg.gg_load_csr(g.n, g.m, g.rowptr, g.colidx, g.weights, gg.GG_DIRECTED)
+    ex, ad, err = [], [], []
+    try:
+        for s in srcs:
+            s = int(s)
+            gg.gg_run(h, "sssp", 1.0, "exact", params(gg, "sssp", s, timing=False))
+            ref, iters = gg.values(h, "sssp"), gg.stats(h).iterations
+            ex.append(gg.stats(h).ms_run)
+            gg.gg_run(h, "sssp", sigma, "adaptive", params(gg, "sssp", s, timing=False, iters=iters))
+            ad.append(gg.stats(h).ms_run)
+            err.append(metrics.stretch_error(gg.values(h, "sssp"), ref, s)["error"])
+    finally:
+        gg.gg_free_graph(h)
+    return {"sources": len(srcs), "sigma": sigma, "exact_ms_mean": round(float(np.mean(ex)), 3),
+            "adaptive_ms_mean": round(float(np.mean(ad)), 3), "stretch_error_mean": round(float(np.mean(err)), 4),
+            "stretch_error_max": round(float(np.max(err)), 4)}
+
+
 def learned_section(g, source):
     """Learned correction (beyond the paper): the scorer is trained on the
     traces of plain adaptive runs on R-MAT scale 12 and on this graph, then
@@ -437,15 +497,15 @@ def learned_section(g, source):
 
 
 # ------------------------------------------------------------- oracle (CPU) --
-def cpu_sample(g):
+def cpu_sample(g, iters=PR_ITERS, nthreads=0):
     """The oracle as it stands on the host cores: one adaptive-correction
     PageRank run (sigma 0.5) over the workload graph, in-edge build and
-    sampling included."""
+    sampling included (nthreads 0: every core)."""
     import oracle
     t0 = time.perf_counter()
     r = oracle.run(g.n, g.rowptr, g.colidx, app="pagerank", policy="adaptive", sigma=0.5,
-                   seed=SAMPLE_SEED, alpha=ALPHA, theta=THETA, max_iters=PR_ITERS, damping=DAMPING,
-                   nthreads=0)
+                   seed=SAMPLE_SEED, alpha=ALPHA, theta=THETA, max_iters=iters, damping=DAMPING,
+                   nthreads=nthreads)
     dt = time.perf_counter() - t0
     return float(r["iter_arcs"].sum()), dt
 
@@ -497,6 +557,8 @@ def main():
     if not a.no_accuracy:
         out["time_to_accuracy"] = accuracy_table(g, source, collected)
         out["learned_correction"] = learned_section(g, source)
+        out["sweep"] = sweep_table(g, source)
+        out["sssp_16_sources"] = sssp_sources(g)
     if not a.no_serving:
         from paper_2104_10039_gb300 import gg, serve
         graphs, queries, scales = serve.make_workload()
@@ -507,6 +569,10 @@ def main():
                                "cores": omp_threads(), "kind": "oracle",
                                "sample": f"one adaptive-correction PageRank run (sigma 0.5, {PR_ITERS} "
                                          f"iterations) on the same graph, {secs:.1f} s"}
+        arcs1, secs1 = cpu_sample(g, iters=3, nthreads=1)
+        out["cpu_baseline"]["single_thread"] = {
+            "value": round(arcs1 / secs1 / 1e9, 4), "unit": "GTEPS", "cores": 1,
+            "sample": f"the same run cut to 3 iterations on one thread, {secs1:.1f} s"}
     print(json.dumps(out), flush=True)
 
 

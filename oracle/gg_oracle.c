@@ -374,7 +374,7 @@ int orc_run(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx,
     if (!(p->sample_ratio > 0.0 && p->sample_ratio <= 1.0)) return -1;
     if (p->policy == ORC_LEARNED && !p->mlp) return -1;
 #ifdef _OPENMP
-    if (p->nthreads > 0) omp_set_num_threads(p->nthreads);
+    omp_set_num_threads(p->nthreads > 0 ? p->nthreads : omp_get_num_procs());
 #endif
     int rc = -1;
     int32_t *in_ptr = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
