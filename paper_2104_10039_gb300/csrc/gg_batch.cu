@@ -115,6 +115,7 @@ struct Shared {
     int32_t claim;
     unsigned long long arcs;
     float red[BT / 32];
+    float seg[BT];          // per warp: row parts of a chunk of light-row arcs
 };
 
 // Relax arc (v -> u) with candidate cand (BFS / SSSP push).
@@ -184,11 +185,36 @@ __device__ void serve_push(const BatchArgs &A, const BatchQuery &Q, const BatchG
             }
             if (tid == 0) sh.hub_n = 0;
             __syncthreads();
-            // thread bin
-            if (v >= 0 && deg < Q.warp_deg) {
-                const uint32_t vv = __ldcg(val + v);
-                for (int32_t e = e0; e < e0 + deg; ++e)
-                    relax(val, stamp, tag, qn, ln, __ldg(G.out_dst + e), cand_of(vv, Q.app, G.out_w, e));
+            // light vertices (degree below warp_deg) of this warp's 32 frontier
+            // entries: the warp relaxes their out-arcs together, 32 at a time
+            {
+                const bool light = v >= 0 && deg < Q.warp_deg;
+                const int32_t ld = light ? deg : 0;
+                const uint32_t vv = light ? __ldcg(val + v) : kInf;
+                int32_t incl = ld;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+                const int32_t excl = incl - ld;
+                for (int32_t j0 = 0; j0 < tot; j0 += 32) {
+                    const int32_t j = j0 + lane;
+                    int r = 0;   // the entry whose out-arcs hold item j
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1) {
+                        const int c = r + step;
+                        if (__shfl_sync(0xFFFFFFFFu, excl, c) <= j) r = c;
+                    }
+                    const int32_t re0 = __shfl_sync(0xFFFFFFFFu, e0, r);
+                    const int32_t rex = __shfl_sync(0xFFFFFFFFu, excl, r);
+                    const uint32_t rvv = __shfl_sync(0xFFFFFFFFu, vv, r);
+                    if (j < tot) {
+                        const int32_t e = re0 + (j - rex);
+                        relax(val, stamp, tag, qn, ln, __ldg(G.out_dst + e), cand_of(rvv, Q.app, G.out_w, e));
+                    }
+                }
             }
             // warp bin
             unsigned mb = __ballot_sync(0xFFFFFFFFu, v >= 0 && deg >= Q.warp_deg && deg < Q.cta_deg);
@@ -266,18 +292,50 @@ __device__ void serve_ppr(const BatchArgs &A, const BatchQuery &Q, const BatchGr
             }
             if (tid == 0) sh.hub_n = 0;
             __syncthreads();
-            if (deg >= 0 && deg < Q.warp_deg) {
-                // four independent gathers in flight, summed in arc order
-                float acc = 0.0f;
-                int32_t k = k0;
-                for (; k + 4 <= k0 + deg; k += 4) {
-                    const int32_t s0 = __ldg(G.in_src + k), s1 = __ldg(G.in_src + k + 1);
-                    const int32_t s2 = __ldg(G.in_src + k + 2), s3 = __ldg(G.in_src + k + 3);
-                    const float c0 = cc[s0], c1 = cc[s1], c2 = cc[s2], c3 = cc[s3];
-                    acc = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(acc, c0), c1), c2), c3);
+            {
+                // light rows (degree below warp_deg) of this warp's 32 rows: the
+                // warp walks their arcs together, 32 at a time (consecutive source
+                // reads), and a segmented scan in arc order sums each row's chunk
+                // part, which the row's lane adds to its total
+                const bool light = deg >= 0 && deg < Q.warp_deg;
+                const int32_t ld = light ? deg : 0;
+                int32_t incl = ld;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                    if (lane >= o) incl += y;
                 }
-                for (; k < k0 + deg; ++k) acc = __fadd_rn(acc, cc[__ldg(G.in_src + k)]);
-                apply(u, acc);
+                const int32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+                const int32_t excl = incl - ld;
+                float acc = 0.0f;
+                for (int32_t j0 = 0; j0 < tot; j0 += 32) {
+                    const int32_t i = j0 + lane;
+                    int r = 0;   // the lane whose row holds item i: last lane with excl <= i
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1) {
+                        const int c = r + step;
+                        if (__shfl_sync(0xFFFFFFFFu, excl, c) <= i) r = c;
+                    }
+                    const int32_t rk0 = __shfl_sync(0xFFFFFFFFu, k0, r);
+                    const int32_t rex = __shfl_sync(0xFFFFFFFFu, excl, r);
+                    const bool valid = i < tot;
+                    const int owner = valid ? r : 32 + lane;
+                    float v = valid ? cc[__ldg(G.in_src + rk0 + (i - rex))] : 0.0f;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const float y = __shfl_up_sync(0xFFFFFFFFu, v, o);
+                        const int yo = __shfl_up_sync(0xFFFFFFFFu, owner, o);
+                        if (lane >= o && yo == owner) v = __fadd_rn(y, v);
+                    }
+                    const int next_owner = __shfl_down_sync(0xFFFFFFFFu, owner, 1);
+                    sh.seg[warp * 32 + lane] = 0.0f;
+                    __syncwarp();
+                    if (valid && (lane == 31 || next_owner != owner)) sh.seg[warp * 32 + r] = v;
+                    __syncwarp();
+                    acc = __fadd_rn(acc, sh.seg[warp * 32 + lane]);
+                    __syncwarp();
+                }
+                if (light) apply(u, acc);
             }
             unsigned mb = __ballot_sync(0xFFFFFFFFu, deg >= Q.warp_deg && deg < Q.cta_deg);
             while (mb) {
