@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-scale24", action="store_true")
     return ap.parse_args()
 
 
@@ -477,6 +478,46 @@ def sssp_sources(g, k=16, sigma=0.5):
             "stretch_error_max": round(float(np.max(err)), 4)}
 
 
+def scale24_section():
+    """The scope's configuration 3: BFS, SSSP and CC on the symmetrised
+    R-MAT scale-24 graph and the Erdos-Renyi graph of the same size (268 M
+    arcs each), exact and adaptive correction at sigma 0.3 (alpha 4, theta
+    0.05), each to its fixed point: device time, arcs, GTEPS and the adaptive
+    run's error (mean stretch; CC relative component-count error)."""
+    import graphgen
+    from paper_2104_10039_gb300 import gg, metrics
+    out = {}
+    for name in ("rmat24", "er24"):
+        g = (graphgen.rmat(24, 16, seed=1, symmetric=True) if name == "rmat24"
+             else graphgen.erdos_renyi(1 << 24, avg_degree=16, seed=1, symmetric=True))
+        graphgen.add_weights(g, seed=WEIGHT_SEED)
+        s = int(graphgen.sources(g, 1, seed=SOURCE_SEED)[0])
+        h = gg.gg_load_csr(g.n, g.m, g.rowptr, g.colidx, g.weights, gg.GG_SYMMETRIC)
+        res = {"vertices": g.n, "arcs": g.m, "load_ms": round(gg.stats(h).ms_load, 3)}
+        try:
+            for app in ("bfs", "sssp", "cc"):
+                row = {}
+                for policy, sigma in (("exact", 1.0), ("adaptive", 0.3)):
+                    p = gg.make_params(alpha=ALPHA, theta=THETA, max_iters=MAX_ITERS_MIN, source=s, seed=SAMPLE_SEED)
+                    gg.gg_run(h, app, sigma, policy, p)   # warm (and the sample)
+                    gg.gg_run(h, app, sigma, policy, p)
+                    st = gg.stats(h)
+                    row[policy] = {"ms": round(st.ms_run, 3), "iterations": st.iterations,
+                                   "arcs": int(st.arcs_processed),
+                                   "gteps": round(st.arcs_processed / (st.ms_run * 1e-3) / 1e9, 2)}
+                    if policy == "exact":
+                        ref = gg.values(h, app)
+                    else:
+                        v = gg.values(h, app)
+                        row[policy]["error"] = round(metrics.wcc_relative_error(v, ref)["error"] if app == "cc"
+                                                     else metrics.stretch_error(v, ref, s)["error"], 5)
+                res[app] = row
+        finally:
+            gg.gg_free_graph(h)
+        out[name] = res
+    return out
+
+
 def learned_section(g, source):
     """Learned correction (beyond the paper): the scorer is trained on the
     traces of plain adaptive runs on R-MAT scale 12 and on this graph, then
@@ -559,6 +600,8 @@ def main():
         out["learned_correction"] = learned_section(g, source)
         out["sweep"] = sweep_table(g, source)
         out["sssp_16_sources"] = sssp_sources(g)
+    if not a.no_scale24:
+        out["scale24_symmetric"] = scale24_section()
     if not a.no_serving:
         from paper_2104_10039_gb300 import gg, serve
         graphs, queries, scales = serve.make_workload()
