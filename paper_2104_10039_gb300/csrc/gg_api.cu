@@ -172,7 +172,7 @@ static void fill_list(const gg_graph *g, bool sparse, TileArgs &a)
         a.num_tiles = g->sp_num_tiles;
     } else {
         a.row_ptr = g->in_ptr;
-        a.arc_src = g->in_src;
+        a.arc_src = g->in_src_h;
         a.arc_w = g->has_w ? g->in_w : nullptr;
         a.list_nnz = g->full_nnz;
         a.tile_info = g->full_tile_info;
@@ -180,6 +180,8 @@ static void fill_list(const gg_graph *g, bool sparse, TileArgs &a)
     }
     a.st_carry = g->st_carry;
     a.err = g->dev_err;
+    a.hub_ids = g->hub_ids;
+    a.n_hubs = g->n_hubs;
     a.tile_cnt = g->tile_cnt;
     a.part = g->part;
     a.part_head = g->part_head;
@@ -191,7 +193,7 @@ static void fill_list(const gg_graph *g, bool sparse, TileArgs &a)
 static gg_status finish_pack(gg_graph *g, bool weighted, IterStatsDev *stats)
 {
     GG_CUDA(launch_scan_u32(g->tile_cnt, g->tile_off, g->full_tiles, g->scan_tmp, g->stream));
-    GG_CUDA(launch_pack(g->full_tile_info, g->tile_off, g->full_tiles, (long long)g->n + g->m, g->mask, g->in_src,
+    GG_CUDA(launch_pack(g->full_tile_info, g->tile_off, g->full_tiles, (long long)g->n + g->m, g->mask, g->in_src_h,
                         weighted ? g->in_w : nullptr, g->sp_ptr, g->sp_src, weighted ? g->sp_w : nullptr, g->sp_nnz,
                         stats, g->num_sms, g->stream));
     GG_CUDA(launch_partition(g->sp_ptr, g->n, g->sp_nnz, g->max_tiles, g->sp_tile_info, g->sp_num_tiles,
@@ -209,6 +211,7 @@ gg_status sample_edges(gg_graph *g, double ratio, uint64_t seed)
     GG_CUDA(cudaEventRecord(g->ev_s0, g->stream));
     TileArgs a{};
     fill_list(g, false, a);
+    a.arc_src = g->in_src;   // the hash keys on vertex ids
     a.mask = g->mask;
     a.sp_ptr = g->sp_ptr;
     a.seed = seed;
@@ -244,7 +247,8 @@ static gg_status ensure_iter_cap(gg_graph *g, uint32_t iters)
 // Active out-degrees of the current flags (GG_RENORM).
 static gg_status refresh_active_outdeg(gg_graph *g)
 {
-    GG_CUDA(launch_active_outdeg(g->sp_src, g->sp_nnz, (uint32_t)g->m, g->n, g->act_outdeg, g->num_sms, g->stream));
+    GG_CUDA(launch_active_outdeg(g->sp_src, g->sp_nnz, (uint32_t)g->m, g->n, g->hub_ids, g->act_outdeg, g->num_sms,
+                                 g->stream));
     g->launches += 2;
     return GG_OK;
 }
@@ -375,7 +379,7 @@ static gg_status learned_correct(gg_graph *g, gg_app app, TileArgs a, uint32_t n
 {
     const bool pr = app == GG_APP_PAGERANK;
     const bool weighted = app == GG_APP_SSSP && g->has_w;
-    GG_CUDA(launch_sub_copy(g->sub_ptr, (int32_t)nsel, total, g->sel_rows, g->in_ptr, g->in_src,
+    GG_CUDA(launch_sub_copy(g->sub_ptr, (int32_t)nsel, total, g->sel_rows, g->in_ptr, g->in_src_h,
                             weighted ? g->in_w : nullptr, g->mask, g->sub_src, g->sub_w, g->sub_pos, g->sub_mask,
                             g->stream));
     const uint32_t sub_tiles = (uint32_t)(((uint64_t)nsel + total + kWT - 1) / kWT) + 1;
@@ -831,6 +835,7 @@ static gg_status alloc_graph(gg_graph *g)
     GG_ALLOC(g->b_out_dst, 4 * m);
     GG_ALLOC(g->b_in_ptr, 4 * (n + 1));
     GG_ALLOC(g->b_in_src, 4 * m);
+    GG_ALLOC(g->b_hub, 4 * (m + n + (size_t)kHubs + 4));
     GG_ALLOC(g->b_out_to_in, 4 * m);
     GG_ALLOC(g->b_sp_ptr, 4 * (n + 1));
     GG_ALLOC(g->b_sp_src, 4 * m);
@@ -861,6 +866,9 @@ static gg_status alloc_graph(gg_graph *g)
     g->out_w = g->has_w ? g->b_out_w.u32() : nullptr;
     g->in_ptr = g->b_in_ptr.i32();
     g->in_src = g->b_in_src.i32();
+    g->in_src_h = g->b_hub.i32();
+    g->hub_slot = g->in_src_h + m;
+    g->hub_ids = g->hub_slot + n;
     g->in_w = g->has_w ? g->b_in_w.u32() : nullptr;
     g->out_to_in = g->b_out_to_in.i32();
     g->sp_ptr = g->b_sp_ptr.i32();
@@ -947,7 +955,7 @@ gg_status gg_load_csr(gg_graph **out, int32_t n, int64_t m, const int32_t *rowpt
             break;
         }
         uint32_t mm = (uint32_t)m;
-        if ((st = validate_csr(g)) != GG_OK || (st = build_csc(g)) != GG_OK) {
+        if ((st = validate_csr(g)) != GG_OK || (st = build_csc(g)) != GG_OK || (st = build_hubs(g)) != GG_OK) {
             cudaEventDestroy(l0);
             cudaEventDestroy(l1);
             break;
@@ -1108,6 +1116,12 @@ gg_status gg_result(gg_graph *g, gg_result_kind kind, void *dst, size_t bytes, i
     if (bytes < need) {
         set_error("gg_result: buffer of %zu bytes, result needs %zu", bytes, need);
         return GG_ERR_INVALID_ARG;
+    }
+    if (kind == GG_RESULT_SPARSE_SRC && need) {   // hub-coded sources back to vertex ids
+        GG_CUDA(launch_decode_src(g->sp_src, g->sp_nnz, (uint32_t)(need / 4), g->hub_ids, (int32_t *)g->stash,
+                                  g->num_sms, g->stream));
+        GG_CUDA(cudaStreamSynchronize(g->stream));
+        src = g->stash;
     }
     if (need) GG_CUDA(cudaMemcpy(dst, src, need, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
     return GG_OK;

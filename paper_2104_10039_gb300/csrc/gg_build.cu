@@ -6,6 +6,8 @@
 // Alg. 2): CSR arcs are taken in CSR order, which lists sources in ascending
 // order; a stable sort by destination therefore leaves every in-row sorted by
 // source, duplicates in CSR order.
+#include <vector>
+
 #include "gg_graph.cuh"
 
 namespace gg {
@@ -462,6 +464,103 @@ gg_status build_csc(gg_graph *g)
     // the temporaries are released only after the queued work has used them
     GG_CUDA(cudaStreamSynchronize(s));
     return GG_OK;
+}
+
+// ------------------------------------------------------------ hub cache ----
+// The sources read most often by pull gathers are the vertices with the most
+// out-arcs: the (at most kHubs) vertices with out-degree >= T, T the smallest
+// threshold that admits no more than kHubs of them (and at least 2), get a
+// slot; in_src_h codes their in-arcs as -(slot + 1).
+constexpr uint32_t kDegBins = 65536;
+
+__global__ void k_deg_hist(const int32_t *__restrict__ out_ptr, int32_t n, uint32_t *__restrict__ hist)
+{
+    for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const int32_t d = out_ptr[v + 1] - out_ptr[v];
+        atomicAdd(&hist[d < (int32_t)kDegBins - 1 ? d : (int32_t)kDegBins - 1], 1u);
+    }
+}
+
+__global__ void k_hub_flag(const int32_t *__restrict__ out_ptr, int32_t n, int32_t thr, uint32_t *__restrict__ flag)
+{
+    for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        flag[v] = (out_ptr[v + 1] - out_ptr[v]) >= thr ? 1u : 0u;
+}
+
+__global__ void k_hub_fill(int32_t n, const uint32_t *__restrict__ flag, const uint32_t *__restrict__ pos,
+                           int32_t *__restrict__ hub_slot, int32_t *__restrict__ hub_ids)
+{
+    for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        if (flag[v]) {
+            hub_slot[v] = (int32_t)pos[v];
+            hub_ids[pos[v]] = v;
+        } else {
+            hub_slot[v] = -1;
+        }
+    }
+}
+
+__global__ void k_hub_code(const int32_t *__restrict__ in_src, long long m, const int32_t *__restrict__ hub_slot,
+                           int32_t *__restrict__ in_src_h)
+{
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (long long)gridDim.x * blockDim.x) {
+        const int32_t v = in_src[k];
+        const int32_t slot = hub_slot[v];
+        in_src_h[k] = slot >= 0 ? -(slot + 1) : v;
+    }
+}
+
+gg_status build_hubs(gg_graph *g)
+{
+    cudaStream_t s = g->stream;
+    const int32_t n = g->n;
+    const long long m = g->m;
+    const int grid = g->num_sms * 8;
+    DevBuf tmp;
+    gg_status st = tmp.alloc(4 * ((size_t)kDegBins + 2 * ((size_t)n + 1)), s);
+    if (st != GG_OK) return st;
+    uint32_t *hist = tmp.u32(), *flag = hist + kDegBins, *pos = flag + n + 1;
+    GG_CUDA(cudaMemsetAsync(hist, 0, 4 * (size_t)kDegBins, s));
+    k_deg_hist<<<grid, 256, 0, s>>>(g->out_ptr, n, hist);
+    std::vector<uint32_t> h(kDegBins);
+    GG_CUDA(cudaMemcpyAsync(h.data(), hist, 4 * (size_t)kDegBins, cudaMemcpyDeviceToHost, s));
+    GG_CUDA(cudaStreamSynchronize(s));
+    uint64_t above = 0;
+    int32_t thr = (int32_t)kDegBins;   // no hub
+    for (int32_t d = (int32_t)kDegBins - 1; d >= 2; --d) {
+        if (above + h[d] > (uint64_t)kHubs) break;
+        above += h[d];
+        thr = d;
+    }
+    k_hub_flag<<<grid, 256, 0, s>>>(g->out_ptr, n, thr, flag);
+    GG_CUDA(launch_scan_u32(flag, pos, (size_t)n, g->scan_tmp, s));
+    k_hub_fill<<<grid, 256, 0, s>>>(n, flag, pos, g->hub_slot, g->hub_ids);
+    if (m > 0) k_hub_code<<<grid, 256, 0, s>>>(g->in_src, m, g->hub_slot, g->in_src_h);
+    g->n_hubs = (int32_t)above;
+    g->load_launches += 8;
+    GG_CUDA(cudaGetLastError());
+    GG_CUDA(cudaStreamSynchronize(s));
+    return GG_OK;
+}
+
+__global__ void k_decode_src(const int32_t *__restrict__ coded, const uint32_t *__restrict__ count,
+                             const int32_t *__restrict__ hub_ids, int32_t *__restrict__ out)
+{
+    const uint32_t c = *count;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < c; k += gridDim.x * blockDim.x) {
+        const int32_t v = coded[k];
+        out[k] = v < 0 ? hub_ids[-v - 1] : v;
+    }
+}
+
+cudaError_t launch_decode_src(const int32_t *coded, const uint32_t *count, uint32_t max_count, const int32_t *hub_ids,
+                              int32_t *out, int num_sms, cudaStream_t s)
+{
+    long long blocks = ((long long)max_count + 255) / 256;
+    if (blocks > (long long)num_sms * 8) blocks = (long long)num_sms * 8;
+    if (blocks < 1) blocks = 1;
+    k_decode_src<<<(unsigned)blocks, 256, 0, s>>>(coded, count, hub_ids, out);
+    return cudaGetLastError();
 }
 
 gg_status validate_csr(gg_graph *g)

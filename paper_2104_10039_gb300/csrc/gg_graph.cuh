@@ -71,6 +71,11 @@ struct gg_graph {
     // CSC (in-arcs), CSR -> CSC positions
     gg::DevBuf b_in_ptr, b_in_src, b_in_w, b_out_to_in;
     int32_t *in_ptr = nullptr, *in_src = nullptr, *out_to_in = nullptr;
+    // hub cache: in-arc sources with hubs coded -(slot + 1), each hub's slot
+    // (-1 otherwise) and each slot's vertex
+    gg::DevBuf b_hub;
+    int32_t *in_src_h = nullptr, *hub_slot = nullptr, *hub_ids = nullptr;
+    int32_t n_hubs = 0;
     uint32_t *in_w = nullptr;
     // partitions: full CSC and packed active CSC
     gg::DevBuf b_full_tile_info, b_sp_tile_info, b_scalars;
@@ -156,6 +161,7 @@ struct gg_graph {
 
 namespace gg {
 gg_status build_csc(gg_graph *g);
+gg_status build_hubs(gg_graph *g);
 gg_status validate_csr(gg_graph *g);
 gg_status sample_edges(gg_graph *g, double ratio, uint64_t seed);
 gg_status run(gg_graph *g, gg_app app, double ratio, gg_policy policy, const gg_params *p);

@@ -19,6 +19,10 @@ constexpr int kWT = 32 * kIPT;
 constexpr int kTile = kThreads * kIPT;   // push-frontier tiles (block-wide)
 constexpr int kWarps = kThreads / 32;
 constexpr uint32_t kInf = 0xFFFFFFFFu;
+// Hub cache: the values of the (at most) kHubs sources with the most
+// out-arcs sit in each gathering block's shared memory; the gathers' source
+// list codes such a source as -(slot + 1).
+constexpr int kHubs = 3072;   // 12 KB: 4 blocks of the gather still fit an SM
 
 // Bounded device waits: a wait gives up after this many polls (each an L2
 // round trip plus a short sleep, about a second in total), flags
@@ -113,6 +117,9 @@ struct TileArgs {
     const int32_t *row_vtx;
     float *hist_out;
     float n_f;                  // vertex count (PageRank change feature = n |old - new|)
+    // hub cache: vertex of every slot, and the number of slots in use
+    const int32_t *hub_ids;
+    int32_t n_hubs;
 };
 
 // K_GATHER: approximate / accurate pull iteration. K_STASH + K_CORRECT: the
@@ -270,7 +277,10 @@ cudaError_t launch_append_frontier(const int32_t *q_src, uint32_t len, const flo
 cudaError_t launch_iter_changed(IterStatsDev *st, const uint32_t *q_len, cudaStream_t s);
 // Active out-degree of every vertex from the packed active in-edges.
 cudaError_t launch_active_outdeg(const int32_t *sp_src, const uint32_t *sp_nnz, uint32_t max_arcs, int32_t n,
-                                 int32_t *act, int num_sms, cudaStream_t s);
+                                 const int32_t *hub_ids, int32_t *act, int num_sms, cudaStream_t s);
+// Source ids of a hub-coded list back to vertex ids (count read on the device).
+cudaError_t launch_decode_src(const int32_t *coded, const uint32_t *count, uint32_t max_count, const int32_t *hub_ids,
+                              int32_t *out, int num_sms, cudaStream_t s);
 // contrib[u] = rank[u] / deg[u], or / the full out-degree when deg is null (0 when the degree is 0).
 cudaError_t launch_contrib(int32_t n, const float *rank, const int32_t *deg, const int32_t *out_ptr,
                            float *contrib, int num_sms, cudaStream_t s);

@@ -242,22 +242,24 @@ cudaError_t launch_iter_changed(IterStatsDev *st, const uint32_t *q_len, cudaStr
 }
 
 __global__ void k_active_outdeg(const int32_t *__restrict__ sp_src, const uint32_t *__restrict__ sp_nnz,
-                                int32_t *__restrict__ act)
+                                const int32_t *__restrict__ hub_ids, int32_t *__restrict__ act)
 {
     const uint32_t nnz = *sp_nnz;
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += gridDim.x * blockDim.x)
-        atomicAdd(&act[sp_src[k]], 1);
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += gridDim.x * blockDim.x) {
+        const int32_t v = sp_src[k];   // hub-coded
+        atomicAdd(&act[v < 0 ? hub_ids[-v - 1] : v], 1);
+    }
 }
 
 cudaError_t launch_active_outdeg(const int32_t *sp_src, const uint32_t *sp_nnz, uint32_t max_arcs, int32_t n,
-                                 int32_t *act, int num_sms, cudaStream_t s)
+                                 const int32_t *hub_ids, int32_t *act, int num_sms, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(act, 0, sizeof(int32_t) * (size_t)n, s);
     if (e != cudaSuccess) return e;
     int blocks = (int)((max_arcs + 255) / 256);
     if (blocks > num_sms * 8) blocks = num_sms * 8;
     if (blocks < 1) blocks = 1;
-    k_active_outdeg<<<blocks, 256, 0, s>>>(sp_src, sp_nnz, act);
+    k_active_outdeg<<<blocks, 256, 0, s>>>(sp_src, sp_nnz, hub_ids, act);
     return cudaGetLastError();
 }
 

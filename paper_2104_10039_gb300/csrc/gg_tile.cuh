@@ -264,6 +264,18 @@ k_tile(TileArgs a)
     constexpr bool kStashed = KIND == K_CORRECT;   // values come from the stash, in arc order
     __shared__ WarpSmem<APP, KIND> smem[kWarps];
     WarpSmem<APP, KIND> &s = smem[threadIdx.x >> 5];
+    // hub cache: the values of the most-read sources, one copy per block
+    constexpr bool kHub = KIND == K_GATHER || KIND == K_STASH;
+    __shared__ uint32_t s_hub[kHub ? kHubs : 1];
+    if constexpr (kHub) {
+        const int nh = a.n_hubs < kHubs ? a.n_hubs : kHubs;
+        for (int j = (int)threadIdx.x; j < nh; j += kThreads) {
+            const int32_t v = a.hub_ids[j];
+            if constexpr (APP == GG_APP_PAGERANK) s_hub[j] = __float_as_uint(__ldg(a.contrib_cur + v));
+            else s_hub[j] = __ldg(a.val_cur + v);
+        }
+        __syncthreads();
+    }
 
     const uint32_t lane = lane_id();
     const int gw = (int)((blockIdx.x * kThreads + threadIdx.x) >> 5);
@@ -317,12 +329,13 @@ k_tile(TileArgs a)
 #pragma unroll
         for (int i = 0; i < kIPT; ++i) {
             const int k = (int)lane + 32 * i;
+            const int32_t sv = src_cur[i];   // a hub is coded -(slot + 1)
             if constexpr (kNoGather || kStashed) {
-                gv[i] = (uint32_t)src_cur[i];
+                gv[i] = (uint32_t)sv;
             } else if constexpr (APP == GG_APP_PAGERANK) {
-                gv[i] = k < narcs ? __float_as_uint(__ldg(a.contrib_cur + src_cur[i])) : 0u;
+                gv[i] = k < narcs ? (sv < 0 ? s_hub[-sv - 1] : __float_as_uint(__ldg(a.contrib_cur + sv))) : 0u;
             } else {
-                gv[i] = k < narcs ? __ldg(a.val_cur + src_cur[i]) : kInf;
+                gv[i] = k < narcs ? (sv < 0 ? s_hub[-sv - 1] : __ldg(a.val_cur + sv)) : kInf;
             }
         }
         uint2 prev_part = make_uint2(1u, A::bits(A::id()));
