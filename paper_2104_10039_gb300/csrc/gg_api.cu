@@ -851,7 +851,7 @@ static gg_status alloc_graph(gg_graph *g)
     GG_ALLOC(g->b_tile_cnt, 4 * (2 * (size_t)g->max_tiles + 4));
     GG_ALLOC(g->b_act, 4 * n);
     GG_ALLOC(g->b_part, 12 * ((size_t)g->max_tiles + 2));
-    GG_ALLOC(g->b_stash, 4 * m);
+    GG_ALLOC(g->b_stash, 8 * m);
     GG_ALLOC(g->b_scalars, 4 * 16);
     g->mask_words = (m + 31) / 32;
     GG_ALLOC(g->b_mask, 4 * (g->mask_words + 1));
@@ -881,7 +881,7 @@ static gg_status alloc_graph(gg_graph *g)
     g->act_outdeg = g->b_act.i32();
     g->part = (uint2 *)g->b_part.p;
     g->part_head = (uint32_t *)(g->part + g->max_tiles + 2);
-    g->stash = g->b_stash.u32();
+    g->stash = (uint2 *)g->b_stash.p;
     uint32_t *sc = g->b_scalars.u32();
     g->full_num_tiles = sc + 0;
     g->sp_num_tiles = sc + 1;
@@ -1121,7 +1121,7 @@ gg_status gg_result(gg_graph *g, gg_result_kind kind, void *dst, size_t bytes, i
         GG_CUDA(launch_decode_src(g->sp_src, g->sp_nnz, (uint32_t)(need / 4), g->hub_ids, (int32_t *)g->stash,
                                   g->num_sms, g->stream));
         GG_CUDA(cudaStreamSynchronize(g->stream));
-        src = g->stash;
+        src = (const void *)g->stash;
     }
     if (need) GG_CUDA(cudaMemcpy(dst, src, need, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
     return GG_OK;

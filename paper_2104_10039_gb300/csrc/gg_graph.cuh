@@ -88,7 +88,7 @@ struct gg_graph {
     // gather partials; the correction's value stash
     gg::DevBuf b_tile_cnt, b_part, b_stash, b_act;
     int32_t *act_outdeg = nullptr;   // active out-degrees (GG_RENORM)
-    uint32_t *stash = nullptr;
+    uint2 *stash = nullptr;
     uint2 *part = nullptr;
     uint32_t *part_head = nullptr;
     uint32_t *tile_cnt = nullptr, *tile_off = nullptr;

@@ -99,8 +99,10 @@ struct TileArgs {
     // last end) and the part before the first end
     uint2 *part;
     uint32_t *part_head;
-    // correction: arc values (candidates) in list order, written by K_STASH
-    uint32_t *stash;
+    // correction: per arc in list order, written by K_STASH: the row's running
+    // value before the arc within its tile (rows continued from an earlier
+    // tile start from the identity there) and the arc's value (candidate)
+    uint2 *stash;
     // active arcs per tile (correction, sampling)
     uint32_t *tile_cnt;
     // look-back

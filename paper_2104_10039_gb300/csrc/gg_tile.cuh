@@ -248,6 +248,7 @@ struct WarpSmem {
     uint32_t bits[(KIND == K_GATHER) ? 1 : (kWT / 32 + 2)];
     uint32_t oldw[(KIND == K_CORRECT && APP != GG_APP_PAGERANK) ? (kWT / 32 + 2) : 1];
     float rowtot[(KIND == K_CORRECT && APP == GG_APP_PAGERANK) ? kWT + 1 : 1];   // influence share
+    uint32_t bef[KIND == K_STASH ? kPadded : 1];   // running value before each arc, in arc order
 };
 
 template <int APP, int KIND>
@@ -305,7 +306,7 @@ k_tile(TileArgs a)
             const int k = (int)lane + 32 * i;
             const bool ok = live && k < b1 - b0;
             if constexpr (KIND == K_RECOUNT) srcv[i] = 0;
-            else if constexpr (kStashed) srcv[i] = ok ? (int32_t)__ldcs(a.stash + b0 + k) : 0;
+            else if constexpr (kStashed) srcv[i] = ok ? (int32_t)__ldcs(&a.stash[b0 + k].y) : 0;
             else srcv[i] = ok ? __ldg(a.arc_src + b0 + k) : 0;
             if constexpr (kWeighted) wv[i] = (ok && load_w) ? __ldg(a.arc_w + b0 + k) : 1u;
         }
@@ -380,7 +381,6 @@ k_tile(TileArgs a)
                     v = (v == kInf || c >= kInf) ? kInf : (uint32_t)c;
                 }
                 s.val[pad(k)] = v;
-                if constexpr (KIND == K_STASH) __stcs(a.stash + a0 + k, v);
             }
         }
         __syncwarp();
@@ -477,6 +477,28 @@ k_tile(TileArgs a)
         uint32_t q_v[kMin ? kIPT : 1];
         int q_n = 0;
         T my_end_run = A::id();   // running value after this lane's items
+        if constexpr (KIND == K_STASH) {
+            // the running value before every arc (within the tile), staged in
+            // arc order, then stored with the arc's value (coalesced)
+            T acc = carry_in;
+            int y = ly;
+#pragma unroll
+            for (int i = 0; i < kIPT; ++i) {
+                if ((arcmask >> i) & 1u) {
+                    s.bef[pad(y)] = A::bits(acc);
+                    acc = A::op(acc, A::from_bits(item_v[i]));
+                    ++y;
+                } else if ((endmask >> i) & 1u) {
+                    acc = A::id();
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < kIPT; ++i) {
+                const int k = (int)lane + 32 * i;
+                if (k < narcs) __stcs(a.stash + a0 + k, make_uint2(s.bef[pad(k)], s.val[pad(k)]));
+            }
+        }
         if constexpr (KIND != K_STASH) {
             T acc = carry_in;
             int x = lx, y = ly;
@@ -691,6 +713,204 @@ k_fixup(TileArgs a)
         if constexpr (kMin) {
             if (a.q_out) frontier_append(a, qu, qv, qn);
         }
+    }
+    flush_stats(a, st);
+}
+
+
+// ------------------------------------------------------ correction, pass 2 --
+// The correction's second launch when the influence is the running-prefix
+// form: K_STASH left, for every arc, the running value before it within its
+// tile and its value, so no merge path or scan is needed here. Per warp tile:
+// the carry of the row continued from earlier tiles (the finished partials),
+// each arc's influence test (Alg. 2 GG-EStatus) from (carry +) its running
+// values, the new flag words, every row ending in the tile applied (GG-Apply,
+// GG-VStatus), and the tile's active count and tile-local row ends for the
+// pack.
+template <int APP>
+__global__ void __launch_bounds__(kThreads, 4)
+k_correct2(TileArgs a)
+{
+    using T = typename Acc<APP>::T;
+    using A = Acc<APP>;
+    constexpr bool kMin = APP != GG_APP_PAGERANK;
+    constexpr int kW = kWT / 32 + 2;
+    __shared__ uint32_t s_bits[kWarps][kW];
+    __shared__ uint32_t s_cnt[kWarps][kW];
+    __shared__ uint32_t s_old[kWarps][kMin ? kW : 1];
+    const int wi = (int)(threadIdx.x >> 5);
+    uint32_t *bits = s_bits[wi], *cnt = s_cnt[wi], *oldw = s_old[wi];
+    const uint32_t lane = lane_id();
+    const int gw = (int)((blockIdx.x * kThreads + threadIdx.x) >> 5);
+    const int W = (int)((gridDim.x * kThreads) >> 5);
+    const uint32_t nnz = *a.list_nnz;
+    const int num_tiles = (int)*a.num_tiles;
+    const long long total = (long long)a.n + nnz;
+    ApplyStats st;
+    // software pipeline: headers two tiles ahead, the stash pairs one ahead
+    auto load_pairs = [&](int tt, uint32_t hdr, uint2 *pv) {
+        const uint32_t h0 = __shfl_sync(0xFFFFFFFFu, hdr, 0), h1 = __shfl_sync(0xFFFFFFFFu, hdr, 1);
+        const long long e0 = (long long)tt * kWT;
+        const long long e1 = e0 + kWT < total ? e0 + kWT : total;
+        const int32_t b0 = (int32_t)(e0 - (int32_t)(h0 & 0x7FFFFFFFu));
+        const int32_t b1 = (int32_t)(e1 - (int32_t)(h1 & 0x7FFFFFFFu));
+        const bool live = tt < num_tiles;
+#pragma unroll
+        for (int j = 0; j < kIPT; ++j) {
+            const int k = (int)lane + 32 * j;
+            pv[j] = (live && k < b1 - b0) ? __ldcs(a.stash + b0 + k) : make_uint2(0u, 0u);
+        }
+    };
+    uint32_t hdr_cur = 0, hdr_nxt = 0;
+    if (lane < 2 && gw < num_tiles) hdr_cur = (uint32_t)a.tile_info[gw + (int)lane];
+    if (lane < 2 && gw + W < num_tiles) hdr_nxt = (uint32_t)a.tile_info[gw + W + (int)lane];
+    uint2 pv_cur[kIPT];
+    load_pairs(gw, hdr_cur, pv_cur);
+    for (int t = gw; t < num_tiles; t += W) {
+        const uint32_t i0 = __shfl_sync(0xFFFFFFFFu, hdr_cur, 0), i1 = __shfl_sync(0xFFFFFFFFu, hdr_cur, 1);
+        const int32_t r0 = (int32_t)(i0 & 0x7FFFFFFFu), r1 = (int32_t)(i1 & 0x7FFFFFFFu);
+        const bool need_carry = (i0 >> 31) != 0u;
+        const long long d0 = (long long)t * kWT;
+        const long long d1 = d0 + kWT < total ? d0 + kWT : total;
+        const int32_t a0 = (int32_t)(d0 - r0), a1 = (int32_t)(d1 - r1);
+        const int nrows = r1 - r0, narcs = a1 - a0;
+        const int w0 = a0 >> 5;
+        const int nwords = narcs > 0 ? ((a1 - 1) >> 5) - w0 + 1 : 0;
+        // the row continued from earlier tiles: its carry and its arcs here
+        T c = A::id();
+        int32_t first_end = a0;
+        if (need_carry) {
+            uint2 prev = make_uint2(0u, 0u);
+            if (lane == 0) prev = a.part[t - 1];
+            prev.x = __shfl_sync(0xFFFFFFFFu, prev.x, 0);
+            prev.y = __shfl_sync(0xFFFFFFFFu, prev.y, 0);
+            c = carry_from_parts<APP>(a.part, t, prev);
+            const int32_t e = a.row_ptr[r0 + 1];
+            first_end = e < a1 ? e : a1;
+        }
+        for (int i = (int)lane; i < nwords; i += 32) {
+            bits[i] = 0u;
+            if constexpr (kMin) oldw[i] = a.mask[w0 + i];
+        }
+        uint2 pv_nxt[kIPT];
+        load_pairs(t + W, hdr_nxt, pv_nxt);
+        uint32_t hdr_far = 0;
+        if (lane < 2 && t + 2 * W < num_tiles) hdr_far = (uint32_t)a.tile_info[t + 2 * W + (int)lane];
+        __syncwarp();
+        // ---- flags: arcs a0 + lane + 32 j (coalesced), one ballot per 32 ----
+        uint32_t active = 0;
+#pragma unroll
+        for (int j = 0; j < kIPT; ++j) {
+            const int k = (int)lane + 32 * j;
+            const int32_t p = a0 + k;
+            uint32_t fl = 0;
+            if (k < narcs) {
+                const uint2 sv = pv_cur[j];
+                T before = A::from_bits(sv.x);
+                const T v = A::from_bits(sv.y);
+                if (p < first_end) before = A::op(c, before);
+                if constexpr (APP == GG_APP_PAGERANK) {
+                    // Alg. 2: influence (new - old) / new > theta, as (new - old) > theta * new
+                    const float after = __fadd_rn(before, v);
+                    fl = (after != 0.0f ? __fsub_rn(after, before) > __fmul_rn(a.theta, after) : 0.0f > a.theta)
+                             ? 1u : 0u;
+                } else {
+                    if (v == kInf) {   // no candidate: the arc keeps its flag
+                        fl = a.est_strict ? 0u : (oldw[(p >> 5) - w0] >> (p & 31)) & 1u;
+                    } else if (a.theta_case == 1) {
+                        fl = 1u;
+                    } else if (a.theta_case == 2) {
+                        fl = 0u;
+                    } else if (v < before) {
+                        if (before == kInf || APP == GG_APP_CC) fl = 1u;
+                        else fl = ((unsigned long long)(before - v) << 32) > a.theta_fx * (unsigned long long)before
+                                      ? 1u : 0u;
+                    }
+                }
+            }
+            const uint32_t b = __ballot_sync(0xFFFFFFFFu, fl != 0u);
+            active += __popc(b);
+            if (lane == 0 && b) {
+                const int q = a0 + 32 * j;   // position of lane 0's arc
+                const int sh = q & 31, wq = (q >> 5) - w0;
+                bits[wq] |= b << sh;
+                if (sh) bits[wq + 1] |= b >> (32 - sh);
+            }
+        }
+        __syncwarp();
+        // active arcs before each word (tile-local)
+        {
+            uint32_t pc = (int)lane < nwords ? __popc(bits[lane]) : 0u;
+            const uint32_t incl = warp_incl_sum_u32(pc);
+            if ((int)lane < nwords) cnt[lane] = incl - pc;
+        }
+        if (lane == 0 && a.tile_cnt) a.tile_cnt[t] = active;
+        __syncwarp();
+        // ---- rows ending in this tile: apply, tile-local row ends -----------
+        for (int rb = 0; rb < nrows; rb += 32) {
+            const int ri = rb + (int)lane;
+            int32_t qu[1];
+            uint32_t qv[1];
+            int qn = 0;
+            if (ri < nrows) {
+                const int32_t r = r0 + ri;
+                const int32_t e = a.row_ptr[r + 1];   // the row's arcs end before list position e
+                // the row's total: the running value after its last arc when that
+                // arc lies in this tile (plus the carry for the continued row),
+                // else the carry (continued row ending at the tile start) or
+                // nothing (a row without arcs)
+                const bool continued = ri == 0 && need_carry;
+                T tot = continued ? c : A::id();
+                if (e > (continued ? a0 : a.row_ptr[r])) {
+                    const uint2 sv = __ldg(a.stash + (e - 1));
+                    tot = A::op(A::from_bits(sv.x), A::from_bits(sv.y));
+                    if (continued) tot = A::op(c, tot);
+                }
+                if (a.sp_ptr) {
+                    const int32_t pe = e - a0;   // tile-local end
+                    uint32_t before = 0;
+                    if (pe > 0) {
+                        const int32_t wl = ((e - 1) >> 5) - w0, b = ((e - 1) & 31) + 1;
+                        before = cnt[wl] + __popc(bits[wl] & (b == 32 ? 0xFFFFFFFFu : ((1u << b) - 1u)));
+                    }
+                    a.sp_ptr[r + 1] = (int32_t)before;
+                }
+                const int32_t u = a.row_vtx ? a.row_vtx[r] : r;
+                if constexpr (APP == GG_APP_PAGERANK) {
+                    apply_pr(a, u, tot, a.rank_cur[u],
+                             a.deg_apply ? a.deg_apply[u] : a.out_ptr[u + 1] - a.out_ptr[u], st);
+                } else {
+                    bool ch;
+                    const uint32_t nw = apply_min(a, u, tot, a.val_cur[u], st, &ch);
+                    if (ch) {
+                        qu[0] = u;
+                        qv[0] = nw;
+                        qn = 1;
+                    }
+                }
+            }
+            if constexpr (kMin) {
+                if (a.q_out) frontier_append(a, qu, qv, qn);
+            }
+        }
+        // ---- flag words: plain stores where the tile owns the word ----------
+        for (int i = (int)lane; i < nwords; i += 32) {
+            const int w = w0 + i;
+            const int lo = a0 > w * 32 ? a0 : w * 32;
+            const int hi = a1 < w * 32 + 32 ? a1 : w * 32 + 32;
+            if (hi - lo == 32) {
+                a.mask[w] = bits[i];
+            } else {
+                const uint32_t range = ((1u << (hi - lo)) - 1u) << (lo & 31);
+                atomicAnd(&a.mask[w], ~range);
+                atomicOr(&a.mask[w], bits[i]);
+            }
+        }
+        __syncwarp();
+        hdr_cur = hdr_nxt;
+        hdr_nxt = hdr_far;
+#pragma unroll
+        for (int j = 0; j < kIPT; ++j) pv_cur[j] = pv_nxt[j];
     }
     flush_stats(a, st);
 }

@@ -32,13 +32,26 @@ static cudaError_t launch_tiles(const TileArgs &a, int max_tiles, int num_sms, c
     return cudaGetLastError();
 }
 
-// A correction iteration: K_STASH then K_CORRECT over the full in-edge list.
+// A correction iteration: K_STASH, then k_correct2 (running-prefix
+// influence) or K_CORRECT (the share influence, which needs whole rows).
 template <int APP>
 static cudaError_t launch_correction(const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s)
 {
     cudaError_t e = launch_tiles<APP, K_STASH>(a, max_tiles, num_sms, s);
     if (e != cudaSuccess) return e;
-    return launch_tiles<APP, K_CORRECT>(a, max_tiles, num_sms, s);
+    if (a.infl_share) return launch_tiles<APP, K_CORRECT>(a, max_tiles, num_sms, s);
+    static int blocks = 0;
+    if (blocks == 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_correct2<APP>, kThreads, 0) != cudaSuccess || b < 1)
+            b = 1;
+        blocks = b;
+    }
+    int g = blocks * num_sms;
+    const int need = (max_tiles + kWarps - 1) / kWarps;
+    g = g < need ? g : (need > 0 ? need : 1);
+    k_correct2<APP><<<g, kThreads, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 template <int APP>
