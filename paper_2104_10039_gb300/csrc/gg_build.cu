@@ -473,12 +473,24 @@ gg_status build_csc(gg_graph *g)
 // slot; in_src_h codes their in-arcs as -(slot + 1).
 constexpr uint32_t kDegBins = 65536;
 
+// Out-degree histogram (degrees clamped to kDegBins - 1); the many small
+// degrees are counted in shared memory first, so their global counters see
+// one atomic per block.
+constexpr int kDegLow = 4096;
+
 __global__ void k_deg_hist(const int32_t *__restrict__ out_ptr, int32_t n, uint32_t *__restrict__ hist)
 {
+    __shared__ uint32_t low[kDegLow];
+    for (int i = threadIdx.x; i < kDegLow; i += blockDim.x) low[i] = 0u;
+    __syncthreads();
     for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         const int32_t d = out_ptr[v + 1] - out_ptr[v];
-        atomicAdd(&hist[d < (int32_t)kDegBins - 1 ? d : (int32_t)kDegBins - 1], 1u);
+        if (d < kDegLow) atomicAdd(&low[d], 1u);
+        else atomicAdd(&hist[d < (int32_t)kDegBins - 1 ? d : (int32_t)kDegBins - 1], 1u);
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kDegLow; i += blockDim.x)
+        if (low[i]) atomicAdd(&hist[i], low[i]);
 }
 
 __global__ void k_hub_flag(const int32_t *__restrict__ out_ptr, int32_t n, int32_t thr, uint32_t *__restrict__ flag)
