@@ -226,11 +226,19 @@ __global__ void __launch_bounds__(256) k_mlp_select(FeatArgs fa, const float *__
     __syncthreads();
     const int l = (int)lane_id(), g = l >> 2, t = l & 3;
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long grp = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); grp * 16 < fa.n;
-         grp += nwarps) {
+    // the next group's features are loaded while this group runs the MLP
+    long long grp = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    int32_t nd0 = 0, nd1 = 0;
+    float2 nx0 = feature_pair(fa, (int32_t)(grp * 16 + g), t, &nd0);
+    float2 nx1 = feature_pair(fa, (int32_t)(grp * 16 + g + 8), t, &nd1);
+    for (; grp * 16 < fa.n; grp += nwarps) {
         const int32_t u0 = (int32_t)(grp * 16 + g), u1 = u0 + 8;
-        int32_t d0 = 0, d1 = 0;
-        const float2 x0 = feature_pair(fa, u0, t, &d0), x1 = feature_pair(fa, u1, t, &d1);
+        const int32_t d0 = nd0, d1 = nd1;
+        const float2 x0 = nx0, x1 = nx1;
+        const long long ng = grp + nwarps;
+        nd0 = nd1 = 0;
+        nx0 = feature_pair(fa, ng * 16 < fa.n ? (int32_t)(ng * 16 + g) : fa.n, t, &nd0);
+        nx1 = feature_pair(fa, ng * 16 < fa.n ? (int32_t)(ng * 16 + g + 8) : fa.n, t, &nd1);
         const float2 z = mlp_forward16(f, x0, x1);
         if (t == 0) {
             if (u0 < fa.n) {
@@ -424,7 +432,7 @@ cudaError_t launch_mlp_select(const FeatArgs &fa, const float *P, float tau, uin
                               float *logits, int num_sms, cudaStream_t s)
 {
     long long blocks = ((long long)fa.n + 127) / 128;
-    if (blocks > (long long)num_sms * 4) blocks = (long long)num_sms * 4;
+    if (blocks > (long long)num_sms * 8) blocks = (long long)num_sms * 8;
     if (blocks < 1) blocks = 1;
     k_mlp_select<<<(unsigned)blocks, 256, 0, s>>>(fa, P, tau, sel_flag, sel_deg, logits);
     return cudaGetLastError();
