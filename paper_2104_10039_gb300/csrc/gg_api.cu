@@ -209,18 +209,12 @@ gg_status sample_edges(gg_graph *g, double ratio, uint64_t seed)
         return GG_ERR_INVALID_ARG;
     }
     GG_CUDA(cudaEventRecord(g->ev_s0, g->stream));
-    TileArgs a{};
-    fill_list(g, false, a);
-    a.arc_src = g->in_src;   // the hash keys on vertex ids
-    a.mask = g->mask;
-    a.sp_ptr = g->sp_ptr;
-    a.seed = seed;
-    a.thr = (unsigned long long)std::floor(ratio * 4294967296.0);
-    a.symmetric = g->symmetric ? 1 : 0;
-    a.epoch = next_epoch(g);
-    a.stats = nullptr;
-    GG_CUDA(launch_tile_sample(a, (int)g->max_tiles, g->num_sms, g->stream));
-    g->launches += 1;
+    // the hash keys on vertex ids (in_src, not the hub-coded copy)
+    GG_CUDA(launch_sample(g->in_src, g->in_dst, g->m, g->symmetric ? 1 : 0, seed,
+                          (unsigned long long)std::floor(ratio * 4294967296.0), g->mask, g->num_sms, g->stream));
+    GG_CUDA(launch_tile_counts(g->full_tile_info, g->full_tiles, (long long)g->n + g->m, g->in_ptr, g->mask,
+                               g->tile_cnt, g->sp_ptr, g->num_sms, g->stream));
+    g->launches += 2;
     gg_status st = finish_pack(g, g->has_w, nullptr);
     if (st != GG_OK) return st;
     GG_CUDA(cudaEventRecord(g->ev_s1, g->stream));
@@ -408,12 +402,8 @@ static gg_status learned_correct(gg_graph *g, gg_app app, TileArgs a, uint32_t n
         else GG_CUDA(launch_tile_min((int)app, K_CORRECT, a, (int)sub_tiles, g->num_sms, g->stream));
     }
     GG_CUDA(launch_scatter_flags(g->sub_pos, g->sub_mask, total, g->mask, g->num_sms, g->stream));
-    TileArgs r{};
-    fill_list(g, false, r);
-    r.mask = g->mask;
-    r.sp_ptr = g->sp_ptr;
-    r.epoch = next_epoch(g);
-    GG_CUDA(launch_tile_recount(r, (int)g->max_tiles, g->num_sms, g->stream));
+    GG_CUDA(launch_tile_counts(g->full_tile_info, g->full_tiles, (long long)g->n + g->m, g->in_ptr, g->mask,
+                               g->tile_cnt, g->sp_ptr, g->num_sms, g->stream));
     g->launches += 8;
     g->stats.learned_corrections += 1;
     return GG_OK;
@@ -835,6 +825,7 @@ static gg_status alloc_graph(gg_graph *g)
     GG_ALLOC(g->b_out_dst, 4 * m);
     GG_ALLOC(g->b_in_ptr, 4 * (n + 1));
     GG_ALLOC(g->b_in_src, 4 * m);
+    GG_ALLOC(g->b_in_dst, 4 * m);
     GG_ALLOC(g->b_hub, 4 * (m + n + (size_t)kHubs + 4));
     GG_ALLOC(g->b_out_to_in, 4 * m);
     GG_ALLOC(g->b_sp_ptr, 4 * (n + 1));
@@ -866,6 +857,7 @@ static gg_status alloc_graph(gg_graph *g)
     g->out_w = g->has_w ? g->b_out_w.u32() : nullptr;
     g->in_ptr = g->b_in_ptr.i32();
     g->in_src = g->b_in_src.i32();
+    g->in_dst = g->b_in_dst.i32();
     g->in_src_h = g->b_hub.i32();
     g->hub_slot = g->in_src_h + m;
     g->hub_ids = g->hub_slot + n;
@@ -955,7 +947,7 @@ gg_status gg_load_csr(gg_graph **out, int32_t n, int64_t m, const int32_t *rowpt
             break;
         }
         uint32_t mm = (uint32_t)m;
-        if ((st = validate_csr(g)) != GG_OK || (st = build_csc(g)) != GG_OK || (st = build_hubs(g)) != GG_OK) {
+        if ((st = validate_csr(g)) != GG_OK || (st = build_hubs(g)) != GG_OK || (st = build_csc(g)) != GG_OK) {
             cudaEventDestroy(l0);
             cudaEventDestroy(l1);
             break;

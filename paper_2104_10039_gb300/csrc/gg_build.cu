@@ -260,22 +260,65 @@ __global__ void k_validate(const int32_t *__restrict__ rowptr, const int32_t *__
     }
 }
 
-// Source vertex of every CSR arc (one warp per row, grid-stride).
+// Source vertex of every CSR arc. A warp takes 32 consecutive rows; when
+// their arcs are few (the usual case) the warp walks those arcs with
+// coalesced stores and finds each arc's row by a binary search over the 32
+// row starts held in its lanes; a warp whose rows hold many arcs walks them
+// row by row.
 __global__ void k_expand_src(const int32_t *__restrict__ rowptr, int32_t n, int32_t *__restrict__ src_of)
 {
+    constexpr int32_t kShort = 2048;
     const int lane = threadIdx.x & 31;
-    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long v = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
-        const int32_t b = rowptr[v], e = rowptr[v + 1];
-        for (int32_t k = b + lane; k < e; k += 32) src_of[k] = (int32_t)v;
+    const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long v0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; v0 < n; v0 += warps * 32) {
+        const long long v = v0 + lane;
+        const int32_t b = rowptr[v < n ? v : n];   // rows past n start at m
+        const int32_t start = __shfl_sync(0xFFFFFFFFu, b, 0);
+        const int32_t end = __shfl_sync(0xFFFFFFFFu, lane == 0 ? rowptr[v0 + 32 < n ? v0 + 32 : n] : 0, 0);
+        if (end - start <= kShort) {
+            for (int32_t base = start; base < end; base += 32) {
+                const int32_t k = base + lane;
+                int lo = 0;   // the last lane whose row starts at or before k
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int32_t bb = __shfl_sync(0xFFFFFFFFu, b, lo + step);
+                    if (bb <= k) lo += step;
+                }
+                if (k < end) src_of[k] = (int32_t)(v0 + lo);
+            }
+        } else {
+            for (int l = 0; l < 32; ++l) {
+                const int32_t rb = __shfl_sync(0xFFFFFFFFu, b, l);
+                const int32_t re = l < 31 ? __shfl_sync(0xFFFFFFFFu, b, l + 1) : end;
+                for (int32_t k = rb + lane; k < re; k += 32) src_of[k] = (int32_t)(v0 + l);
+            }
+        }
     }
 }
 
 // ------------------------------------------------------------ radix sort ----
+// Stable LSD radix sort of the CSR arcs by destination, 8 bits per pass. The
+// arcs' payload travels with them: the CSR position e (for the CSR -> CSC
+// map), the source and the weight; the first pass reads them from the CSR
+// (e = position), the last pass writes the in-edge arrays themselves and the
+// hub-coded copy of the sources.
 constexpr int kRadixThreads = 256;
 constexpr int kRadixItems = 16;
 constexpr int kRadixTile = kRadixThreads * kRadixItems;
 constexpr int kRadixWarps = kRadixThreads / 32;
+
+struct RadixIO {
+    const uint32_t *keys_in;
+    uint32_t *keys_out;
+    const uint32_t *e_in;   // nullptr: the input position (first pass)
+    uint32_t *e_out;
+    const int32_t *src_in;
+    int32_t *src_out;
+    int32_t *src_h_out;     // last pass: sources with hubs coded -(slot + 1)
+    const int32_t *hub_slot;
+    const uint32_t *w_in;   // nullptr: no weights
+    uint32_t *w_out;
+};
 
 __global__ void k_radix_upsweep(const uint32_t *__restrict__ keys, long long m, int shift,
                                 uint32_t num_tiles, uint32_t *__restrict__ counts)
@@ -295,14 +338,14 @@ __global__ void k_radix_upsweep(const uint32_t *__restrict__ keys, long long m, 
 
 // Stable scatter of one 8-bit digit. Warp w ranks positions
 // [w*512, w*512+512) of the tile in rounds of 32, so the order of equal
-// digits inside the tile is (warp, round, lane) = input order.
-__global__ void __launch_bounds__(kRadixThreads)
-k_radix_downsweep(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
-                  uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, long long m,
-                  int shift, uint32_t num_tiles, const uint32_t *__restrict__ offsets)
+// digits inside the tile is (warp, round, lane) = input order. The keys go
+// through shared memory in tile order first, which fixes every item's global
+// position; each payload array then follows through the same staging buffer.
+__global__ void __launch_bounds__(kRadixThreads, 3)
+k_radix_downsweep(RadixIO io, long long m, int shift, uint32_t num_tiles, const uint32_t *__restrict__ offsets)
 {
-    __shared__ uint32_t s_keys[kRadixTile];
-    __shared__ uint32_t s_vals[kRadixTile];
+    __shared__ uint32_t s_stage[kRadixTile];
+    __shared__ uint32_t s_gpos[kRadixTile];
     __shared__ uint32_t s_whist[kRadixWarps][256];
     __shared__ uint32_t s_tile_excl[256];
     __shared__ uint32_t s_glob[256];
@@ -313,14 +356,17 @@ k_radix_downsweep(const uint32_t *__restrict__ keys_in, const uint32_t *__restri
     for (int i = tid; i < kRadixWarps * 256; i += kRadixThreads) (&s_whist[0][0])[i] = 0;
     __syncthreads();
 
-    uint32_t key[kRadixItems], val[kRadixItems], rank[kRadixItems];
+    uint32_t key[kRadixItems], lp[kRadixItems];
     const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
     for (int r = 0; r < kRadixItems; ++r) {
         const int p = warp * (kRadixItems * 32) + r * 32 + lane;
+        key[r] = p < count ? io.keys_in[base + p] : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < kRadixItems; ++r) {
+        const int p = warp * (kRadixItems * 32) + r * 32 + lane;
         const bool valid = p < count;
-        key[r] = valid ? keys_in[base + p] : 0u;
-        val[r] = valid ? vals_in[base + p] : 0u;
         const uint32_t digit = valid ? ((key[r] >> shift) & 255u) : 256u;
         const uint32_t peers = __match_any_sync(0xFFFFFFFFu, digit);
         uint32_t before = 0;
@@ -328,7 +374,7 @@ k_radix_downsweep(const uint32_t *__restrict__ keys_in, const uint32_t *__restri
         __syncwarp();
         if (valid && (peers & lt) == 0) s_whist[warp][digit] = before + __popc(peers);
         __syncwarp();
-        rank[r] = before + __popc(peers & lt);
+        lp[r] = before + __popc(peers & lt);
     }
     __syncthreads();
     {
@@ -348,19 +394,47 @@ k_radix_downsweep(const uint32_t *__restrict__ keys_in, const uint32_t *__restri
         const int p = warp * (kRadixItems * 32) + r * 32 + lane;
         if (p < count) {
             const uint32_t digit = (key[r] >> shift) & 255u;
-            const uint32_t lp = s_tile_excl[digit] + s_whist[warp][digit] + rank[r];
-            s_keys[lp] = key[r];
-            s_vals[lp] = val[r];
+            lp[r] += s_tile_excl[digit] + s_whist[warp][digit];
+            s_stage[lp[r]] = key[r];
         }
     }
     __syncthreads();
     for (int i = tid; i < count; i += kRadixThreads) {
-        const uint32_t k = s_keys[i];
+        const uint32_t k = s_stage[i];
         const uint32_t digit = (k >> shift) & 255u;
         const uint32_t g = s_glob[digit] + (uint32_t)i - s_tile_excl[digit];
-        keys_out[g] = k;
-        vals_out[g] = s_vals[i];
+        io.keys_out[g] = k;
+        s_gpos[i] = g;
     }
+    // one payload array: loaded in the keys' order, staged, stored in place
+    auto move = [&](auto load, auto store) {
+        uint32_t v[kRadixItems];
+#pragma unroll
+        for (int r = 0; r < kRadixItems; ++r) {
+            const int p = warp * (kRadixItems * 32) + r * 32 + lane;
+            v[r] = p < count ? load(base + p) : 0u;
+        }
+        __syncthreads();   // the previous array's stores have read s_stage
+#pragma unroll
+        for (int r = 0; r < kRadixItems; ++r) {
+            const int p = warp * (kRadixItems * 32) + r * 32 + lane;
+            if (p < count) s_stage[lp[r]] = v[r];
+        }
+        __syncthreads();
+        for (int i = tid; i < count; i += kRadixThreads) store(s_gpos[i], s_stage[i]);
+    };
+    move([&](long long q) { return io.e_in ? __ldcs(io.e_in + q) : (uint32_t)q; },
+         [&](uint32_t g, uint32_t x) { io.e_out[g] = x; });
+    move([&](long long q) { return (uint32_t)__ldcs(io.src_in + q); },
+         [&](uint32_t g, uint32_t x) {
+             io.src_out[g] = (int32_t)x;
+             if (io.src_h_out) {
+                 const int32_t slot = __ldg(io.hub_slot + x);
+                 io.src_h_out[g] = slot >= 0 ? -(slot + 1) : (int32_t)x;
+             }
+         });
+    if (io.w_in)
+        move([&](long long q) { return __ldcs(io.w_in + q); }, [&](uint32_t g, uint32_t x) { io.w_out[g] = x; });
 }
 
 // in_ptr from destination-sorted keys: every boundary writes the row starts
@@ -377,45 +451,30 @@ __global__ void k_csc_rowptr(const uint32_t *__restrict__ keys, long long m, int
     }
 }
 
-// CSC sources / weights from the sorted CSR positions, and the CSR -> CSC map.
-// Every access is random, so each thread keeps four arcs in flight.
-__global__ void k_csc_finalize(const uint32_t *__restrict__ vals, long long m, const int32_t *__restrict__ src_of,
-                               const uint32_t *__restrict__ w_out, int32_t *__restrict__ in_src,
-                               uint32_t *__restrict__ in_w, int32_t *__restrict__ out_to_in)
+// CSR -> CSC map: out_to_in[e] = k for the sorted position k of CSR arc e. The
+// stores are random, so they are made in windows of e small enough to stay in
+// L2 until every word of a sector is written; each launch reads the sorted
+// positions once.
+constexpr long long kMapWindow = 8ll << 20;   // 32 MB of out_to_in per launch
+
+__global__ void k_out_to_in(const uint32_t *__restrict__ e_sorted, long long m, long long lo, long long hi,
+                            int32_t *__restrict__ out_to_in)
 {
     constexpr int U = 4;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long k0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; k0 < m; k0 += U * stride) {
         uint32_t e[U];
-        int32_t sv[U];
-        uint32_t wv[U];
 #pragma unroll
         for (int i = 0; i < U; ++i) {
             const long long k = k0 + i * stride;
-            e[i] = k < m ? __ldcs(vals + k) : 0u;
+            e[i] = k < m ? __ldcs(e_sorted + k) : 0xFFFFFFFFu;
         }
 #pragma unroll
         for (int i = 0; i < U; ++i) {
             const long long k = k0 + i * stride;
-            sv[i] = k < m ? __ldg(src_of + e[i]) : 0;
-            wv[i] = (k < m && w_out) ? __ldg(w_out + e[i]) : 0u;
-        }
-#pragma unroll
-        for (int i = 0; i < U; ++i) {
-            const long long k = k0 + i * stride;
-            if (k < m) {
-                in_src[k] = sv[i];
-                if (w_out) in_w[k] = wv[i];
-                out_to_in[e[i]] = (int32_t)k;
-            }
+            if (k < m && (long long)e[i] >= lo && (long long)e[i] < hi) out_to_in[e[i]] = (int32_t)k;
         }
     }
-}
-
-__global__ void k_iota(uint32_t *v, long long m)
-{
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += stride) v[k] = (uint32_t)k;
 }
 
 // -------------------------------------------------------------- host side ----
@@ -435,31 +494,46 @@ gg_status build_csc(gg_graph *g)
     const uint32_t num_tiles = (uint32_t)((m + kRadixTile - 1) / kRadixTile);
     const size_t ncounts = (size_t)256 * num_tiles;
 
+    // working arrays: keys, sources and weights alternate between a
+    // temporary and the final in-edge array (the last pass lands in the
+    // final one); the CSR positions alternate between two temporaries
     DevBuf tmp;
-    const size_t words = 4 * (size_t)m + ncounts + 1 + scan_tmp_words(ncounts) + (size_t)m;
+    const size_t words = 5 * (size_t)m + ncounts + 1 + scan_tmp_words(ncounts) + (size_t)m;
     gg_status st = tmp.alloc(words * sizeof(uint32_t), s);
     if (st != GG_OK) return st;
-    uint32_t *keys[2] = {tmp.u32(), tmp.u32() + m};
-    uint32_t *vals[2] = {tmp.u32() + 2 * m, tmp.u32() + 3 * m};
-    uint32_t *counts = tmp.u32() + 4 * m;
+    uint32_t *t_keys = tmp.u32(), *t_src = t_keys + m, *t_w = t_src + m;
+    uint32_t *t_e[2] = {t_w + m, t_w + 2 * m};
+    uint32_t *counts = t_w + 3 * m;
     uint32_t *scan_tmp = counts + ncounts + 1;
     int32_t *src_of = (int32_t *)(scan_tmp + scan_tmp_words(ncounts));
 
-    GG_CUDA(cudaMemcpyAsync(keys[0], g->out_dst, sizeof(uint32_t) * m, cudaMemcpyDeviceToDevice, s));
-    k_iota<<<grid, 256, 0, s>>>(vals[0], m);
     k_expand_src<<<grid, 256, 0, s>>>(g->out_ptr, n, src_of);
-    int cur = 0;
+    RadixIO io{};
+    io.keys_in = (const uint32_t *)g->out_dst;
+    io.e_in = nullptr;
+    io.src_in = src_of;
+    io.w_in = g->out_w;
+    io.hub_slot = g->hub_slot;
     for (int p = 0; p < passes; ++p) {
-        const int shift = 8 * p;
-        k_radix_upsweep<<<num_tiles, kRadixThreads, 0, s>>>(keys[cur], m, shift, num_tiles, counts);
+        const bool to_final = ((passes - 1 - p) & 1) == 0;
+        const bool last = p == passes - 1;
+        io.keys_out = to_final ? (uint32_t *)g->in_dst : t_keys;
+        io.e_out = t_e[p & 1];
+        io.src_out = to_final ? g->in_src : (int32_t *)t_src;
+        io.src_h_out = last ? g->in_src_h : nullptr;
+        io.w_out = g->out_w ? (to_final ? g->in_w : t_w) : nullptr;
+        k_radix_upsweep<<<num_tiles, kRadixThreads, 0, s>>>(io.keys_in, m, 8 * p, num_tiles, counts);
         GG_CUDA(launch_scan_u32(counts, counts, ncounts, scan_tmp, s));
-        k_radix_downsweep<<<num_tiles, kRadixThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1],
-                                                              vals[cur ^ 1], m, shift, num_tiles, counts);
-        cur ^= 1;
+        k_radix_downsweep<<<num_tiles, kRadixThreads, 0, s>>>(io, m, 8 * p, num_tiles, counts);
+        io.keys_in = io.keys_out;
+        io.e_in = io.e_out;
+        io.src_in = io.src_out;
+        io.w_in = io.w_out;
     }
-    k_csc_rowptr<<<grid, 256, 0, s>>>(keys[cur], m, n, g->in_ptr);
-    k_csc_finalize<<<grid, 256, 0, s>>>(vals[cur], m, src_of, g->out_w, g->in_src, g->in_w, g->out_to_in);
-    g->load_launches += 4 + 5 * passes;
+    k_csc_rowptr<<<grid, 256, 0, s>>>((const uint32_t *)g->in_dst, m, n, g->in_ptr);
+    for (long long lo = 0; lo < m; lo += kMapWindow)
+        k_out_to_in<<<grid, 256, 0, s>>>(io.e_in, m, lo, lo + kMapWindow, g->out_to_in);
+    g->load_launches += 2 + 5 * passes + (uint32_t)((m + kMapWindow - 1) / kMapWindow);
     GG_CUDA(cudaGetLastError());
     // the temporaries are released only after the queued work has used them
     GG_CUDA(cudaStreamSynchronize(s));
@@ -470,7 +544,8 @@ gg_status build_csc(gg_graph *g)
 // The sources read most often by pull gathers are the vertices with the most
 // out-arcs: the (at most kHubs) vertices with out-degree >= T, T the smallest
 // threshold that admits no more than kHubs of them (and at least 2), get a
-// slot; in_src_h codes their in-arcs as -(slot + 1).
+// slot; the last pass of the in-edge sort codes their in-arcs as -(slot + 1)
+// in in_src_h, so the slots are chosen before the sort.
 constexpr uint32_t kDegBins = 65536;
 
 // Out-degree histogram (degrees clamped to kDegBins - 1); the many small
@@ -512,21 +587,10 @@ __global__ void k_hub_fill(int32_t n, const uint32_t *__restrict__ flag, const u
     }
 }
 
-__global__ void k_hub_code(const int32_t *__restrict__ in_src, long long m, const int32_t *__restrict__ hub_slot,
-                           int32_t *__restrict__ in_src_h)
-{
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (long long)gridDim.x * blockDim.x) {
-        const int32_t v = in_src[k];
-        const int32_t slot = hub_slot[v];
-        in_src_h[k] = slot >= 0 ? -(slot + 1) : v;
-    }
-}
-
 gg_status build_hubs(gg_graph *g)
 {
     cudaStream_t s = g->stream;
     const int32_t n = g->n;
-    const long long m = g->m;
     const int grid = g->num_sms * 8;
     DevBuf tmp;
     gg_status st = tmp.alloc(4 * ((size_t)kDegBins + 2 * ((size_t)n + 1)), s);
@@ -547,9 +611,8 @@ gg_status build_hubs(gg_graph *g)
     k_hub_flag<<<grid, 256, 0, s>>>(g->out_ptr, n, thr, flag);
     GG_CUDA(launch_scan_u32(flag, pos, (size_t)n, g->scan_tmp, s));
     k_hub_fill<<<grid, 256, 0, s>>>(n, flag, pos, g->hub_slot, g->hub_ids);
-    if (m > 0) k_hub_code<<<grid, 256, 0, s>>>(g->in_src, m, g->hub_slot, g->in_src_h);
     g->n_hubs = (int32_t)above;
-    g->load_launches += 8;
+    g->load_launches += 7;
     GG_CUDA(cudaGetLastError());
     GG_CUDA(cudaStreamSynchronize(s));
     return GG_OK;

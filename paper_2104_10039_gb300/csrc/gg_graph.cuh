@@ -68,9 +68,10 @@ struct gg_graph {
     gg::DevBuf b_out_ptr, b_out_dst, b_out_w;
     int32_t *out_ptr = nullptr, *out_dst = nullptr;
     uint32_t *out_w = nullptr;
-    // CSC (in-arcs), CSR -> CSC positions
-    gg::DevBuf b_in_ptr, b_in_src, b_in_w, b_out_to_in;
-    int32_t *in_ptr = nullptr, *in_src = nullptr, *out_to_in = nullptr;
+    // CSC (in-arcs; in_dst = each arc's row, for the sampling hash), CSR ->
+    // CSC positions
+    gg::DevBuf b_in_ptr, b_in_src, b_in_dst, b_in_w, b_out_to_in;
+    int32_t *in_ptr = nullptr, *in_src = nullptr, *in_dst = nullptr, *out_to_in = nullptr;
     // hub cache: in-arc sources with hubs coded -(slot + 1), each hub's slot
     // (-1 otherwise) and each slot's vertex
     gg::DevBuf b_hub;

@@ -92,9 +92,6 @@ struct TileArgs {
     unsigned long long theta_fx;
     int theta_case;             // 0 compare, 1 theta < 0, 2 theta >= 1
     int est_strict;
-    unsigned long long seed;
-    unsigned long long thr;     // floor(sigma * 2^32)
-    int symmetric;
     // per-tile partials of a gather for k_fixup: (has row end, part after the
     // last end) and the part before the first end
     uint2 *part;
@@ -103,7 +100,7 @@ struct TileArgs {
     // value before the arc within its tile (rows continued from an earlier
     // tile start from the identity there) and the arc's value (candidate)
     uint2 *stash;
-    // active arcs per tile (correction, sampling)
+    // active arcs per tile (correction)
     uint32_t *tile_cnt;
     // look-back
     unsigned long long *st_carry;
@@ -124,11 +121,10 @@ struct TileArgs {
     int32_t n_hubs;
 };
 
-// K_GATHER: approximate / accurate pull iteration. K_STASH + K_CORRECT: the
-// two launches of a correction iteration. K_SAMPLE: sparsification.
-// K_RECOUNT: tile counts and tile-local row ends of the flags already in the
-// bitmap (after a learned correction rewrote some rows' flags).
-enum TileKind { K_GATHER = 0, K_CORRECT = 1, K_SAMPLE = 2, K_STASH = 3, K_RECOUNT = 4 };
+// K_GATHER: approximate / accurate pull iteration. K_STASH + k_correct2 (or
+// K_CORRECT for the share influence): the two launches of a correction
+// iteration.
+enum TileKind { K_GATHER = 0, K_CORRECT = 1, K_STASH = 2 };
 
 // Inputs of the learned correction's vertex features.
 struct FeatArgs {
@@ -256,8 +252,16 @@ cudaError_t launch_pack(const int32_t *tile_info, const uint32_t *tile_off, uint
 // Tile kernels run a persistent grid: min(max_tiles, resident warps).
 cudaError_t launch_tile_pr(int kind, const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s);
 cudaError_t launch_tile_min(int app, int kind, const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s);
-cudaError_t launch_tile_sample(const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s);
-cudaError_t launch_tile_recount(const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s);
+// Sampling (Sec. 3.4): the flag of every arc of the full in-edge list from
+// the hash of its endpoints (in_dst: each arc's row).
+cudaError_t launch_sample(const int32_t *in_src, const int32_t *in_dst, long long m, int symmetric,
+                          unsigned long long seed, unsigned long long thr, uint32_t *mask, int num_sms,
+                          cudaStream_t s);
+// Per merge-path tile of a list: its active arcs (flags in the bitmap) and the
+// tile-local row ends of the packed list, as k_pack expects them.
+cudaError_t launch_tile_counts(const int32_t *tile_info, uint32_t num_tiles, long long total_items,
+                               const int32_t *row_ptr, const uint32_t *mask, uint32_t *tile_cnt, int32_t *sp_ptr,
+                               int num_sms, cudaStream_t s);
 // Rows a gather left open at tile starts (one launch after every gather).
 cudaError_t launch_fixup(int app, const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s);
 cudaError_t launch_push(const PushArgs &a, uint32_t max_arcs, int grid, cudaStream_t s);

@@ -1,5 +1,5 @@
 // gg_tile.cuh - the merge-path tile engine behind the pull gather (approximate
-// and accurate iterations), the correction iteration and the edge sampler.
+// and accurate iterations) and the correction iteration.
 //
 // A list (CSC rows: row_ptr + per-arc source/weight) is viewed as the merged
 // sequence "arcs of row 0, end of row 0, arcs of row 1, end of row 1, ...".
@@ -14,19 +14,22 @@
 //   walk    each lane takes its kIPT items into registers once;
 //   scan    a warp segmented scan gives every lane the running value of the
 //           row open at its start; the tile publishes its partials;
-//   pass 2  per arc, influence and new flag (correction, Alg. 2 GG-EStatus)
-//           or sampled flag (Sec. 3.4); per row end, GG-Apply + GG-VStatus;
-//   flags   (correction, sampling) the new flags go to the bitmap with the
-//           tile's active count and the tile-local row ends; a tile-count
-//           scan and k_pack then build the packed active-CSC from the bitmap.
+//   pass 2  per arc, influence and new flag (correction, Alg. 2 GG-EStatus);
+//           per row end, GG-Apply + GG-VStatus;
+//   flags   (correction) the new flags go to the bitmap with the tile's
+//           active count and the tile-local row ends; a tile-count scan and
+//           k_pack then build the packed active-CSC from the bitmap.
 // A row that began in an earlier tile needs those tiles' partials. The gather
 // leaves that row to k_fixup. The correction, whose per-arc influence needs
 // the running value before each arc (Alg. 2, GG-Gather's return), runs in two
-// launches: K_STASH gathers the values, publishes the partials and stashes
-// the values in arc order; K_CORRECT then reads them back with coalesced loads
-// and takes its carry from the finished partials.
+// launches: K_STASH gathers the values, publishes the partials and stashes,
+// for every arc in arc order, its value and the running value before it;
+// k_correct2 then reads those pairs back with coalesced loads and takes its
+// carry from the finished partials. The share influence, which needs whole
+// rows first, runs the full second pass K_CORRECT over the stashed values.
 #pragma once
 
+#include "gg_hash.cuh"
 #include "gg_internal.cuh"
 
 namespace gg {
@@ -48,26 +51,6 @@ struct Acc<GG_APP_PAGERANK> {  // PageRank: FP32 sum
     __device__ static __forceinline__ uint32_t bits(T v) { return __float_as_uint(v); }
     __device__ static __forceinline__ T from_bits(uint32_t b) { return __uint_as_float(b); }
 };
-
-// SplitMix64 output for one state (Steele, Lea, Flood 2014): advance by the
-// golden gamma, then the variant-13 finaliser.
-__device__ __forceinline__ unsigned long long splitmix64(unsigned long long state)
-{
-    unsigned long long z = state + 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
-// Initial flag of arc src -> dst under ratio threshold thr = floor(sigma*2^32).
-__device__ __forceinline__ uint32_t sampled_flag(int32_t src, int32_t dst, int symmetric,
-                                                 unsigned long long seed, unsigned long long thr)
-{
-    uint32_t a = (uint32_t)src, b = (uint32_t)dst;
-    if (symmetric && a > b) { uint32_t t = a; a = b; b = t; }
-    const unsigned long long key = ((unsigned long long)a << 32) | b;
-    return (splitmix64(seed ^ key) >> 32) < thr ? 1u : 0u;
-}
 
 // Shared-memory slot of tile-local item k: one padding word per 8 items, so
 // lanes reading their own 8 consecutive items hit distinct banks.
@@ -243,7 +226,7 @@ template <int APP, int KIND>
 struct WarpSmem {
     int32_t rowend[kWT + 1];
     uint32_t val[kPadded];   // arc values (bits of T), or arc sources when sampling
-    uint32_t vtx[(KIND == K_SAMPLE || KIND == K_STASH || KIND == K_RECOUNT) ? 1 : kWT];   // rows' current value
+    uint32_t vtx[KIND == K_STASH ? 1 : kWT];   // rows' current value
     int32_t deg[(KIND == K_GATHER || KIND == K_CORRECT) && APP == GG_APP_PAGERANK ? kWT : 1];  // rows' out-degree
     uint32_t bits[(KIND == K_GATHER) ? 1 : (kWT / 32 + 2)];
     uint32_t oldw[(KIND == K_CORRECT && APP != GG_APP_PAGERANK) ? (kWT / 32 + 2) : 1];
@@ -257,8 +240,7 @@ k_tile(TileArgs a)
 {
     using T = typename Acc<APP>::T;
     using A = Acc<APP>;
-    constexpr bool kPack = KIND == K_CORRECT || KIND == K_SAMPLE || KIND == K_RECOUNT;
-    constexpr bool kNoGather = KIND == K_SAMPLE || KIND == K_RECOUNT;   // flags only, no values
+    constexpr bool kPack = KIND == K_CORRECT;
     constexpr bool kMin = APP != GG_APP_PAGERANK;
     constexpr bool kWeighted = APP == GG_APP_SSSP && (KIND == K_GATHER || KIND == K_STASH);
     constexpr bool kApply = KIND == K_GATHER || KIND == K_CORRECT;
@@ -305,8 +287,7 @@ k_tile(TileArgs a)
         for (int i = 0; i < kIPT; ++i) {
             const int k = (int)lane + 32 * i;
             const bool ok = live && k < b1 - b0;
-            if constexpr (KIND == K_RECOUNT) srcv[i] = 0;
-            else if constexpr (kStashed) srcv[i] = ok ? (int32_t)__ldcs(&a.stash[b0 + k].y) : 0;
+            if constexpr (kStashed) srcv[i] = ok ? (int32_t)__ldcs(&a.stash[b0 + k].y) : 0;
             else srcv[i] = ok ? __ldg(a.arc_src + b0 + k) : 0;
             if constexpr (kWeighted) wv[i] = (ok && load_w) ? __ldg(a.arc_w + b0 + k) : 1u;
         }
@@ -331,7 +312,7 @@ k_tile(TileArgs a)
         for (int i = 0; i < kIPT; ++i) {
             const int k = (int)lane + 32 * i;
             const int32_t sv = src_cur[i];   // a hub is coded -(slot + 1)
-            if constexpr (kNoGather || kStashed) {
+            if constexpr (kStashed) {
                 gv[i] = (uint32_t)sv;
             } else if constexpr (APP == GG_APP_PAGERANK) {
                 gv[i] = k < narcs ? (sv < 0 ? s_hub[-sv - 1] : __float_as_uint(__ldg(a.contrib_cur + sv))) : 0u;
@@ -425,7 +406,7 @@ k_tile(TileArgs a)
         // ---- fold + warp segmented scan --------------------------------------
         T carry_in = A::id();
         bool defer_first = false;   // gather: the tile's first row end waits for k_fixup
-        if constexpr (!kNoGather) {
+        {
             T v = A::id(), head = A::id();
             uint32_t f = 0;
 #pragma unroll
@@ -505,16 +486,7 @@ k_tile(TileArgs a)
 #pragma unroll
             for (int i = 0; i < kIPT; ++i) {
                 if ((arcmask >> i) & 1u) {
-                    if constexpr (KIND == K_SAMPLE) {
-                        const uint32_t fl = sampled_flag((int32_t)item_v[i], r0 + x, a.symmetric, a.seed, a.thr);
-                        my_flags |= fl << i;
-                        my_active += fl;
-                    } else if constexpr (KIND == K_RECOUNT) {
-                        const int k = a0 + y;
-                        const uint32_t fl = (__ldg(a.mask + (k >> 5)) >> (k & 31)) & 1u;
-                        my_flags |= fl << i;
-                        my_active += fl;
-                    } else {
+                    {
                         const T v = A::from_bits(item_v[i]);
                         if constexpr (KIND == K_CORRECT) {
                             uint32_t fl;
@@ -636,7 +608,7 @@ k_tile(TileArgs a)
                 }
             }
             __syncwarp();
-            for (int i = (int)lane; KIND != K_RECOUNT && i < nwords; i += 32) {
+            for (int i = (int)lane; i < nwords; i += 32) {
                 const int w = w0 + i;
                 const int lo = a0 > w * 32 ? a0 : w * 32;
                 const int hi = a1 < w * 32 + 32 ? a1 : w * 32 + 32;

@@ -1,5 +1,5 @@
 // gg_tile_min.cu - SSSP, BFS and CC instantiations of the tile engine (pull
-// gather and correction on a min accumulator) and the edge sampler.
+// gather and correction on a min accumulator).
 #include "gg_tile_launch.cuh"
 
 namespace gg {
@@ -15,21 +15,6 @@ cudaError_t launch_tile_min(int app, int kind, const TileArgs &a, int max_tiles,
     case GG_APP_CC * 2 + 1: return launch_correction<GG_APP_CC>(a, max_tiles, num_sms, s);
     default: return cudaErrorInvalidValue;
     }
-}
-
-// Sampling (Sec. 3.4) reuses the tile walk over the full in-edge list: the
-// hash decides each flag and the active arcs are packed. The value type of
-// the instantiation is irrelevant (no gather).
-cudaError_t launch_tile_sample(const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s)
-{
-    return launch_tiles<GG_APP_CC, K_SAMPLE>(a, max_tiles, num_sms, s);
-}
-
-// Tile counts and tile-local row ends of the flags in the bitmap (no hash,
-// no gather): after a learned correction rewrote the flags of some rows.
-cudaError_t launch_tile_recount(const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s)
-{
-    return launch_tiles<GG_APP_CC, K_RECOUNT>(a, max_tiles, num_sms, s);
 }
 
 cudaError_t launch_fixup_pr(const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s);
