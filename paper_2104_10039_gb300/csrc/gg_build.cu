@@ -242,22 +242,35 @@ cudaError_t launch_scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint32_
 }
 
 // ------------------------------------------------------------ validation ----
+// colidx (library-owned, 16-byte aligned) is read with 16-byte loads, four in
+// flight per thread.
 __global__ void k_validate(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
                            int32_t n, long long m, uint32_t *err)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)n + 1 || i < m; i += stride) {
-        if (i <= n) {
-            const int32_t r = rowptr[i];
-            bool bad = (i == 0 && r != 0) || (i == n && (long long)r != m) || r < 0 || (long long)r > m;
-            if (i < n && rowptr[i + 1] < r) bad = true;
-            if (bad) atomicOr(err, DEVERR_BAD_GRAPH);
-        }
-        if (i < m) {
-            const int32_t c = colidx[i];
-            if (c < 0 || c >= n) atomicOr(err, DEVERR_BAD_GRAPH);
-        }
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool bad = false;
+    for (long long i = tid; i <= n; i += stride) {
+        const int32_t r = rowptr[i];
+        bad |= (i == 0 && r != 0) || (i == n && (long long)r != m) || r < 0 || (long long)r > m;
+        if (i < n && rowptr[i + 1] < r) bad = true;
     }
+    auto out = [n](int32_t c) { return c < 0 || c >= n; };
+    constexpr int U = 4;
+    const long long m4 = m >> 2;
+    const int4 *c4 = reinterpret_cast<const int4 *>(colidx);
+    for (long long q0 = tid; q0 < m4; q0 += U * stride) {
+        int4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long q = q0 + u * stride;
+            v[u] = q < m4 ? __ldcs(c4 + q) : make_int4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) bad |= out(v[u].x) || out(v[u].y) || out(v[u].z) || out(v[u].w);
+    }
+    for (long long i = 4 * m4 + tid; i < m; i += stride) bad |= out(colidx[i]);
+    if (bad) atomicOr(err, DEVERR_BAD_GRAPH);
 }
 
 // Source vertex of every CSR arc. A warp takes 32 consecutive rows; when
@@ -439,15 +452,29 @@ k_radix_downsweep(RadixIO io, long long m, int shift, uint32_t num_tiles, const 
 
 // in_ptr from destination-sorted keys: every boundary writes the row starts
 // of the rows it opens (empty rows included).
+// Four keys per thread (one 16-byte load; keys are library-owned and 16-byte
+// aligned).
 __global__ void k_csc_rowptr(const uint32_t *__restrict__ keys, long long m, int32_t n, int32_t *__restrict__ in_ptr)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += stride) {
-        const int32_t u = (int32_t)keys[k];
-        const int32_t prev = k == 0 ? -1 : (int32_t)keys[k - 1];
-        for (int32_t v = prev + 1; v <= u; ++v) in_ptr[v] = (int32_t)k;
-        if (k == m - 1)
-            for (int32_t v = u + 1; v <= n; ++v) in_ptr[v] = (int32_t)m;
+    const long long q_end = (m + 3) >> 2;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < q_end; q += stride) {
+        const long long k0 = 4 * q;
+        uint32_t c[4];
+        if (k0 + 4 <= m) {
+            const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(keys) + q);
+            c[0] = v.x, c[1] = v.y, c[2] = v.z, c[3] = v.w;
+        } else {
+            for (int i = 0; i < 4; ++i) c[i] = k0 + i < m ? keys[k0 + i] : 0u;
+        }
+        int32_t prev = k0 == 0 ? -1 : (int32_t)keys[k0 - 1];
+        for (int i = 0; i < 4 && k0 + i < m; ++i) {
+            const int32_t u = (int32_t)c[i];
+            for (int32_t v = prev + 1; v <= u; ++v) in_ptr[v] = (int32_t)(k0 + i);
+            if (k0 + i == m - 1)
+                for (int32_t v = u + 1; v <= n; ++v) in_ptr[v] = (int32_t)m;
+            prev = u;
+        }
     }
 }
 
@@ -455,7 +482,7 @@ __global__ void k_csc_rowptr(const uint32_t *__restrict__ keys, long long m, int
 // stores are random, so they are made in windows of e small enough to stay in
 // L2 until every word of a sector is written; each launch reads the sorted
 // positions once.
-constexpr long long kMapWindow = 8ll << 20;   // 32 MB of out_to_in per launch
+constexpr long long kMapWindow = 16ll << 20;   // 64 MB of out_to_in per launch
 
 __global__ void k_out_to_in(const uint32_t *__restrict__ e_sorted, long long m, long long lo, long long hi,
                             int32_t *__restrict__ out_to_in)

@@ -661,12 +661,14 @@ k_fixup(TileArgs a)
             const uint32_t info = (uint32_t)a.tile_info[t];
             const uint2 me = a.part[t];
             if ((info >> 31) && me.x) {
-                long long j = t - 1;
-                while (j > 0 && a.part[j].x == 0u) --j;
+                // row r began after the end of row r - 1, the item at merged
+                // index row_ptr[r] + r - 1: its tile j is the nearest earlier
+                // tile with a row end, and the tiles between hold only row r
+                const int32_t r = (int32_t)(info & 0x7FFFFFFFu);
+                const long long j = r > 0 ? ((long long)a.row_ptr[r] + r - 1) / kWT : 0;
                 T acc = A::from_bits(a.part[j].y);
                 for (long long k = j + 1; k < t; ++k) acc = A::op(acc, A::from_bits(a.part[k].y));
                 acc = A::op(acc, A::from_bits(a.part_head[t]));
-                const int32_t r = (int32_t)(info & 0x7FFFFFFFu);
                 const int32_t u = a.row_vtx ? a.row_vtx[r] : r;
                 if constexpr (APP == GG_APP_PAGERANK) {
                     apply_pr(a, u, acc, a.rank_cur[u],
