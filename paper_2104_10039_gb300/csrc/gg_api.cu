@@ -542,18 +542,21 @@ static gg_status run_pagerank(gg_graph *g, gg_policy policy, const gg_params *p)
     return GG_OK;
 }
 
-// Out-degree prefix of the frontier q[qc] (q_len known); returns its total.
-static gg_status frontier_degrees(gg_graph *g, int qc, uint32_t qlen, uint64_t *total)
+// The frontier q[qc] after an iteration, in one device-to-host read: its
+// length, the out-arcs of its vertices (each vertex's out-degree stays in
+// q_deg for the scan a push needs) and the packed list's arc count.
+static gg_status frontier_summary(gg_graph *g, int qc, uint32_t *qlen, uint64_t *arcs)
 {
-    *total = 0;
-    if (qlen == 0) return GG_OK;
-    GG_CUDA(launch_qdeg(g->q[qc], &g->q_len[qc], g->out_ptr, g->q_deg, qlen, g->num_sms, g->stream));
-    GG_CUDA(launch_scan_u32(g->q_deg, g->q_deg, qlen, g->scan_tmp, g->stream));
-    g->launches += 4;
-    uint32_t t = 0;
-    gg_status st = read_u32(g, g->q_deg + qlen, &t);
-    *total = t;
-    return st;
+    GG_CUDA(cudaMemsetAsync(g->front_dev, 0, sizeof(FrontSum), g->stream));
+    GG_CUDA(launch_qdeg(g->q[qc], &g->q_len[qc], g->out_ptr, g->q_deg, g->front_dev, g->sp_nnz, (uint32_t)g->n,
+                        g->num_sms, g->stream));
+    GG_CUDA(cudaMemcpyAsync(&g->front_host, g->front_dev, sizeof(FrontSum), cudaMemcpyDeviceToHost, g->stream));
+    GG_CUDA(cudaStreamSynchronize(g->stream));
+    g->launches += 1;
+    *qlen = g->front_host.len;
+    *arcs = g->front_host.arcs;
+    g->sp_nnz_host = g->front_host.nnz;
+    return GG_OK;
 }
 
 static gg_status run_min(gg_graph *g, gg_app app, gg_policy policy, const gg_params *p)
@@ -565,14 +568,10 @@ static gg_status run_min(gg_graph *g, gg_app app, gg_policy policy, const gg_par
     GG_CUDA(launch_init_min(g->n, (int)app, p->source, g->val[0], g->q[0], g->q_val[0], &g->q_len[0], g->num_sms,
                             g->stream));
     g->launches += 1;
-    uint32_t qlen = app == GG_APP_CC ? (uint32_t)g->n : 1u;
+    uint32_t qlen = 0;
     uint64_t front_arcs = 0;
-    gg_status st = frontier_degrees(g, qc, qlen, &front_arcs);
+    gg_status st = frontier_summary(g, qc, &qlen, &front_arcs);
     if (st != GG_OK) return st;
-    if (policy != GG_POLICY_EXACT) {
-        st = read_u32(g, g->sp_nnz, &g->sp_nnz_host);
-        if (st != GG_OK) return st;
-    }
     int theta_case = 0;
     unsigned long long theta_fx = 0;
     const double th = (double)p->theta;
@@ -599,6 +598,9 @@ static gg_status run_min(gg_graph *g, gg_app app, gg_policy policy, const gg_par
                 g->stamp_tag = 1;
             }
             if (hs) GG_CUDA(cudaMemsetAsync(hs, 0, sizeof(float) * g->n, g->stream));
+            // arc offsets of the frontier vertices (their degrees are in q_deg)
+            GG_CUDA(launch_scan_u32(g->q_deg, g->q_deg, qlen, g->scan_tmp, g->stream));
+            g->launches += 3;
             PushArgs pa{};
             pa.q = g->q[qc];
             pa.q_val = g->q_val[qc];
@@ -682,8 +684,6 @@ static gg_status run_min(gg_graph *g, gg_app app, gg_policy policy, const gg_par
                 if (st != GG_OK) return st;
                 g->sample_clean = false;
                 g->stats.corrections += 1;
-                st = read_u32(g, g->sp_nnz, &g->sp_nnz_host);
-                if (st != GG_OK) return st;
             }
             g->cur ^= 1;
             g->stats.pull_iterations += 1;
@@ -691,7 +691,7 @@ static gg_status run_min(gg_graph *g, gg_app app, gg_policy policy, const gg_par
         const uint32_t prev_qlen = qlen;
         const int prev_qc = qc;
         qc = nq;
-        st = read_u32(g, &g->q_len[qc], &qlen);
+        st = frontier_summary(g, qc, &qlen, &front_arcs);
         if (st != GG_OK) return st;
         g->iterations = i + 1;
         g->executed += 1;
@@ -703,7 +703,7 @@ static gg_status run_min(gg_graph *g, gg_app app, gg_policy policy, const gg_par
             GG_CUDA(launch_append_frontier(g->q[prev_qc], prev_qlen, hs, g->val[g->cur], g->q[qc], g->q_val[qc],
                                            &g->q_len[qc], g->num_sms, g->stream));
             g->launches += 1;
-            st = read_u32(g, &g->q_len[qc], &qlen);
+            st = frontier_summary(g, qc, &qlen, &front_arcs);
             if (st != GG_OK) return st;
         }
         if (qlen == 0 && !learned) {
@@ -723,8 +723,6 @@ static gg_status run_min(gg_graph *g, gg_app app, gg_policy policy, const gg_par
             front_arcs = 0;
             continue;
         }
-        st = frontier_degrees(g, qc, qlen, &front_arcs);
-        if (st != GG_OK) return st;
     }
     uint32_t err = 0;
     st = read_u32(g, g->dev_err, &err);
@@ -881,6 +879,7 @@ static gg_status alloc_graph(gg_graph *g)
     g->sp_nnz = sc + 3;
     g->dev_err = sc + 4;
     g->q_len = sc + 6;  // two entries
+    g->front_dev = reinterpret_cast<FrontSum *>(sc + 8);
     g->mask = g->b_mask.u32();
     float *v = g->b_vals.f32();
     g->rank[0] = v;

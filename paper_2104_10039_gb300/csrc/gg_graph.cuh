@@ -104,6 +104,9 @@ struct gg_graph {
     double sample_ratio = 0.0;
     uint64_t sample_seed = 0;
     uint32_t sp_nnz_host = 0;
+    // frontier summary on the device and its host copy
+    gg::FrontSum *front_dev = nullptr;
+    gg::FrontSum front_host{};
     // vertex values (double-buffered)
     gg::DevBuf b_vals;
     float *rank[2] = {nullptr, nullptr}, *contrib[2] = {nullptr, nullptr};

@@ -267,8 +267,15 @@ cudaError_t launch_fixup(int app, const TileArgs &a, int max_tiles, int num_sms,
 cudaError_t launch_push(const PushArgs &a, uint32_t max_arcs, int grid, cudaStream_t s);
 cudaError_t launch_scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint32_t *tmp, cudaStream_t s);
 size_t scan_tmp_words(size_t n);
+// What the host reads about a frontier after an iteration, in one copy: the
+// out-arcs of its vertices, its length, and the packed list's arc count.
+struct FrontSum {
+    unsigned long long arcs;
+    uint32_t len;
+    uint32_t nnz;
+};
 cudaError_t launch_qdeg(const int32_t *q, const uint32_t *q_len, const int32_t *out_ptr, uint32_t *deg,
-                        uint32_t max_n, int num_sms, cudaStream_t s);
+                        FrontSum *sum, const uint32_t *nnz, uint32_t max_n, int num_sms, cudaStream_t s);
 cudaError_t launch_snapshot(const int32_t *q, const uint32_t *q_len, const uint32_t *val, uint32_t *q_val,
                             float *hist, uint32_t max_n, int num_sms, cudaStream_t s);
 cudaError_t launch_init_pr(int32_t n, const int32_t *out_ptr, float *rank, float *contrib, int num_sms,

@@ -83,14 +83,28 @@ cudaError_t launch_push(const PushArgs &a, uint32_t max_arcs, int grid, cudaStre
 }
 
 // Out-degrees of the frontier vertices (scanned afterwards into q_deg).
+// Out-degree of every frontier vertex (the push scans them into arc offsets)
+// and the frontier summary: its length, its out-arcs (sum is zeroed before the
+// launch) and the packed list's arc count.
 __global__ void k_qdeg(const int32_t *__restrict__ q, const uint32_t *__restrict__ q_len,
-                       const int32_t *__restrict__ out_ptr, uint32_t *__restrict__ deg)
+                       const int32_t *__restrict__ out_ptr, uint32_t *__restrict__ deg, FrontSum *sum,
+                       const uint32_t *__restrict__ nnz)
 {
     const uint32_t qn = *q_len;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sum->len = qn;
+        sum->nnz = nnz ? *nnz : 0u;
+    }
+    unsigned long long arcs = 0;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < qn; i += gridDim.x * blockDim.x) {
         const int32_t v = q[i];
-        deg[i] = (uint32_t)(out_ptr[v + 1] - out_ptr[v]);
+        const uint32_t d = (uint32_t)(out_ptr[v + 1] - out_ptr[v]);
+        deg[i] = d;
+        arcs += d;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) arcs += __shfl_xor_sync(0xFFFFFFFFu, arcs, o);
+    if ((threadIdx.x & 31) == 0 && arcs) atomicAdd(&sum->arcs, arcs);
 }
 
 // Values of the frontier vertices at the end of a push iteration; with hist,
@@ -195,12 +209,12 @@ cudaError_t launch_append_frontier(const int32_t *q_src, uint32_t len, const flo
 __global__ void k_iter_changed(IterStatsDev *s, const uint32_t *q_len) { s->changed = *q_len; }
 
 cudaError_t launch_qdeg(const int32_t *q, const uint32_t *q_len, const int32_t *out_ptr, uint32_t *deg,
-                        uint32_t max_n, int num_sms, cudaStream_t s)
+                        FrontSum *sum, const uint32_t *nnz, uint32_t max_n, int num_sms, cudaStream_t s)
 {
     int blocks = (int)((max_n + 255) / 256);
     if (blocks > num_sms * 8) blocks = num_sms * 8;
     if (blocks < 1) blocks = 1;
-    k_qdeg<<<blocks, 256, 0, s>>>(q, q_len, out_ptr, deg);
+    k_qdeg<<<blocks, 256, 0, s>>>(q, q_len, out_ptr, deg, sum, nnz);
     return cudaGetLastError();
 }
 
