@@ -323,8 +323,8 @@ def bench_ours(a, rank, world, local):
         avg_s = classes[dom][0] * 1e-3 / classes[dom][1]
         bytes_per = classes[dom][2] / classes[dom][1]
         achieved = bytes_per / avg_s / 1e9
-        name = {"gather": "k_tile<{a}, K_GATHER> + k_fixup<{a}>",
-                "correct": "k_tile<{a}, K_STASH> + k_tile<{a}, K_CORRECT>"}[dom[1]].format(a=dom[0])
+        name = {"gather": "k_arcs<{a}, K_GATHER> + k_fixup<{a}>",
+                "correct": "k_arcs<{a}, K_STASH> + k_correct2<{a}>"}[dom[1]].format(a=dom[0])
         roof = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
                 "traffic": recorded_traffic(f"{dom[0]}/{dom[1]}", bytes_per),

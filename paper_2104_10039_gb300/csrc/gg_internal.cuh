@@ -96,7 +96,7 @@ struct TileArgs {
     // last end) and the part before the first end
     uint2 *part;
     uint32_t *part_head;
-    // correction: per arc in list order, written by K_STASH: the row's running
+    // correction: per arc in list order, written by k_arcs<., K_STASH>: the row's running
     // value before the arc within its tile (rows continued from an earlier
     // tile start from the identity there) and the arc's value (candidate)
     uint2 *stash;
@@ -121,9 +121,9 @@ struct TileArgs {
     int32_t n_hubs;
 };
 
-// K_GATHER: approximate / accurate pull iteration. K_STASH + k_correct2 (or
-// K_CORRECT for the share influence): the two launches of a correction
-// iteration.
+// K_GATHER: approximate / accurate pull iteration (k_arcs<., K_GATHER>).
+// K_CORRECT: a correction iteration as the launchers take it, run as
+// k_arcs<., K_STASH> then k_correct2 (or k_share for the share influence).
 enum TileKind { K_GATHER = 0, K_CORRECT = 1, K_STASH = 2 };
 
 // Inputs of the learned correction's vertex features.

@@ -1,5 +1,7 @@
-// gg_tile.cuh - the merge-path tile engine behind the pull gather (approximate
-// and accurate iterations) and the correction iteration.
+// gg_tile.cuh - the merge-path tile engine: shared pieces of the tile
+// kernels (value ops, warp scans, partial carries, the row apply), the
+// second launches of a correction iteration (k_correct2, k_share) and the
+// completion of rows split across tiles (k_fixup).
 //
 // A list (CSC rows: row_ptr + per-arc source/weight) is viewed as the merged
 // sequence "arcs of row 0, end of row 0, arcs of row 1, end of row 1, ...".
@@ -7,26 +9,18 @@
 // whether that row began in an earlier tile) comes from a precomputed
 // partition. Every warp works on its own tiles (t = warp, warp + W, ...) with
 // no barrier and no wait on another warp, and loads the next tile's header
-// and arc data while it works on the current one:
-//   load    the tile's row ends and its rows' vertex data into shared memory,
-//           and the arcs' values with random loads (the GG-Gather reads of
-//           Alg. 1 / Alg. 2), staged in shared memory;
-//   walk    each lane takes its kIPT items into registers once;
-//   scan    a warp segmented scan gives every lane the running value of the
-//           row open at its start; the tile publishes its partials;
-//   pass 2  per arc, influence and new flag (correction, Alg. 2 GG-EStatus);
-//           per row end, GG-Apply + GG-VStatus;
-//   flags   (correction) the new flags go to the bitmap with the tile's
-//           active count and the tile-local row ends; a tile-count scan and
-//           k_pack then build the packed active-CSC from the bitmap.
+// and arc data while it works on the current one. Each tile publishes two
+// partials: whether it holds a row end with the part of the row open at its
+// end, and the part before its first row end.
 // A row that began in an earlier tile needs those tiles' partials. The gather
-// leaves that row to k_fixup. The correction, whose per-arc influence needs
-// the running value before each arc (Alg. 2, GG-Gather's return), runs in two
-// launches: K_STASH gathers the values, publishes the partials and stashes,
-// for every arc in arc order, its value and the running value before it;
-// k_correct2 then reads those pairs back with coalesced loads and takes its
-// carry from the finished partials. The share influence, which needs whole
-// rows first, runs the full second pass K_CORRECT over the stashed values.
+// (k_arcs<., K_GATHER>, gg_gather.cuh) leaves that row to k_fixup. The
+// correction, whose per-arc influence needs the running value before each arc
+// (Alg. 2, GG-Gather's return), runs in two launches: k_arcs<., K_STASH>
+// gathers the values, publishes the partials and stashes, for every arc in
+// arc order, its value and the running value before it; k_correct2 then
+// reads those pairs back with coalesced loads and takes its carry from the
+// finished partials. The share influence, which needs whole rows first, runs
+// k_share over the stashed values instead.
 #pragma once
 
 #include "gg_hash.cuh"
@@ -221,44 +215,34 @@ __device__ __forceinline__ void flush_stats(const TileArgs &a, ApplyStats st)
     }
 }
 
-// ------------------------------------------------------------ tile kernel ----
-template <int APP, int KIND>
-struct WarpSmem {
+// ------------------------------------------------- share-influence pass ----
+// The correction's second launch when a PageRank arc's influence is its share
+// of the row total (GG_INFL_SHARE): the stashing gather has left every arc's
+// value in the stash and the tile partials, so this pass walks the tile's
+// merged items again (merge path: each lane takes kIPT consecutive items), adds
+// up rows with a warp segmented scan, finds the total of every row in the tile
+// (the row still open at the tile end adds the later tiles' partials), tests
+// each arc's share against theta (GG-EStatus), applies the rows ending in the
+// tile (GG-Apply, GG-VStatus) and writes the new flags with the tile's active
+// count and tile-local row ends for the pack.
+struct ShareSmem {
     int32_t rowend[kWT + 1];
-    uint32_t val[kPadded];   // arc values (bits of T), or arc sources when sampling
-    uint32_t vtx[KIND == K_STASH ? 1 : kWT];   // rows' current value
-    int32_t deg[(KIND == K_GATHER || KIND == K_CORRECT) && APP == GG_APP_PAGERANK ? kWT : 1];  // rows' out-degree
-    uint32_t bits[(KIND == K_GATHER) ? 1 : (kWT / 32 + 2)];
-    uint32_t oldw[(KIND == K_CORRECT && APP != GG_APP_PAGERANK) ? (kWT / 32 + 2) : 1];
-    float rowtot[(KIND == K_CORRECT && APP == GG_APP_PAGERANK) ? kWT + 1 : 1];   // influence share
-    uint32_t bef[KIND == K_STASH ? kPadded : 1];   // running value before each arc, in arc order
+    uint32_t val[kPadded];      // arc values
+    uint32_t vtx[kWT];          // rows' current rank
+    int32_t deg[kWT];           // rows' out-degree
+    uint32_t bits[kWT / 32 + 2];
+    float rowtot[kWT + 1];      // row totals
 };
 
-template <int APP, int KIND>
+template <int APP>
 __global__ void __launch_bounds__(kThreads, 4)
-k_tile(TileArgs a)
+k_share(TileArgs a)
 {
-    using T = typename Acc<APP>::T;
-    using A = Acc<APP>;
-    constexpr bool kPack = KIND == K_CORRECT;
-    constexpr bool kMin = APP != GG_APP_PAGERANK;
-    constexpr bool kWeighted = APP == GG_APP_SSSP && (KIND == K_GATHER || KIND == K_STASH);
-    constexpr bool kApply = KIND == K_GATHER || KIND == K_CORRECT;
-    constexpr bool kStashed = KIND == K_CORRECT;   // values come from the stash, in arc order
-    __shared__ WarpSmem<APP, KIND> smem[kWarps];
-    WarpSmem<APP, KIND> &s = smem[threadIdx.x >> 5];
-    // hub cache: the values of the most-read sources, one copy per block
-    constexpr bool kHub = KIND == K_GATHER || KIND == K_STASH;
-    __shared__ uint32_t s_hub[kHub ? kHubs : 1];
-    if constexpr (kHub) {
-        const int nh = a.n_hubs < kHubs ? a.n_hubs : kHubs;
-        for (int j = (int)threadIdx.x; j < nh; j += kThreads) {
-            const int32_t v = a.hub_ids[j];
-            if constexpr (APP == GG_APP_PAGERANK) s_hub[j] = __float_as_uint(__ldg(a.contrib_cur + v));
-            else s_hub[j] = __ldg(a.val_cur + v);
-        }
-        __syncthreads();
-    }
+    static_assert(APP == GG_APP_PAGERANK, "the share influence is PageRank's");
+    using T = float;
+    using A = Acc<GG_APP_PAGERANK>;
+    __shared__ ShareSmem smem[kWarps];
+    ShareSmem &s = smem[threadIdx.x >> 5];
 
     const uint32_t lane = lane_id();
     const int gw = (int)((blockIdx.x * kThreads + threadIdx.x) >> 5);
@@ -266,17 +250,14 @@ k_tile(TileArgs a)
     const uint32_t nnz = *a.list_nnz;
     const int num_tiles = (int)*a.num_tiles;
     const long long total = (long long)a.n + nnz;
-    const bool load_w = kWeighted && a.arc_w != nullptr;
-
     ApplyStats st;
 
-    // ---- software pipeline: headers two tiles ahead, sources one ahead ------
+    // ---- software pipeline: headers two tiles ahead, values one ahead -------
     uint32_t hdr_cur = 0, hdr_nxt = 0;
     if (lane < 2 && gw < num_tiles) hdr_cur = (uint32_t)a.tile_info[gw + (int)lane];
     if (lane < 2 && gw + W < num_tiles) hdr_nxt = (uint32_t)a.tile_info[gw + W + (int)lane];
-    int32_t src_cur[kIPT];
-    uint32_t w_cur[kWeighted ? kIPT : 1];
-    auto load_arcs = [&](int tt, uint32_t hdr, int32_t *srcv, uint32_t *wv) {
+    uint32_t v_cur[kIPT];
+    auto load_vals = [&](int tt, uint32_t hdr, uint32_t *vv) {
         const uint32_t h0 = __shfl_sync(0xFFFFFFFFu, hdr, 0), h1 = __shfl_sync(0xFFFFFFFFu, hdr, 1);
         const long long e0 = (long long)tt * kWT;
         const long long e1 = e0 + kWT < total ? e0 + kWT : total;
@@ -286,13 +267,10 @@ k_tile(TileArgs a)
 #pragma unroll
         for (int i = 0; i < kIPT; ++i) {
             const int k = (int)lane + 32 * i;
-            const bool ok = live && k < b1 - b0;
-            if constexpr (kStashed) srcv[i] = ok ? (int32_t)__ldcs(&a.stash[b0 + k].y) : 0;
-            else srcv[i] = ok ? __ldg(a.arc_src + b0 + k) : 0;
-            if constexpr (kWeighted) wv[i] = (ok && load_w) ? __ldg(a.arc_w + b0 + k) : 1u;
+            vv[i] = (live && k < b1 - b0) ? __ldcs(&a.stash[b0 + k].y) : 0u;
         }
     };
-    load_arcs(gw, hdr_cur, src_cur, w_cur);
+    load_vals(gw, hdr_cur, v_cur);
 
     for (int t = gw; t < num_tiles; t += W) {
         const uint32_t i0 = __shfl_sync(0xFFFFFFFFu, hdr_cur, 0);
@@ -306,67 +284,29 @@ k_tile(TileArgs a)
         const int w0 = a0 >> 5;
         const int nwords = narcs > 0 ? ((a1 - 1) >> 5) - w0 + 1 : 0;
 
-        // ---- issue this tile's value gathers and row loads ------------------
-        uint32_t gv[kIPT];
-#pragma unroll
-        for (int i = 0; i < kIPT; ++i) {
-            const int k = (int)lane + 32 * i;
-            const int32_t sv = src_cur[i];   // a hub is coded -(slot + 1)
-            if constexpr (kStashed) {
-                gv[i] = (uint32_t)sv;
-            } else if constexpr (APP == GG_APP_PAGERANK) {
-                gv[i] = k < narcs ? (sv < 0 ? s_hub[-sv - 1] : __float_as_uint(__ldg(a.contrib_cur + sv))) : 0u;
-            } else {
-                gv[i] = k < narcs ? (sv < 0 ? s_hub[-sv - 1] : __ldg(a.val_cur + sv)) : kInf;
-            }
-        }
         uint2 prev_part = make_uint2(1u, A::bits(A::id()));
-        if constexpr (kStashed) {
-            if (need_carry && lane == 0) prev_part = a.part[t - 1];
-        }
+        if (need_carry && lane == 0) prev_part = a.part[t - 1];
         for (int i = (int)lane; i < nrows; i += 32) {
             s.rowend[i] = a.row_ptr[r0 + i + 1];
-            if constexpr (kApply) {
-                const int32_t v = a.row_vtx ? a.row_vtx[r0 + i] : r0 + i;
-                if constexpr (APP == GG_APP_PAGERANK) {
-                    s.vtx[i] = __float_as_uint(a.rank_cur[v]);
-                    s.deg[i] = a.deg_apply ? a.deg_apply[v] : a.out_ptr[v + 1] - a.out_ptr[v];
-                } else {
-                    s.vtx[i] = a.val_cur[v];
-                }
-            }
+            const int32_t v = a.row_vtx ? a.row_vtx[r0 + i] : r0 + i;
+            s.vtx[i] = __float_as_uint(a.rank_cur[v]);
+            s.deg[i] = a.deg_apply ? a.deg_apply[v] : a.out_ptr[v + 1] - a.out_ptr[v];
         }
         if (lane == 0) s.rowend[nrows] = 0x7FFFFFFF;   // row r1 stays open past the tile
-        if constexpr (KIND == K_CORRECT && kMin) {
-            for (int i = (int)lane; i < nwords; i += 32) s.oldw[i] = a.mask[w0 + i];
-        }
-        if constexpr (kPack) {
-            for (int i = (int)lane; i < nwords; i += 32) s.bits[i] = 0u;
-        }
-        // ---- prefetch: next tile's sources, header two tiles ahead ---------
-        int32_t src_nxt[kIPT];
-        uint32_t w_nxt[kWeighted ? kIPT : 1];
-        load_arcs(t + W, hdr_nxt, src_nxt, w_nxt);
+        for (int i = (int)lane; i < nwords; i += 32) s.bits[i] = 0u;
+        // ---- prefetch: next tile's values, header two tiles ahead ----------
+        uint32_t v_nxt[kIPT];
+        load_vals(t + W, hdr_nxt, v_nxt);
         uint32_t hdr_far = 0;
         if (lane < 2 && t + 2 * W < num_tiles) hdr_far = (uint32_t)a.tile_info[t + 2 * W + (int)lane];
-
-        // ---- stage values (candidates for the min applications) ------------
 #pragma unroll
         for (int i = 0; i < kIPT; ++i) {
             const int k = (int)lane + 32 * i;
-            if (k < narcs) {
-                uint32_t v = gv[i];
-                if constexpr ((KIND == K_GATHER || KIND == K_STASH) && kMin && APP != GG_APP_CC) {
-                    const uint32_t step = (APP == GG_APP_BFS) ? 1u : w_cur[kWeighted ? i : 0];
-                    const unsigned long long c = (unsigned long long)v + step;
-                    v = (v == kInf || c >= kInf) ? kInf : (uint32_t)c;
-                }
-                s.val[pad(k)] = v;
-            }
+            if (k < narcs) s.val[pad(k)] = v_cur[i];
         }
         __syncwarp();
 
-        // ---- this lane's items into registers ------------------------------
+        // ---- this lane's items into registers (merge-path search) ----------
         const int tile_items = (int)(d1 - d0);
         const int ld = (int)lane * kIPT < tile_items ? (int)lane * kIPT : tile_items;
         int cnt = tile_items - ld;
@@ -403,223 +343,124 @@ k_tile(TileArgs a)
         }
         const uint32_t endmask = ((1u << cnt) - 1u) & ~arcmask;
 
-        // ---- fold + warp segmented scan --------------------------------------
-        T carry_in = A::id();
-        bool defer_first = false;   // gather: the tile's first row end waits for k_fixup
+        // ---- fold + warp segmented scan; carry of the continued row ---------
+        T carry_in;
         {
-            T v = A::id(), head = A::id();
+            T v = A::id();
             uint32_t f = 0;
 #pragma unroll
             for (int i = 0; i < kIPT; ++i) {
                 if ((arcmask >> i) & 1u) {
                     v = A::op(v, A::from_bits(item_v[i]));
                 } else if ((endmask >> i) & 1u) {
-                    if (!f) head = v;
                     f = 1u;
                     v = A::id();
                 }
             }
-            if (!f) head = v;
-            const uint32_t lane_f = f;
-            warp_seg_scan_incl<APP>(v, f);
+            warp_seg_scan_incl<GG_APP_PAGERANK>(v, f);
             T ex_v = __shfl_up_sync(0xFFFFFFFFu, v, 1);
             uint32_t ex_f = __shfl_up_sync(0xFFFFFFFFu, f, 1);
-            if (lane == 0) { ex_v = A::id(); ex_f = 0u; }
-            const T tail = __shfl_sync(0xFFFFFFFFu, v, 31);
-            const uint32_t tf = __shfl_sync(0xFFFFFFFFu, f, 31);
-            if constexpr (KIND == K_GATHER || KIND == K_STASH) {
-                // partials for k_fixup / K_CORRECT: (has a row end, part after
-                // the last end) and the part before the first end
-                const unsigned first_end = __ballot_sync(0xFFFFFFFFu, lane_f != 0u);
-                const int lstar = first_end ? __ffs(first_end) - 1 : 31;
-                const T head_t = __shfl_sync(0xFFFFFFFFu, A::op(ex_v, head), lstar);
-                if (lane == 0) {
-                    a.part[t] = make_uint2(tf, A::bits(tail));
-                    a.part_head[t] = A::bits(first_end ? head_t : tail);
-                }
-                carry_in = ex_v;                    // rows open at the tile start: see k_fixup
-                defer_first = need_carry && !ex_f;
-            } else {
-                T c = A::id();
-                if (need_carry) {
-                    prev_part.x = __shfl_sync(0xFFFFFFFFu, prev_part.x, 0);
-                    prev_part.y = __shfl_sync(0xFFFFFFFFu, prev_part.y, 0);
-                    c = carry_from_parts<APP>(a.part, t, prev_part);
-                }
-                carry_in = ex_f ? ex_v : A::op(c, ex_v);
-                (void)tail;
-                (void)tf;
+            if (lane == 0) {
+                ex_v = A::id();
+                ex_f = 0u;
             }
+            T c = A::id();
+            if (need_carry) {
+                prev_part.x = __shfl_sync(0xFFFFFFFFu, prev_part.x, 0);
+                prev_part.y = __shfl_sync(0xFFFFFFFFu, prev_part.y, 0);
+                c = carry_from_parts<GG_APP_PAGERANK>(a.part, t, prev_part);
+            }
+            carry_in = ex_f ? ex_v : A::op(c, ex_v);
         }
 
-        // ---- pass 2: flags per arc, apply per row end ------------------------
-        uint32_t my_active = 0, my_flags = 0;
-        int32_t q_u[kMin ? kIPT : 1];
-        uint32_t q_v[kMin ? kIPT : 1];
-        int q_n = 0;
-        T my_end_run = A::id();   // running value after this lane's items
-        if constexpr (KIND == K_STASH) {
-            // the running value before every arc (within the tile), staged in
-            // arc order, then stored with the arc's value (coalesced)
+        // ---- row totals and the apply of every row ending in the tile --------
+        T end_run;
+        {
             T acc = carry_in;
-            int y = ly;
+            int x = lx;
 #pragma unroll
             for (int i = 0; i < kIPT; ++i) {
                 if ((arcmask >> i) & 1u) {
-                    s.bef[pad(y)] = A::bits(acc);
                     acc = A::op(acc, A::from_bits(item_v[i]));
-                    ++y;
                 } else if ((endmask >> i) & 1u) {
-                    acc = A::id();
-                }
-            }
-            __syncwarp();
-#pragma unroll
-            for (int i = 0; i < kIPT; ++i) {
-                const int k = (int)lane + 32 * i;
-                if (k < narcs) __stcs(a.stash + a0 + k, make_uint2(s.bef[pad(k)], s.val[pad(k)]));
-            }
-        }
-        if constexpr (KIND != K_STASH) {
-            T acc = carry_in;
-            int x = lx, y = ly;
-#pragma unroll
-            for (int i = 0; i < kIPT; ++i) {
-                if ((arcmask >> i) & 1u) {
-                    {
-                        const T v = A::from_bits(item_v[i]);
-                        if constexpr (KIND == K_CORRECT) {
-                            uint32_t fl;
-                            if constexpr (APP == GG_APP_PAGERANK) {
-                                // GG-Gather's returned influence (Alg. 2): (new - old) / new
-                                // > theta, tested without the division as (new - old) >
-                                // theta * new (new >= 0); with the share variant, decided
-                                // after the row totals
-                                const float after = __fadd_rn(acc, v);
-                                const bool hit = after != 0.0f ? __fsub_rn(after, acc) > __fmul_rn(a.theta, after)
-                                                               : 0.0f > a.theta;
-                                fl = (!a.infl_share && hit) ? 1u : 0u;
-                            } else {
-                                if (v == kInf) {   // no candidate: the arc keeps its flag
-                                    const int k = a0 + y;
-                                    fl = a.est_strict ? 0u : (s.oldw[(k >> 5) - w0] >> (k & 31)) & 1u;
-                                } else if (a.theta_case == 1) {
-                                    fl = 1u;
-                                } else if (a.theta_case == 2) {
-                                    fl = 0u;
-                                } else if (v < acc) {
-                                    if (acc == kInf || APP == GG_APP_CC) fl = 1u;
-                                    else fl = ((unsigned long long)(acc - v) << 32) > a.theta_fx * (unsigned long long)acc ? 1u : 0u;
-                                } else {
-                                    fl = 0u;
-                                }
-                            }
-                            my_flags |= fl << i;
-                            my_active += fl;
-                        }
-                        acc = A::op(acc, v);
-                    }
-                    ++y;
-                } else if ((endmask >> i) & 1u) {
-                    if constexpr (KIND == K_CORRECT && APP == GG_APP_PAGERANK) s.rowtot[x] = acc;
-                    if constexpr (kApply) {
-                        if (defer_first) {
-                            defer_first = false;   // completed by k_fixup
-                        } else {
-                            const int32_t u = a.row_vtx ? a.row_vtx[r0 + x] : r0 + x;
-                            if constexpr (APP == GG_APP_PAGERANK) {
-                                apply_pr(a, u, acc, __uint_as_float(s.vtx[x]), s.deg[x], st);
-                            } else {
-                                bool ch;
-                                const uint32_t nw = apply_min(a, u, acc, s.vtx[x], st, &ch);
-                                if (ch) {
-                                    q_u[q_n] = u;
-                                    q_v[q_n] = nw;
-                                    ++q_n;
-                                }
-                            }
-                        }
-                    }
+                    s.rowtot[x] = acc;
+                    const int32_t u = a.row_vtx ? a.row_vtx[r0 + x] : r0 + x;
+                    apply_pr(a, u, acc, __uint_as_float(s.vtx[x]), s.deg[x], st);
                     acc = A::id();
                     ++x;
                 }
             }
-            my_end_run = acc;
+            end_run = acc;
         }
-        (void)my_end_run;
-        if constexpr (KIND == K_CORRECT && APP == GG_APP_PAGERANK) {
-            if (a.infl_share) {
-                // influence = the arc's share of its row total; the row still
-                // open at the tile end adds the later tiles' parts
-                const int last = (tile_items - 1) / kIPT;
-                const float end_run = __shfl_sync(0xFFFFFFFFu, my_end_run, last);
-                const float later = lookahead_parts<APP>(a.part, a.part_head, t, num_tiles);
-                if (lane == 0) s.rowtot[nrows] = __fadd_rn(end_run, later);
-                __syncwarp();
-                int x = lx;
+        // the row still open at the tile end: the later tiles' parts
+        {
+            const int last = (tile_items - 1) / kIPT;
+            const float tail_run = __shfl_sync(0xFFFFFFFFu, end_run, last);
+            const float later = lookahead_parts<GG_APP_PAGERANK>(a.part, a.part_head, t, num_tiles);
+            if (lane == 0) s.rowtot[nrows] = __fadd_rn(tail_run, later);
+        }
+        __syncwarp();
+        // ---- flags: share c / total > theta, tested as c > theta * total -----
+        uint32_t my_active = 0, my_flags = 0;
+        {
+            int x = lx;
 #pragma unroll
-                for (int i = 0; i < kIPT; ++i) {
-                    if ((arcmask >> i) & 1u) {
-                        const float tot = s.rowtot[x];   // share c / tot > theta as c > theta * tot
-                        const bool hit = tot != 0.0f ? __uint_as_float(item_v[i]) > __fmul_rn(a.theta, tot)
-                                                     : 0.0f > a.theta;
-                        const uint32_t fl = hit ? 1u : 0u;
-                        my_flags |= fl << i;
-                        my_active += fl;
-                    } else if ((endmask >> i) & 1u) {
-                        ++x;
-                    }
+            for (int i = 0; i < kIPT; ++i) {
+                if ((arcmask >> i) & 1u) {
+                    const float tot = s.rowtot[x];
+                    const bool hit = tot != 0.0f ? __uint_as_float(item_v[i]) > __fmul_rn(a.theta, tot)
+                                                 : 0.0f > a.theta;
+                    const uint32_t fl = hit ? 1u : 0u;
+                    my_flags |= fl << i;
+                    my_active += fl;
+                } else if ((endmask >> i) & 1u) {
+                    ++x;
                 }
             }
-        }
-        if constexpr (kMin && kApply) {
-            if (a.q_out) frontier_append(a, q_u, q_v, q_n);
         }
 
         // ---- new flags into the bitmap; tile count and tile-local row ends --
-        if constexpr (kPack) {
+        {
             const uint32_t incl = warp_incl_sum_u32(my_active);
             if (lane == 31 && a.tile_cnt) a.tile_cnt[t] = incl;
             uint32_t off = incl - my_active;   // active arcs of the tile before this lane's items
-            {
-                // this lane's arcs are the consecutive list positions a0+ly ..,
-                // so its flags form one run of at most kIPT bits: at most two
-                // shared-memory ORs per lane
-                uint32_t run = 0;
-                int na = 0, x = lx;
+            // this lane's arcs are the consecutive list positions a0+ly ..,
+            // so its flags form one run of at most kIPT bits: at most two
+            // shared-memory ORs per lane
+            uint32_t run = 0;
+            int na = 0, x = lx;
 #pragma unroll
-                for (int i = 0; i < kIPT; ++i) {
-                    if ((arcmask >> i) & 1u) {
-                        if ((my_flags >> i) & 1u) {
-                            run |= 1u << na;
-                            ++off;
-                        }
-                        ++na;
-                    } else if ((endmask >> i) & 1u) {
-                        if (a.sp_ptr) a.sp_ptr[r0 + x + 1] = (int32_t)off;   // tile-local; k_pack adds the tile offset
-                        ++x;
+            for (int i = 0; i < kIPT; ++i) {
+                if ((arcmask >> i) & 1u) {
+                    if ((my_flags >> i) & 1u) {
+                        run |= 1u << na;
+                        ++off;
                     }
-                }
-                if (run) {
-                    const int k0 = a0 + ly;
-                    const int sh = k0 & 31, wi = (k0 >> 5) - w0;
-                    atomicOr(&s.bits[wi], run << sh);
-                    if (sh + na > 32) atomicOr(&s.bits[wi + 1], run >> (32 - sh));
+                    ++na;
+                } else if ((endmask >> i) & 1u) {
+                    if (a.sp_ptr) a.sp_ptr[r0 + x + 1] = (int32_t)off;   // tile-local; k_pack adds the tile offset
+                    ++x;
                 }
             }
-            __syncwarp();
-            for (int i = (int)lane; i < nwords; i += 32) {
-                const int w = w0 + i;
-                const int lo = a0 > w * 32 ? a0 : w * 32;
-                const int hi = a1 < w * 32 + 32 ? a1 : w * 32 + 32;
-                const uint32_t bits = s.bits[i];
-                if (hi - lo == 32) {
-                    a.mask[w] = bits;
-                } else {
-                    const uint32_t range = ((1u << (hi - lo)) - 1u) << (lo & 31);
-                    atomicAnd(&a.mask[w], ~range);
-                    atomicOr(&a.mask[w], bits);
-                }
+            if (run) {
+                const int k0 = a0 + ly;
+                const int sh = k0 & 31, wi = (k0 >> 5) - w0;
+                atomicOr(&s.bits[wi], run << sh);
+                if (sh + na > 32) atomicOr(&s.bits[wi + 1], run >> (32 - sh));
+            }
+        }
+        __syncwarp();
+        for (int i = (int)lane; i < nwords; i += 32) {
+            const int w = w0 + i;
+            const int lo = a0 > w * 32 ? a0 : w * 32;
+            const int hi = a1 < w * 32 + 32 ? a1 : w * 32 + 32;
+            const uint32_t bits = s.bits[i];
+            if (hi - lo == 32) {
+                a.mask[w] = bits;
+            } else {
+                const uint32_t range = ((1u << (hi - lo)) - 1u) << (lo & 31);
+                atomicAnd(&a.mask[w], ~range);
+                atomicOr(&a.mask[w], bits);
             }
         }
         __syncwarp();
@@ -628,12 +469,9 @@ k_tile(TileArgs a)
         hdr_cur = hdr_nxt;
         hdr_nxt = hdr_far;
 #pragma unroll
-        for (int i = 0; i < kIPT; ++i) {
-            src_cur[i] = src_nxt[i];
-            if constexpr (kWeighted) w_cur[i] = w_nxt[i];
-        }
+        for (int i = 0; i < kIPT; ++i) v_cur[i] = v_nxt[i];
     }
-    if constexpr (kApply) flush_stats(a, st);
+    flush_stats(a, st);
 }
 
 // ----------------------------------------------------------------- fixup ----

@@ -1,57 +1,50 @@
-// gg_tile_launch.cuh - cooperative persistent launch of one tile-kernel
-// instantiation (included by the instantiation units).
+// gg_tile_launch.cuh - persistent launches of the tile kernels (included by
+// the instantiation units).
 #pragma once
 
+#include "gg_gather.cuh"
 #include "gg_tile.cuh"
 
 namespace gg {
 
-// Co-resident blocks of k_tile<APP, KIND> on this device (cached).
-template <int APP, int KIND>
-static int resident_blocks(int num_sms)
+// Persistent grid of `kernel`: as many blocks as fit at once (each warp then
+// walks its tiles t, t + W, ...), never more than there are tiles for. The
+// occupancy query runs once per kernel (`blocks` is the caller's cache).
+static cudaError_t launch_persistent(void (*kernel)(TileArgs), int &blocks, const TileArgs &a, int max_tiles,
+                                     int num_sms, cudaStream_t s)
 {
-    static int blocks = 0;
     if (blocks == 0) {
         int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_tile<APP, KIND>, kThreads, 0) != cudaSuccess || b < 1)
-            b = 1;
-        blocks = b;
-    }
-    return blocks * num_sms;
-}
-
-// Persistent grid: as many blocks as fit at once (each warp then walks its
-// tiles t, t + W, ...), never more than there are tiles for.
-template <int APP, int KIND>
-static cudaError_t launch_tiles(const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s)
-{
-    int g = resident_blocks<APP, KIND>(num_sms);
-    const int need = (max_tiles + kWarps - 1) / kWarps;
-    g = g < need ? g : (need > 0 ? need : 1);
-    k_tile<APP, KIND><<<g, kThreads, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-// A correction iteration: K_STASH, then k_correct2 (running-prefix
-// influence) or K_CORRECT (the share influence, which needs whole rows).
-template <int APP>
-static cudaError_t launch_correction(const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s)
-{
-    cudaError_t e = launch_tiles<APP, K_STASH>(a, max_tiles, num_sms, s);
-    if (e != cudaSuccess) return e;
-    if (a.infl_share) return launch_tiles<APP, K_CORRECT>(a, max_tiles, num_sms, s);
-    static int blocks = 0;
-    if (blocks == 0) {
-        int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_correct2<APP>, kThreads, 0) != cudaSuccess || b < 1)
-            b = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kThreads, 0) != cudaSuccess || b < 1) b = 1;
         blocks = b;
     }
     int g = blocks * num_sms;
     const int need = (max_tiles + kWarps - 1) / kWarps;
     g = g < need ? g : (need > 0 ? need : 1);
-    k_correct2<APP><<<g, kThreads, 0, s>>>(a);
+    kernel<<<g, kThreads, 0, s>>>(a);
     return cudaGetLastError();
+}
+
+// The pull gather of an approximate or accurate iteration.
+template <int APP>
+static cudaError_t launch_gather(const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s)
+{
+    static int blocks = 0;
+    return launch_persistent(k_arcs<APP, K_GATHER>, blocks, a, max_tiles, num_sms, s);
+}
+
+// A correction iteration: the stashing gather, then k_correct2 (running-prefix
+// influence) or, for PageRank with the share influence, k_share.
+template <int APP>
+static cudaError_t launch_correction(const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s)
+{
+    static int b_stash = 0, b_correct = 0, b_share = 0;
+    cudaError_t e = launch_persistent(k_arcs<APP, K_STASH>, b_stash, a, max_tiles, num_sms, s);
+    if (e != cudaSuccess) return e;
+    if constexpr (APP == GG_APP_PAGERANK) {
+        if (a.infl_share) return launch_persistent(k_share<APP>, b_share, a, max_tiles, num_sms, s);
+    }
+    return launch_persistent(k_correct2<APP>, b_correct, a, max_tiles, num_sms, s);
 }
 
 template <int APP>

@@ -7,11 +7,11 @@ namespace gg {
 cudaError_t launch_tile_min(int app, int kind, const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s)
 {
     switch (app * 2 + (kind == K_CORRECT ? 1 : 0)) {
-    case GG_APP_SSSP * 2: return launch_tiles<GG_APP_SSSP, K_GATHER>(a, max_tiles, num_sms, s);
+    case GG_APP_SSSP * 2: return launch_gather<GG_APP_SSSP>(a, max_tiles, num_sms, s);
     case GG_APP_SSSP * 2 + 1: return launch_correction<GG_APP_SSSP>(a, max_tiles, num_sms, s);
-    case GG_APP_BFS * 2: return launch_tiles<GG_APP_BFS, K_GATHER>(a, max_tiles, num_sms, s);
+    case GG_APP_BFS * 2: return launch_gather<GG_APP_BFS>(a, max_tiles, num_sms, s);
     case GG_APP_BFS * 2 + 1: return launch_correction<GG_APP_BFS>(a, max_tiles, num_sms, s);
-    case GG_APP_CC * 2: return launch_tiles<GG_APP_CC, K_GATHER>(a, max_tiles, num_sms, s);
+    case GG_APP_CC * 2: return launch_gather<GG_APP_CC>(a, max_tiles, num_sms, s);
     case GG_APP_CC * 2 + 1: return launch_correction<GG_APP_CC>(a, max_tiles, num_sms, s);
     default: return cudaErrorInvalidValue;
     }

@@ -6,7 +6,7 @@ namespace gg {
 
 cudaError_t launch_tile_pr(int kind, const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s)
 {
-    if (kind == K_GATHER) return launch_tiles<GG_APP_PAGERANK, K_GATHER>(a, max_tiles, num_sms, s);
+    if (kind == K_GATHER) return launch_gather<GG_APP_PAGERANK>(a, max_tiles, num_sms, s);
     return launch_correction<GG_APP_PAGERANK>(a, max_tiles, num_sms, s);
 }
 

@@ -30,7 +30,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
-KERNEL_FILES = ("gg_tile.cuh", "gg_tile_launch.cuh", "gg_tile_pr.cu", "gg_tile_min.cu")
+KERNEL_FILES = ("gg_gather.cuh", "gg_tile.cuh", "gg_tile_launch.cuh", "gg_tile_pr.cu", "gg_tile_min.cu")
 
 
 def kernel_hash() -> str:
