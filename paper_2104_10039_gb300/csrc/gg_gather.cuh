@@ -34,8 +34,8 @@ struct ArcSmem {
     static constexpr bool kApply = KIND == K_GATHER;
     int32_t end[kWT];                // tile-local arc position where each row of the tile ends
     uint32_t val[kPadded];           // arc values in arc order; gather: segment totals at segment ends
-    uint32_t vtx[kApply ? kWT : 1];  // rows' current value
-    int32_t deg[kApply && APP == GG_APP_PAGERANK ? kWT : 1];   // rows' out-degree (PageRank)
+    uint32_t vtx[kApply ? kWT : 1];  // rows' current value; min applications: then the frontier values
+    int32_t aux[kApply ? kWT : 1];   // PageRank: rows' out-degree; min applications: frontier vertices
     uint32_t bef[KIND == K_STASH ? kPadded : 1];   // stash: running value before each arc
     uint32_t head[kWT / 32 + 2];     // bit p: a row ends at arc position p (p = 0 .. kWT)
 };
@@ -120,18 +120,30 @@ k_arcs(TileArgs a)
         if (lane < kWT / 32 + 2) s.head[lane] = 0u;
         __syncwarp();
         // ---- rows ending in the tile: end positions, heads (vertex data) ------
-        for (int x = (int)lane; x < nrows; x += 32) {
-            const int32_t e = a.row_ptr[r0 + x + 1] - a0;   // 0 <= e <= narcs
-            s.end[x] = e;
-            atomicOr(&s.head[e >> 5], 1u << (e & 31));
-            if constexpr (kApply) {
-                const int32_t v = a.row_vtx ? a.row_vtx[r0 + x] : r0 + x;
-                if constexpr (APP == GG_APP_PAGERANK) {
-                    s.vtx[x] = __float_as_uint(a.rank_cur[v]);
-                    s.deg[x] = a.deg_apply ? a.deg_apply[v] : a.out_ptr[v + 1] - a.out_ptr[v];
-                } else {
-                    s.vtx[x] = a.val_cur[v];
+        for (int rb = 0; rb < nrows; rb += 32) {
+            const int x = rb + (int)lane;
+            int32_t e = 0;
+            if (x < nrows) {
+                e = a.row_ptr[r0 + x + 1] - a0;   // 0 <= e <= narcs
+                s.end[x] = e;
+                if constexpr (kApply) {
+                    const int32_t v = a.row_vtx ? a.row_vtx[r0 + x] : r0 + x;
+                    if constexpr (APP == GG_APP_PAGERANK) {
+                        s.vtx[x] = __float_as_uint(a.rank_cur[v]);
+                        s.aux[x] = a.deg_apply ? a.deg_apply[v] : a.out_ptr[v + 1] - a.out_ptr[v];
+                    } else {
+                        s.vtx[x] = a.val_cur[v];
+                    }
                 }
+            }
+            // head bits: the batch's ends do not decrease with x, so its words
+            // run from the first lane's end to the last valid lane's; each word
+            // is the OR over the lanes (no shared-memory atomics)
+            const int last = nrows - 1 - rb < 31 ? nrows - 1 - rb : 31;
+            const int wl = __shfl_sync(0xFFFFFFFFu, e, 0) >> 5, wh = __shfl_sync(0xFFFFFFFFu, e, last) >> 5;
+            for (int w = wl; w <= wh; ++w) {
+                const uint32_t word = __reduce_or_sync(0xFFFFFFFFu, (x < nrows && (e >> 5) == w) ? 1u << (e & 31) : 0u);
+                if (lane == 0) s.head[w] |= word;
             }
         }
         // ---- prefetch: next tile's sources, header two tiles ahead ----------
@@ -235,30 +247,46 @@ k_arcs(TileArgs a)
             }
         } else {
             // ---- apply every row ending in the tile (GG-Apply, GG-VStatus) ---
+            // min applications: the changed vertices are collected in shared
+            // memory (entry q of the tile overwrites aux / vtx slot q <= its
+            // row, read before) and appended to the frontier once per tile
+            uint32_t q_n = 0;
             for (int rb = 0; rb < nrows; rb += 32) {
                 const int x = rb + (int)lane;
-                int32_t qu[1];
-                uint32_t qv[1];
-                int qn = 0;
+                bool ch = false;
+                int32_t u = 0;
+                uint32_t nw = 0;
                 if (x < nrows && !(x == 0 && need_carry)) {   // row r0 continued: k_fixup
                     const int32_t e = s.end[x];
                     const int32_t eb = x > 0 ? s.end[x - 1] : 0;
                     const T acc = e > eb ? A::from_bits(s.val[pad(e - 1)]) : A::id();
-                    const int32_t u = a.row_vtx ? a.row_vtx[r0 + x] : r0 + x;
+                    u = a.row_vtx ? a.row_vtx[r0 + x] : r0 + x;
                     if constexpr (APP == GG_APP_PAGERANK) {
-                        apply_pr(a, u, acc, __uint_as_float(s.vtx[x]), s.deg[x], st);
+                        apply_pr(a, u, acc, __uint_as_float(s.vtx[x]), s.aux[x], st);
                     } else {
-                        bool ch;
-                        const uint32_t nw = apply_min(a, u, acc, s.vtx[x], st, &ch);
-                        if (ch) {
-                            qu[0] = u;
-                            qv[0] = nw;
-                            qn = 1;
-                        }
+                        nw = apply_min(a, u, acc, s.vtx[x], st, &ch);
                     }
                 }
                 if constexpr (kMin) {
-                    if (a.q_out) frontier_append(a, qu, qv, qn);
+                    const unsigned b = __ballot_sync(0xFFFFFFFFu, ch);
+                    if (ch) {
+                        const uint32_t q = q_n + __popc(b & ((1u << lane) - 1u));
+                        s.aux[q] = u;
+                        s.vtx[q] = nw;
+                    }
+                    q_n += __popc(b);
+                }
+            }
+            if constexpr (kMin) {
+                if (a.q_out && q_n) {
+                    __syncwarp();
+                    uint32_t base = 0;
+                    if (lane == 0) base = atomicAdd(a.q_out_len, q_n);
+                    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+                    for (uint32_t i = lane; i < q_n; i += 32) {
+                        a.q_out[base + i] = s.aux[i];
+                        a.q_out_val[base + i] = s.vtx[i];
+                    }
                 }
             }
         }

@@ -532,13 +532,16 @@ k_fixup(TileArgs a)
 
 // ------------------------------------------------------ correction, pass 2 --
 // The correction's second launch when the influence is the running-prefix
-// form: K_STASH left, for every arc, the running value before it within its
-// tile and its value, so no merge path or scan is needed here. Per warp tile:
-// the carry of the row continued from earlier tiles (the finished partials),
-// each arc's influence test (Alg. 2 GG-EStatus) from (carry +) its running
-// values, the new flag words, every row ending in the tile applied (GG-Apply,
-// GG-VStatus), and the tile's active count and tile-local row ends for the
-// pack.
+// form: k_arcs<., K_STASH> left, for every arc, the running value before it
+// within its tile and its value, so no merge path or scan is needed here. Per
+// warp tile: the carry of the row continued from earlier tiles (the finished
+// partials), each arc's influence test (Alg. 2 GG-EStatus) from (carry +) its
+// running values, the new flag words, every row ending in the tile applied
+// (GG-Apply, GG-VStatus), and the tile's active count and tile-local row ends
+// for the pack. The stash pairs, the ends of the tile's first 32 rows and the
+// old flag words are loaded one tile ahead; the pairs are also staged in
+// shared memory, where a row finds its total (the pair at its last arc); the
+// first 32 rows' vertex data are requested before the flag work.
 template <int APP>
 __global__ void __launch_bounds__(kThreads, 4)
 k_correct2(TileArgs a)
@@ -550,8 +553,10 @@ k_correct2(TileArgs a)
     __shared__ uint32_t s_bits[kWarps][kW];
     __shared__ uint32_t s_cnt[kWarps][kW];
     __shared__ uint32_t s_old[kWarps][kMin ? kW : 1];
+    __shared__ uint2 s_pair[kWarps][kWT];
     const int wi = (int)(threadIdx.x >> 5);
     uint32_t *bits = s_bits[wi], *cnt = s_cnt[wi], *oldw = s_old[wi];
+    uint2 *pair = s_pair[wi];
     const uint32_t lane = lane_id();
     const int gw = (int)((blockIdx.x * kThreads + threadIdx.x) >> 5);
     const int W = (int)((gridDim.x * kThreads) >> 5);
@@ -559,25 +564,34 @@ k_correct2(TileArgs a)
     const int num_tiles = (int)*a.num_tiles;
     const long long total = (long long)a.n + nnz;
     ApplyStats st;
-    // software pipeline: headers two tiles ahead, the stash pairs one ahead
-    auto load_pairs = [&](int tt, uint32_t hdr, uint2 *pv) {
+    // software pipeline: headers two tiles ahead; the stash pairs, the ends of
+    // the first 32 rows and (min applications) the old flag words one ahead
+    auto load_tile = [&](int tt, uint32_t hdr, uint2 *pv, int32_t &re, uint32_t &ow) {
         const uint32_t h0 = __shfl_sync(0xFFFFFFFFu, hdr, 0), h1 = __shfl_sync(0xFFFFFFFFu, hdr, 1);
+        const int32_t q0 = (int32_t)(h0 & 0x7FFFFFFFu), q1 = (int32_t)(h1 & 0x7FFFFFFFu);
         const long long e0 = (long long)tt * kWT;
         const long long e1 = e0 + kWT < total ? e0 + kWT : total;
-        const int32_t b0 = (int32_t)(e0 - (int32_t)(h0 & 0x7FFFFFFFu));
-        const int32_t b1 = (int32_t)(e1 - (int32_t)(h1 & 0x7FFFFFFFu));
+        const int32_t b0 = (int32_t)(e0 - q0);
+        const int32_t b1 = (int32_t)(e1 - q1);
         const bool live = tt < num_tiles;
 #pragma unroll
         for (int j = 0; j < kIPT; ++j) {
             const int k = (int)lane + 32 * j;
             pv[j] = (live && k < b1 - b0) ? __ldcs(a.stash + b0 + k) : make_uint2(0u, 0u);
         }
+        re = (live && (int)lane < q1 - q0) ? a.row_ptr[q0 + (int)lane + 1] : 0;
+        if constexpr (kMin) {
+            const int nw = (live && b1 > b0) ? ((b1 - 1) >> 5) - (b0 >> 5) + 1 : 0;
+            ow = (int)lane < nw ? a.mask[(b0 >> 5) + (int)lane] : 0u;
+        }
     };
     uint32_t hdr_cur = 0, hdr_nxt = 0;
     if (lane < 2 && gw < num_tiles) hdr_cur = (uint32_t)a.tile_info[gw + (int)lane];
     if (lane < 2 && gw + W < num_tiles) hdr_nxt = (uint32_t)a.tile_info[gw + W + (int)lane];
     uint2 pv_cur[kIPT];
-    load_pairs(gw, hdr_cur, pv_cur);
+    int32_t re_cur = 0;
+    uint32_t ow_cur = 0;
+    load_tile(gw, hdr_cur, pv_cur, re_cur, ow_cur);
     for (int t = gw; t < num_tiles; t += W) {
         const uint32_t i0 = __shfl_sync(0xFFFFFFFFu, hdr_cur, 0), i1 = __shfl_sync(0xFFFFFFFFu, hdr_cur, 1);
         const int32_t r0 = (int32_t)(i0 & 0x7FFFFFFFu), r1 = (int32_t)(i1 & 0x7FFFFFFFu);
@@ -588,6 +602,19 @@ k_correct2(TileArgs a)
         const int nrows = r1 - r0, narcs = a1 - a0;
         const int w0 = a0 >> 5;
         const int nwords = narcs > 0 ? ((a1 - 1) >> 5) - w0 + 1 : 0;
+        // vertex data of the tile's first 32 rows, requested before the flag work
+        int32_t u_first = 0;
+        uint32_t old_first = 0;
+        int32_t deg_first = 0;
+        if ((int)lane < nrows) {
+            u_first = a.row_vtx ? a.row_vtx[r0 + (int)lane] : r0 + (int)lane;
+            if constexpr (APP == GG_APP_PAGERANK) {
+                old_first = __float_as_uint(a.rank_cur[u_first]);
+                deg_first = a.deg_apply ? a.deg_apply[u_first] : a.out_ptr[u_first + 1] - a.out_ptr[u_first];
+            } else {
+                old_first = a.val_cur[u_first];
+            }
+        }
         // the row continued from earlier tiles: its carry and its arcs here
         T c = A::id();
         int32_t first_end = a0;
@@ -597,15 +624,18 @@ k_correct2(TileArgs a)
             prev.x = __shfl_sync(0xFFFFFFFFu, prev.x, 0);
             prev.y = __shfl_sync(0xFFFFFFFFu, prev.y, 0);
             c = carry_from_parts<APP>(a.part, t, prev);
-            const int32_t e = a.row_ptr[r0 + 1];
-            first_end = e < a1 ? e : a1;
+            // row r0's end, or past the tile when the tile holds no row end
+            const int32_t e = __shfl_sync(0xFFFFFFFFu, re_cur, 0);
+            first_end = (nrows > 0 && e < a1) ? e : a1;
         }
-        for (int i = (int)lane; i < nwords; i += 32) {
-            bits[i] = 0u;
-            if constexpr (kMin) oldw[i] = a.mask[w0 + i];
+        if ((int)lane < nwords) {   // nwords <= kWT / 32 + 1
+            bits[lane] = 0u;
+            if constexpr (kMin) oldw[lane] = ow_cur;
         }
         uint2 pv_nxt[kIPT];
-        load_pairs(t + W, hdr_nxt, pv_nxt);
+        int32_t re_nxt;
+        uint32_t ow_nxt = 0;
+        load_tile(t + W, hdr_nxt, pv_nxt, re_nxt, ow_nxt);
         uint32_t hdr_far = 0;
         if (lane < 2 && t + 2 * W < num_tiles) hdr_far = (uint32_t)a.tile_info[t + 2 * W + (int)lane];
         __syncwarp();
@@ -618,6 +648,7 @@ k_correct2(TileArgs a)
             uint32_t fl = 0;
             if (k < narcs) {
                 const uint2 sv = pv_cur[j];
+                pair[k] = sv;
                 T before = A::from_bits(sv.x);
                 const T v = A::from_bits(sv.y);
                 if (p < first_end) before = A::op(c, before);
@@ -659,22 +690,27 @@ k_correct2(TileArgs a)
         if (lane == 0 && a.tile_cnt) a.tile_cnt[t] = active;
         __syncwarp();
         // ---- rows ending in this tile: apply, tile-local row ends -----------
+        int32_t prev_e = a0;   // where the batch's first row starts (row r0: the tile start)
         for (int rb = 0; rb < nrows; rb += 32) {
             const int ri = rb + (int)lane;
+            int32_t e = 0;
+            if (ri < nrows) e = rb == 0 ? re_cur : a.row_ptr[r0 + ri + 1];   // the row's arcs end before e
+            int32_t start = __shfl_up_sync(0xFFFFFFFFu, e, 1);
+            if (lane == 0) start = prev_e;
+            prev_e = __shfl_sync(0xFFFFFFFFu, e, 31);
             int32_t qu[1];
             uint32_t qv[1];
             int qn = 0;
             if (ri < nrows) {
                 const int32_t r = r0 + ri;
-                const int32_t e = a.row_ptr[r + 1];   // the row's arcs end before list position e
-                // the row's total: the running value after its last arc when that
-                // arc lies in this tile (plus the carry for the continued row),
-                // else the carry (continued row ending at the tile start) or
-                // nothing (a row without arcs)
+                // the row's total: the running value after its last arc when
+                // that arc lies in this tile (plus the carry for the continued
+                // row), else the carry (continued row ending at the tile start)
+                // or nothing (a row without arcs)
                 const bool continued = ri == 0 && need_carry;
                 T tot = continued ? c : A::id();
-                if (e > (continued ? a0 : a.row_ptr[r])) {
-                    const uint2 sv = __ldg(a.stash + (e - 1));
+                if (e > start) {
+                    const uint2 sv = pair[e - 1 - a0];
                     tot = A::op(A::from_bits(sv.x), A::from_bits(sv.y));
                     if (continued) tot = A::op(c, tot);
                 }
@@ -687,13 +723,23 @@ k_correct2(TileArgs a)
                     }
                     a.sp_ptr[r + 1] = (int32_t)before;
                 }
-                const int32_t u = a.row_vtx ? a.row_vtx[r] : r;
+                int32_t u = u_first;
+                uint32_t old = old_first;
+                int32_t deg = deg_first;
+                if (rb > 0) {
+                    u = a.row_vtx ? a.row_vtx[r] : r;
+                    if constexpr (APP == GG_APP_PAGERANK) {
+                        old = __float_as_uint(a.rank_cur[u]);
+                        deg = a.deg_apply ? a.deg_apply[u] : a.out_ptr[u + 1] - a.out_ptr[u];
+                    } else {
+                        old = a.val_cur[u];
+                    }
+                }
                 if constexpr (APP == GG_APP_PAGERANK) {
-                    apply_pr(a, u, tot, a.rank_cur[u],
-                             a.deg_apply ? a.deg_apply[u] : a.out_ptr[u + 1] - a.out_ptr[u], st);
+                    apply_pr(a, u, tot, __uint_as_float(old), deg, st);
                 } else {
                     bool ch;
-                    const uint32_t nw = apply_min(a, u, tot, a.val_cur[u], st, &ch);
+                    const uint32_t nw = apply_min(a, u, tot, old, st, &ch);
                     if (ch) {
                         qu[0] = u;
                         qv[0] = nw;
@@ -721,6 +767,8 @@ k_correct2(TileArgs a)
         __syncwarp();
         hdr_cur = hdr_nxt;
         hdr_nxt = hdr_far;
+        re_cur = re_nxt;
+        ow_cur = ow_nxt;
 #pragma unroll
         for (int j = 0; j < kIPT; ++j) pv_cur[j] = pv_nxt[j];
     }
