@@ -22,8 +22,9 @@
  *    CC are uint32 with GG_INF = 0xFFFFFFFF meaning "unreached".
  *  - The library owns all device memory it allocates; it is released by
  *    gg_free_graph.
- *  - A device-side wait that runs out of its iteration limit makes the call
- *    return GG_ERR_TIMEOUT instead of hanging.
+ *  - No kernel of the library waits on another block or another launch, so
+ *    no call can hang on the device; GG_ERR_TIMEOUT stays reserved in the
+ *    status enum and is not returned.
  */
 #ifndef GG_H
 #define GG_H
@@ -42,7 +43,7 @@ typedef enum {
     GG_ERR_OOM = 3,           /* a device allocation failed */
     GG_ERR_CUDA = 4,          /* a CUDA call failed; the CUDA error string is in gg_last_error() */
     GG_ERR_STATE = 5,         /* call not valid in the graph's current state */
-    GG_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
+    GG_ERR_TIMEOUT = 6,       /* reserved (no device-side waits) */
     GG_ERR_UNSUPPORTED = 7    /* combination not implemented */
 } gg_status;
 

@@ -253,14 +253,6 @@ static gg_status refresh_active_outdeg(gg_graph *g)
         if (s_ != GG_OK) return s_;                               \
     } while (0)
 
-// Read a device scalar (synchronises the stream).
-static gg_status read_u32(gg_graph *g, const uint32_t *d, uint32_t *h)
-{
-    GG_CUDA(cudaMemcpyAsync(h, d, sizeof(uint32_t), cudaMemcpyDeviceToHost, g->stream));
-    GG_CUDA(cudaStreamSynchronize(g->stream));
-    return GG_OK;
-}
-
 // ---------------------------------------------- learned correction, traces --
 static gg_status ensure_hist(gg_graph *g)
 {
@@ -724,13 +716,6 @@ static gg_status run_min(gg_graph *g, gg_app app, gg_policy policy, const gg_par
             continue;
         }
     }
-    uint32_t err = 0;
-    st = read_u32(g, g->dev_err, &err);
-    if (st != GG_OK) return st;
-    if (err & DEVERR_TIMEOUT) {
-        set_error("a bounded device-side wait gave up");
-        return GG_ERR_TIMEOUT;
-    }
     return GG_OK;
 }
 
@@ -1078,14 +1063,6 @@ gg_status gg_result(gg_graph *g, gg_result_kind kind, void *dst, size_t bytes, i
 {
     if (!g || !dst) { set_error("gg_result: graph or dst is NULL"); return GG_ERR_INVALID_ARG; }
     GG_CUDA(cudaStreamSynchronize(g->stream));
-    if (kind != GG_RESULT_STATS) {
-        uint32_t err = 0;
-        GG_CUDA(cudaMemcpy(&err, g->dev_err, sizeof err, cudaMemcpyDeviceToHost));
-        if (err & DEVERR_TIMEOUT) {
-            set_error("gg_result: a bounded device-side wait of the last run gave up");
-            return GG_ERR_TIMEOUT;
-        }
-    }
     if ((int)kind < GG_RESULT_VALUES || (int)kind > GG_RESULT_SCORES) {
         set_error("gg_result: unknown kind %d", (int)kind);
         return GG_ERR_INVALID_ARG;

@@ -24,22 +24,14 @@ constexpr uint32_t kInf = 0xFFFFFFFFu;
 // list codes such a source as -(slot + 1).
 constexpr int kHubs = 3072;   // 12 KB: 4 blocks of the gather still fit an SM
 
-// Bounded device waits: a wait gives up after this many polls (each an L2
-// round trip plus a short sleep, about a second in total), flags
-// DEVERR_TIMEOUT and returns; once the flag is up, later waits give up at
-// their next check instead of spending their own second.
-constexpr int kSpinLimit = 1 << 21;
-constexpr int kSpinCheck = 1 << 10;
-
+// Device error flags (the graph's error word; k_validate sets them).
 enum DevErr : uint32_t {
-    DEVERR_TIMEOUT = 1u,
     DEVERR_BAD_GRAPH = 2u,
-    DEVERR_QUEUE = 4u,
 };
 
 // Per-launch dynamic tile scheduler. Tiles are handed out in increasing order
-// by an atomic counter, so every tile a tile waits on has already started.
-// The last block to leave resets both counters for the next launch.
+// by an atomic counter; the last block to leave resets both counters for the
+// next launch.
 struct TileSched {
     uint32_t next_tile;
     uint32_t done_blocks;
@@ -161,45 +153,6 @@ struct PushArgs {
 
 // ------------------------------------------------------- device helpers ----
 #ifdef __CUDACC__
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
-{
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v)
-{
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-// Status word of a tile: [epoch:31 | flag:1 | value:32]. A word is ready for a
-// launch when its epoch field equals the launch's epoch, so the arrays never
-// need clearing between launches.
-__device__ __forceinline__ unsigned long long pack_status(uint32_t epoch, uint32_t flag, uint32_t value)
-{
-    return ((unsigned long long)epoch << 33) | ((unsigned long long)(flag & 1u) << 32) | value;
-}
-__device__ __forceinline__ uint32_t status_epoch(unsigned long long w) { return (uint32_t)(w >> 33); }
-__device__ __forceinline__ uint32_t status_flag(unsigned long long w) { return (uint32_t)(w >> 32) & 1u; }
-__device__ __forceinline__ uint32_t status_value(unsigned long long w) { return (uint32_t)w; }
-
-// Poll a status word until it carries `epoch`; on running out of polls, flag
-// a timeout and return `fallback`.
-__device__ __forceinline__ unsigned long long wait_status(const unsigned long long *p, uint32_t epoch,
-                                                         uint32_t *err, unsigned long long fallback)
-{
-    for (int it = 0; it < kSpinLimit; ++it) {
-        unsigned long long w = ld_acquire_u64(p);
-        if (status_epoch(w) == epoch) return w;
-        if ((it & (kSpinCheck - 1)) == kSpinCheck - 1 &&
-            (*(volatile uint32_t *)err & DEVERR_TIMEOUT)) return fallback;
-        __nanosleep(64);
-    }
-    atomicOr(err, DEVERR_TIMEOUT);
-    return fallback;
-}
-
 // Fetch the next tile of a launch (block-uniform); returns -1 when exhausted.
 __device__ __forceinline__ int next_tile(TileSched *s, uint32_t num_tiles, int *s_slot)
 {
