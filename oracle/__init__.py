@@ -18,8 +18,10 @@ paper it restates:
                        edge influence, GG-Apply, GG-VStatus, GG-EStatus) under
                        the accurate / approximate modes of Sec. 3.3.
 
-Parity of approximate-mode PageRank beyond mask replay is unpinned: the paper
-prints no worked numeric example (its influence figures are missing).
+The paper prints no worked numeric example of approximate-mode PageRank
+after a correction (its influence figures are missing); that part is pinned
+against a replica in exact rational arithmetic on tiny graphs (the tests'
+brute-force module), and the GPU's FP32 flags are judged by mask replay.
 """
 from __future__ import annotations
 

@@ -116,3 +116,57 @@ def ppr_dense(g, damping, iters, source):
     for _ in range(iters):
         x = (1.0 - d) * e + d * (P.T @ x)
     return x
+
+
+def graphguess_pagerank_rational(g, damping, iters, initial_flags, alpha, theta, policy="gg"):
+    """GraphGuess PageRank (Alg. 2, Sec. 3.4) on a tiny graph in exact rational
+    arithmetic, written as a different program from the oracle: in-edges
+    listed by sorting the arcs on (destination, source) with Python's stable
+    sort, ranks as fractions, each iteration a fresh pass over that list.
+
+    * Iteration i of policy "gg" is a correction when i mod (alpha+1) = alpha,
+      otherwise approximate; policy "sms" is approximate before alpha, a
+      correction at alpha and accurate (every arc, flags kept) after it.
+    * Approximate: u gathers rank(v)/outdeg(v) over its flagged in-arcs only
+      (the full out-degree: the graph itself is unchanged); accurate and
+      correction iterations gather over every in-arc.
+    * A correction gives in-arc e of u the influence (acc_after - acc_before)
+      / acc_after of the running sum over u's in-arcs in source order (0 when
+      the sum is 0), and e stays active iff that influence exceeds theta.
+    * rank'(u) = (1 - d)/N + d * sum (synchronous), rank_0 = 1/N.
+
+    initial_flags: dict (src, dst, CSR index) -> 0/1 from the sampler.
+    Returns (ranks float64[n], flags uint8 in (dst, src)-sorted order,
+    smallest |influence - theta| met at a correction)."""
+    from fractions import Fraction
+    n = g.n
+    arcs = arcs_of(g)
+    outdeg = [0] * n
+    for s, _, _ in arcs:
+        outdeg[s] += 1
+    order = sorted(range(len(arcs)), key=lambda e: (arcs[e][1], arcs[e][0]))
+    flag = {e: initial_flags[e] for e in range(len(arcs))}
+    d = Fraction(float(np.float32(damping)))
+    th = Fraction(float(np.float32(theta)))
+    rank = [Fraction(1, n)] * n
+    margin = None
+    for i in range(iters):
+        if policy == "gg":
+            mode = "correct" if i % (alpha + 1) == alpha else "approx"
+        else:
+            mode = "approx" if i < alpha else ("correct" if i == alpha else "accurate")
+        acc = [Fraction(0)] * n
+        for e in order:
+            s, t, _ = arcs[e]
+            if mode == "approx" and not flag[e]:
+                continue
+            before = acc[t]
+            acc[t] = before + rank[s] / outdeg[s]
+            if mode == "correct":
+                infl = (acc[t] - before) / acc[t] if acc[t] != 0 else Fraction(0)
+                gap = abs(infl - th)
+                margin = gap if margin is None or gap < margin else margin
+                flag[e] = 1 if infl > th else 0
+        rank = [(1 - d) / n + d * acc[u] for u in range(n)]
+    return (np.array([float(r) for r in rank]), np.array([flag[e] for e in order], np.uint8),
+            None if margin is None else float(margin))

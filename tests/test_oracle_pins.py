@@ -492,3 +492,32 @@ def test_ppr_averaged_over_sources_is_pagerank():
         mean /= g.n
         pr = oracle.run(g.n, g.rowptr, g.colidx, app="pagerank", max_iters=T)["values"]
         assert np.abs(mean - pr).sum() <= 1e-13
+
+
+# ------------------------------------- GraphGuess PageRank, exact rationals --
+
+@pytest.mark.parametrize("policy", ["gg", "sms"])
+def test_graphguess_pagerank_matches_rational_replica(policy):
+    # Approximate iterations after a correction depend on the flags the
+    # correction chose; a replica in exact rational arithmetic (a different
+    # program: sorted arc list, fractions, dense passes) pins the oracle's
+    # values and flags through several corrections.
+    rng = np.random.default_rng(5)
+    checked = 0
+    for trial in range(12):
+        n = int(rng.integers(3, 9))
+        m = int(rng.integers(n, 3 * n))
+        arcs = [(int(rng.integers(0, n)), int(rng.integers(0, n))) for _ in range(m)]
+        g = graphgen.from_arcs(n, arcs)
+        sigma, seed = (0.4, 0.7)[trial % 2], 30 + trial
+        init = {e: int(oracle.arc_sampled(s, d, sigma, seed)) for e, (s, d, _) in enumerate(brute.arcs_of(g))}
+        for alpha, theta, iters in ((1, 0.3071, 7), (2, 0.1193, 9), (0, 0.5517, 4)):
+            want, want_flags, margin = brute.graphguess_pagerank_rational(g, 0.85, iters, init, alpha, theta, policy)
+            if margin is not None and margin < 1e-9:
+                continue   # an influence within rounding of theta: FP64 may decide it either way
+            r = oracle.run(g.n, g.rowptr, g.colidx, policy=policy, sigma=sigma, seed=seed, alpha=alpha,
+                           theta=theta, max_iters=iters)
+            assert np.abs(r["values"] - want).sum() <= 1e-13 * np.abs(want).sum(), (trial, alpha)
+            assert np.array_equal(np.asarray(r["mask"], np.uint8), want_flags), (trial, alpha)
+            checked += 1
+    assert checked >= 30
