@@ -170,3 +170,77 @@ def graphguess_pagerank_rational(g, damping, iters, initial_flags, alpha, theta,
         rank = [(1 - d) / n + d * acc[u] for u in range(n)]
     return (np.array([float(r) for r in rank]), np.array([flag[e] for e in order], np.uint8),
             None if margin is None else float(margin))
+
+
+def graphguess_min_replica(g, app, source, iters, initial_flags, alpha, theta, policy="gg", strict=False):
+    """GraphGuess for the min applications (SSSP, BFS, CC) on a tiny graph,
+    written as a different program from the oracle: in-edges from a stable
+    sort of the arcs on (destination, source), values in Python integers
+    (unbounded, so saturation is an explicit comparison), influence as an
+    exact fraction.
+
+    * Initial values: SSSP / BFS: 0 at the source, unreached elsewhere; CC: the
+      vertex id. Unreached = 2^32 - 1, and a candidate that would reach it is
+      no candidate.
+    * Candidates of arc v->u: val(v) + w (SSSP), val(v) + 1 (BFS), val(v) (CC);
+      none when v is unreached.
+    * Modes as in the PageRank replica ("gg": correction when i mod (alpha+1)
+      = alpha; "sms": approximate before alpha, correction at alpha, accurate
+      after; "sp": always approximate).
+    * A correction gives every arc with a candidate the influence of the
+      running minimum over u's in-arcs in source order: 1 for the first
+      candidate, (acc - cand) / acc when the candidate lowers the minimum
+      (CC: 1), 0 otherwise; the arc stays active iff influence > theta. Arcs
+      without a candidate keep their flag (strict: they are cleared).
+    * new(u) = min(old(u), acc); the run stops after a correction or accurate
+      iteration that changed nothing (SP: after any quiet iteration).
+
+    Returns (values uint32[n], flags uint8 in (dst, src)-sorted order)."""
+    from fractions import Fraction
+    inf = INF
+    n = g.n
+    arcs = arcs_of(g)
+    order = sorted(range(len(arcs)), key=lambda e: (arcs[e][1], arcs[e][0]))
+    flag = {e: initial_flags[e] for e in range(len(arcs))}
+    th = Fraction(float(np.float32(theta)))
+    if app == "cc":
+        val = list(range(n))
+    else:
+        val = [inf] * n
+        val[source] = 0
+    for i in range(iters):
+        if policy == "gg":
+            mode = "correct" if i % (alpha + 1) == alpha else "approx"
+        elif policy == "sms":
+            mode = "approx" if i < alpha else ("correct" if i == alpha else "accurate")
+        else:
+            mode = "approx"
+        acc = [inf] * n
+        for e in order:
+            s, t, w = arcs[e]
+            if mode == "approx" and not flag[e]:
+                continue
+            if val[s] == inf:
+                cand = None
+            else:
+                cand = val[s] + (w if app == "sssp" else 1 if app == "bfs" else 0)
+                if cand >= inf:
+                    cand = None
+            if cand is None:
+                if mode == "correct" and strict:
+                    flag[e] = 0
+                continue
+            if mode == "correct":
+                if cand < acc[t]:
+                    infl = Fraction(1) if (acc[t] == inf or app == "cc") else Fraction(acc[t] - cand, acc[t])
+                else:
+                    infl = Fraction(0)
+                flag[e] = 1 if infl > th else 0
+            if cand < acc[t]:
+                acc[t] = cand
+        new = [min(val[u], acc[u]) for u in range(n)]
+        changed = new != val
+        val = new
+        if not changed and (mode != "approx" or policy == "sp"):
+            break
+    return np.array(val, np.uint32), np.array([flag[e] for e in order], np.uint8)

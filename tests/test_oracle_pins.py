@@ -521,3 +521,38 @@ def test_graphguess_pagerank_matches_rational_replica(policy):
             assert np.array_equal(np.asarray(r["mask"], np.uint8), want_flags), (trial, alpha)
             checked += 1
     assert checked >= 30
+
+
+@pytest.mark.parametrize("app", ["sssp", "bfs", "cc"])
+def test_graphguess_min_apps_match_replica(app):
+    # Values and flags of the min applications through corrections under the
+    # GG, SMS and SP schedules, against a replica with unbounded integers and
+    # exact-fraction influence.
+    rng = np.random.default_rng(11)
+    checked = 0
+    for trial in range(16):
+        n = int(rng.integers(3, 12))
+        m = int(rng.integers(n, 4 * n))
+        arcs = [(int(rng.integers(0, n)), int(rng.integers(0, n))) for _ in range(m)]
+        g = graphgen.from_arcs(n, arcs, symmetric=(app == "cc"))
+        w = rng.integers(1, 256, g.m).astype(np.uint32)
+        if app == "cc":
+            w = np.ones(g.m, np.uint32)
+        g.weights = w
+        sigma, seed = (0.3, 0.6, 0.9)[trial % 3], 70 + trial
+        src = int(rng.integers(0, n))
+        init = {e: int(oracle.arc_sampled(s, d, sigma, seed, symmetric=g.symmetric))
+                for e, (s, d, _) in enumerate(brute.arcs_of(g))}
+        for policy, alpha, theta, strict in (("gg", 1, 0.05, False), ("gg", 2, 0.2, False), ("gg", 0, 0.5, True),
+                                             ("sms", 2, 0.125, False), ("sp", 0, 0.05, False)):
+            # to the fixed point, and cut after 2 and 4 iterations (the states
+            # on the way depend on the schedule; the fixed point does not)
+            for iters in (200, 2, 4):
+                want, want_flags = brute.graphguess_min_replica(g, app, src, iters, init, alpha, theta, policy, strict)
+                r = oracle.run(g.n, g.rowptr, g.colidx, g.weights, app=app, policy=policy, sigma=sigma, seed=seed,
+                               alpha=alpha, theta=theta, max_iters=iters, source=src, symmetric=g.symmetric,
+                               flags=oracle.EST_STRICT if strict else 0)
+                assert np.array_equal(r["values"], want), (trial, policy, alpha, iters)
+                assert np.array_equal(np.asarray(r["mask"], np.uint8), want_flags), (trial, policy, alpha, iters)
+                checked += 1
+    assert checked == 240
