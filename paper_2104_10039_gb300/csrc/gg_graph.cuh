@@ -120,7 +120,7 @@ struct gg_graph {
     uint32_t *q_deg = nullptr;
     uint32_t *stamp = nullptr;
     uint32_t stamp_tag = 0;
-    // scheduling and look-back
+    // push-frontier tile scheduler; per-tile status words (unused)
     gg::DevBuf b_sched, b_status;
     gg::TileSched *sched = nullptr;
     unsigned long long *st_carry = nullptr;

@@ -94,7 +94,7 @@ struct TileArgs {
     uint2 *stash;
     // active arcs per tile (correction)
     uint32_t *tile_cnt;
-    // look-back
+    // set by the host, not read by the current kernels
     unsigned long long *st_carry;
     uint32_t epoch;
     uint32_t *err;

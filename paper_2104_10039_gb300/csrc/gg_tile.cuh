@@ -143,7 +143,8 @@ __device__ __forceinline__ typename Acc<APP>::T lookahead_parts(const uint2 *par
 
 // ------------------------------------------------------------- row apply ----
 // GG-Apply + GG-VStatus of Alg. 2 for PageRank; min for the min applications
-// (a vertex is active when its value decreased). Shared by k_tile and k_fixup.
+// (a vertex is active when its value decreased). Shared by the gather, k_fixup,
+// k_correct2 and k_share.
 struct ApplyStats {
     unsigned long long changed = 0, sum = 0;
     uint32_t max = 0;
@@ -478,7 +479,7 @@ k_share(TileArgs a)
 // Rows of a gather that began in an earlier tile and end in tile t: their
 // value is the partials of the tiles from the one where the row began up to
 // t-1, then tile t's part before its first row end, added in tile order.
-// One thread per tile (warp-uniform loop); runs after k_tile<., K_GATHER>.
+// One thread per tile (warp-uniform loop); runs after k_arcs<., K_GATHER>.
 template <int APP>
 __global__ void __launch_bounds__(kThreads)
 k_fixup(TileArgs a)

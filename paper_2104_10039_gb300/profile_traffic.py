@@ -33,18 +33,27 @@ TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 KERNEL_FILES = ("gg_gather.cuh", "gg_tile.cuh", "gg_tile_launch.cuh", "gg_tile_pr.cu", "gg_tile_min.cu")
 
 
+def _code(text: str) -> str:
+    """Source text without comments and with whitespace runs collapsed, so
+    that the hash follows the code and not its commentary."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_hash() -> str:
     """Hash of the tile engine's device code: its own files plus the
-    constants and the argument struct it is compiled with."""
+    constants and the argument struct it is compiled with (comments and
+    layout ignored)."""
     h = hashlib.sha256()
     for f in KERNEL_FILES:
-        with open(os.path.join(CSRC, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(CSRC, f)) as fh:
+            h.update(_code(fh.read()).encode())
     with open(os.path.join(CSRC, "gg_internal.cuh")) as fh:
         text = fh.read()
     for pat in (r"constexpr int kThreads.*?constexpr uint32_t kInf[^\n]*", r"struct TileArgs \{.*?\n\};"):
         m = re.search(pat, text, re.S)
-        h.update((m.group(0) if m else "").encode())
+        h.update(_code(m.group(0) if m else "").encode())
     return h.hexdigest()[:16]
 
 
