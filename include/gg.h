@@ -140,7 +140,7 @@ typedef struct {
     uint64_t arcs_processed;  /* sum over iterations of the iteration's edge-set size */
     uint64_t active_arcs;     /* arcs active at the end of the run */
     uint64_t changed_last;    /* vertices active after the last iteration */
-    uint32_t device_error;    /* nonzero if a bounded wait gave up (then the run failed) */
+    uint32_t device_error;    /* error flags of the device-side CSR validation (2: bad graph), else 0 */
     uint32_t kernels_load;    /* kernels this library launched during gg_load_csr */
     float ms_load;            /* device time of the last gg_load_csr (copy + validate + CSC build) */
     float ms_sample;          /* device time of the last sampling */
