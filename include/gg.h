@@ -240,30 +240,6 @@ void gg_free_graph(gg_graph *g);
 const char *gg_last_error(void);
 
 /*
- * gg_sample_csc_noalloc - the sampling step of gg_sample_edges applied to a
- * caller-owned in-edge list, without allocating any device memory. The paper
- * has no counterpart: this entry point exists for callers that cannot
- * allocate device memory when they need the step (code inside a CUDA graph
- * being captured, allocator callbacks, processes whose device memory budget
- * is fixed in advance).
- *   n, m       vertices and arcs, n >= 1, n + m <= GG_NOALLOC_MAX_ITEMS
- *   in_ptr     device int32[n+1], in_src device int32[m]: in-edge rows, each
- *              listing its sources (the order defines the packed order)
- *   sample_ratio, seed, symmetric: as in gg_sample_edges / GG_SYMMETRIC
- *   mask       device uint32[ceil(m/32)] out: flag bits of the m arcs (bits
- *              past m in the last word are left as they were)
- *   sp_ptr     device int32[n+1] out, sp_src device int32[m] out (the first
- *              *sp_nnz entries used), sp_nnz device uint32[1] out: the
- *              packed active in-edges
- *   stream     cudaStream_t to run on (NULL = legacy default stream)
- * Working memory is one fixed device array inside libgg.so (about 0.8 MB
- * per GPU that loads the library, kept until the process exits). Every call
- * on a device shares it, so calls that overlap on the GPU race. The first
- * call on a device looks up the array's address (cudaGetSymbolAddress);
- * make that first call before any stream capture. Sizes above the limit
- * return GG_ERR_INVALID_ARG. Returns after enqueueing the work.
- */
-/*
  * Learned correction (beyond the paper). The scorer is a per-vertex MLP
  * 8 -> 64 -> 64 -> 1 with ReLU after both hidden layers; its parameters are
  * GG_MLP_NPARAM floats, row-major: W1[64][8], b1[64], W2[64][64], b2[64],
@@ -373,6 +349,30 @@ gg_status gg_batch_query_stats(gg_batch *b, gg_query_stats *out, int32_t n);
 gg_status gg_batch_result(gg_batch *b, int32_t q, void *dst, size_t bytes);
 void gg_batch_free(gg_batch *b);
 
+/*
+ * gg_sample_csc_noalloc - the sampling step of gg_sample_edges applied to a
+ * caller-owned in-edge list, without allocating any device memory. The paper
+ * has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory when they need the step: code that runs inside an
+ * allocator's own callbacks, processes whose device memory budget is handed
+ * out in full up front, or loops that must not call into the allocator.
+ *   n, m       vertices and arcs, n >= 1, n + m <= GG_NOALLOC_MAX_ITEMS
+ *   in_ptr     device int32[n+1], in_src device int32[m]: in-edge rows, each
+ *              listing its sources (the order defines the packed order)
+ *   sample_ratio, seed, symmetric: as in gg_sample_edges / GG_SYMMETRIC
+ *   mask       device uint32[ceil(m/32)] out: flag bits of the m arcs (bits
+ *              past m in the last word are left as they were)
+ *   sp_ptr     device int32[n+1] out, sp_src device int32[m] out (the first
+ *              *sp_nnz entries used), sp_nnz device uint32[1] out: the
+ *              packed active in-edges
+ *   stream     cudaStream_t to run on (NULL = legacy default stream)
+ * Working memory is one fixed device array inside libgg.so (about 0.8 MB
+ * per GPU that loads the library, kept until the process exits). Every call
+ * on a device shares it, so calls that overlap on the GPU race. The first
+ * call on a device looks up the array's address (cudaGetSymbolAddress);
+ * make that first call before any stream capture. Sizes above the limit
+ * return GG_ERR_INVALID_ARG. Returns after enqueueing the work.
+ */
 #define GG_NOALLOC_MAX_ITEMS (1u << 24)
 gg_status gg_sample_csc_noalloc(int32_t n, int64_t m, const int32_t *in_ptr, const int32_t *in_src,
                                 double sample_ratio, uint64_t seed, int symmetric, uint32_t *mask,

@@ -2,9 +2,9 @@
 // in-edge list that allocates no device memory.
 //
 // Some callers cannot allocate device memory at the moment they need this
-// step: code running inside a CUDA graph being captured, an allocator
-// callback, or a process whose memory budget is fixed up front and already
-// handed out. They pass their own inputs and outputs; the working memory this
+// step: code running inside an allocator's own callbacks, a process whose
+// device memory budget is fixed up front and already handed out, or a loop
+// that must not call into the allocator. They pass their own inputs and outputs; the working memory this
 // step needs (the tile partition, the per-tile active counts and their scan)
 // lives in one fixed file-scope device array below, sized for
 // n + m <= GG_NOALLOC_MAX_ITEMS. Every GPU that loads the library holds that

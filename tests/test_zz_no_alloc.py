@@ -1,8 +1,9 @@
 """gg_sample_csc_noalloc: the sampling step for callers that cannot allocate
-device memory (code inside a CUDA graph capture, allocator callbacks, fixed
-memory budgets). It must give exactly what gg_sample_edges gives for the same
-in-edge list, call after call, with its working memory in a fixed array
-inside the library. Kept in its own file so that it runs last."""
+device memory (allocator callbacks, memory budgets handed out up front,
+loops that must not call into the allocator). It must give exactly what
+gg_sample_edges gives for the same in-edge list, call after call, with its
+working memory in a fixed array inside the library. Kept in its own file so
+that it runs last."""
 import numpy as np
 import pytest
 
