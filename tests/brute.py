@@ -118,7 +118,8 @@ def ppr_dense(g, damping, iters, source):
     return x
 
 
-def graphguess_pagerank_rational(g, damping, iters, initial_flags, alpha, theta, policy="gg"):
+def graphguess_pagerank_rational(g, damping, iters, initial_flags, alpha, theta, policy="gg",
+                                 renorm=False, share=False):
     """GraphGuess PageRank (Alg. 2, Sec. 3.4) on a tiny graph in exact rational
     arithmetic, written as a different program from the oracle: in-edges
     listed by sorting the arcs on (destination, source) with Python's stable
@@ -134,6 +135,10 @@ def graphguess_pagerank_rational(g, damping, iters, initial_flags, alpha, theta,
       / acc_after of the running sum over u's in-arcs in source order (0 when
       the sum is 0), and e stays active iff that influence exceeds theta.
     * rank'(u) = (1 - d)/N + d * sum (synchronous), rank_0 = 1/N.
+    * renorm: an approximate iteration divides by the source's number of
+      active out-arcs instead (none active: it passes nothing on).
+    * share: a correction keeps arc e of u iff its contribution exceeds theta
+      times the total over all of u's in-arcs (order-free; total 0: 0 > theta).
 
     initial_flags: dict (src, dst, CSR index) -> 0/1 from the sampler.
     Returns (ranks float64[n], flags uint8 in (dst, src)-sorted order,
@@ -155,18 +160,32 @@ def graphguess_pagerank_rational(g, damping, iters, initial_flags, alpha, theta,
             mode = "correct" if i % (alpha + 1) == alpha else "approx"
         else:
             mode = "approx" if i < alpha else ("correct" if i == alpha else "accurate")
+        deg = outdeg
+        if renorm and mode == "approx":
+            deg = [0] * n
+            for e in range(len(arcs)):
+                if flag[e]:
+                    deg[arcs[e][0]] += 1
         acc = [Fraction(0)] * n
+        contrib = {}
         for e in order:
             s, t, _ = arcs[e]
             if mode == "approx" and not flag[e]:
                 continue
+            contrib[e] = rank[s] / deg[s]
             before = acc[t]
-            acc[t] = before + rank[s] / outdeg[s]
-            if mode == "correct":
+            acc[t] = before + contrib[e]
+            if mode == "correct" and not share:
                 infl = (acc[t] - before) / acc[t] if acc[t] != 0 else Fraction(0)
                 gap = abs(infl - th)
                 margin = gap if margin is None or gap < margin else margin
                 flag[e] = 1 if infl > th else 0
+        if mode == "correct" and share:
+            for e in order:
+                t = arcs[e][1]
+                gap = abs(contrib[e] - th * acc[t]) / (acc[t] if acc[t] != 0 else 1)
+                margin = gap if margin is None or gap < margin else margin
+                flag[e] = 1 if (contrib[e] > th * acc[t] if acc[t] != 0 else 0 > th) else 0
         rank = [(1 - d) / n + d * acc[u] for u in range(n)]
     return (np.array([float(r) for r in rank]), np.array([flag[e] for e in order], np.uint8),
             None if margin is None else float(margin))

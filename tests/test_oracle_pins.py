@@ -496,8 +496,9 @@ def test_ppr_averaged_over_sources_is_pagerank():
 
 # ------------------------------------- GraphGuess PageRank, exact rationals --
 
-@pytest.mark.parametrize("policy", ["gg", "sms"])
-def test_graphguess_pagerank_matches_rational_replica(policy):
+@pytest.mark.parametrize("policy,variant", [("gg", 0), ("sms", 0), ("gg", oracle.RENORM),
+                                            ("gg", oracle.INFL_SHARE), ("sms", oracle.RENORM | oracle.INFL_SHARE)])
+def test_graphguess_pagerank_matches_rational_replica(policy, variant):
     # Approximate iterations after a correction depend on the flags the
     # correction chose; a replica in exact rational arithmetic (a different
     # program: sorted arc list, fractions, dense passes) pins the oracle's
@@ -512,11 +513,13 @@ def test_graphguess_pagerank_matches_rational_replica(policy):
         sigma, seed = (0.4, 0.7)[trial % 2], 30 + trial
         init = {e: int(oracle.arc_sampled(s, d, sigma, seed)) for e, (s, d, _) in enumerate(brute.arcs_of(g))}
         for alpha, theta, iters in ((1, 0.3071, 7), (2, 0.1193, 9), (0, 0.5517, 4)):
-            want, want_flags, margin = brute.graphguess_pagerank_rational(g, 0.85, iters, init, alpha, theta, policy)
+            want, want_flags, margin = brute.graphguess_pagerank_rational(
+                g, 0.85, iters, init, alpha, theta, policy,
+                renorm=bool(variant & oracle.RENORM), share=bool(variant & oracle.INFL_SHARE))
             if margin is not None and margin < 1e-9:
                 continue   # an influence within rounding of theta: FP64 may decide it either way
             r = oracle.run(g.n, g.rowptr, g.colidx, policy=policy, sigma=sigma, seed=seed, alpha=alpha,
-                           theta=theta, max_iters=iters)
+                           theta=theta, max_iters=iters, flags=variant)
             assert np.abs(r["values"] - want).sum() <= 1e-13 * np.abs(want).sum(), (trial, alpha)
             assert np.array_equal(np.asarray(r["mask"], np.uint8), want_flags), (trial, alpha)
             checked += 1
