@@ -45,3 +45,21 @@ def test_single_rank_aggregate_is_identity():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.aggregate(3.5, 7, 1) == (3.5, 7)
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` (the CPU oracle on a bounded sample) prints
+    one JSON line with the keys the bench contract names."""
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--scale", "10",
+                          "--steps", "2", "--warmup", "1"], capture_output=True, text=True, timeout=300, check=True)
+    lines = [ln for ln in out.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "GTEPS" and d["value"] > 0
+    assert (d["steps"], d["warmup"], d["n_gpus"]) == (2, 1, 1) and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"].startswith("rmat10")
