@@ -1,8 +1,9 @@
 #!/usr/bin/env python
 """Bench of the GraphGuess hot path on one GB300 (or N replicas).
 
-One step = one pass over every step of the hot path on the R-MAT scale-22
-workload (4 194 304 vertices, 67 108 864 directed arcs, weights in [1, 255]):
+One step = one pass over every step of the hot path on the directed R-MAT
+scale-24 workload (16 777 216 vertices, 268 435 456 arcs, weights in
+[1, 255]):
   load the CSR already resident in HBM and build the in-edge view (gg_load_csr),
   exact PageRank (20 iterations) and exact SSSP (the baselines of Sec. 5),
   then for every sample ratio sigma in {0.1, 0.3, 0.5, 0.7, 0.9}: PageRank
@@ -15,8 +16,12 @@ iteration's edge set) / step time, summed over ranks. e2e = the same with the
 CSR in pinned host memory (host-to-device copies inside the step) and every
 run's vertex values copied back to the host.
 
+The same step on directed R-MAT scale 22 (4 194 304 vertices, 67 108 864
+arcs) is reported under "rmat22"; the parameter sweep, the 16-source SSSP
+table and the learned scorer's training traces use that graph (and scale 12).
+
 --impl reference times the CPU oracle (the reference arm of this repository)
-on a bounded sample of the same workload.
+on a bounded sample of the workload, described in its line.
 """
 from __future__ import annotations
 
@@ -34,7 +39,8 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-SCALE = 22
+SCALE = 24
+SECONDARY_SCALE = 22
 EDGEFACTOR = 16
 GRAPH_SEED, WEIGHT_SEED, SOURCE_SEED, SAMPLE_SEED = 1, 7, 2, 1
 SIGMAS = (0.1, 0.3, 0.5, 0.7, 0.9)
@@ -52,7 +58,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--scale", type=int, default=SCALE, help="R-MAT scale (the workload is 22)")
+    ap.add_argument("--scale", type=int, default=SCALE, help="R-MAT scale (the workload is 24)")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the R-MAT 22 step and its tables")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
@@ -98,7 +105,7 @@ def workload_config(scale, n, m, source, world):
             "pagerank_iters": PR_ITERS, "damping": DAMPING, "sssp_source": source,
             "sssp_iters": "exact run to its fixed point; adaptive runs the same count",
             "runs_per_step": len(run_list(source)), "parallelism": f"replicas x{world}",
-            "l2": "inputs larger than L2 (268 MB of arcs + 268 MB of weights per load)"}
+            "l2": f"inputs larger than L2 ({4 * m / 1e6:.0f} MB of arcs + {4 * m / 1e6:.0f} MB of weights per load)"}
 
 
 def run_list(source):
@@ -212,13 +219,27 @@ def bench_ours(a, rank, world, local):
     import torch
     from paper_2104_10039_gb300 import build
     build.build()
-    from paper_2104_10039_gb300 import gg, metrics
+    from paper_2104_10039_gb300 import gg  # noqa: F401  (fails loudly without libgg.so)
 
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     g, source = workload(a.scale)
+    out, collected = measure(g, source, a.scale, a.steps, a.warmup, rank, world, local, e2e=True, clocks=True)
+    if rank != 0:
+        return None
+    return out, g, source, collected
+
+
+def measure(g, source, scale, steps, warmup, rank, world, local, e2e=True, clocks=True):
+    """Time `steps` executions of the step on graph g (after `warmup`): device
+    time with the CSR resident in HBM, then (e2e) the same with the CSR in
+    pinned host memory and every run's values copied back. Returns the JSON
+    fields of the line and the per-run statistics of the last timed step."""
+    import torch
+    from paper_2104_10039_gb300 import gg
+
     n, m = g.n, g.m
     d_rowptr = torch.from_numpy(g.rowptr).cuda()
     d_colidx = torch.from_numpy(g.colidx).cuda()
@@ -263,46 +284,67 @@ def bench_ours(a, rank, world, local):
             import torch.distributed as dist
             dist.barrier()
 
-    for _ in range(a.warmup):
+    for _ in range(warmup):
         step()
     # ---- timed region: device-resident inputs ------------------------------
-    clk = clocks_sampler() if rank == 0 else None
+    clk = clocks_sampler() if (rank == 0 and clocks) else None
     collected = []
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     arcs_total, launches_total, eq_total = 0, 0, 0
-    for k in range(a.steps):
-        arcs, launches, per = step(collect=collected if k == a.steps - 1 else None)
+    for k in range(steps):
+        arcs, launches, per = step(collect=collected if k == steps - 1 else None)
         arcs_total += arcs
         launches_total += launches
         eq_total += per["exact_equivalent_arcs"]
     ev1.record(stream)
     barrier()
-    clocks = clocks_summary(clk, local) if rank == 0 else None
+    clk_sum = clocks_summary(clk, local) if clk is not None else None
     ms, arcs_all = aggregate(ev0.elapsed_time(ev1), arcs_total, world, "cuda")
     value = arcs_all / (ms * 1e-3) / 1e9
     _, eq_all = aggregate(ev0.elapsed_time(ev1), eq_total, world, "cuda")
 
     # ---- end to end: host buffers, copies inside ---------------------------
-    for _ in range(1):
+    e_value = None
+    if e2e:
         step(e2e=True)
-    barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    e_arcs = 0
-    for _ in range(a.steps):
-        e_arcs += step(e2e=True)[0]
-    e1.record(stream)
-    barrier()
-    e_ms, e_arcs_all = aggregate(e0.elapsed_time(e1), e_arcs, world, "cuda")
-    e_value = e_arcs_all / (e_ms * 1e-3) / 1e9
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e_arcs = 0
+        for _ in range(steps):
+            e_arcs += step(e2e=True)[0]
+        e1.record(stream)
+        barrier()
+        e_ms, e_arcs_all = aggregate(e0.elapsed_time(e1), e_arcs, world, "cuda")
+        e_value = e_arcs_all / (e_ms * 1e-3) / 1e9
+    del d_rowptr, d_colidx, d_w, h_rowptr, h_colidx, h_w, out_host
+    torch.cuda.empty_cache()
 
-    if rank != 0:
-        return None
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "GTEPS", "n_gpus": world,
+        "steps": steps, "warmup": warmup, "ms_per_step": round(ms / steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/u32",
+        "data": "synthetic (seeded R-MAT; the paper's datasets are not available)",
+        "config": workload_config(scale, n, m, source, world),
+        "roofline": roofline(collected, n, m),
+    }
+    if e2e:
+        out["e2e"] = {"value": round(e_value, 3), "unit": "GTEPS",
+                      "h2d_bytes_per_step": int(4 * (n + 1) + 8 * m),
+                      "d2h_bytes_per_step": int(4 * n * len(runs))}
+    out["gpu_launches"] = int(launches_total)
+    out["exact_equivalent_gteps"] = round(eq_all / (ms * 1e-3) / 1e9, 3)
+    if clocks:
+        out["clocks"] = clk_sum
+    return out, collected
 
-    # ---- roofline of the dominant kernel (last timed step) -----------------
-    # per (application, kernel class): device time, launches, algorithmic bytes
+
+def roofline(collected, n, m):
+    """Roofline of the kernel class (application, gather / correction / push)
+    with the most device time in the last timed step: algorithmic bytes per
+    launch / average CUDA-event launch time, against the measured HBM peak."""
     classes = {}
     for app, sigma, policy, st, it in collected:
         for cls, ms_c, n_c in (("gather", st.ms_gather, st.n_gather), ("correct", st.ms_correct, st.n_correct),
@@ -316,45 +358,34 @@ def bench_ours(a, rank, world, local):
                 classes[(app, "gather")][2] += gather_bytes(app, n, int(row["arcs"]))
             elif mode == 2:
                 classes[(app, "correct")][2] += correct_bytes(app, n, m, int(row["active_after"]))
-    dom = max((k for k in classes if classes[k][2] > 0), key=lambda k: classes[k][0])
+    cands = [k for k in classes if classes[k][2] > 0 and classes[k][1]]
+    if not cands:
+        return None
+    dom = max(cands, key=lambda k: classes[k][0])
     peak, peak_kind = peak_hbm()
-    roof = None
-    if classes[dom][1]:
-        avg_s = classes[dom][0] * 1e-3 / classes[dom][1]
-        bytes_per = classes[dom][2] / classes[dom][1]
-        achieved = bytes_per / avg_s / 1e9
-        name = {"gather": "k_arcs<{a}, K_GATHER> + k_fixup<{a}>",
-                "correct": "k_arcs<{a}, K_STASH> + k_correct2<{a}>"}[dom[1]].format(a=dom[0])
-        roof = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
-                "traffic": recorded_traffic(f"{dom[0]}/{dom[1]}", bytes_per),
-                "algorithmic_bytes_per_launch": int(bytes_per),
-                "avg_launch_ms": round(classes[dom][0] / classes[dom][1], 4),
-                "ms_last_step": {f"{k[0]}/{k[1]}": round(v[0], 3) for k, v in classes.items()}}
-
-    out = {
-        "metric": METRIC, "value": round(value, 3), "unit": "GTEPS", "n_gpus": world,
-        "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms / a.steps, 3),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/u32",
-        "data": "synthetic (seeded R-MAT; the paper's datasets are not available)",
-        "config": workload_config(a.scale, n, m, source, world),
-        "roofline": roof,
-        "e2e": {"value": round(e_value, 3), "unit": "GTEPS",
-                "h2d_bytes_per_step": int(4 * (n + 1) + 8 * m),
-                "d2h_bytes_per_step": int(4 * n * len(runs))},
-        "gpu_launches": int(launches_total),
-        "exact_equivalent_gteps": round(eq_all / (ms * 1e-3) / 1e9, 3),
-        "clocks": clocks,
-    }
-    return out, g, source, collected
+    avg_s = classes[dom][0] * 1e-3 / classes[dom][1]
+    bytes_per = classes[dom][2] / classes[dom][1]
+    achieved = bytes_per / avg_s / 1e9
+    name = KERNEL_NAMES[dom[1]].format(a=dom[0])
+    return {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+            "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+            "traffic": recorded_traffic(f"{dom[0]}/{dom[1]}", bytes_per),
+            "algorithmic_bytes_per_launch": int(bytes_per),
+            "avg_launch_ms": round(classes[dom][0] / classes[dom][1], 4),
+            "ms_last_step": {f"{k[0]}/{k[1]}": round(v[0], 3) for k, v in classes.items()}}
 
 
-def accuracy_table(g, source, collected):
+KERNEL_NAMES = {"gather": "k_arcs<{a}, K_GATHER> + k_fixup<{a}>",
+                "correct": "k_arcs<{a}, K_STASH> + k_correct2<{a}>"}
+
+
+def accuracy_table(g, source, collected, full=True):
     """Time to accuracy (Sec. 4.2 metrics, target error <= 1 %): for the exact
     run and for adaptive correction over sigma x theta, the fewest iterations T
     whose result is within 1 % of the reference (the exact run at its full
     iteration count) and the device time of that run; plus the accuracy of
-    every adaptive run of the timed step."""
+    every adaptive run of the timed step. full=False searches the plain
+    adaptive policy only, up to the exact run's iteration count."""
     from paper_2104_10039_gb300 import gg, metrics
     h = gg.gg_load_csr(g.n, g.m, g.rowptr, g.colidx, g.weights, gg.GG_DIRECTED)
     target = 0.01
@@ -401,13 +432,16 @@ def accuracy_table(g, source, collected):
             # (policy, theta, flags, alpha, trigger ratio)
             variants = [("adaptive", 0.05, 0, 4, 0), ("adaptive", 0.005, 0, 4, 0), ("adaptive", 0.05, 0, 2, 0),
                         ("triggered", 0.05, 0, 8, 0.3), ("triggered", 0.005, 0, 8, 0.1)]
-            if app == "pagerank":   # the share influence and renormalisation flags
+            if not full:
+                variants = variants[:1]
+            elif app == "pagerank":   # the share influence and renormalisation flags
                 variants += [("adaptive", 0.05, gg.GG_RENORM, 4, 0), ("adaptive", 0.05, gg.GG_RENORM, 2, 0),
                              ("adaptive", 0.0005, gg.GG_INFL_SHARE | gg.GG_RENORM, 4, 0),
                              ("triggered", 0.0005, gg.GG_INFL_SHARE | gg.GG_RENORM, 8, 0.3)]
             for policy, theta, fl, alpha, ratio in variants:
                 for sigma in (0.5, 0.9):
-                    r = first_within(app, sigma, policy, theta, 2 * full_iters[app], fl, alpha, ratio)
+                    r = first_within(app, sigma, policy, theta, (2 if full else 1) * full_iters[app], fl, alpha,
+                                     ratio)
                     if r and (best is None or r["ms"] < best["ms"]):
                         best = {"policy": policy, "sigma": sigma, "theta": theta, "alpha": alpha,
                                 **({"trigger_ratio": ratio} if policy == "triggered" else {}),
@@ -518,22 +552,24 @@ def scale24_section():
     return out
 
 
-def learned_section(g, source):
+def learned_section(g, source, train_graphs):
     """Learned correction (beyond the paper): the scorer is trained on the
-    traces of plain adaptive runs on R-MAT scale 12 and on this graph, then
-    GG_POLICY_LEARNED is compared with plain adaptive correction on this
-    graph (device time and error at equal iteration counts, time to 1 %)."""
+    traces of plain adaptive runs on R-MAT scale 12 and scale 22 (the
+    workloads' small and mid-size graphs), then GG_POLICY_LEARNED is compared
+    with plain adaptive correction on graph g (device time and error at equal
+    iteration counts, time to 1 %)."""
     import torch
 
     import graphgen
     from paper_2104_10039_gb300 import gg, learned_eval
     g12 = graphgen.add_weights(graphgen.rmat(12, EDGEFACTOR, seed=GRAPH_SEED), seed=WEIGHT_SEED)
     s12 = int(graphgen.sources(g12, 1, seed=SOURCE_SEED)[0])
-    X, Y = learned_eval.collect_traces(gg, torch, [(g12, s12), (g, source)])
+    X, Y = learned_eval.collect_traces(gg, torch, [(g12, s12)] + list(train_graphs))
     P, tr = learned_eval.train(gg, torch, X, Y)
     del X, Y
     torch.cuda.empty_cache()
-    return {"training": tr, "alpha": learned_eval.ALPHA, "theta": learned_eval.THETA,
+    return {"evaluated_on": f"rmat{int(np.log2(g.n))} directed", "trained_on": "rmat12 + rmat22 directed traces",
+            "training": tr, "alpha": learned_eval.ALPHA, "theta": learned_eval.THETA,
             "results": learned_eval.compare(gg, g, source, P, sigmas=(0.5,))}
 
 
@@ -557,9 +593,18 @@ def omp_threads():
 
 
 def bench_reference(a, rank, world):
+    """The reference arm: the CPU oracle as it stands on the host cores. Its
+    in-edge build alone takes about 20 s at scale 24, so each step is a
+    bounded sample: one adaptive-correction PageRank run on directed R-MAT
+    scale SECONDARY_SCALE (the same generator and parameters, a quarter of
+    the workload's vertices and arcs), in-edge build and sampling included."""
     if rank != 0:
         return None
-    g, source = workload(a.scale)
+    g_full_n, g_full_m = 1 << a.scale, EDGEFACTOR << a.scale
+    sample_scale = min(a.scale, SECONDARY_SCALE)
+    g, source = workload(sample_scale)
+    if a.scale != sample_scale:
+        source = workload_source(a.scale)
     for _ in range(a.warmup):
         cpu_sample(g)
     arcs, secs = 0.0, 0.0
@@ -568,19 +613,28 @@ def bench_reference(a, rank, world):
         arcs += x
         secs += dt
     v = arcs / secs / 1e9
-    sample = (f"each step: one adaptive-correction PageRank run of the workload (sigma 0.5, alpha {ALPHA}, "
-              f"theta {THETA}, {PR_ITERS} iterations) on rmat{a.scale}, in-edge build and sampling included; "
-              f"value = its arcs / its time")
+    sample = (f"each step: one adaptive-correction PageRank run (sigma 0.5, alpha {ALPHA}, theta {THETA}, "
+              f"{PR_ITERS} iterations) on directed rmat{sample_scale} (ef {EDGEFACTOR}, same generator), in-edge "
+              f"build and sampling included; value = its arcs / its time")
     return {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GTEPS",
             "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": round(1e3 * secs / a.steps, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded R-MAT)",
-            "config": workload_config(a.scale, g.n, g.m, source, world),
+            "config": workload_config(a.scale, g_full_n, g_full_m, source, world),
+            "reference_step": {"runs_per_step": 1, "app": "pagerank", "policy": "adaptive", "sigma": 0.5,
+                               "iterations": PR_ITERS, "graph": f"rmat{sample_scale}-ef{EDGEFACTOR}-directed",
+                               "vertices": g.n, "arcs": g.m},
             "cpu_baseline": {"value": round(v, 4), "unit": "GTEPS", "cores": omp_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": round(v, 4), "unit": "GTEPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
+
+
+def workload_source(scale):
+    """The workload's SSSP source (the reference line names the same
+    configuration as ours); the graph itself is dropped."""
+    return workload(scale)[1]
 
 
 def main():
@@ -595,27 +649,38 @@ def main():
     if res is None:
         return
     out, g, source, collected = res
+    g2 = s2 = None
+    if not a.no_secondary and a.scale != SECONDARY_SCALE:
+        g2, s2 = workload(SECONDARY_SCALE)
+        sec, coll2 = measure(g2, s2, SECONDARY_SCALE, min(a.steps, 10), 3, rank, 1, local, e2e=False, clocks=False)
+        out["rmat22"] = {k: sec[k] for k in ("value", "unit", "ms_per_step", "steps", "roofline",
+                                             "exact_equivalent_gteps", "config")}
     if not a.no_accuracy:
-        out["time_to_accuracy"] = accuracy_table(g, source, collected)
-        out["learned_correction"] = learned_section(g, source)
-        out["sweep"] = sweep_table(g, source)
-        out["sssp_16_sources"] = sssp_sources(g)
+        out["time_to_accuracy"] = accuracy_table(g, source, collected, full=(g2 is None))
+        if g2 is not None:
+            out["rmat22"]["time_to_accuracy"] = accuracy_table(g2, s2, coll2)
+        out["learned_correction"] = learned_section(g, source, [(g2, s2)] if g2 is not None else [])
+        gs, ss = (g2, s2) if g2 is not None else (g, source)
+        out["sweep"] = sweep_table(gs, ss)
+        out["sssp_16_sources"] = sssp_sources(gs)
     if not a.no_scale24:
         out["scale24_symmetric"] = scale24_section()
     if not a.no_serving:
         from paper_2104_10039_gb300 import gg, serve
         graphs, queries, scales = serve.make_workload()
         out["serving"] = serve.measure(gg, graphs, queries, scales)
-    if not a.no_cpu_baseline and world >= 1:
+    if not a.no_cpu_baseline and world == 1:
         arcs, secs = cpu_sample(g)
         out["cpu_baseline"] = {"value": round(arcs / secs / 1e9, 4), "unit": "GTEPS",
                                "cores": omp_threads(), "kind": "oracle",
                                "sample": f"one adaptive-correction PageRank run (sigma 0.5, {PR_ITERS} "
-                                         f"iterations) on the same graph, {secs:.1f} s"}
-        arcs1, secs1 = cpu_sample(g, iters=3, nthreads=1)
+                                         f"iterations) on the workload graph, in-edge build and sampling "
+                                         f"included, {secs:.1f} s"}
+        g1 = g2 if g2 is not None else g
+        arcs1, secs1 = cpu_sample(g1, iters=3, nthreads=1)
         out["cpu_baseline"]["single_thread"] = {
             "value": round(arcs1 / secs1 / 1e9, 4), "unit": "GTEPS", "cores": 1,
-            "sample": f"the same run cut to 3 iterations on one thread, {secs1:.1f} s"}
+            "sample": f"the same run cut to 3 iterations on one thread on rmat{int(np.log2(g1.n))}, {secs1:.1f} s"}
     print(json.dumps(out), flush=True)
 
 

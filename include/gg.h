@@ -226,7 +226,10 @@ gg_status gg_run(gg_graph *g, gg_app app, double sample_ratio, gg_policy policy,
 gg_status gg_result(gg_graph *g, gg_result_kind kind, void *dst, size_t bytes,
                     int dst_is_device);
 
-/* Size in bytes of a result (0 if it does not exist yet). */
+/* Size in bytes of a result (0 if it does not exist yet). Synchronises the
+ * graph's stream. Returns GG_RESULT_SIZE_ERROR ((size_t)-1) if g is NULL or a
+ * CUDA call failed; gg_last_error() then says which. */
+#define GG_RESULT_SIZE_ERROR ((size_t)-1)
 size_t gg_result_size(gg_graph *g, gg_result_kind kind);
 
 /* gg_set_stream - enqueue all later work of g on this cudaStream_t (e.g.
@@ -358,7 +361,11 @@ void gg_batch_free(gg_batch *b);
  * out in full up front, or loops that must not call into the allocator.
  *   n, m       vertices and arcs, n >= 1, n + m <= GG_NOALLOC_MAX_ITEMS
  *   in_ptr     device int32[n+1], in_src device int32[m]: in-edge rows, each
- *              listing its sources (the order defines the packed order)
+ *              listing its sources (the order defines the packed order).
+ *              in_ptr[0] must be 0, in_ptr[n] must be m and the row pointers
+ *              must never decrease; the call checks this on the device and,
+ *              if it fails, writes neither mask nor sp_ptr / sp_src and sets
+ *              *sp_nnz = 0xFFFFFFFF
  *   sample_ratio, seed, symmetric: as in gg_sample_edges / GG_SYMMETRIC
  *   mask       device uint32[ceil(m/32)] out: flag bits of the m arcs (bits
  *              past m in the last word are left as they were)
@@ -367,11 +374,15 @@ void gg_batch_free(gg_batch *b);
  *              packed active in-edges
  *   stream     cudaStream_t to run on (NULL = legacy default stream)
  * Working memory is one fixed device array inside libgg.so (about 0.8 MB
- * per GPU that loads the library, kept until the process exits). Every call
- * on a device shares it, so calls that overlap on the GPU race. The first
- * call on a device looks up the array's address (cudaGetSymbolAddress);
- * make that first call before any stream capture. Sizes above the limit
- * return GG_ERR_INVALID_ARG. Returns after enqueueing the work.
+ * per GPU that uses it, kept until the process exits). Every call on a
+ * device shares it, so calls that overlap on the GPU race. The first call on
+ * a device looks up the array's address (cudaGetSymbolAddress); under CUDA's
+ * default lazy module loading that first call is also what loads the
+ * library's module on the device and creates the array, so it does take
+ * device memory once: callers with a fixed budget make it before they hand
+ * the budget out, and before any stream capture. The cached address is not
+ * refreshed after cudaDeviceReset. Sizes above the limit return
+ * GG_ERR_INVALID_ARG. Returns after enqueueing the work.
  */
 #define GG_NOALLOC_MAX_ITEMS (1u << 24)
 gg_status gg_sample_csc_noalloc(int32_t n, int64_t m, const int32_t *in_ptr, const int32_t *in_src,

@@ -985,42 +985,64 @@ gg_status gg_run(gg_graph *g, gg_app app, double sample_ratio, gg_policy policy,
     return run(g, app, sample_ratio, policy, p);
 }
 
-static size_t result_size(gg_graph *g, gg_result_kind kind, const void **src)
+// Where a result lives and its size in bytes (0: it does not exist yet).
+// The packed list's length is read back on the graph's stream.
+static gg_status result_size(gg_graph *g, gg_result_kind kind, const void **src, size_t *bytes)
 {
     *src = nullptr;
+    *bytes = 0;
     const size_t n = (size_t)g->n, m = (size_t)g->m;
     switch (kind) {
     case GG_RESULT_VALUES:
-        if (g->last_app < 0) return 0;
+        if (g->last_app < 0) break;
         *src = g->last_app == GG_APP_PAGERANK ? (const void *)g->rank[g->cur] : (const void *)g->val[g->cur];
-        return 4 * n;
+        *bytes = 4 * n;
+        break;
     case GG_RESULT_MASK:
-        if (!g->sampled) return 0;
+        if (!g->sampled) break;
         *src = g->mask;
-        return 4 * g->mask_words;
-    case GG_RESULT_STATS: return sizeof(gg_stats);
-    case GG_RESULT_ITER_STATS: *src = g->iter_stats; return sizeof(gg_iter_stats) * g->iterations;
-    case GG_RESULT_CSC_PTR: *src = g->in_ptr; return 4 * (n + 1);
-    case GG_RESULT_CSC_SRC: *src = g->in_src; return 4 * m;
-    case GG_RESULT_CSC_W: if (!g->has_w) return 0; *src = g->in_w; return 4 * m;
-    case GG_RESULT_SPARSE_PTR: if (!g->sampled) return 0; *src = g->sp_ptr; return 4 * (n + 1);
+        *bytes = 4 * g->mask_words;
+        break;
+    case GG_RESULT_STATS: *bytes = sizeof(gg_stats); break;
+    case GG_RESULT_ITER_STATS: *src = g->iter_stats; *bytes = sizeof(gg_iter_stats) * g->iterations; break;
+    case GG_RESULT_CSC_PTR: *src = g->in_ptr; *bytes = 4 * (n + 1); break;
+    case GG_RESULT_CSC_SRC: *src = g->in_src; *bytes = 4 * m; break;
+    case GG_RESULT_CSC_W:
+        if (!g->has_w) break;
+        *src = g->in_w;
+        *bytes = 4 * m;
+        break;
+    case GG_RESULT_SPARSE_PTR:
+        if (!g->sampled) break;
+        *src = g->sp_ptr;
+        *bytes = 4 * (n + 1);
+        break;
     case GG_RESULT_SPARSE_SRC:
-        if (!g->sampled) return 0;
-        if (cudaMemcpy(&g->sp_nnz_host, g->sp_nnz, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return 0;
+        if (!g->sampled) break;
+        GG_CUDA(cudaMemcpyAsync(&g->sp_nnz_host, g->sp_nnz, 4, cudaMemcpyDeviceToHost, g->stream));
+        GG_CUDA(cudaStreamSynchronize(g->stream));
         *src = g->sp_src;
-        return 4 * (size_t)g->sp_nnz_host;
-    case GG_RESULT_OUT_TO_IN: *src = g->out_to_in; return 4 * m;
-    case GG_RESULT_SCORES: if (!g->logits_valid) return 0; *src = g->logits; return 4 * n;
+        *bytes = 4 * (size_t)g->sp_nnz_host;
+        break;
+    case GG_RESULT_OUT_TO_IN: *src = g->out_to_in; *bytes = 4 * m; break;
+    case GG_RESULT_SCORES:
+        if (!g->logits_valid) break;
+        *src = g->logits;
+        *bytes = 4 * n;
+        break;
     }
-    return 0;
+    return GG_OK;
 }
 
 size_t gg_result_size(gg_graph *g, gg_result_kind kind)
 {
-    if (!g) return 0;
-    if (cudaStreamSynchronize(g->stream) != cudaSuccess) return 0;
+    if (!g) { set_error("gg_result_size: graph is NULL"); return GG_RESULT_SIZE_ERROR; }
+    cudaError_t e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) { cuda_fail(e, "cudaStreamSynchronize"); return GG_RESULT_SIZE_ERROR; }
     const void *src;
-    return result_size(g, kind, &src);
+    size_t bytes = 0;
+    if (result_size(g, kind, &src, &bytes) != GG_OK) return GG_RESULT_SIZE_ERROR;
+    return bytes;
 }
 
 static gg_status fill_stats(gg_graph *g)
@@ -1029,8 +1051,10 @@ static gg_status fill_stats(gg_graph *g)
     if (g->iterations > 0) {
         gg_iter_stats *h = new (std::nothrow) gg_iter_stats[g->iterations];
         if (!h) { set_error("host allocation failed"); return GG_ERR_OOM; }
-        cudaError_t e = cudaMemcpy(h, g->iter_stats, sizeof(gg_iter_stats) * g->iterations, cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) { delete[] h; return cuda_fail(e, "cudaMemcpy (iteration stats)"); }
+        cudaError_t e = cudaMemcpyAsync(h, g->iter_stats, sizeof(gg_iter_stats) * g->iterations,
+                                        cudaMemcpyDeviceToHost, g->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+        if (e != cudaSuccess) { delete[] h; return cuda_fail(e, "cudaMemcpyAsync (iteration stats)"); }
         uint64_t arcs = 0;
         for (uint32_t i = 0; i < g->iterations; ++i) arcs += (h[i].mode & 0xFFu) == MODE_SKIPPED ? 0 : h[i].arcs;
         s.arcs_processed = arcs;
@@ -1038,20 +1062,20 @@ static gg_status fill_stats(gg_graph *g)
         delete[] h;
     }
     uint32_t nnz = (uint32_t)g->m;
-    if (g->sampled && !g->sample_clean) cudaMemcpy(&nnz, g->sp_nnz, 4, cudaMemcpyDeviceToHost);
-    else if (g->sampled) cudaMemcpy(&nnz, g->sp_nnz, 4, cudaMemcpyDeviceToHost);
+    if (g->sampled) GG_CUDA(cudaMemcpyAsync(&nnz, g->sp_nnz, 4, cudaMemcpyDeviceToHost, g->stream));
+    uint32_t err = 0;
+    GG_CUDA(cudaMemcpyAsync(&err, g->dev_err, 4, cudaMemcpyDeviceToHost, g->stream));
+    GG_CUDA(cudaStreamSynchronize(g->stream));
     s.active_arcs = nnz;
     s.trace_rows = g->trace_rows;
-    uint32_t err = 0;
-    cudaMemcpy(&err, g->dev_err, 4, cudaMemcpyDeviceToHost);
     s.device_error = err;
-    if (g->run_timed) cudaEventElapsedTime(&s.ms_run, g->ev_run0, g->ev_run1);
-    if (g->sample_timed) cudaEventElapsedTime(&s.ms_sample, g->ev_s0, g->ev_s1);
+    if (g->run_timed) GG_CUDA(cudaEventElapsedTime(&s.ms_run, g->ev_run0, g->ev_run1));
+    if (g->sample_timed) GG_CUDA(cudaEventElapsedTime(&s.ms_sample, g->ev_s0, g->ev_s1));
     s.ms_gather = s.ms_correct = s.ms_push = 0.0f;
     s.n_gather = s.n_correct = s.n_push = 0;
     for (size_t i = 0; i < g->timed_used; ++i) {
         float ms = 0.0f;
-        cudaEventElapsedTime(&ms, g->timed[i].start, g->timed[i].stop);
+        GG_CUDA(cudaEventElapsedTime(&ms, g->timed[i].start, g->timed[i].stop));
         if (g->timed[i].cls == 0) { s.ms_gather += ms; s.n_gather++; }
         else if (g->timed[i].cls == 1) { s.ms_correct += ms; s.n_correct++; }
         else { s.ms_push += ms; s.n_push++; }
@@ -1071,12 +1095,18 @@ gg_status gg_result(gg_graph *g, gg_result_kind kind, void *dst, size_t bytes, i
         if (bytes < sizeof(gg_stats)) { set_error("gg_result: buffer too small"); return GG_ERR_INVALID_ARG; }
         gg_status st = fill_stats(g);
         if (st != GG_OK) return st;
-        if (dst_is_device) GG_CUDA(cudaMemcpy(dst, &g->stats, sizeof(gg_stats), cudaMemcpyHostToDevice));
-        else memcpy(dst, &g->stats, sizeof(gg_stats));
+        if (dst_is_device) {
+            GG_CUDA(cudaMemcpyAsync(dst, &g->stats, sizeof(gg_stats), cudaMemcpyHostToDevice, g->stream));
+            GG_CUDA(cudaStreamSynchronize(g->stream));
+        } else {
+            memcpy(dst, &g->stats, sizeof(gg_stats));
+        }
         return GG_OK;
     }
     const void *src;
-    const size_t need = result_size(g, kind, &src);
+    size_t need = 0;
+    gg_status rs = result_size(g, kind, &src, &need);
+    if (rs != GG_OK) return rs;
     if (!src && need == 0 && kind != GG_RESULT_SPARSE_SRC && kind != GG_RESULT_ITER_STATS) {
         set_error("gg_result: result %d does not exist yet", (int)kind);
         return GG_ERR_STATE;
@@ -1091,7 +1121,11 @@ gg_status gg_result(gg_graph *g, gg_result_kind kind, void *dst, size_t bytes, i
         GG_CUDA(cudaStreamSynchronize(g->stream));
         src = (const void *)g->stash;
     }
-    if (need) GG_CUDA(cudaMemcpy(dst, src, need, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+    if (need) {
+        GG_CUDA(cudaMemcpyAsync(dst, src, need, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                g->stream));
+        GG_CUDA(cudaStreamSynchronize(g->stream));
+    }
     return GG_OK;
 }
 

@@ -11,6 +11,7 @@
 // array until the process exits, and every call on a device shares it, so
 // calls that overlap on the GPU race; the array keeps the last call's
 // contents and every call rewrites what it reads.
+#include <atomic>
 #include <cmath>
 
 #include "gg_tile.cuh"
@@ -27,25 +28,46 @@ static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoallocWords];
 
 // Device address of the scratch array on the current device. Host code may
 // not use the symbol itself as an address; the address is looked up once per
-// device and cached.
+// device and cached (several host threads may race to fill an entry: they
+// store the same address). The cache is not refreshed after cudaDeviceReset.
 static uint32_t *noalloc_scratch(gg_status *st)
 {
-    static uint32_t *ptrs[64] = {};
+    static std::atomic<uint32_t *> ptrs[64];
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) { *st = cuda_fail(e, "cudaGetDevice"); return nullptr; }
     if (dev < 0 || dev >= 64) { set_error("gg_sample_csc_noalloc: device %d not supported", dev); *st = GG_ERR_UNSUPPORTED; return nullptr; }
-    if (!ptrs[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    uint32_t *p = ptrs[dev].load(std::memory_order_acquire);
+    if (!p) {
+        void *a = nullptr;
+        e = cudaGetSymbolAddress(&a, g_noalloc_scratch);
         if (e != cudaSuccess) { *st = cuda_fail(e, "cudaGetSymbolAddress"); return nullptr; }
-        ptrs[dev] = (uint32_t *)p;
+        p = (uint32_t *)a;
+        ptrs[dev].store(p, std::memory_order_release);
     }
     *st = GG_OK;
-    return ptrs[dev];
+    return p;
 }
 
-__global__ void k_na_set(uint32_t *p, uint32_t v) { *p = v; }
+// scal[0] = m, scal[2] = 0 (the row-pointer check below sets it).
+__global__ void k_na_set(uint32_t *scal, uint32_t m)
+{
+    scal[0] = m;
+    scal[2] = 0u;
+}
+
+// The in-edge row pointers must start at 0, end at m and never decrease;
+// otherwise the partition and the tile kernels would index outside the
+// caller's arrays. A failed check sets scal[2]: the tile kernels then do
+// nothing and *sp_nnz is set to 0xFFFFFFFF.
+__global__ void k_na_check(const int32_t *__restrict__ in_ptr, int32_t n, uint32_t m, uint32_t *scal)
+{
+    bool bad = false;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        bad |= in_ptr[i] > in_ptr[i + 1];
+    if (blockIdx.x == 0 && threadIdx.x == 0) bad |= in_ptr[0] != 0 || (uint32_t)in_ptr[n] != m;
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(scal + 2, 1u);
+}
 
 struct NaSmem {
     int32_t rowend[kWT + 1];
@@ -83,7 +105,7 @@ k_na_flags(const int32_t *__restrict__ in_ptr, const int32_t *__restrict__ in_sr
     NaSmem &s = smem[threadIdx.x >> 5];
     const uint32_t lane = lane_id();
     const long long total = (long long)n + scal[0];
-    const int num_tiles = (int)scal[1];
+    const int num_tiles = scal[2] ? 0 : (int)scal[1];   // rejected row pointers: no work
     const int W = (int)((gridDim.x * kThreads) >> 5);
     for (int t = (int)((blockIdx.x * kThreads + threadIdx.x) >> 5); t < num_tiles; t += W) {
         const int32_t r0 = tile_info[t] & 0x7FFFFFFF, r1 = tile_info[t + 1] & 0x7FFFFFFF;
@@ -142,11 +164,15 @@ k_na_pack(const int32_t *__restrict__ in_ptr, const int32_t *__restrict__ in_src
     NaSmem &s = smem[threadIdx.x >> 5];
     const uint32_t lane = lane_id();
     const long long total = (long long)n + scal[0];
-    const int num_tiles = (int)scal[1];
+    const int num_tiles = scal[2] ? 0 : (int)scal[1];   // rejected row pointers: no work
     const int W = (int)((gridDim.x * kThreads) >> 5);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        sp_ptr[0] = 0;
-        *sp_nnz = tile_off[num_tiles];
+        if (scal[2]) {
+            *sp_nnz = 0xFFFFFFFFu;
+        } else {
+            sp_ptr[0] = 0;
+            *sp_nnz = tile_off[num_tiles];
+        }
     }
     for (int t = (int)((blockIdx.x * kThreads + threadIdx.x) >> 5); t < num_tiles; t += W) {
         const int32_t r0 = tile_info[t] & 0x7FFFFFFF, r1 = tile_info[t + 1] & 0x7FFFFFFF;
@@ -217,7 +243,7 @@ extern "C" gg_status gg_sample_csc_noalloc(int32_t n, int64_t m, const int32_t *
     uint32_t *tile_cnt = scratch + (kNoallocTiles + 2);
     uint32_t *tile_off = scratch + 2 * ((size_t)kNoallocTiles + 2);
     uint32_t *partials = scratch + 3 * ((size_t)kNoallocTiles + 2);
-    uint32_t *scal = partials + kNoallocPartials;   // [0] arcs, [1] tiles
+    uint32_t *scal = partials + kNoallocPartials;   // [0] arcs, [1] tiles, [2] row pointers rejected
     const uint32_t nt = (uint32_t)(((uint64_t)n + (uint64_t)m + kWT - 1) / kWT);
     const unsigned long long thr = (unsigned long long)std::floor(sample_ratio * 4294967296.0);
     int dev = 0, sms = 0;
@@ -227,6 +253,10 @@ extern "C" gg_status gg_sample_csc_noalloc(int32_t n, int64_t m, const int32_t *
     if (grid > sms * 4) grid = sms * 4;
     if (grid < 1) grid = 1;
     k_na_set<<<1, 1, 0, s>>>(scal, (uint32_t)m);
+    GG_CUDA(cudaGetLastError());
+    int cgrid = (int)(((long long)n + 255) / 256);
+    if (cgrid > sms * 4) cgrid = sms * 4;
+    k_na_check<<<cgrid, 256, 0, s>>>(in_ptr, n, (uint32_t)m, scal);
     GG_CUDA(cudaGetLastError());
     GG_CUDA(launch_partition(in_ptr, n, scal, nt, tile_info, scal + 1, s));
     k_na_flags<<<grid, kThreads, 0, s>>>(in_ptr, in_src, n, scal, tile_info, symmetric ? 1 : 0, seed, thr,

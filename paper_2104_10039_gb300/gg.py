@@ -162,8 +162,14 @@ def gg_run(g: int, app, sample_ratio: float, policy, params: gg_params):
     _check(_lib.gg_run(g, a, sample_ratio, p, ctypes.byref(params)), "gg_run")
 
 
+GG_RESULT_SIZE_ERROR = (1 << 64) - 1
+
+
 def gg_result_size(g: int, kind: int) -> int:
-    return int(_lib.gg_result_size(g, kind))
+    n = int(_lib.gg_result_size(g, kind))
+    if n == GG_RESULT_SIZE_ERROR:
+        raise GGError(GG_ERR_CUDA, "gg_result_size")
+    return n
 
 
 def gg_result(g: int, kind: int, dst, nbytes: int, dst_is_device: bool = False):

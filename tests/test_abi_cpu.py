@@ -63,3 +63,12 @@ def test_binding_layouts_match_the_header():
     assert int(out["gg_iter_stats"]) == gg.ITER_STATS_DTYPE.itemsize
     for fname in gg.ITER_STATS_DTYPE.names:
         assert int(out[f"gg_iter_stats.{fname}"]) == gg.ITER_STATS_DTYPE.fields[fname][1], fname
+
+
+def test_noalloc_limit_matches_the_header():
+    """The binding's copy of GG_NOALLOC_MAX_ITEMS is the header's #define."""
+    from paper_2104_10039_gb300 import gg
+    with open(os.path.join(ROOT, "include", "gg.h")) as f:
+        m = re.search(r"#define\s+GG_NOALLOC_MAX_ITEMS\s+\((\d+)u\s*<<\s*(\d+)\)", f.read())
+    assert m, "GG_NOALLOC_MAX_ITEMS not found in gg.h"
+    assert int(m.group(1)) << int(m.group(2)) == gg.GG_NOALLOC_MAX_ITEMS

@@ -63,3 +63,4 @@ def test_reference_arm_prints_the_contract_line():
     assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"].startswith("rmat10")
+    assert d["reference_step"]["runs_per_step"] == 1 and d["reference_step"]["graph"].startswith("rmat10")

@@ -1,5 +1,6 @@
 """GPU parity at the workloads' full sizes, in the configuration bench.py
-times: R-MAT scale 22 (67 108 864 directed arcs) for PageRank and SSSP, and
+times: the directed R-MAT scale-24 graph (16 777 216 vertices, 268 435 456
+arcs) for PageRank and SSSP, R-MAT scale 22 (67 108 864 directed arcs), and
 the symmetrised R-MAT scale-24 and Erdos-Renyi graphs (268 435 456 arcs) for
 BFS, SSSP and CC at sample ratio 0.3. The oracle runs on every host core
 (its results do not depend on the thread count).
@@ -26,6 +27,76 @@ BIG = 1 << 20
 @pytest.fixture(scope="module")
 def gg():
     return gc.lib()
+
+
+@pytest.fixture(scope="module")
+def rmat24():
+    g = graphgen.rmat(24, 16, seed=1)
+    graphgen.add_weights(g, seed=7)
+    return g, int(graphgen.sources(g, 1, seed=2)[0])
+
+
+def test_rmat24_directed_build_and_sampler(gg, rmat24):
+    """In-edge build and sampled flags of the 268 M-arc directed graph, every
+    element (Sec. 2.1 in-edges sorted by source, Sec. 3.4 sampling)."""
+    g, _ = rmat24
+    h = gc.load(gg, g, device_ptrs=True)
+    try:
+        ip, isrc, iw, pos = oracle.csc_from_csr(g.n, g.rowptr, g.colidx, g.weights)
+        assert np.array_equal(gg.result_array(h, gg.GG_RESULT_CSC_PTR), ip)
+        assert np.array_equal(gg.result_array(h, gg.GG_RESULT_CSC_SRC), isrc)
+        assert np.array_equal(gg.result_array(h, gg.GG_RESULT_CSC_W), iw)
+        gg.gg_sample_edges(h, 0.3, 1)
+        assert np.array_equal(gg.mask_bits(h, g.m), oracle.sample_mask(g.n, ip, isrc, 0.3, 1))
+    finally:
+        gg.gg_free_graph(h)
+
+
+def test_rmat24_directed_pagerank(gg, rmat24):
+    """PageRank on the directed scale-24 graph: exact within 1e-5 relative L1
+    of the FP64 oracle; adaptive correction (alpha 4, theta 0.05) at sigma 0.1
+    and 0.5 through mask replay, as bench.py runs it."""
+    g, _ = rmat24
+    h = gc.load(gg, g)
+    try:
+        got, _, _ = gc.gpu_run(gg, h, g, "pagerank", "exact", T=PR_ITERS)
+        ref = oracle.run(g.n, g.rowptr, g.colidx, app="pagerank", policy="exact", max_iters=PR_ITERS,
+                         nthreads=0)
+        assert gc.rel_l1(got, ref["values"]) <= 1e-5
+        del ref
+        for sigma in (0.1, 0.5):
+            vals, ref, st = gc.pagerank_with_replay(gg, h, g, "adaptive", sigma, ALPHA, THETA, PR_ITERS, seed=1)
+            assert ref["replay_violations"] == 0, ref["replay_max_margin"]
+            assert ref["replay_mismatch"] <= g.m // 10000
+            assert gc.rel_l1(vals, ref["values"]) <= 1e-5
+            assert st.corrections == 4
+    finally:
+        gg.gg_free_graph(h)
+
+
+def test_rmat24_directed_sssp_bit_exact(gg, rmat24):
+    """SSSP on the directed scale-24 graph: exact, and adaptive correction at
+    sigma 0.5 and 0.1 cut at the exact run's iteration count (bench.py's
+    protocol) and run to its own fixed point; values and flags bit-exact."""
+    g, s = rmat24
+    h = gc.load(gg, g)
+    try:
+        got, _, st = gc.gpu_run(gg, h, g, "sssp", "exact", T=BIG, source=s)
+        ref = oracle.run(g.n, g.rowptr, g.colidx, g.weights, app="sssp", policy="exact", max_iters=BIG,
+                         source=s, nthreads=0)
+        assert np.array_equal(got, ref["values"])
+        assert st.iterations == ref["iterations"]
+        t_exact = st.iterations
+        for sigma, T in ((0.5, t_exact), (0.1, t_exact), (0.5, BIG)):
+            got, mask, st = gc.gpu_run(gg, h, g, "sssp", "adaptive", sigma=sigma, alpha=ALPHA, theta=THETA,
+                                       T=T, source=s, seed=1)
+            ref = oracle.run(g.n, g.rowptr, g.colidx, g.weights, app="sssp", policy="adaptive", sigma=sigma,
+                             seed=1, alpha=ALPHA, theta=THETA, max_iters=T, source=s, nthreads=0)
+            assert np.array_equal(got, ref["values"]), (sigma, T)
+            assert np.array_equal(mask, ref["mask"]), (sigma, T)
+            assert st.iterations == ref["iterations"]
+    finally:
+        gg.gg_free_graph(h)
 
 
 @pytest.fixture(scope="module")
