@@ -366,7 +366,7 @@ def roofline(collected, n, m):
     avg_s = classes[dom][0] * 1e-3 / classes[dom][1]
     bytes_per = classes[dom][2] / classes[dom][1]
     achieved = bytes_per / avg_s / 1e9
-    name = KERNEL_NAMES[dom[1]].format(a=dom[0])
+    name = KERNEL_NAMES.get(dom, KERNEL_NAMES.get(dom[1], "")).format(a=dom[0])
     return {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
             "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
             "traffic": recorded_traffic(f"{dom[0]}/{dom[1]}", bytes_per),
@@ -375,7 +375,8 @@ def roofline(collected, n, m):
             "ms_last_step": {f"{k[0]}/{k[1]}": round(v[0], 3) for k, v in classes.items()}}
 
 
-KERNEL_NAMES = {"gather": "k_arcs<{a}, K_GATHER> + k_fixup<{a}>",
+KERNEL_NAMES = {("pagerank", "gather"): "k_pr_arcs + k_pr_fix + k_pr_apply",
+                "gather": "k_arcs<{a}, K_GATHER> + k_fixup<{a}>",
                 "correct": "k_arcs<{a}, K_STASH> + k_correct2<{a}>"}
 
 

@@ -190,19 +190,23 @@ static void fill_list(const gg_graph *g, bool sparse, TileArgs &a)
 
 // After a correction or sampling pass: place the tiles' local packs into the
 // packed active in-edge list and partition it for the next gathers.
-static gg_status finish_pack(gg_graph *g, bool weighted, IterStatsDev *stats)
+// plain: pack vertex ids (the PageRank pull path reads them) rather than the
+// hub-coded sources the other gathers read.
+static gg_status finish_pack(gg_graph *g, bool weighted, IterStatsDev *stats, bool plain = false)
 {
     GG_CUDA(launch_scan_u32(g->tile_cnt, g->tile_off, g->full_tiles, g->scan_tmp, g->stream));
-    GG_CUDA(launch_pack(g->full_tile_info, g->tile_off, g->full_tiles, (long long)g->n + g->m, g->mask, g->in_src_h,
-                        weighted ? g->in_w : nullptr, g->sp_ptr, g->sp_src, weighted ? g->sp_w : nullptr, g->sp_nnz,
-                        stats, g->num_sms, g->stream));
+    GG_CUDA(launch_pack(g->full_tile_info, g->tile_off, g->full_tiles, (long long)g->n + g->m, g->mask,
+                        plain ? g->in_src : g->in_src_h, weighted ? g->in_w : nullptr, g->sp_ptr, g->sp_src,
+                        weighted ? g->sp_w : nullptr, g->sp_nnz, stats, g->num_sms, g->stream));
+    g->sp_is_plain = plain;
+    g->plan[1].valid = false;
     GG_CUDA(launch_partition(g->sp_ptr, g->n, g->sp_nnz, g->max_tiles, g->sp_tile_info, g->sp_num_tiles,
                              g->stream));
     g->launches += 5;
     return GG_OK;
 }
 
-gg_status sample_edges(gg_graph *g, double ratio, uint64_t seed)
+gg_status sample_edges(gg_graph *g, double ratio, uint64_t seed, bool plain)
 {
     if (!(ratio > 0.0 && ratio <= 1.0)) {
         set_error("sample_ratio must be in (0, 1], got %g", ratio);
@@ -215,7 +219,7 @@ gg_status sample_edges(gg_graph *g, double ratio, uint64_t seed)
     GG_CUDA(launch_tile_counts(g->full_tile_info, g->full_tiles, (long long)g->n + g->m, g->in_ptr, g->mask,
                                g->tile_cnt, g->sp_ptr, g->num_sms, g->stream));
     g->launches += 2;
-    gg_status st = finish_pack(g, g->has_w, nullptr);
+    gg_status st = finish_pack(g, g->has_w, nullptr, plain);
     if (st != GG_OK) return st;
     GG_CUDA(cudaEventRecord(g->ev_s1, g->stream));
     g->sample_timed = true;
@@ -408,6 +412,11 @@ static gg_status run_pagerank(gg_graph *g, gg_policy policy, const gg_params *p)
     const bool learned_policy = policy == GG_POLICY_LEARNED;
     Trigger trig(policy, p);
     g->cur = 0;
+    {
+        gg_status st = ensure_pull(g);
+        if (st == GG_OK) st = sp_plain(g);
+        if (st != GG_OK) return st;
+    }
     GG_CUDA(launch_init_pr(g->n, g->out_ptr, g->rank[0], g->contrib[0], g->num_sms, g->stream));
     g->launches += 1;
     if (renorm) {
@@ -466,10 +475,45 @@ static gg_status run_pagerank(gg_graph *g, gg_policy policy, const gg_params *p)
                 if (st != GG_OK) return st;
             }
             GG_CUDA(launch_iter_header(a.stats, (uint32_t)mode, a.list_nnz, 0, g->stream));
-            timed_begin(g, timing, kind == K_CORRECT ? 1 : 0, &slot);
-            GG_CUDA(launch_tile_pr(kind, a, (int)g->max_tiles, g->num_sms, g->stream));
-            if (kind == K_GATHER) GG_CUDA(launch_fixup(GG_APP_PAGERANK, a, (int)g->max_tiles, g->num_sms, g->stream));
-            timed_end(g, slot);
+            if (kind == K_GATHER) {
+                const int which = mode == MODE_APPROX ? 1 : 0;
+                if (!g->plan[which].valid) {
+                    gg_status st = build_pull_plan(g, which);
+                    if (st != GG_OK) return st;
+                }
+                const PullPlan &pl = g->plan[which];
+                PullArgs pa{};
+                pa.src = which ? g->sp_src : g->in_src;
+                pa.nnz = a.list_nnz;
+                pa.hb = pl.hb;
+                pa.trow = pl.trow;
+                pa.tj = pl.tj;
+                pa.thead = pl.thead;
+                pa.nzb = pl.nzb;
+                pa.nzc = pl.nzc;
+                pa.contrib = a.contrib_cur;
+                pa.acc = g->pull_acc;
+                pa.lead = g->pull_lead;
+                pa.n = g->n;
+                pa.rank_cur = a.rank_cur;
+                pa.rank_next = a.rank_next;
+                pa.contrib_next = a.contrib_next;
+                pa.out_ptr = g->out_ptr;
+                pa.deg_apply = a.deg_apply;
+                pa.base = a.base;
+                pa.damping = a.damping;
+                pa.epsilon = a.epsilon;
+                pa.n_f = a.n_f;
+                pa.hist_out = a.hist_out;
+                pa.stats = a.stats;
+                timed_begin(g, timing, 0, &slot);
+                GG_CUDA(launch_pr_pull(pa, (uint32_t)pl.tiles, g->num_sms, g->stream));
+                timed_end(g, slot);
+            } else {
+                timed_begin(g, timing, 1, &slot);
+                GG_CUDA(launch_tile_pr(kind, a, (int)g->max_tiles, g->num_sms, g->stream));
+                timed_end(g, slot);
+            }
             g->launches += 3;
             if (tracing) {
                 gg_status st = trace_labels(g, true);
@@ -477,7 +521,7 @@ static gg_status run_pagerank(gg_graph *g, gg_policy policy, const gg_params *p)
             }
         }
         if (kind == K_CORRECT) {
-            gg_status st = finish_pack(g, false, a.stats);
+            gg_status st = finish_pack(g, false, a.stats, true);
             if (st != GG_OK) return st;
             g->sample_clean = false;
             g->stats.corrections += 1;
@@ -778,7 +822,7 @@ gg_status run(gg_graph *g, gg_app app, double ratio, gg_policy policy, const gg_
     GG_CUDA(cudaEventRecord(g->ev_run0, g->stream));
     if (policy != GG_POLICY_EXACT &&
         !(g->sampled && g->sample_clean && g->sample_ratio == ratio && g->sample_seed == p->seed)) {
-        st = sample_edges(g, ratio, p->seed);
+        st = sample_edges(g, ratio, p->seed, app == GG_APP_PAGERANK);
         if (st != GG_OK) return st;
     }
     st = app == GG_APP_PAGERANK ? run_pagerank(g, policy, p) : run_min(g, app, policy, p);
@@ -976,7 +1020,7 @@ gg_status gg_load_csr(gg_graph **out, int32_t n, int64_t m, const int32_t *rowpt
 gg_status gg_sample_edges(gg_graph *g, double sample_ratio, uint64_t seed)
 {
     if (!g) { set_error("gg_sample_edges: graph is NULL"); return GG_ERR_INVALID_ARG; }
-    return sample_edges(g, sample_ratio, seed);
+    return sample_edges(g, sample_ratio, seed, false);
 }
 
 gg_status gg_run(gg_graph *g, gg_app app, double sample_ratio, gg_policy policy, const gg_params *p)

@@ -48,6 +48,18 @@ struct DevBuf {
     float *f32() const { return (float *)p; }
 };
 
+// Plan of one list for the PageRank pull path (gg_pull.cu): row-start bits,
+// per-tile row ranks and first tiles, non-empty-row bitmap and counts.
+struct PullPlan {
+    DevBuf buf;
+    uint32_t *hb = nullptr;
+    int32_t *trow = nullptr, *tj = nullptr;
+    uint8_t *thead = nullptr;
+    uint32_t *nzb = nullptr, *nzc = nullptr, *nzcnt = nullptr;
+    size_t hb_words = 0, tiles = 0, nzw = 0;
+    bool valid = false;
+};
+
 struct TimedLaunch {
     int cls;               // 0 gather, 1 correct, 2 push
     cudaEvent_t start, stop;
@@ -156,6 +168,13 @@ struct gg_graph {
     uint32_t *sub_w = nullptr, *sub_mask = nullptr;
     int32_t *sub_tile_info = nullptr;
     uint32_t *sub_num_tiles = nullptr;
+    // PageRank pull path: plans of the full (0) and packed (1) lists, row sums
+    // and tile leading parts; whether sp_src holds vertex ids (not hub-coded)
+    gg::PullPlan plan[2];
+    gg::DevBuf b_pull;
+    float *pull_acc = nullptr, *pull_lead = nullptr;
+    bool pull_ready = false;
+    bool sp_is_plain = false;
     // training trace (caller-owned device buffers)
     float *trace_x = nullptr;
     uint8_t *trace_y = nullptr;
@@ -167,7 +186,10 @@ namespace gg {
 gg_status build_csc(gg_graph *g);
 gg_status build_hubs(gg_graph *g);
 gg_status validate_csr(gg_graph *g);
-gg_status sample_edges(gg_graph *g, double ratio, uint64_t seed);
+gg_status sample_edges(gg_graph *g, double ratio, uint64_t seed, bool plain);
 gg_status run(gg_graph *g, gg_app app, double ratio, gg_policy policy, const gg_params *p);
 uint32_t next_epoch(gg_graph *g);
+gg_status ensure_pull(gg_graph *g);
+gg_status build_pull_plan(gg_graph *g, int which);
+gg_status sp_plain(gg_graph *g);
 }  // namespace gg

@@ -118,6 +118,34 @@ struct TileArgs {
 // k_arcs<., K_STASH> then k_correct2 (or k_share for the share influence).
 enum TileKind { K_GATHER = 0, K_CORRECT = 1, K_STASH = 2 };
 
+// The PageRank pull path (gg_pull.cu): a list (sources as vertex ids), its
+// plan, and the vertex state of one iteration.
+struct PullArgs {
+    const int32_t *src;         // list arcs: source vertex (no hub coding)
+    const uint32_t *nnz;        // device scalar: arcs in the list
+    const uint32_t *hb;         // plan: row-start bit per arc
+    const int32_t *trow;        // plan: per tile, non-empty-row rank of the row holding its first arc
+    const int32_t *tj;          // plan: per tile, tile of that row's first arc
+    const uint8_t *thead;       // plan: per tile, a row starts inside it
+    const uint32_t *nzb;        // plan: non-empty row bitmap
+    const uint32_t *nzc;        // plan: non-empty rows before each bitmap word
+    const float *contrib;       // gathered vector (rank / degree of the previous iteration)
+    float *acc;                 // per non-empty row: its sum
+    float *lead;                // per tile: the part before its first row start
+    int32_t n;
+    const float *rank_cur;
+    float *rank_next;
+    float *contrib_next;
+    const int32_t *out_ptr;     // CSR row pointers (full out-degree)
+    const int32_t *deg_apply;   // degrees for the next contributions (renormalised), or nullptr
+    float base;                 // (1-d)/N
+    float damping;
+    float epsilon;
+    float n_f;
+    float *hist_out;            // change feature of every vertex (learned policy / traces), or nullptr
+    IterStatsDev *stats;
+};
+
 // Inputs of the learned correction's vertex features.
 struct FeatArgs {
     int32_t n;
@@ -247,6 +275,8 @@ cudaError_t launch_active_outdeg(const int32_t *sp_src, const uint32_t *sp_nnz, 
 // Source ids of a hub-coded list back to vertex ids (count read on the device).
 cudaError_t launch_decode_src(const int32_t *coded, const uint32_t *count, uint32_t max_count, const int32_t *hub_ids,
                               int32_t *out, int num_sms, cudaStream_t s);
+// PageRank pull iteration (gg_pull.cu): arcs, continued rows, apply.
+cudaError_t launch_pr_pull(const PullArgs &a, uint32_t max_tiles, int num_sms, cudaStream_t s);
 // contrib[u] = rank[u] / deg[u], or / the full out-degree when deg is null (0 when the degree is 0).
 cudaError_t launch_contrib(int32_t n, const float *rank, const int32_t *deg, const int32_t *out_ptr,
                            float *contrib, int num_sms, cudaStream_t s);

@@ -1,0 +1,378 @@
+// gg_pull.cu - the PageRank pull gather of approximate and accurate
+// iterations (Alg. 1 / Alg. 2: GG-Gather over a row's flagged in-edges,
+// GG-Apply, GG-VStatus) as three launches over a precomputed plan of the
+// list it walks.
+//
+// Why a separate path for PageRank: its gather reads one 4-byte value per arc
+// at a random address, and on this GPU those reads are bounded by how many
+// scattered L1 misses each SM keeps in flight (the L1 capacity left beside
+// shared memory), not by DRAM. This path therefore keeps the arc work free of
+// shared memory: every lane holds its arcs' values in registers, row
+// boundaries come from a bit per arc computed once per list, and the vertex
+// work (apply, change statistics) is a separate coalesced pass.
+//
+//   k_pr_arcs   warp tiles of kPT = 256 consecutive arcs; lane L takes arcs
+//               4L..4L+3 and 128+4L..128+4L+3 (two 16-byte source loads),
+//               fetches their contributions, and a segmented sum over the
+//               tile (lane-local, then a warp scan) gives every row's total.
+//               A row whose first arc lies in the tile writes its total (or,
+//               if it continues past the tile, the part in the tile) to
+//               acc[k], k = its rank among the list's non-empty rows; the
+//               part of the tile before its first row start goes to
+//               lead[tile].
+//   k_pr_fix    every row continued across tile ends: its first part plus
+//               the later tiles' leading parts, in tile order.
+//   k_pr_apply  one thread per vertex: rank' = (1-d)/N + d acc (0 for a row
+//               with no arcs in the list), contrib' = rank' / degree, change
+//               statistics.
+//
+// The sums use a fixed grouping (lane-local prefix, warp scan, tile order),
+// so results are deterministic. The plan of a list (built by build_pull_plan
+// whenever the list changes):
+//   hb[w]     bit j: arc 32w + j is the first arc of a row
+//   trow[t]   rank among non-empty rows of the row holding arc 256t
+//   tj[t]     tile of that row's first arc
+//   thead[t]  1 if a row starts inside tile t
+//   nzb[w]    bit j: row 32w + j has arcs;  nzc[w]: non-empty rows before row 32w
+#include "gg_graph.cuh"
+
+namespace gg {
+
+namespace {
+
+constexpr int kPT = 256;          // arcs per pull tile
+constexpr int kPullThreads = 256;
+
+// ------------------------------------------------------------------ plan ----
+__global__ void k_plan_nz(const int32_t *__restrict__ ptr, int32_t n, uint32_t *__restrict__ nzb,
+                          uint32_t *__restrict__ nzcnt)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); v0 < n; v0 += stride) {
+        const long long v = v0 + (threadIdx.x & 31u);
+        const bool ne = v < n && ptr[v + 1] > ptr[v];
+        const uint32_t b = __ballot_sync(0xFFFFFFFFu, ne);
+        if ((threadIdx.x & 31u) == 0) {
+            nzb[v0 >> 5] = b;
+            nzcnt[v0 >> 5] = (uint32_t)__popc(b);
+        }
+    }
+}
+
+__global__ void k_plan_heads(const int32_t *__restrict__ ptr, int32_t n, const uint32_t *__restrict__ nzb,
+                             const uint32_t *__restrict__ nzc, uint32_t *__restrict__ hb,
+                             int32_t *__restrict__ trow, int32_t *__restrict__ tj, uint8_t *__restrict__ thead)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const int32_t s = ptr[v], e = ptr[v + 1];
+        if (e <= s) continue;
+        const uint32_t w = (uint32_t)(v >> 5), bit = (uint32_t)(v & 31);
+        const int32_t k = (int32_t)(nzc[w] + (uint32_t)__popc(nzb[w] & ((1u << bit) - 1u)));
+        atomicOr(hb + (s >> 5), 1u << (s & 31));
+        thead[s >> 8] = 1;
+        for (long long t = ((long long)s + kPT - 1) / kPT; t * kPT < e; ++t) {
+            trow[t] = k;
+            tj[t] = s / kPT;
+        }
+    }
+}
+
+// Hub-coded sources of a packed list back to vertex ids, in place.
+__global__ void k_decode_inplace(int32_t *src, const uint32_t *count, const int32_t *__restrict__ hub_ids)
+{
+    const uint32_t c = *count;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < c; k += gridDim.x * blockDim.x) {
+        const int32_t v = src[k];
+        if (v < 0) src[k] = hub_ids[-v - 1];
+    }
+}
+
+}  // namespace
+
+namespace {
+
+__device__ __forceinline__ uint32_t pick4(const uint4 &w, uint32_t i)
+{
+    return i == 0 ? w.x : (i == 1 ? w.y : (i == 2 ? w.z : w.w));
+}
+
+// Row-start bits of word i of a tile holding `rel` valid arcs: positions at
+// or past `rel` count as row starts (each a one-arc segment that is skipped),
+// so the last real row ends at the last valid arc.
+__device__ __forceinline__ uint32_t tail_bits(uint32_t word, int i, uint32_t rel)
+{
+    const uint32_t lo = 32u * (uint32_t)i;
+    if (rel <= lo) return 0xFFFFFFFFu;
+    if (rel >= lo + 32u) return word;
+    return word | ~((1u << (rel - lo)) - 1u);
+}
+
+// ---------------------------------------------------------------- gather ----
+template <int MINB>
+__global__ void __launch_bounds__(kPullThreads, MINB) k_pr_arcs(PullArgs a)
+{
+    constexpr uint32_t FULL = 0xFFFFFFFFu;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t nnz = *a.nnz;
+    const long long nt = ((long long)nnz + kPT - 1) / kPT;
+    const long long W = (long long)gridDim.x * (kPullThreads / 32);
+    for (long long t = (long long)blockIdx.x * (kPullThreads / 32) + (threadIdx.x >> 5); t < nt; t += W) {
+        const long long a0 = t * kPT;
+        const uint32_t rel = nnz - (uint32_t)a0 < (uint32_t)kPT ? nnz - (uint32_t)a0 : (uint32_t)kPT;
+        // ---- sources (16-byte loads) and their contributions -----------------
+        int32_t s[8];
+        if (rel == (uint32_t)kPT) {
+            const int4 x = __ldg(reinterpret_cast<const int4 *>(a.src + a0) + lane);
+            const int4 y = __ldg(reinterpret_cast<const int4 *>(a.src + a0 + 128) + lane);
+            s[0] = x.x; s[1] = x.y; s[2] = x.z; s[3] = x.w;
+            s[4] = y.x; s[5] = y.y; s[6] = y.z; s[7] = y.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t q = 4u * lane + (uint32_t)j;
+                s[j] = q < rel ? a.src[a0 + q] : -1;
+                s[4 + j] = q + 128u < rel ? a.src[a0 + 128 + q] : -1;
+            }
+        }
+        float v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = s[i] >= 0 ? __ldg(a.contrib + s[i]) : 0.0f;
+        // ---- row starts of the tile ------------------------------------------
+        uint4 h0 = __ldg(reinterpret_cast<const uint4 *>(a.hb + t * 8));
+        uint4 h1 = __ldg(reinterpret_cast<const uint4 *>(a.hb + t * 8 + 4));
+        const uint32_t next_head = a0 + kPT >= (long long)nnz ? 1u : (__ldg(a.hb + (t + 1) * 8) & 1u);
+        if (rel < (uint32_t)kPT) {
+            h0.x = tail_bits(h0.x, 0, rel); h0.y = tail_bits(h0.y, 1, rel);
+            h0.z = tail_bits(h0.z, 2, rel); h0.w = tail_bits(h0.w, 3, rel);
+            h1.x = tail_bits(h1.x, 4, rel); h1.y = tail_bits(h1.y, 5, rel);
+            h1.z = tail_bits(h1.z, 6, rel); h1.w = tail_bits(h1.w, 7, rel);
+        }
+        // first row start in the tile (kPT: none)
+        uint32_t fh = kPT;
+        {
+            const uint32_t wv[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+#pragma unroll
+            for (int i = 7; i >= 0; --i)
+                if (wv[i]) fh = 32u * (uint32_t)i + (uint32_t)(__ffs(wv[i]) - 1);
+        }
+        const int32_t tr = __ldg(a.trow + t);
+        const uint32_t h0bit = h0.x & 1u;
+        float carry = 0.0f;      // running value of the segment open at the end of the previous half
+        uint32_t before = 0;     // row starts in earlier halves
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint4 hw = h ? h1 : h0;
+            const uint32_t wi = lane >> 3, sh = 4u * (lane & 7u);
+            const uint32_t word = pick4(hw, wi);
+            const uint32_t f = (word >> sh) & 0xFu;     // bit j: arc j of this lane starts a row
+            uint32_t cnt = before + (uint32_t)__popc(word & ((1u << sh) - 1u));
+            cnt += wi > 0 ? (uint32_t)__popc(hw.x) : 0u;
+            cnt += wi > 1 ? (uint32_t)__popc(hw.y) : 0u;
+            cnt += wi > 2 ? (uint32_t)__popc(hw.z) : 0u;
+            // does a row start right after this lane's last arc?
+            uint32_t nxt = __shfl_down_sync(FULL, f, 1) & 1u;
+            if (lane == 31) nxt = h == 0 ? (h1.x & 1u) : next_head;
+            // lane-local running values, restarting at row starts
+            const float v0 = v[4 * h], v1 = v[4 * h + 1], v2 = v[4 * h + 2], v3 = v[4 * h + 3];
+            const float r0 = v0;
+            const float r1 = (f & 2u) ? v1 : r0 + v1;
+            const float r2 = (f & 4u) ? v2 : r1 + v2;
+            const float r3 = (f & 8u) ? v3 : r2 + v3;
+            // warp segmented inclusive scan of the lanes' open tails
+            const uint32_t heads = __ballot_sync(FULL, f != 0u);
+            const uint32_t le = heads & (FULL >> (31u - lane));
+            const int start = le ? 31 - __clz(le) : -1;   // lane where the segment open at this lane's end starts
+            float x = r3;
+            if (lane == 0 && f == 0u) x = carry + r3;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const float y = __shfl_up_sync(FULL, x, o);
+                if ((int)lane >= o && (int)lane - o >= start) x = y + x;
+            }
+            float E = __shfl_up_sync(FULL, x, 1);
+            if (lane == 0) E = carry;
+            const uint32_t fj = f ? (uint32_t)(__ffs(f) - 1) : 4u;   // first row start in the lane
+            float run[4];
+            run[0] = fj > 0 ? E + r0 : r0;
+            run[1] = fj > 1 ? E + r1 : r1;
+            run[2] = fj > 2 ? E + r2 : r2;
+            run[3] = fj > 3 ? E + r3 : r3;
+            // segment ends: a row starts at the next arc, or the tile ends
+            const uint32_t ends = (f >> 1) | (nxt << 3) | ((h == 1 && lane == 31) ? 8u : 0u);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t q = 128u * (uint32_t)h + 4u * lane + (uint32_t)j;
+                if (((ends >> j) & 1u) && q < rel) {
+                    if (q < fh) {
+                        a.lead[t] = run[j];    // the row continued from an earlier tile
+                    } else {
+                        const uint32_t c = cnt + (uint32_t)__popc(f & ((2u << j) - 1u)) - h0bit;
+                        a.acc[tr + (int32_t)c] = run[j];
+                    }
+                }
+            }
+            before += (uint32_t)(__popc(hw.x) + __popc(hw.y) + __popc(hw.z) + __popc(hw.w));
+            carry = __shfl_sync(FULL, x, 31);
+        }
+    }
+}
+
+}  // namespace
+
+namespace {
+
+// ----------------------------------------------------------------- fixup ----
+// A row that began in tile j < t and ends in tile t (a row starts inside t,
+// or the next tile starts with one, or t is the last tile): its part in tile
+// j (written by the gather to acc) plus the leading parts of tiles j+1 .. t,
+// in tile order. One thread per tile.
+__global__ void __launch_bounds__(kPullThreads) k_pr_fix(PullArgs a)
+{
+    const uint32_t nnz = *a.nnz;
+    const long long nt = ((long long)nnz + kPT - 1) / kPT;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += stride) {
+        const int32_t j = a.tj[t];
+        if (j >= t) continue;
+        const bool ends_here = a.thead[t] || t == nt - 1 || a.tj[t + 1] == t + 1;
+        if (!ends_here) continue;
+        const int32_t k = a.trow[t];
+        float acc = a.acc[k];
+        for (long long u = (long long)j + 1; u <= t; ++u) acc += a.lead[u];
+        a.acc[k] = acc;
+    }
+}
+
+// ----------------------------------------------------------------- apply ----
+// GG-Apply + GG-VStatus (Alg. 2) for every vertex, in vertex order.
+__global__ void __launch_bounds__(kPullThreads) k_pr_apply(PullArgs a)
+{
+    unsigned long long changed = 0, sum = 0;
+    uint32_t mx = 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += stride) {
+        const uint32_t w = (uint32_t)(v >> 5), bit = (uint32_t)(v & 31);
+        const uint32_t word = __ldg(a.nzb + w);
+        float acc = 0.0f;
+        if ((word >> bit) & 1u) acc = a.acc[__ldg(a.nzc + w) + (uint32_t)__popc(word & ((1u << bit) - 1u))];
+        const float old = a.rank_cur[v];
+        const int32_t deg = a.deg_apply ? a.deg_apply[v] : __ldg(a.out_ptr + v + 1) - __ldg(a.out_ptr + v);
+        const float nw = __fmaf_rn(a.damping, acc, a.base);
+        const float delta = fabsf(__fsub_rn(nw, old));
+        a.rank_next[v] = nw;
+        a.contrib_next[v] = deg > 0 ? __fdiv_rn(nw, (float)deg) : 0.0f;
+        if (a.hist_out) a.hist_out[v] = __fmul_rn(a.n_f, delta);
+        changed += delta > a.epsilon ? 1ull : 0ull;
+        sum += __float2ull_rz(delta * 1099511627776.0f);   // fixed point 2^-40
+        const uint32_t db = __float_as_uint(delta);
+        mx = db > mx ? db : mx;
+    }
+    if (!a.stats) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        changed += __shfl_xor_sync(0xFFFFFFFFu, changed, o);
+        sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+        const uint32_t om = __shfl_xor_sync(0xFFFFFFFFu, mx, o);
+        mx = om > mx ? om : mx;
+    }
+    if ((threadIdx.x & 31u) == 0 && (changed | sum | mx)) {
+        atomicAdd(&a.stats->changed, changed);
+        atomicAdd(&a.stats->sum_delta, sum);
+        atomicMax(&a.stats->max_delta_bits, mx);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_pr_pull(const PullArgs &a, uint32_t max_tiles, int num_sms, cudaStream_t s)
+{
+    const int arc_blocks_per_sm = 5;
+    long long blocks = ((long long)max_tiles + kPullThreads / 32 - 1) / (kPullThreads / 32);
+    if (blocks > (long long)num_sms * arc_blocks_per_sm) blocks = (long long)num_sms * arc_blocks_per_sm;
+    if (blocks < 1) blocks = 1;
+    k_pr_arcs<arc_blocks_per_sm><<<(unsigned)blocks, kPullThreads, 0, s>>>(a);
+    long long fb = ((long long)max_tiles + kPullThreads - 1) / kPullThreads;
+    if (fb > (long long)num_sms * 8) fb = (long long)num_sms * 8;
+    if (fb < 1) fb = 1;
+    k_pr_fix<<<(unsigned)fb, kPullThreads, 0, s>>>(a);
+    long long ab = ((long long)a.n + kPullThreads - 1) / kPullThreads;
+    if (ab > (long long)num_sms * 8) ab = (long long)num_sms * 8;
+    if (ab < 1) ab = 1;
+    k_pr_apply<<<(unsigned)ab, kPullThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------- plan (host) ----
+gg_status ensure_pull(gg_graph *g)
+{
+    if (g->pull_ready) return GG_OK;
+    const size_t tiles = ((size_t)g->m + kPT - 1) / kPT + 1;
+    const size_t nzw = ((size_t)g->n + 31) / 32 + 1;
+    // per plan: hb (8 words per tile + 8), trow, tj (tiles + 1 each), nzb, nzc, nzcnt, thead (bytes)
+    const size_t words = 8 * tiles + 8 + 2 * (tiles + 1) + 3 * nzw + (tiles + 1 + 15) / 4 + 8;
+    for (int i = 0; i < 2; ++i) {
+        PullPlan &p = g->plan[i];
+        gg_status st = p.buf.alloc(4 * words, g->stream);
+        if (st != GG_OK) return st;
+        uint32_t *w = p.buf.u32();
+        p.hb = w; w += 8 * tiles + 8;
+        p.trow = (int32_t *)w; w += tiles + 1;
+        p.tj = (int32_t *)w; w += tiles + 1;
+        p.nzb = w; w += nzw;
+        p.nzc = w; w += nzw;
+        p.nzcnt = w; w += nzw;
+        p.thead = (uint8_t *)w;
+        p.hb_words = 8 * tiles + 8;
+        p.tiles = tiles;
+        p.nzw = nzw;
+        p.valid = false;
+    }
+    gg_status st = g->b_pull.alloc(4 * ((size_t)g->n + tiles + 8), g->stream);
+    if (st != GG_OK) return st;
+    g->pull_acc = g->b_pull.f32();
+    g->pull_lead = g->pull_acc + g->n + 4;
+    g->pull_ready = true;
+    return GG_OK;
+}
+
+// Plan of the full in-edge list (which 0) or of the packed active list (1).
+gg_status build_pull_plan(gg_graph *g, int which)
+{
+    PullPlan &p = g->plan[which];
+    const int32_t *ptr = which ? g->sp_ptr : g->in_ptr;
+    cudaStream_t s = g->stream;
+    GG_CUDA(cudaMemsetAsync(p.hb, 0, 4 * p.hb_words, s));
+    GG_CUDA(cudaMemsetAsync(p.thead, 0, p.tiles + 1, s));
+    int grid = (int)(((size_t)g->n + 255) / 256);
+    if (grid > g->num_sms * 8) grid = g->num_sms * 8;
+    if (grid < 1) grid = 1;
+    k_plan_nz<<<grid, 256, 0, s>>>(ptr, g->n, p.nzb, p.nzcnt);
+    GG_CUDA(cudaGetLastError());
+    // exclusive scan of the words' counts (it also writes the total at
+    // nzc[words], inside the array: nzw = words + 1)
+    const size_t words = ((size_t)g->n + 31) / 32;
+    GG_CUDA(launch_scan_u32(p.nzcnt, p.nzc, words, g->scan_tmp, s));
+    k_plan_heads<<<grid, 256, 0, s>>>(ptr, g->n, p.nzb, p.nzc, p.hb, p.trow, p.tj, p.thead);
+    GG_CUDA(cudaGetLastError());
+    g->launches += 7;
+    p.valid = true;
+    return GG_OK;
+}
+
+// The packed list as vertex ids (a correction or sampling pass of another
+// application may have packed hub-coded sources).
+gg_status sp_plain(gg_graph *g)
+{
+    if (!g->sampled || g->sp_is_plain) return GG_OK;
+    int grid = (int)(((size_t)g->m + 255) / 256);
+    if (grid > g->num_sms * 8) grid = g->num_sms * 8;
+    if (grid < 1) grid = 1;
+    k_decode_inplace<<<grid, 256, 0, g->stream>>>(g->sp_src, g->sp_nnz, g->hub_ids);
+    GG_CUDA(cudaGetLastError());
+    g->launches += 1;
+    g->sp_is_plain = true;
+    return GG_OK;
+}
+
+}  // namespace gg
