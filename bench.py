@@ -375,7 +375,8 @@ def roofline(collected, n, m):
             "ms_last_step": {f"{k[0]}/{k[1]}": round(v[0], 3) for k, v in classes.items()}}
 
 
-KERNEL_NAMES = {("pagerank", "gather"): "k_pr_arcs + k_pr_fix + k_pr_apply",
+KERNEL_NAMES = {("pagerank", "gather"): "k_pr_arcs + k_pr_apply",
+                ("pagerank", "correct"): "k_pr_arcs (values kept) + k_prc_flags + k_pr_apply + k_tile_counts",
                 "gather": "k_arcs<{a}, K_GATHER> + k_fixup<{a}>",
                 "correct": "k_arcs<{a}, K_STASH> + k_correct2<{a}>"}
 

@@ -405,6 +405,40 @@ static gg_status learned_correct(gg_graph *g, gg_app app, TileArgs a, uint32_t n
     return GG_OK;
 }
 
+// Arguments of the PageRank pull path over the full in-edge list (which 0) or
+// the packed active list (1), from the iteration's tile arguments; builds the
+// list's plan if it is not current.
+static gg_status pull_args(gg_graph *g, int which, const TileArgs &a, PullArgs *pa)
+{
+    if (!g->plan[which].valid) {
+        gg_status st = build_pull_plan(g, which);
+        if (st != GG_OK) return st;
+    }
+    const PullPlan &pl = g->plan[which];
+    pa->src = which ? g->sp_src : g->in_src;
+    pa->row_ptr = which ? g->sp_ptr : g->in_ptr;
+    pa->nnz = which ? g->sp_nnz : g->full_nnz;
+    pa->hb = pl.hb;
+    pa->trow = pl.trow;
+    pa->nzv = pl.nzv;
+    pa->contrib = a.contrib_cur;
+    pa->acc = g->pull_acc;
+    pa->lead = g->pull_lead;
+    pa->n = g->n;
+    pa->rank_cur = a.rank_cur;
+    pa->rank_next = a.rank_next;
+    pa->contrib_next = a.contrib_next;
+    pa->out_ptr = g->out_ptr;
+    pa->deg_apply = a.deg_apply;
+    pa->base = a.base;
+    pa->damping = a.damping;
+    pa->epsilon = a.epsilon;
+    pa->n_f = a.n_f;
+    pa->hist_out = a.hist_out;
+    pa->stats = a.stats;
+    return GG_OK;
+}
+
 static gg_status run_pagerank(gg_graph *g, gg_policy policy, const gg_params *p)
 {
     const bool timing = (p->flags & GG_TIMING) != 0;
@@ -475,46 +509,33 @@ static gg_status run_pagerank(gg_graph *g, gg_policy policy, const gg_params *p)
                 if (st != GG_OK) return st;
             }
             GG_CUDA(launch_iter_header(a.stats, (uint32_t)mode, a.list_nnz, 0, g->stream));
-            if (kind == K_GATHER) {
+            if (kind == K_GATHER || !a.infl_share) {
+                // pull path: gathers over either list, corrections over the full one
                 const int which = mode == MODE_APPROX ? 1 : 0;
-                if (!g->plan[which].valid) {
-                    gg_status st = build_pull_plan(g, which);
-                    if (st != GG_OK) return st;
-                }
-                const PullPlan &pl = g->plan[which];
                 PullArgs pa{};
-                pa.src = which ? g->sp_src : g->in_src;
-                pa.nnz = a.list_nnz;
-                pa.hb = pl.hb;
-                pa.trow = pl.trow;
-                pa.tj = pl.tj;
-                pa.thead = pl.thead;
-                pa.nzb = pl.nzb;
-                pa.nzc = pl.nzc;
-                pa.contrib = a.contrib_cur;
-                pa.acc = g->pull_acc;
-                pa.lead = g->pull_lead;
-                pa.n = g->n;
-                pa.rank_cur = a.rank_cur;
-                pa.rank_next = a.rank_next;
-                pa.contrib_next = a.contrib_next;
-                pa.out_ptr = g->out_ptr;
-                pa.deg_apply = a.deg_apply;
-                pa.base = a.base;
-                pa.damping = a.damping;
-                pa.epsilon = a.epsilon;
-                pa.n_f = a.n_f;
-                pa.hist_out = a.hist_out;
-                pa.stats = a.stats;
-                timed_begin(g, timing, 0, &slot);
-                GG_CUDA(launch_pr_pull(pa, (uint32_t)pl.tiles, g->num_sms, g->stream));
+                gg_status st = pull_args(g, which, a, &pa);
+                if (st != GG_OK) return st;
+                timed_begin(g, timing, kind == K_CORRECT ? 1 : 0, &slot);
+                if (kind == K_GATHER) {
+                    GG_CUDA(launch_pr_pull(pa, (uint32_t)g->plan[which].tiles, g->num_sms, g->stream));
+                    g->launches += 2;
+                } else {
+                    pa.vals = reinterpret_cast<float *>(g->stash);
+                    pa.mask = g->mask;
+                    pa.theta = p->theta;
+                    GG_CUDA(launch_pr_correct(pa, (uint32_t)g->plan[which].tiles, g->num_sms, g->stream));
+                    GG_CUDA(launch_tile_counts(g->full_tile_info, g->full_tiles, (long long)g->n + g->m, g->in_ptr,
+                                               g->mask, g->tile_cnt, g->sp_ptr, g->num_sms, g->stream));
+                    g->launches += 4;
+                }
                 timed_end(g, slot);
             } else {
+                // share influence: the merge-path correction (stash + share pass)
                 timed_begin(g, timing, 1, &slot);
                 GG_CUDA(launch_tile_pr(kind, a, (int)g->max_tiles, g->num_sms, g->stream));
                 timed_end(g, slot);
+                g->launches += 2;
             }
-            g->launches += 3;
             if (tracing) {
                 gg_status st = trace_labels(g, true);
                 if (st != GG_OK) return st;

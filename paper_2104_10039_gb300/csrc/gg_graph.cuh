@@ -49,12 +49,12 @@ struct DevBuf {
 };
 
 // Plan of one list for the PageRank pull path (gg_pull.cu): row-start bits,
-// per-tile row ranks and first tiles, non-empty-row bitmap and counts.
+// per-tile row ranks, the vertex of every non-empty row, and the non-empty-row
+// bitmap and counts that rank them.
 struct PullPlan {
     DevBuf buf;
     uint32_t *hb = nullptr;
-    int32_t *trow = nullptr, *tj = nullptr;
-    uint8_t *thead = nullptr;
+    int32_t *trow = nullptr, *nzv = nullptr;
     uint32_t *nzb = nullptr, *nzc = nullptr, *nzcnt = nullptr;
     size_t hb_words = 0, tiles = 0, nzw = 0;
     bool valid = false;

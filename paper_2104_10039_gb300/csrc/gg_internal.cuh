@@ -122,16 +122,17 @@ enum TileKind { K_GATHER = 0, K_CORRECT = 1, K_STASH = 2 };
 // plan, and the vertex state of one iteration.
 struct PullArgs {
     const int32_t *src;         // list arcs: source vertex (no hub coding)
+    const int32_t *row_ptr;     // list row pointers (n + 1)
     const uint32_t *nnz;        // device scalar: arcs in the list
     const uint32_t *hb;         // plan: row-start bit per arc
     const int32_t *trow;        // plan: per tile, non-empty-row rank of the row holding its first arc
-    const int32_t *tj;          // plan: per tile, tile of that row's first arc
-    const uint8_t *thead;       // plan: per tile, a row starts inside it
-    const uint32_t *nzb;        // plan: non-empty row bitmap
-    const uint32_t *nzc;        // plan: non-empty rows before each bitmap word
+    const int32_t *nzv;         // plan: vertex of each non-empty row
     const float *contrib;       // gathered vector (rank / degree of the previous iteration)
-    float *acc;                 // per non-empty row: its sum
+    float *acc;                 // per vertex: its row's sum over the tile holding the row's first arc
     float *lead;                // per tile: the part before its first row start
+    float *vals;                // correction: every arc's contribution, in list order (or nullptr)
+    uint32_t *mask;             // correction: the new flag bitmap of the list
+    float theta;
     int32_t n;
     const float *rank_cur;
     float *rank_next;
@@ -275,8 +276,11 @@ cudaError_t launch_active_outdeg(const int32_t *sp_src, const uint32_t *sp_nnz, 
 // Source ids of a hub-coded list back to vertex ids (count read on the device).
 cudaError_t launch_decode_src(const int32_t *coded, const uint32_t *count, uint32_t max_count, const int32_t *hub_ids,
                               int32_t *out, int num_sms, cudaStream_t s);
-// PageRank pull iteration (gg_pull.cu): arcs, continued rows, apply.
+// PageRank pull iteration (gg_pull.cu): arcs, then apply.
 cudaError_t launch_pr_pull(const PullArgs &a, uint32_t max_tiles, int num_sms, cudaStream_t s);
+// PageRank correction over the full list (gg_pull.cu): arcs (values kept),
+// influence and flags, apply.
+cudaError_t launch_pr_correct(const PullArgs &a, uint32_t max_tiles, int num_sms, cudaStream_t s);
 // contrib[u] = rank[u] / deg[u], or / the full out-degree when deg is null (0 when the degree is 0).
 cudaError_t launch_contrib(int32_t n, const float *rank, const int32_t *deg, const int32_t *out_ptr,
                            float *contrib, int num_sms, cudaStream_t s);

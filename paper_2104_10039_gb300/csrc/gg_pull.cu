@@ -1,7 +1,7 @@
 // gg_pull.cu - the PageRank pull gather of approximate and accurate
 // iterations (Alg. 1 / Alg. 2: GG-Gather over a row's flagged in-edges,
-// GG-Apply, GG-VStatus) as three launches over a precomputed plan of the
-// list it walks.
+// GG-Apply, GG-VStatus) as two launches over a precomputed plan of the list
+// it walks.
 //
 // Why a separate path for PageRank: its gather reads one 4-byte value per arc
 // at a random address, and on this GPU those reads are bounded by how many
@@ -17,13 +17,12 @@
 //               tile (lane-local, then a warp scan) gives every row's total.
 //               A row whose first arc lies in the tile writes its total (or,
 //               if it continues past the tile, the part in the tile) to
-//               acc[k], k = its rank among the list's non-empty rows; the
-//               part of the tile before its first row start goes to
-//               lead[tile].
-//   k_pr_fix    every row continued across tile ends: its first part plus
-//               the later tiles' leading parts, in tile order.
-//   k_pr_apply  one thread per vertex: rank' = (1-d)/N + d acc (0 for a row
-//               with no arcs in the list), contrib' = rank' / degree, change
+//               acc[v]; the part of the tile before its first row start goes
+//               to lead[tile].
+//   k_pr_apply  one thread per vertex: the row's sum (acc[v] plus the later
+//               tiles' leading parts of a row continued across tile ends, in
+//               tile order; 0 for a row with no arcs in the list), then
+//               rank' = (1-d)/N + d sum, contrib' = rank' / degree, change
 //               statistics.
 //
 // The sums use a fixed grouping (lane-local prefix, warp scan, tile order),
@@ -31,9 +30,8 @@
 // whenever the list changes):
 //   hb[w]     bit j: arc 32w + j is the first arc of a row
 //   trow[t]   rank among non-empty rows of the row holding arc 256t
-//   tj[t]     tile of that row's first arc
-//   thead[t]  1 if a row starts inside tile t
-//   nzb[w]    bit j: row 32w + j has arcs;  nzc[w]: non-empty rows before row 32w
+//   nzv[k]    vertex of the k-th non-empty row
+//   nzb, nzc  non-empty-row bitmap and counts (to rank the rows)
 #include "gg_graph.cuh"
 
 namespace gg {
@@ -61,7 +59,7 @@ __global__ void k_plan_nz(const int32_t *__restrict__ ptr, int32_t n, uint32_t *
 
 __global__ void k_plan_heads(const int32_t *__restrict__ ptr, int32_t n, const uint32_t *__restrict__ nzb,
                              const uint32_t *__restrict__ nzc, uint32_t *__restrict__ hb,
-                             int32_t *__restrict__ trow, int32_t *__restrict__ tj, uint8_t *__restrict__ thead)
+                             int32_t *__restrict__ trow, int32_t *__restrict__ nzv)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
@@ -70,11 +68,8 @@ __global__ void k_plan_heads(const int32_t *__restrict__ ptr, int32_t n, const u
         const uint32_t w = (uint32_t)(v >> 5), bit = (uint32_t)(v & 31);
         const int32_t k = (int32_t)(nzc[w] + (uint32_t)__popc(nzb[w] & ((1u << bit) - 1u)));
         atomicOr(hb + (s >> 5), 1u << (s & 31));
-        thead[s >> 8] = 1;
-        for (long long t = ((long long)s + kPT - 1) / kPT; t * kPT < e; ++t) {
-            trow[t] = k;
-            tj[t] = s / kPT;
-        }
+        nzv[k] = (int32_t)v;
+        for (long long t = ((long long)s + kPT - 1) / kPT; t * kPT < e; ++t) trow[t] = k;
     }
 }
 
@@ -109,7 +104,10 @@ __device__ __forceinline__ uint32_t tail_bits(uint32_t word, int i, uint32_t rel
 }
 
 // ---------------------------------------------------------------- gather ----
-template <int MINB>
+// PF: the next tile's sources are loaded while this tile's values are in
+// flight (full tiles only). a.vals != nullptr (a correction's first pass):
+// every arc's contribution is also stored, in list order.
+template <int MINB, bool PF>
 __global__ void __launch_bounds__(kPullThreads, MINB) k_pr_arcs(PullArgs a)
 {
     constexpr uint32_t FULL = 0xFFFFFFFFu;
@@ -117,12 +115,17 @@ __global__ void __launch_bounds__(kPullThreads, MINB) k_pr_arcs(PullArgs a)
     const uint32_t nnz = *a.nnz;
     const long long nt = ((long long)nnz + kPT - 1) / kPT;
     const long long W = (long long)gridDim.x * (kPullThreads / 32);
+    int32_t pf[8];
+    bool have_pf = false;
     for (long long t = (long long)blockIdx.x * (kPullThreads / 32) + (threadIdx.x >> 5); t < nt; t += W) {
         const long long a0 = t * kPT;
         const uint32_t rel = nnz - (uint32_t)a0 < (uint32_t)kPT ? nnz - (uint32_t)a0 : (uint32_t)kPT;
         // ---- sources (16-byte loads) and their contributions -----------------
         int32_t s[8];
-        if (rel == (uint32_t)kPT) {
+        if (PF && have_pf) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) s[i] = pf[i];
+        } else if (rel == (uint32_t)kPT) {
             const int4 x = __ldg(reinterpret_cast<const int4 *>(a.src + a0) + lane);
             const int4 y = __ldg(reinterpret_cast<const int4 *>(a.src + a0 + 128) + lane);
             s[0] = x.x; s[1] = x.y; s[2] = x.z; s[3] = x.w;
@@ -138,6 +141,29 @@ __global__ void __launch_bounds__(kPullThreads, MINB) k_pr_arcs(PullArgs a)
         float v[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) v[i] = s[i] >= 0 ? __ldg(a.contrib + s[i]) : 0.0f;
+        if (a.vals) {
+            if (rel == (uint32_t)kPT) {
+                reinterpret_cast<float4 *>(a.vals + a0)[lane] = make_float4(v[0], v[1], v[2], v[3]);
+                reinterpret_cast<float4 *>(a.vals + a0 + 128)[lane] = make_float4(v[4], v[5], v[6], v[7]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t q = 4u * lane + (uint32_t)j;
+                    if (q < rel) a.vals[a0 + q] = v[j];
+                    if (q + 128u < rel) a.vals[a0 + 128 + q] = v[4 + j];
+                }
+            }
+        }
+        if (PF) {
+            const long long tn = t + W;
+            have_pf = tn < nt && (tn + 1) * kPT <= (long long)nnz;
+            if (have_pf) {
+                const int4 x = __ldg(reinterpret_cast<const int4 *>(a.src + tn * kPT) + lane);
+                const int4 y = __ldg(reinterpret_cast<const int4 *>(a.src + tn * kPT + 128) + lane);
+                pf[0] = x.x; pf[1] = x.y; pf[2] = x.z; pf[3] = x.w;
+                pf[4] = y.x; pf[5] = y.y; pf[6] = y.z; pf[7] = y.w;
+            }
+        }
         // ---- row starts of the tile ------------------------------------------
         uint4 h0 = __ldg(reinterpret_cast<const uint4 *>(a.hb + t * 8));
         uint4 h1 = __ldg(reinterpret_cast<const uint4 *>(a.hb + t * 8 + 4));
@@ -208,7 +234,7 @@ __global__ void __launch_bounds__(kPullThreads, MINB) k_pr_arcs(PullArgs a)
                         a.lead[t] = run[j];    // the row continued from an earlier tile
                     } else {
                         const uint32_t c = cnt + (uint32_t)__popc(f & ((2u << j) - 1u)) - h0bit;
-                        a.acc[tr + (int32_t)c] = run[j];
+                        a.acc[__ldg(a.nzv + tr + (int32_t)c)] = run[j];
                     }
                 }
             }
@@ -222,51 +248,167 @@ __global__ void __launch_bounds__(kPullThreads, MINB) k_pr_arcs(PullArgs a)
 
 namespace {
 
-// ----------------------------------------------------------------- fixup ----
-// A row that began in tile j < t and ends in tile t (a row starts inside t,
-// or the next tile starts with one, or t is the last tile): its part in tile
-// j (written by the gather to acc) plus the leading parts of tiles j+1 .. t,
-// in tile order. One thread per tile.
-__global__ void __launch_bounds__(kPullThreads) k_pr_fix(PullArgs a)
+// ------------------------------------------------------ correction flags ----
+// Second pass of a PageRank correction (Sec. 3.4, Alg. 2 GG-Gather influence
+// and GG-EStatus) over the full in-edge list, after k_pr_arcs stored every
+// arc's contribution: the running sum of its row before and after each arc,
+// influence (after - before) / after > theta tested as
+// (after - before) > theta * after, one flag bit per arc. The row continued
+// from earlier tiles starts from its carry: its part in the tile of its first
+// arc (acc[v]) plus the leading parts of the tiles in between, in tile order.
+__device__ __forceinline__ float warp_sum_fixed(float x)
 {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
+    return __shfl_sync(0xFFFFFFFFu, x, 0);
+}
+
+__global__ void __launch_bounds__(kPullThreads, 4) k_prc_flags(PullArgs a)
+{
+    constexpr uint32_t FULL = 0xFFFFFFFFu;
+    const uint32_t lane = threadIdx.x & 31u;
     const uint32_t nnz = *a.nnz;
     const long long nt = ((long long)nnz + kPT - 1) / kPT;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += stride) {
-        const int32_t j = a.tj[t];
-        if (j >= t) continue;
-        const bool ends_here = a.thead[t] || t == nt - 1 || a.tj[t + 1] == t + 1;
-        if (!ends_here) continue;
-        const int32_t k = a.trow[t];
-        float acc = a.acc[k];
-        for (long long u = (long long)j + 1; u <= t; ++u) acc += a.lead[u];
-        a.acc[k] = acc;
+    const long long mask_words = ((long long)nnz + 31) / 32;
+    const long long W = (long long)gridDim.x * (kPullThreads / 32);
+    for (long long t = (long long)blockIdx.x * (kPullThreads / 32) + (threadIdx.x >> 5); t < nt; t += W) {
+        const long long a0 = t * kPT;
+        const uint32_t rel = nnz - (uint32_t)a0 < (uint32_t)kPT ? nnz - (uint32_t)a0 : (uint32_t)kPT;
+        float v[8];
+        if (rel == (uint32_t)kPT) {
+            const float4 x = reinterpret_cast<const float4 *>(a.vals + a0)[lane];
+            const float4 y = reinterpret_cast<const float4 *>(a.vals + a0 + 128)[lane];
+            v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+            v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t q = 4u * lane + (uint32_t)j;
+                v[j] = q < rel ? a.vals[a0 + q] : 0.0f;
+                v[4 + j] = q + 128u < rel ? a.vals[a0 + 128 + q] : 0.0f;
+            }
+        }
+        uint4 h0 = __ldg(reinterpret_cast<const uint4 *>(a.hb + t * 8));
+        uint4 h1 = __ldg(reinterpret_cast<const uint4 *>(a.hb + t * 8 + 4));
+        if (rel < (uint32_t)kPT) {
+            h0.x = tail_bits(h0.x, 0, rel); h0.y = tail_bits(h0.y, 1, rel);
+            h0.z = tail_bits(h0.z, 2, rel); h0.w = tail_bits(h0.w, 3, rel);
+            h1.x = tail_bits(h1.x, 4, rel); h1.y = tail_bits(h1.y, 5, rel);
+            h1.z = tail_bits(h1.z, 6, rel); h1.w = tail_bits(h1.w, 7, rel);
+        }
+        // carry of the row open at the tile start (tiles that start mid-row)
+        float carry = 0.0f;
+        if (!(h0.x & 1u)) {
+            const int32_t vr = __ldg(a.nzv + __ldg(a.trow + t));
+            const long long j0 = __ldg(a.row_ptr + vr) / kPT;   // tile of the row's first arc (< t)
+            carry = a.acc[vr];
+            for (long long u0 = j0 + 1; u0 < t; u0 += 32) {
+                const long long u = u0 + lane;
+                carry = carry + warp_sum_fixed(u < t ? a.lead[u] : 0.0f);
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint4 hw = h ? h1 : h0;
+            const uint32_t sh = 4u * (lane & 7u);
+            const uint32_t f = (pick4(hw, lane >> 3) >> sh) & 0xFu;
+            const float v0 = v[4 * h], v1 = v[4 * h + 1], v2 = v[4 * h + 2], v3 = v[4 * h + 3];
+            // lane tails for the scan (as in k_pr_arcs)
+            const float r0 = v0;
+            const float r1 = (f & 2u) ? v1 : r0 + v1;
+            const float r2 = (f & 4u) ? v2 : r1 + v2;
+            const float r3 = (f & 8u) ? v3 : r2 + v3;
+            const uint32_t heads = __ballot_sync(FULL, f != 0u);
+            const uint32_t le = heads & (FULL >> (31u - lane));
+            const int start = le ? 31 - __clz(le) : -1;
+            float x = r3;
+            if (lane == 0 && f == 0u) x = carry + r3;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const float y = __shfl_up_sync(FULL, x, o);
+                if ((int)lane >= o && (int)lane - o >= start) x = y + x;
+            }
+            float run = __shfl_up_sync(FULL, x, 1);
+            if (lane == 0) run = carry;
+            // running sums before / after each arc, in arc order from the
+            // segment's value at the lane start
+            uint32_t nib = 0;
+            const float vv[4] = {v0, v1, v2, v3};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t q = 128u * (uint32_t)h + 4u * lane + (uint32_t)j;
+                const float before = ((f >> j) & 1u) ? 0.0f : run;
+                const float after = __fadd_rn(before, vv[j]);
+                run = after;
+                const bool fl = after != 0.0f ? __fsub_rn(after, before) > __fmul_rn(a.theta, after)
+                                              : 0.0f > a.theta;
+                if (fl && q < rel) nib |= 1u << j;
+            }
+            uint32_t word = nib << sh;
+            word |= __shfl_xor_sync(FULL, word, 1);
+            word |= __shfl_xor_sync(FULL, word, 2);
+            word |= __shfl_xor_sync(FULL, word, 4);
+            const long long wi = t * 8 + 4 * h + (lane >> 3);
+            if ((lane & 7u) == 0 && wi < mask_words) a.mask[wi] = word;
+            carry = __shfl_sync(FULL, x, 31);
+        }
     }
 }
 
 // ----------------------------------------------------------------- apply ----
-// GG-Apply + GG-VStatus (Alg. 2) for every vertex, in vertex order.
+// GG-Apply + GG-VStatus (Alg. 2) for every vertex, in vertex order. A row's
+// sum is acc[v] (written by the tile holding its first arc), plus, for a row
+// continued across tile ends, the leading parts of the later tiles it covers,
+// in tile order; a row with no arcs in the list sums to 0. Each thread takes
+// four vertices a stride apart per step, all loads issued first.
 __global__ void __launch_bounds__(kPullThreads) k_pr_apply(PullArgs a)
 {
+    constexpr int U = 4;
     unsigned long long changed = 0, sum = 0;
     uint32_t mx = 0;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += stride) {
-        const uint32_t w = (uint32_t)(v >> 5), bit = (uint32_t)(v & 31);
-        const uint32_t word = __ldg(a.nzb + w);
-        float acc = 0.0f;
-        if ((word >> bit) & 1u) acc = a.acc[__ldg(a.nzc + w) + (uint32_t)__popc(word & ((1u << bit) - 1u))];
-        const float old = a.rank_cur[v];
-        const int32_t deg = a.deg_apply ? a.deg_apply[v] : __ldg(a.out_ptr + v + 1) - __ldg(a.out_ptr + v);
-        const float nw = __fmaf_rn(a.damping, acc, a.base);
-        const float delta = fabsf(__fsub_rn(nw, old));
-        a.rank_next[v] = nw;
-        a.contrib_next[v] = deg > 0 ? __fdiv_rn(nw, (float)deg) : 0.0f;
-        if (a.hist_out) a.hist_out[v] = __fmul_rn(a.n_f, delta);
-        changed += delta > a.epsilon ? 1ull : 0ull;
-        sum += __float2ull_rz(delta * 1099511627776.0f);   // fixed point 2^-40
-        const uint32_t db = __float_as_uint(delta);
-        mx = db > mx ? db : mx;
+    const long long S = (long long)gridDim.x * blockDim.x;
+    for (long long v0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; v0 < a.n; v0 += U * S) {
+        int32_t rs[U], re[U], d[U];
+        float old[U], acc[U];
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+            const long long v = v0 + i * S;
+            rs[i] = re[i] = d[i] = 0;
+            old[i] = acc[i] = 0.0f;
+            if (v < a.n) {
+                rs[i] = __ldg(a.row_ptr + v);
+                re[i] = __ldg(a.row_ptr + v + 1);
+                acc[i] = a.acc[v];   // stale for a row without arcs: replaced by 0 below
+                old[i] = a.rank_cur[v];
+                d[i] = a.deg_apply ? a.deg_apply[v] : __ldg(a.out_ptr + v + 1) - __ldg(a.out_ptr + v);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+            if (re[i] > rs[i]) {
+                const int32_t t0 = rs[i] / kPT, t1 = (re[i] - 1) / kPT;
+                float x = acc[i];
+#pragma unroll 4
+                for (int32_t u = t0 + 1; u <= t1; ++u) x += a.lead[u];
+                acc[i] = x;
+            } else {
+                acc[i] = 0.0f;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+            const long long v = v0 + i * S;
+            if (v >= a.n) continue;
+            const float nw = __fmaf_rn(a.damping, acc[i], a.base);
+            const float delta = fabsf(__fsub_rn(nw, old[i]));
+            a.rank_next[v] = nw;
+            a.contrib_next[v] = d[i] > 0 ? __fdiv_rn(nw, (float)d[i]) : 0.0f;
+            if (a.hist_out) a.hist_out[v] = __fmul_rn(a.n_f, delta);
+            changed += delta > a.epsilon ? 1ull : 0ull;
+            sum += __float2ull_rz(delta * 1099511627776.0f);   // fixed point 2^-40
+            const uint32_t db = __float_as_uint(delta);
+            mx = db > mx ? db : mx;
+        }
     }
     if (!a.stats) return;
 #pragma unroll
@@ -287,17 +429,30 @@ __global__ void __launch_bounds__(kPullThreads) k_pr_apply(PullArgs a)
 
 cudaError_t launch_pr_pull(const PullArgs &a, uint32_t max_tiles, int num_sms, cudaStream_t s)
 {
-    const int arc_blocks_per_sm = 5;
+    constexpr int arc_blocks_per_sm = 4;
+    constexpr bool prefetch = true;
     long long blocks = ((long long)max_tiles + kPullThreads / 32 - 1) / (kPullThreads / 32);
     if (blocks > (long long)num_sms * arc_blocks_per_sm) blocks = (long long)num_sms * arc_blocks_per_sm;
     if (blocks < 1) blocks = 1;
-    k_pr_arcs<arc_blocks_per_sm><<<(unsigned)blocks, kPullThreads, 0, s>>>(a);
-    long long fb = ((long long)max_tiles + kPullThreads - 1) / kPullThreads;
-    if (fb > (long long)num_sms * 8) fb = (long long)num_sms * 8;
-    if (fb < 1) fb = 1;
-    k_pr_fix<<<(unsigned)fb, kPullThreads, 0, s>>>(a);
+    k_pr_arcs<arc_blocks_per_sm, prefetch><<<(unsigned)blocks, kPullThreads, 0, s>>>(a);
+    // persistent: the blocks one wave holds (48 registers: 5 blocks of 256 per SM)
     long long ab = ((long long)a.n + kPullThreads - 1) / kPullThreads;
-    if (ab > (long long)num_sms * 8) ab = (long long)num_sms * 8;
+    if (ab > (long long)num_sms * 5) ab = (long long)num_sms * 5;
+    if (ab < 1) ab = 1;
+    k_pr_apply<<<(unsigned)ab, kPullThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pr_correct(const PullArgs &a, uint32_t max_tiles, int num_sms, cudaStream_t s)
+{
+    constexpr int arc_blocks_per_sm = 4;
+    long long blocks = ((long long)max_tiles + kPullThreads / 32 - 1) / (kPullThreads / 32);
+    if (blocks > (long long)num_sms * arc_blocks_per_sm) blocks = (long long)num_sms * arc_blocks_per_sm;
+    if (blocks < 1) blocks = 1;
+    k_pr_arcs<arc_blocks_per_sm, true><<<(unsigned)blocks, kPullThreads, 0, s>>>(a);
+    k_prc_flags<<<(unsigned)blocks, kPullThreads, 0, s>>>(a);
+    long long ab = ((long long)a.n + kPullThreads - 1) / kPullThreads;
+    if (ab > (long long)num_sms * 5) ab = (long long)num_sms * 5;
     if (ab < 1) ab = 1;
     k_pr_apply<<<(unsigned)ab, kPullThreads, 0, s>>>(a);
     return cudaGetLastError();
@@ -309,8 +464,8 @@ gg_status ensure_pull(gg_graph *g)
     if (g->pull_ready) return GG_OK;
     const size_t tiles = ((size_t)g->m + kPT - 1) / kPT + 1;
     const size_t nzw = ((size_t)g->n + 31) / 32 + 1;
-    // per plan: hb (8 words per tile + 8), trow, tj (tiles + 1 each), nzb, nzc, nzcnt, thead (bytes)
-    const size_t words = 8 * tiles + 8 + 2 * (tiles + 1) + 3 * nzw + (tiles + 1 + 15) / 4 + 8;
+    // per plan: hb (8 words per tile + 8), trow (tiles + 1), nzb, nzc, nzcnt, nzv (n + 4)
+    const size_t words = 8 * tiles + 8 + (tiles + 1) + 3 * nzw + ((size_t)g->n + 4) + 8;
     for (int i = 0; i < 2; ++i) {
         PullPlan &p = g->plan[i];
         gg_status st = p.buf.alloc(4 * words, g->stream);
@@ -318,11 +473,10 @@ gg_status ensure_pull(gg_graph *g)
         uint32_t *w = p.buf.u32();
         p.hb = w; w += 8 * tiles + 8;
         p.trow = (int32_t *)w; w += tiles + 1;
-        p.tj = (int32_t *)w; w += tiles + 1;
         p.nzb = w; w += nzw;
         p.nzc = w; w += nzw;
         p.nzcnt = w; w += nzw;
-        p.thead = (uint8_t *)w;
+        p.nzv = (int32_t *)w;
         p.hb_words = 8 * tiles + 8;
         p.tiles = tiles;
         p.nzw = nzw;
@@ -343,7 +497,6 @@ gg_status build_pull_plan(gg_graph *g, int which)
     const int32_t *ptr = which ? g->sp_ptr : g->in_ptr;
     cudaStream_t s = g->stream;
     GG_CUDA(cudaMemsetAsync(p.hb, 0, 4 * p.hb_words, s));
-    GG_CUDA(cudaMemsetAsync(p.thead, 0, p.tiles + 1, s));
     int grid = (int)(((size_t)g->n + 255) / 256);
     if (grid > g->num_sms * 8) grid = g->num_sms * 8;
     if (grid < 1) grid = 1;
@@ -353,7 +506,7 @@ gg_status build_pull_plan(gg_graph *g, int which)
     // nzc[words], inside the array: nzw = words + 1)
     const size_t words = ((size_t)g->n + 31) / 32;
     GG_CUDA(launch_scan_u32(p.nzcnt, p.nzc, words, g->scan_tmp, s));
-    k_plan_heads<<<grid, 256, 0, s>>>(ptr, g->n, p.nzb, p.nzc, p.hb, p.trow, p.tj, p.thead);
+    k_plan_heads<<<grid, 256, 0, s>>>(ptr, g->n, p.nzb, p.nzc, p.hb, p.trow, p.nzv);
     GG_CUDA(cudaGetLastError());
     g->launches += 7;
     p.valid = true;
