@@ -190,8 +190,8 @@ static void fill_list(const gg_graph *g, bool sparse, TileArgs &a)
 
 // After a correction or sampling pass: place the tiles' local packs into the
 // packed active in-edge list and partition it for the next gathers.
-// plain: pack vertex ids (the PageRank pull path reads them) rather than the
-// hub-coded sources the other gathers read.
+// plain: pack vertex ids (the pull path reads them) rather than the
+// hub-coded sources of the merge-path kernels.
 static gg_status finish_pack(gg_graph *g, bool weighted, IterStatsDev *stats, bool plain = false)
 {
     GG_CUDA(launch_scan_u32(g->tile_cnt, g->tile_off, g->full_tiles, g->scan_tmp, g->stream));
@@ -405,13 +405,17 @@ static gg_status learned_correct(gg_graph *g, gg_app app, TileArgs a, uint32_t n
     return GG_OK;
 }
 
-// Arguments of the PageRank pull path over the full in-edge list (which 0) or
-// the packed active list (1), from the iteration's tile arguments; builds the
-// list's plan if it is not current.
+// Arguments of the pull path over the full in-edge list (which 0) or the
+// packed active list (1), from the iteration's tile arguments; builds the
+// list's plan if it is not current (and, on the graph's first pull, the
+// plans' and row sums' buffers).
 static gg_status pull_args(gg_graph *g, int which, const TileArgs &a, PullArgs *pa)
 {
+    gg_status st = ensure_pull(g);   // plans and row-sum buffers (first pull on this graph)
+    if (st == GG_OK && which == 1) st = sp_plain(g);
+    if (st != GG_OK) return st;
     if (!g->plan[which].valid) {
-        gg_status st = build_pull_plan(g, which);
+        st = build_pull_plan(g, which);
         if (st != GG_OK) return st;
     }
     const PullPlan &pl = g->plan[which];
@@ -436,6 +440,11 @@ static gg_status pull_args(gg_graph *g, int which, const TileArgs &a, PullArgs *
     pa->n_f = a.n_f;
     pa->hist_out = a.hist_out;
     pa->stats = a.stats;
+    pa->val_cur = a.val_cur;
+    pa->val_next = a.val_next;
+    pa->q_out = a.q_out;
+    pa->q_out_val = a.q_out_val;
+    pa->q_out_len = a.q_out_len;
     return GG_OK;
 }
 
@@ -446,11 +455,6 @@ static gg_status run_pagerank(gg_graph *g, gg_policy policy, const gg_params *p)
     const bool learned_policy = policy == GG_POLICY_LEARNED;
     Trigger trig(policy, p);
     g->cur = 0;
-    {
-        gg_status st = ensure_pull(g);
-        if (st == GG_OK) st = sp_plain(g);
-        if (st != GG_OK) return st;
-    }
     GG_CUDA(launch_init_pr(g->n, g->out_ptr, g->rank[0], g->contrib[0], g->num_sms, g->stream));
     g->launches += 1;
     if (renorm) {
@@ -517,13 +521,15 @@ static gg_status run_pagerank(gg_graph *g, gg_policy policy, const gg_params *p)
                 if (st != GG_OK) return st;
                 timed_begin(g, timing, kind == K_CORRECT ? 1 : 0, &slot);
                 if (kind == K_GATHER) {
-                    GG_CUDA(launch_pr_pull(pa, (uint32_t)g->plan[which].tiles, g->num_sms, g->stream));
+                    GG_CUDA(launch_pull(GG_APP_PAGERANK, pa, false, (uint32_t)g->plan[which].tiles, g->num_sms,
+                                        g->stream));
                     g->launches += 2;
                 } else {
                     pa.vals = reinterpret_cast<float *>(g->stash);
                     pa.mask = g->mask;
                     pa.theta = p->theta;
-                    GG_CUDA(launch_pr_correct(pa, (uint32_t)g->plan[which].tiles, g->num_sms, g->stream));
+                    GG_CUDA(launch_pull(GG_APP_PAGERANK, pa, true, (uint32_t)g->plan[which].tiles, g->num_sms,
+                                        g->stream));
                     GG_CUDA(launch_tile_counts(g->full_tile_info, g->full_tiles, (long long)g->n + g->m, g->in_ptr,
                                                g->mask, g->tile_cnt, g->sp_ptr, g->num_sms, g->stream));
                     g->launches += 4;
@@ -726,18 +732,34 @@ static gg_status run_min(gg_graph *g, gg_app app, gg_policy policy, const gg_par
                     if (st != GG_OK) return st;
                 }
                 GG_CUDA(launch_iter_header(sti, (uint32_t)mode, nullptr, list_nnz, g->stream));
+                const int which = mode == MODE_APPROX ? 1 : 0;
+                PullArgs pa{};
+                st = pull_args(g, which, a, &pa);
+                if (st != GG_OK) return st;
+                pa.w = (app == GG_APP_SSSP && g->has_w) ? (which ? g->sp_w : g->in_w) : nullptr;
                 timed_begin(g, timing, kind == K_CORRECT ? 1 : 0, &slot);
-                GG_CUDA(launch_tile_min((int)app, kind, a, (int)g->max_tiles, g->num_sms, g->stream));
-                if (kind == K_GATHER) GG_CUDA(launch_fixup((int)app, a, (int)g->max_tiles, g->num_sms, g->stream));
+                if (kind == K_CORRECT) {
+                    pa.vals = reinterpret_cast<float *>(g->stash);
+                    pa.mask = g->mask;
+                    pa.theta_case = theta_case;
+                    pa.theta_fx = theta_fx;
+                    pa.est_strict = (p->flags & GG_EST_STRICT) ? 1 : 0;
+                }
+                GG_CUDA(launch_pull((int)app, pa, kind == K_CORRECT, (uint32_t)g->plan[which].tiles, g->num_sms,
+                                    g->stream));
+                if (kind == K_CORRECT) {
+                    GG_CUDA(launch_tile_counts(g->full_tile_info, g->full_tiles, (long long)g->n + g->m, g->in_ptr,
+                                               g->mask, g->tile_cnt, g->sp_ptr, g->num_sms, g->stream));
+                }
                 timed_end(g, slot);
-                g->launches += 3;
+                g->launches += kind == K_CORRECT ? 4 : 2;
                 if (tracing) {
                     st = trace_labels(g, false);
                     if (st != GG_OK) return st;
                 }
             }
             if (kind == K_CORRECT) {
-                st = finish_pack(g, app == GG_APP_SSSP && g->has_w, sti);
+                st = finish_pack(g, app == GG_APP_SSSP && g->has_w, sti, true);
                 if (st != GG_OK) return st;
                 g->sample_clean = false;
                 g->stats.corrections += 1;
@@ -843,7 +865,7 @@ gg_status run(gg_graph *g, gg_app app, double ratio, gg_policy policy, const gg_
     GG_CUDA(cudaEventRecord(g->ev_run0, g->stream));
     if (policy != GG_POLICY_EXACT &&
         !(g->sampled && g->sample_clean && g->sample_ratio == ratio && g->sample_seed == p->seed)) {
-        st = sample_edges(g, ratio, p->seed, app == GG_APP_PAGERANK);
+        st = sample_edges(g, ratio, p->seed, true);
         if (st != GG_OK) return st;
     }
     st = app == GG_APP_PAGERANK ? run_pagerank(g, policy, p) : run_min(g, app, policy, p);
@@ -1041,7 +1063,7 @@ gg_status gg_load_csr(gg_graph **out, int32_t n, int64_t m, const int32_t *rowpt
 gg_status gg_sample_edges(gg_graph *g, double sample_ratio, uint64_t seed)
 {
     if (!g) { set_error("gg_sample_edges: graph is NULL"); return GG_ERR_INVALID_ARG; }
-    return sample_edges(g, sample_ratio, seed, false);
+    return sample_edges(g, sample_ratio, seed, true);
 }
 
 gg_status gg_run(gg_graph *g, gg_app app, double sample_ratio, gg_policy policy, const gg_params *p)

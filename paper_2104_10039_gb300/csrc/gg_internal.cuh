@@ -130,9 +130,18 @@ struct PullArgs {
     const float *contrib;       // gathered vector (rank / degree of the previous iteration)
     float *acc;                 // per vertex: its row's sum over the tile holding the row's first arc
     float *lead;                // per tile: the part before its first row start
-    float *vals;                // correction: every arc's contribution, in list order (or nullptr)
-    uint32_t *mask;             // correction: the new flag bitmap of the list
-    float theta;
+    float *vals;                // correction: every arc's value (contribution / candidate), in list order
+    uint32_t *mask;             // correction: the flag bitmap of the list (old flags in, new flags out)
+    float theta;                // PageRank correction threshold
+    int theta_case;             // SSSP / BFS / CC correction: 0 compare, 1 theta < 0, 2 theta >= 1
+    unsigned long long theta_fx;   // ... floor(theta 2^32)
+    int est_strict;             // ... arcs without a candidate lose their flag
+    const uint32_t *w;          // SSSP: list arcs' weights, or nullptr (weight 1)
+    const uint32_t *val_cur;    // SSSP / BFS / CC values
+    uint32_t *val_next;
+    int32_t *q_out;             // SSSP / BFS / CC: next frontier (vertex, value), length
+    uint32_t *q_out_val;
+    uint32_t *q_out_len;
     int32_t n;
     const float *rank_cur;
     float *rank_next;
@@ -276,11 +285,9 @@ cudaError_t launch_active_outdeg(const int32_t *sp_src, const uint32_t *sp_nnz, 
 // Source ids of a hub-coded list back to vertex ids (count read on the device).
 cudaError_t launch_decode_src(const int32_t *coded, const uint32_t *count, uint32_t max_count, const int32_t *hub_ids,
                               int32_t *out, int num_sms, cudaStream_t s);
-// PageRank pull iteration (gg_pull.cu): arcs, then apply.
-cudaError_t launch_pr_pull(const PullArgs &a, uint32_t max_tiles, int num_sms, cudaStream_t s);
-// PageRank correction over the full list (gg_pull.cu): arcs (values kept),
-// influence and flags, apply.
-cudaError_t launch_pr_correct(const PullArgs &a, uint32_t max_tiles, int num_sms, cudaStream_t s);
+// Pull iteration of an application (gg_pull.cu): arcs, then apply; with
+// `correct`, arcs (values kept), influence and flags, then apply.
+cudaError_t launch_pull(int app, const PullArgs &a, bool correct, uint32_t max_tiles, int num_sms, cudaStream_t s);
 // contrib[u] = rank[u] / deg[u], or / the full out-degree when deg is null (0 when the degree is 0).
 cudaError_t launch_contrib(int32_t n, const float *rank, const int32_t *deg, const int32_t *out_ptr,
                            float *contrib, int num_sms, cudaStream_t s);

@@ -1,32 +1,40 @@
-// gg_pull.cu - the PageRank pull gather of approximate and accurate
-// iterations (Alg. 1 / Alg. 2: GG-Gather over a row's flagged in-edges,
-// GG-Apply, GG-VStatus) as two launches over a precomputed plan of the list
-// it walks.
+// gg_pull.cu - the pull iterations of every application: approximate and
+// accurate gathers (Alg. 1 / Alg. 2: GG-Gather over a row's flagged in-edges,
+// GG-Apply, GG-VStatus) and corrections (influence, GG-EStatus) over a
+// precomputed plan of the list they walk.
 //
-// Why a separate path for PageRank: its gather reads one 4-byte value per arc
-// at a random address, and on this GPU those reads are bounded by how many
-// scattered L1 misses each SM keeps in flight (the L1 capacity left beside
-// shared memory), not by DRAM. This path therefore keeps the arc work free of
-// shared memory: every lane holds its arcs' values in registers, row
-// boundaries come from a bit per arc computed once per list, and the vertex
-// work (apply, change statistics) is a separate coalesced pass.
+// A gather reads one 4-byte value per arc at a random address, and on this
+// GPU those reads are bounded by how many scattered L1 misses each SM keeps
+// in flight (the L1 capacity left beside shared memory), not by DRAM. These
+// kernels therefore keep the arc work free of shared memory: every lane holds
+// its arcs' values in registers, row boundaries come from a bit per arc
+// computed once per list, and the vertex work (apply, change statistics,
+// frontier) is a separate coalesced pass.
 //
-//   k_pr_arcs   warp tiles of kPT = 256 consecutive arcs; lane L takes arcs
-//               4L..4L+3 and 128+4L..128+4L+3 (two 16-byte source loads),
-//               fetches their contributions, and a segmented sum over the
-//               tile (lane-local, then a warp scan) gives every row's total.
-//               A row whose first arc lies in the tile writes its total (or,
-//               if it continues past the tile, the part in the tile) to
-//               acc[v]; the part of the tile before its first row start goes
-//               to lead[tile].
-//   k_pr_apply  one thread per vertex: the row's sum (acc[v] plus the later
-//               tiles' leading parts of a row continued across tile ends, in
-//               tile order; 0 for a row with no arcs in the list), then
-//               rank' = (1-d)/N + d sum, contrib' = rank' / degree, change
-//               statistics.
+//   k_pull_arcs  warp tiles of kPT = 256 consecutive arcs; lane L takes arcs
+//                4L..4L+3 and 128+4L..128+4L+3 (two 16-byte source loads, and
+//                weights for SSSP), fetches their values, and a segmented
+//                fold over the tile (lane-local, then a warp scan) gives every
+//                row's total: a sum of contributions for PageRank, a minimum of
+//                candidates for SSSP / BFS / CC. A row whose first arc lies in
+//                the tile writes its total (or, if it continues past the tile,
+//                the part in the tile) to acc[v]; the part of the tile before
+//                its first row start goes to lead[tile].
+//   k_prc_flags, k_minc_flags
+//                a correction's second pass: every arc's influence from the
+//                running value of its row before and after it (the values kept
+//                by the first pass, the carry of a continued row from acc and
+//                the leads), one flag bit per arc.
+//   k_pr_apply, k_min_apply
+//                one thread per vertex: the row's total (acc[v] folded with the
+//                later tiles' leading parts of a row continued across tile
+//                ends, in tile order; the identity for a row with no arcs in
+//                the list), then GG-Apply and GG-VStatus (PageRank: rank',
+//                contrib', change statistics; SSSP / BFS / CC: the minimum with
+//                the old value, the changed vertices appended to the frontier).
 //
 // The sums use a fixed grouping (lane-local prefix, warp scan, tile order),
-// so results are deterministic. The plan of a list (built by build_pull_plan
+// so PageRank results are deterministic (the minimum is exact anyway). The plan of a list (built by build_pull_plan
 // whenever the list changes):
 //   hb[w]     bit j: arc 32w + j is the first arc of a row
 //   trow[t]   rank among non-empty rows of the row holding arc 256t
@@ -103,54 +111,113 @@ __device__ __forceinline__ uint32_t tail_bits(uint32_t word, int i, uint32_t rel
     return word | ~((1u << (rel - lo)) - 1u);
 }
 
+// What a pull gather folds per application: PageRank sums contributions
+// (FP32, identity 0); SSSP / BFS / CC take the minimum of candidates (exact,
+// identity INF): SSSP value + weight and BFS value + 1, saturating at INF (a
+// candidate that would reach INF is no candidate), CC the label itself.
+template <int APP>
+struct PullOp {
+    using T = uint32_t;
+    static __device__ __forceinline__ T id() { return kInf; }
+    static __device__ __forceinline__ T op(T x, T y) { return x < y ? x : y; }
+    static __device__ __forceinline__ T cand(const PullArgs &a, int32_t src, uint32_t w)
+    {
+        const uint32_t u = __ldg(a.val_cur + src);
+        if (APP == GG_APP_CC) return u;
+        const unsigned long long c = (unsigned long long)u + (APP == GG_APP_BFS ? 1u : w);
+        return (u == kInf || c >= kInf) ? kInf : (uint32_t)c;
+    }
+};
+template <>
+struct PullOp<GG_APP_PAGERANK> {
+    using T = float;
+    static __device__ __forceinline__ T id() { return 0.0f; }
+    static __device__ __forceinline__ T op(T x, T y) { return x + y; }
+    static __device__ __forceinline__ T cand(const PullArgs &a, int32_t src, uint32_t)
+    {
+        return __ldg(a.contrib + src);
+    }
+};
+
 // ---------------------------------------------------------------- gather ----
-// PF: the next tile's sources are loaded while this tile's values are in
-// flight (full tiles only). a.vals != nullptr (a correction's first pass):
-// every arc's contribution is also stored, in list order.
-template <int MINB, bool PF>
-__global__ void __launch_bounds__(kPullThreads, MINB) k_pr_arcs(PullArgs a)
+// PF: the next tile's sources (and weights) are loaded while this tile's
+// values are in flight (full tiles only). a.vals != nullptr (a correction's
+// first pass): every arc's value is also stored, in list order.
+template <int APP, int MINB, bool PF>
+__global__ void __launch_bounds__(kPullThreads, MINB) k_pull_arcs(PullArgs a)
 {
+    using Op = PullOp<APP>;
+    using T = typename Op::T;
     constexpr uint32_t FULL = 0xFFFFFFFFu;
+    constexpr bool kW = APP == GG_APP_SSSP;
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t nnz = *a.nnz;
     const long long nt = ((long long)nnz + kPT - 1) / kPT;
     const long long W = (long long)gridDim.x * (kPullThreads / 32);
+    const bool has_w = kW && a.w != nullptr;
     int32_t pf[8];
+    uint32_t pw[kW ? 8 : 1];
     bool have_pf = false;
     for (long long t = (long long)blockIdx.x * (kPullThreads / 32) + (threadIdx.x >> 5); t < nt; t += W) {
         const long long a0 = t * kPT;
         const uint32_t rel = nnz - (uint32_t)a0 < (uint32_t)kPT ? nnz - (uint32_t)a0 : (uint32_t)kPT;
-        // ---- sources (16-byte loads) and their contributions -----------------
+        // ---- sources (16-byte loads), weights, and the arcs' values ----------
         int32_t s[8];
+        uint32_t w[kW ? 8 : 1];
         if (PF && have_pf) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) s[i] = pf[i];
+            for (int i = 0; i < 8; ++i) {
+                s[i] = pf[i];
+                if constexpr (kW) w[i] = pw[i];
+            }
         } else if (rel == (uint32_t)kPT) {
             const int4 x = __ldg(reinterpret_cast<const int4 *>(a.src + a0) + lane);
             const int4 y = __ldg(reinterpret_cast<const int4 *>(a.src + a0 + 128) + lane);
             s[0] = x.x; s[1] = x.y; s[2] = x.z; s[3] = x.w;
             s[4] = y.x; s[5] = y.y; s[6] = y.z; s[7] = y.w;
+            if constexpr (kW) {
+                if (has_w) {
+                    const uint4 p = __ldg(reinterpret_cast<const uint4 *>(a.w + a0) + lane);
+                    const uint4 q = __ldg(reinterpret_cast<const uint4 *>(a.w + a0 + 128) + lane);
+                    w[0] = p.x; w[1] = p.y; w[2] = p.z; w[3] = p.w;
+                    w[4] = q.x; w[5] = q.y; w[6] = q.z; w[7] = q.w;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) w[i] = 1u;
+                }
+            }
         } else {
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const uint32_t q = 4u * lane + (uint32_t)j;
                 s[j] = q < rel ? a.src[a0 + q] : -1;
                 s[4 + j] = q + 128u < rel ? a.src[a0 + 128 + q] : -1;
+                if constexpr (kW) {
+                    w[j] = (has_w && q < rel) ? a.w[a0 + q] : 1u;
+                    w[4 + j] = (has_w && q + 128u < rel) ? a.w[a0 + 128 + q] : 1u;
+                }
             }
         }
-        float v[8];
+        T v[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = s[i] >= 0 ? __ldg(a.contrib + s[i]) : 0.0f;
+        for (int i = 0; i < 8; ++i) v[i] = s[i] >= 0 ? Op::cand(a, s[i], kW ? w[kW ? i : 0] : 1u) : Op::id();
         if (a.vals) {
+            uint32_t *vb = reinterpret_cast<uint32_t *>(a.vals);
+            uint32_t b[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if constexpr (APP == GG_APP_PAGERANK) b[i] = __float_as_uint(v[i]);
+                else b[i] = v[i];
+            }
             if (rel == (uint32_t)kPT) {
-                reinterpret_cast<float4 *>(a.vals + a0)[lane] = make_float4(v[0], v[1], v[2], v[3]);
-                reinterpret_cast<float4 *>(a.vals + a0 + 128)[lane] = make_float4(v[4], v[5], v[6], v[7]);
+                reinterpret_cast<uint4 *>(vb + a0)[lane] = make_uint4(b[0], b[1], b[2], b[3]);
+                reinterpret_cast<uint4 *>(vb + a0 + 128)[lane] = make_uint4(b[4], b[5], b[6], b[7]);
             } else {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const uint32_t q = 4u * lane + (uint32_t)j;
-                    if (q < rel) a.vals[a0 + q] = v[j];
-                    if (q + 128u < rel) a.vals[a0 + 128 + q] = v[4 + j];
+                    if (q < rel) vb[a0 + q] = b[j];
+                    if (q + 128u < rel) vb[a0 + 128 + q] = b[4 + j];
                 }
             }
         }
@@ -162,6 +229,17 @@ __global__ void __launch_bounds__(kPullThreads, MINB) k_pr_arcs(PullArgs a)
                 const int4 y = __ldg(reinterpret_cast<const int4 *>(a.src + tn * kPT + 128) + lane);
                 pf[0] = x.x; pf[1] = x.y; pf[2] = x.z; pf[3] = x.w;
                 pf[4] = y.x; pf[5] = y.y; pf[6] = y.z; pf[7] = y.w;
+                if constexpr (kW) {
+                    if (has_w) {
+                        const uint4 p = __ldg(reinterpret_cast<const uint4 *>(a.w + tn * kPT) + lane);
+                        const uint4 q = __ldg(reinterpret_cast<const uint4 *>(a.w + tn * kPT + 128) + lane);
+                        pw[0] = p.x; pw[1] = p.y; pw[2] = p.z; pw[3] = p.w;
+                        pw[4] = q.x; pw[5] = q.y; pw[6] = q.z; pw[7] = q.w;
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) pw[i] = 1u;
+                    }
+                }
             }
         }
         // ---- row starts of the tile ------------------------------------------
@@ -184,7 +262,7 @@ __global__ void __launch_bounds__(kPullThreads, MINB) k_pr_arcs(PullArgs a)
         }
         const int32_t tr = __ldg(a.trow + t);
         const uint32_t h0bit = h0.x & 1u;
-        float carry = 0.0f;      // running value of the segment open at the end of the previous half
+        T carry = Op::id();      // running value of the segment open at the end of the previous half
         uint32_t before = 0;     // row starts in earlier halves
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -200,41 +278,43 @@ __global__ void __launch_bounds__(kPullThreads, MINB) k_pr_arcs(PullArgs a)
             uint32_t nxt = __shfl_down_sync(FULL, f, 1) & 1u;
             if (lane == 31) nxt = h == 0 ? (h1.x & 1u) : next_head;
             // lane-local running values, restarting at row starts
-            const float v0 = v[4 * h], v1 = v[4 * h + 1], v2 = v[4 * h + 2], v3 = v[4 * h + 3];
-            const float r0 = v0;
-            const float r1 = (f & 2u) ? v1 : r0 + v1;
-            const float r2 = (f & 4u) ? v2 : r1 + v2;
-            const float r3 = (f & 8u) ? v3 : r2 + v3;
+            const T v0 = v[4 * h], v1 = v[4 * h + 1], v2 = v[4 * h + 2], v3 = v[4 * h + 3];
+            const T r0 = v0;
+            const T r1 = (f & 2u) ? v1 : Op::op(r0, v1);
+            const T r2 = (f & 4u) ? v2 : Op::op(r1, v2);
+            const T r3 = (f & 8u) ? v3 : Op::op(r2, v3);
             // warp segmented inclusive scan of the lanes' open tails
             const uint32_t heads = __ballot_sync(FULL, f != 0u);
             const uint32_t le = heads & (FULL >> (31u - lane));
             const int start = le ? 31 - __clz(le) : -1;   // lane where the segment open at this lane's end starts
-            float x = r3;
-            if (lane == 0 && f == 0u) x = carry + r3;
+            T x = r3;
+            if (lane == 0 && f == 0u) x = Op::op(carry, r3);
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const float y = __shfl_up_sync(FULL, x, o);
-                if ((int)lane >= o && (int)lane - o >= start) x = y + x;
+                const T y = __shfl_up_sync(FULL, x, o);
+                if ((int)lane >= o && (int)lane - o >= start) x = Op::op(y, x);
             }
-            float E = __shfl_up_sync(FULL, x, 1);
+            T E = __shfl_up_sync(FULL, x, 1);
             if (lane == 0) E = carry;
             const uint32_t fj = f ? (uint32_t)(__ffs(f) - 1) : 4u;   // first row start in the lane
-            float run[4];
-            run[0] = fj > 0 ? E + r0 : r0;
-            run[1] = fj > 1 ? E + r1 : r1;
-            run[2] = fj > 2 ? E + r2 : r2;
-            run[3] = fj > 3 ? E + r3 : r3;
+            T run[4];
+            run[0] = fj > 0 ? Op::op(E, r0) : r0;
+            run[1] = fj > 1 ? Op::op(E, r1) : r1;
+            run[2] = fj > 2 ? Op::op(E, r2) : r2;
+            run[3] = fj > 3 ? Op::op(E, r3) : r3;
             // segment ends: a row starts at the next arc, or the tile ends
             const uint32_t ends = (f >> 1) | (nxt << 3) | ((h == 1 && lane == 31) ? 8u : 0u);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const uint32_t q = 128u * (uint32_t)h + 4u * lane + (uint32_t)j;
                 if (((ends >> j) & 1u) && q < rel) {
+                    T *lead = reinterpret_cast<T *>(a.lead);
+                    T *acc = reinterpret_cast<T *>(a.acc);
                     if (q < fh) {
-                        a.lead[t] = run[j];    // the row continued from an earlier tile
+                        lead[t] = run[j];    // the row continued from an earlier tile
                     } else {
                         const uint32_t c = cnt + (uint32_t)__popc(f & ((2u << j) - 1u)) - h0bit;
-                        a.acc[__ldg(a.nzv + tr + (int32_t)c)] = run[j];
+                        acc[__ldg(a.nzv + tr + (int32_t)c)] = run[j];
                     }
                 }
             }
@@ -250,7 +330,7 @@ namespace {
 
 // ------------------------------------------------------ correction flags ----
 // Second pass of a PageRank correction (Sec. 3.4, Alg. 2 GG-Gather influence
-// and GG-EStatus) over the full in-edge list, after k_pr_arcs stored every
+// and GG-EStatus) over the full in-edge list, after k_pull_arcs stored every
 // arc's contribution: the running sum of its row before and after each arc,
 // influence (after - before) / after > theta tested as
 // (after - before) > theta * after, one flag bit per arc. The row continued
@@ -313,7 +393,7 @@ __global__ void __launch_bounds__(kPullThreads, 4) k_prc_flags(PullArgs a)
             const uint32_t sh = 4u * (lane & 7u);
             const uint32_t f = (pick4(hw, lane >> 3) >> sh) & 0xFu;
             const float v0 = v[4 * h], v1 = v[4 * h + 1], v2 = v[4 * h + 2], v3 = v[4 * h + 3];
-            // lane tails for the scan (as in k_pr_arcs)
+            // lane tails for the scan (as in k_pull_arcs)
             const float r0 = v0;
             const float r1 = (f & 2u) ? v1 : r0 + v1;
             const float r2 = (f & 4u) ? v2 : r1 + v2;
@@ -352,6 +432,206 @@ __global__ void __launch_bounds__(kPullThreads, 4) k_prc_flags(PullArgs a)
             if ((lane & 7u) == 0 && wi < mask_words) a.mask[wi] = word;
             carry = __shfl_sync(FULL, x, 31);
         }
+    }
+}
+
+// Second pass of a correction of SSSP / BFS / CC (Sec. 3.4; influence on a
+// min accumulator as the reading of Alg. 2 for these applications): the
+// running minimum of its row before each arc (INF before the first), the
+// candidate's influence, one flag bit per arc. An arc without a candidate
+// (source unreached) keeps its flag (cleared under GG_EST_STRICT); theta < 0
+// sets every other flag, theta >= 1 clears it; otherwise the flag is set when
+// the candidate lowers the running minimum by more than theta of it
+// ((before - cand) 2^32 > theta_fx before, exact), or is the row's first
+// candidate (or, for CC, lowers it at all).
+template <int APP>
+__global__ void __launch_bounds__(kPullThreads, 4) k_minc_flags(PullArgs a)
+{
+    constexpr uint32_t FULL = 0xFFFFFFFFu;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t nnz = *a.nnz;
+    const long long nt = ((long long)nnz + kPT - 1) / kPT;
+    const long long mask_words = ((long long)nnz + 31) / 32;
+    const long long W = (long long)gridDim.x * (kPullThreads / 32);
+    const uint32_t *cv = reinterpret_cast<const uint32_t *>(a.vals);
+    const uint32_t *acc = reinterpret_cast<const uint32_t *>(a.acc);
+    const uint32_t *lead = reinterpret_cast<const uint32_t *>(a.lead);
+    for (long long t = (long long)blockIdx.x * (kPullThreads / 32) + (threadIdx.x >> 5); t < nt; t += W) {
+        const long long a0 = t * kPT;
+        const uint32_t rel = nnz - (uint32_t)a0 < (uint32_t)kPT ? nnz - (uint32_t)a0 : (uint32_t)kPT;
+        uint32_t v[8];
+        if (rel == (uint32_t)kPT) {
+            const uint4 x = reinterpret_cast<const uint4 *>(cv + a0)[lane];
+            const uint4 y = reinterpret_cast<const uint4 *>(cv + a0 + 128)[lane];
+            v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+            v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t q = 4u * lane + (uint32_t)j;
+                v[j] = q < rel ? cv[a0 + q] : kInf;
+                v[4 + j] = q + 128u < rel ? cv[a0 + 128 + q] : kInf;
+            }
+        }
+        uint4 h0 = __ldg(reinterpret_cast<const uint4 *>(a.hb + t * 8));
+        uint4 h1 = __ldg(reinterpret_cast<const uint4 *>(a.hb + t * 8 + 4));
+        if (rel < (uint32_t)kPT) {
+            h0.x = tail_bits(h0.x, 0, rel); h0.y = tail_bits(h0.y, 1, rel);
+            h0.z = tail_bits(h0.z, 2, rel); h0.w = tail_bits(h0.w, 3, rel);
+            h1.x = tail_bits(h1.x, 4, rel); h1.y = tail_bits(h1.y, 5, rel);
+            h1.z = tail_bits(h1.z, 6, rel); h1.w = tail_bits(h1.w, 7, rel);
+        }
+        // running minimum of the row open at the tile start (tiles that start mid-row)
+        uint32_t carry = kInf;
+        if (!(h0.x & 1u)) {
+            const int32_t vr = __ldg(a.nzv + __ldg(a.trow + t));
+            const long long j0 = __ldg(a.row_ptr + vr) / kPT;
+            uint32_t m = acc[vr];
+            for (long long u0 = j0 + 1; u0 < t; u0 += 32) {
+                const long long u = u0 + lane;
+                m = min(m, __reduce_min_sync(FULL, u < t ? lead[u] : kInf));
+            }
+            carry = m;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint4 hw = h ? h1 : h0;
+            const uint32_t sh = 4u * (lane & 7u);
+            const long long wi = t * 8 + 4 * h + (lane >> 3);
+            const uint32_t f = (pick4(hw, lane >> 3) >> sh) & 0xFu;
+            const uint32_t oldw = (wi < mask_words) ? a.mask[wi] : 0u;   // this tile's flag words, before
+            const uint32_t v0 = v[4 * h], v1 = v[4 * h + 1], v2 = v[4 * h + 2], v3 = v[4 * h + 3];
+            const uint32_t r0 = v0;
+            const uint32_t r1 = (f & 2u) ? v1 : min(r0, v1);
+            const uint32_t r2 = (f & 4u) ? v2 : min(r1, v2);
+            const uint32_t r3 = (f & 8u) ? v3 : min(r2, v3);
+            const uint32_t heads = __ballot_sync(FULL, f != 0u);
+            const uint32_t le = heads & (FULL >> (31u - lane));
+            const int start = le ? 31 - __clz(le) : -1;
+            uint32_t x = r3;
+            if (lane == 0 && f == 0u) x = min(carry, r3);
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(FULL, x, o);
+                if ((int)lane >= o && (int)lane - o >= start) x = min(y, x);
+            }
+            uint32_t run = __shfl_up_sync(FULL, x, 1);
+            if (lane == 0) run = carry;
+            uint32_t nib = 0;
+            const uint32_t vv[4] = {v0, v1, v2, v3};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t q = 128u * (uint32_t)h + 4u * lane + (uint32_t)j;
+                const uint32_t before = ((f >> j) & 1u) ? kInf : run;
+                const uint32_t c = vv[j];
+                run = min(before, c);
+                uint32_t fl = 0;
+                if (c == kInf) {
+                    fl = a.est_strict ? 0u : (oldw >> (sh + (uint32_t)j)) & 1u;
+                } else if (a.theta_case == 1) {
+                    fl = 1u;
+                } else if (a.theta_case == 2) {
+                    fl = 0u;
+                } else if (c < before) {
+                    if (before == kInf || APP == GG_APP_CC) fl = 1u;
+                    else fl = ((unsigned long long)(before - c) << 32) > a.theta_fx * (unsigned long long)before ? 1u : 0u;
+                }
+                if (fl && q < rel) nib |= 1u << j;
+            }
+            uint32_t word = nib << sh;
+            word |= __shfl_xor_sync(FULL, word, 1);
+            word |= __shfl_xor_sync(FULL, word, 2);
+            word |= __shfl_xor_sync(FULL, word, 4);
+            if ((lane & 7u) == 0 && wi < mask_words) a.mask[wi] = word;
+            carry = __shfl_sync(FULL, x, 31);
+        }
+    }
+}
+
+// GG-Apply + GG-VStatus for SSSP / BFS / CC: new = min(old, the row's
+// minimum candidate); a vertex whose value decreased joins the next frontier
+// (vertex, new value), appended once per warp.
+template <int APP>
+__global__ void __launch_bounds__(kPullThreads) k_min_apply(PullArgs a)
+{
+    constexpr int U = 4;
+    const uint32_t *acc_u = reinterpret_cast<const uint32_t *>(a.acc);
+    const uint32_t *lead = reinterpret_cast<const uint32_t *>(a.lead);
+    const uint32_t lane = threadIdx.x & 31u;
+    unsigned long long changed = 0, sum = 0;
+    uint32_t mx = 0;
+    const long long S = (long long)gridDim.x * blockDim.x;
+    const long long nround = ((long long)a.n + U * S - 1) / (U * S) * (U * S);   // whole warps stay in the loop
+    for (long long v0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; v0 < nround; v0 += U * S) {
+        int32_t rs[U], re[U];
+        uint32_t old[U], ac[U];
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+            const long long v = v0 + i * S;
+            rs[i] = re[i] = 0;
+            old[i] = ac[i] = kInf;
+            if (v < a.n) {
+                rs[i] = __ldg(a.row_ptr + v);
+                re[i] = __ldg(a.row_ptr + v + 1);
+                ac[i] = acc_u[v];   // stale for a row without arcs: replaced by INF below
+                old[i] = a.val_cur[v];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+            if (re[i] > rs[i]) {
+                const int32_t t0 = rs[i] / kPT, t1 = (re[i] - 1) / kPT;
+                uint32_t m = ac[i];
+                for (int32_t u = t0 + 1; u <= t1; ++u) m = min(m, lead[u]);
+                ac[i] = m;
+            } else {
+                ac[i] = kInf;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+            const long long v = v0 + i * S;
+            const bool live = v < a.n;
+            const uint32_t nw = min(old[i], ac[i]);
+            const bool ch = live && nw < old[i];
+            if (live) {
+                a.val_next[v] = nw;
+                if (a.hist_out) a.hist_out[v] = ch ? 1.0f : 0.0f;
+            }
+            if (ch) {
+                changed += 1;
+                if (old[i] != kInf) {
+                    sum += old[i] - nw;
+                    mx = (old[i] - nw) > mx ? (old[i] - nw) : mx;
+                }
+            }
+            if (a.q_out) {
+                const uint32_t b = __ballot_sync(0xFFFFFFFFu, ch);
+                if (b) {
+                    uint32_t base = 0;
+                    if (lane == 0) base = atomicAdd(a.q_out_len, (uint32_t)__popc(b));
+                    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+                    if (ch) {
+                        const uint32_t pos = base + (uint32_t)__popc(b & ((1u << lane) - 1u));
+                        a.q_out[pos] = (int32_t)v;
+                        a.q_out_val[pos] = nw;
+                    }
+                }
+            }
+        }
+    }
+    if (!a.stats) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        changed += __shfl_xor_sync(0xFFFFFFFFu, changed, o);
+        sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+        const uint32_t om = __shfl_xor_sync(0xFFFFFFFFu, mx, o);
+        mx = om > mx ? om : mx;
+    }
+    if (lane == 0 && (changed | sum | mx)) {
+        atomicAdd(&a.stats->changed, changed);
+        atomicAdd(&a.stats->sum_delta, sum);
+        atomicMax(&a.stats->max_delta_bits, mx);
     }
 }
 
@@ -427,35 +707,59 @@ __global__ void __launch_bounds__(kPullThreads) k_pr_apply(PullArgs a)
 
 }  // namespace
 
-cudaError_t launch_pr_pull(const PullArgs &a, uint32_t max_tiles, int num_sms, cudaStream_t s)
+namespace {
+
+template <int APP>
+void launch_arcs(const PullArgs &a, uint32_t max_tiles, int num_sms, cudaStream_t s)
 {
     constexpr int arc_blocks_per_sm = 4;
-    constexpr bool prefetch = true;
     long long blocks = ((long long)max_tiles + kPullThreads / 32 - 1) / (kPullThreads / 32);
     if (blocks > (long long)num_sms * arc_blocks_per_sm) blocks = (long long)num_sms * arc_blocks_per_sm;
     if (blocks < 1) blocks = 1;
-    k_pr_arcs<arc_blocks_per_sm, prefetch><<<(unsigned)blocks, kPullThreads, 0, s>>>(a);
-    // persistent: the blocks one wave holds (48 registers: 5 blocks of 256 per SM)
+    k_pull_arcs<APP, arc_blocks_per_sm, true><<<(unsigned)blocks, kPullThreads, 0, s>>>(a);
+}
+
+template <int APP>
+void launch_flags(const PullArgs &a, uint32_t max_tiles, int num_sms, cudaStream_t s)
+{
+    long long blocks = ((long long)max_tiles + kPullThreads / 32 - 1) / (kPullThreads / 32);
+    if (blocks > (long long)num_sms * 4) blocks = (long long)num_sms * 4;
+    if (blocks < 1) blocks = 1;
+    if constexpr (APP == GG_APP_PAGERANK) k_prc_flags<<<(unsigned)blocks, kPullThreads, 0, s>>>(a);
+    else k_minc_flags<APP><<<(unsigned)blocks, kPullThreads, 0, s>>>(a);
+}
+
+template <int APP>
+void launch_apply(const PullArgs &a, int num_sms, cudaStream_t s)
+{
+    // persistent: the blocks one wave holds (5 blocks of 256 per SM)
     long long ab = ((long long)a.n + kPullThreads - 1) / kPullThreads;
     if (ab > (long long)num_sms * 5) ab = (long long)num_sms * 5;
     if (ab < 1) ab = 1;
-    k_pr_apply<<<(unsigned)ab, kPullThreads, 0, s>>>(a);
+    if constexpr (APP == GG_APP_PAGERANK) k_pr_apply<<<(unsigned)ab, kPullThreads, 0, s>>>(a);
+    else k_min_apply<APP><<<(unsigned)ab, kPullThreads, 0, s>>>(a);
+}
+
+template <int APP>
+cudaError_t pull_iteration(const PullArgs &a, bool correct, uint32_t max_tiles, int num_sms, cudaStream_t s)
+{
+    launch_arcs<APP>(a, max_tiles, num_sms, s);
+    if (correct) launch_flags<APP>(a, max_tiles, num_sms, s);
+    launch_apply<APP>(a, num_sms, s);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pr_correct(const PullArgs &a, uint32_t max_tiles, int num_sms, cudaStream_t s)
+}  // namespace
+
+cudaError_t launch_pull(int app, const PullArgs &a, bool correct, uint32_t max_tiles, int num_sms, cudaStream_t s)
 {
-    constexpr int arc_blocks_per_sm = 4;
-    long long blocks = ((long long)max_tiles + kPullThreads / 32 - 1) / (kPullThreads / 32);
-    if (blocks > (long long)num_sms * arc_blocks_per_sm) blocks = (long long)num_sms * arc_blocks_per_sm;
-    if (blocks < 1) blocks = 1;
-    k_pr_arcs<arc_blocks_per_sm, true><<<(unsigned)blocks, kPullThreads, 0, s>>>(a);
-    k_prc_flags<<<(unsigned)blocks, kPullThreads, 0, s>>>(a);
-    long long ab = ((long long)a.n + kPullThreads - 1) / kPullThreads;
-    if (ab > (long long)num_sms * 5) ab = (long long)num_sms * 5;
-    if (ab < 1) ab = 1;
-    k_pr_apply<<<(unsigned)ab, kPullThreads, 0, s>>>(a);
-    return cudaGetLastError();
+    switch (app) {
+    case GG_APP_PAGERANK: return pull_iteration<GG_APP_PAGERANK>(a, correct, max_tiles, num_sms, s);
+    case GG_APP_SSSP: return pull_iteration<GG_APP_SSSP>(a, correct, max_tiles, num_sms, s);
+    case GG_APP_BFS: return pull_iteration<GG_APP_BFS>(a, correct, max_tiles, num_sms, s);
+    case GG_APP_CC: return pull_iteration<GG_APP_CC>(a, correct, max_tiles, num_sms, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 // ---------------------------------------------------------- plan (host) ----

@@ -1,4 +1,4 @@
-"""DRAM traffic of the tile-engine kernels from ncu captures, for bench.py's
+"""DRAM traffic of the pull kernels from ncu captures, for bench.py's
 roofline line.
 
 Each capture is one case run by ``profile_case`` under ``ncu`` (one launch
@@ -30,7 +30,9 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
-KERNEL_FILES = ("gg_gather.cuh", "gg_tile.cuh", "gg_tile_launch.cuh", "gg_tile_pr.cu", "gg_tile_min.cu")
+# the pull kernels (gathers and corrections of every application) and the
+# tile count kernel a correction ends with
+KERNEL_FILES = ("gg_pull.cu", "gg_sample.cu")
 
 
 def _code(text: str) -> str:
@@ -42,8 +44,8 @@ def _code(text: str) -> str:
 
 
 def kernel_hash() -> str:
-    """Hash of the tile engine's device code: its own files plus the
-    constants and the argument struct it is compiled with (comments and
+    """Hash of the measured kernels' device code: their files plus the
+    constants and the argument struct they are compiled with (comments and
     layout ignored)."""
     h = hashlib.sha256()
     for f in KERNEL_FILES:
@@ -51,7 +53,7 @@ def kernel_hash() -> str:
             h.update(_code(fh.read()).encode())
     with open(os.path.join(CSRC, "gg_internal.cuh")) as fh:
         text = fh.read()
-    for pat in (r"constexpr int kThreads.*?constexpr uint32_t kInf[^\n]*", r"struct TileArgs \{.*?\n\};"):
+    for pat in (r"constexpr int kThreads.*?constexpr uint32_t kInf[^\n]*", r"struct PullArgs \{.*?\n\};"):
         m = re.search(pat, text, re.S)
         h.update(_code(m.group(0) if m else "").encode())
     return h.hexdigest()[:16]
