@@ -425,6 +425,10 @@ static gg_status pull_args(gg_graph *g, int which, const TileArgs &a, PullArgs *
     pa->hb = pl.hb;
     pa->trow = pl.trow;
     pa->nzv = pl.nzv;
+    pa->topen = pl.topen;
+    pa->lrows = pl.lrows;
+    pa->nlong = pl.nlong;
+    pa->carry = g->pull_carry;
     pa->contrib = a.contrib_cur;
     pa->acc = g->pull_acc;
     pa->lead = g->pull_lead;

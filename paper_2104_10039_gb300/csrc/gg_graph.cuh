@@ -54,7 +54,9 @@ struct DevBuf {
 struct PullPlan {
     DevBuf buf;
     uint32_t *hb = nullptr;
-    int32_t *trow = nullptr, *nzv = nullptr;
+    int32_t *trow = nullptr, *nzv = nullptr, *lrows = nullptr;
+    int2 *topen = nullptr;
+    uint32_t *nlong = nullptr;
     uint32_t *nzb = nullptr, *nzc = nullptr, *nzcnt = nullptr;
     size_t hb_words = 0, tiles = 0, nzw = 0;
     bool valid = false;
@@ -172,7 +174,7 @@ struct gg_graph {
     // and tile leading parts; whether sp_src holds vertex ids (not hub-coded)
     gg::PullPlan plan[2];
     gg::DevBuf b_pull;
-    float *pull_acc = nullptr, *pull_lead = nullptr;
+    float *pull_acc = nullptr, *pull_lead = nullptr, *pull_carry = nullptr;
     bool pull_ready = false;
     bool sp_is_plain = false;
     // training trace (caller-owned device buffers)

@@ -127,6 +127,10 @@ struct PullArgs {
     const uint32_t *hb;         // plan: row-start bit per arc
     const int32_t *trow;        // plan: per tile, non-empty-row rank of the row holding its first arc
     const int32_t *nzv;         // plan: vertex of each non-empty row
+    const int2 *topen;          // plan: per tile, the row open at its start: vertex, its first tile | long << 31
+    const int32_t *lrows;       // plan: the long rows (vertices)
+    const uint32_t *nlong;      // plan: device scalar, number of long rows
+    float *carry;               // correction: per tile inside a long row, the row's value before the tile
     const float *contrib;       // gathered vector (rank / degree of the previous iteration)
     float *acc;                 // per vertex: its row's sum over the tile holding the row's first arc
     float *lead;                // per tile: the part before its first row start

@@ -20,6 +20,9 @@
 //                the tile writes its total (or, if it continues past the tile,
 //                the part in the tile) to acc[v]; the part of the tile before
 //                its first row start goes to lead[tile].
+//   k_long_rows  one block per long row: its total and, for a correction,
+//                every tile's carry (the row's value before the tile).
+//   k_carries    a correction's carries of the tiles inside shorter rows.
 //   k_prc_flags, k_minc_flags
 //                a correction's second pass: every arc's influence from the
 //                running value of its row before and after it (the values kept
@@ -39,6 +42,8 @@
 //   hb[w]     bit j: arc 32w + j is the first arc of a row
 //   trow[t]   rank among non-empty rows of the row holding arc 256t
 //   nzv[k]    vertex of the k-th non-empty row
+//   topen[t]  the row holding arc 256t: vertex, tile of its first arc, long flag
+//   lrows     the long rows (more than kLongTiles tiles past their first one)
 //   nzb, nzc  non-empty-row bitmap and counts (to rank the rows)
 #include "gg_graph.cuh"
 
@@ -48,6 +53,10 @@ namespace {
 
 constexpr int kPT = 256;          // arcs per pull tile
 constexpr int kPullThreads = 256;
+// A row whose arcs reach more than kLongTiles tiles past the tile of its
+// first arc is "long": one block completes its sum and its tiles' carries
+// (k_long_rows); shorter rows fold at most kLongTiles leading parts inline.
+constexpr int kLongTiles = 8;
 
 // ------------------------------------------------------------------ plan ----
 __global__ void k_plan_nz(const int32_t *__restrict__ ptr, int32_t n, uint32_t *__restrict__ nzb,
@@ -67,7 +76,8 @@ __global__ void k_plan_nz(const int32_t *__restrict__ ptr, int32_t n, uint32_t *
 
 __global__ void k_plan_heads(const int32_t *__restrict__ ptr, int32_t n, const uint32_t *__restrict__ nzb,
                              const uint32_t *__restrict__ nzc, uint32_t *__restrict__ hb,
-                             int32_t *__restrict__ trow, int32_t *__restrict__ nzv)
+                             int32_t *__restrict__ trow, int32_t *__restrict__ nzv, int2 *__restrict__ topen,
+                             int32_t *__restrict__ lrows, uint32_t *__restrict__ nlong)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
@@ -77,7 +87,13 @@ __global__ void k_plan_heads(const int32_t *__restrict__ ptr, int32_t n, const u
         const int32_t k = (int32_t)(nzc[w] + (uint32_t)__popc(nzb[w] & ((1u << bit) - 1u)));
         atomicOr(hb + (s >> 5), 1u << (s & 31));
         nzv[k] = (int32_t)v;
-        for (long long t = ((long long)s + kPT - 1) / kPT; t * kPT < e; ++t) trow[t] = k;
+        const int32_t t0 = s / kPT, t1 = (e - 1) / kPT;
+        const bool is_long = t1 - t0 > kLongTiles;
+        if (is_long) lrows[atomicAdd(nlong, 1u)] = (int32_t)v;
+        for (long long t = ((long long)s + kPT - 1) / kPT; t * kPT < e; ++t) {
+            trow[t] = k;
+            topen[t] = make_int2((int32_t)v, t0 | (is_long ? (int32_t)0x80000000 : 0));
+        }
     }
 }
 
@@ -328,21 +344,89 @@ __global__ void __launch_bounds__(kPullThreads, MINB) k_pull_arcs(PullArgs a)
 
 namespace {
 
+// ------------------------------------------------------------- long rows ----
+// One block per long row (its arcs reach more than kLongTiles tiles past the
+// tile of its first arc): the leading parts of its later tiles folded in tile
+// order onto its first part, 256 at a time (a block scan with a fixed
+// grouping). With a.carry, every such tile's carry (the row's value before
+// the tile) is stored for the correction's flag pass; acc[v] ends as the
+// row's total. Runs after k_pull_arcs, before the flag pass and the apply.
+template <int APP>
+__global__ void __launch_bounds__(kPullThreads) k_long_rows(PullArgs a)
+{
+    using Op = PullOp<APP>;
+    using T = typename Op::T;
+    __shared__ T s_w[kPullThreads / 32];
+    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    T *acc = reinterpret_cast<T *>(a.acc);
+    const T *lead = reinterpret_cast<const T *>(a.lead);
+    T *carry = reinterpret_cast<T *>(a.carry);
+    const uint32_t nl = *a.nlong;
+    for (uint32_t r = blockIdx.x; r < nl; r += gridDim.x) {
+        const int32_t v = a.lrows[r];
+        const int32_t t0 = __ldg(a.row_ptr + v) / kPT, t1 = (__ldg(a.row_ptr + v + 1) - 1) / kPT;
+        T run = acc[v];
+        for (int32_t base = t0 + 1; base <= t1; base += kPullThreads) {
+            const int32_t u = base + (int32_t)threadIdx.x;
+            T x = u <= t1 ? lead[u] : Op::id();
+            // inclusive warp scan, then the warps' totals in order
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const T y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+                if ((int)lane >= o) x = Op::op(y, x);
+            }
+            if (lane == 31) s_w[wid] = x;
+            __syncthreads();
+            T before_warp = Op::id(), chunk = Op::id();
+#pragma unroll
+            for (int i = 0; i < kPullThreads / 32; ++i) {
+                if (i < (int)wid) before_warp = Op::op(before_warp, s_w[i]);
+                chunk = Op::op(chunk, s_w[i]);
+            }
+            const T excl_lane = __shfl_up_sync(0xFFFFFFFFu, x, 1);
+            const T excl = lane ? Op::op(before_warp, excl_lane) : before_warp;
+            if (carry && u <= t1) carry[u] = Op::op(run, excl);
+            run = Op::op(run, chunk);
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) acc[v] = run;
+        __syncthreads();
+    }
+}
+
+// Carry of every tile that starts inside a short row (a correction's flag
+// pass reads it): the row's first part and the leading parts of the tiles in
+// between, in tile order. One thread per tile; long rows' carries come from
+// k_long_rows.
+template <int APP>
+__global__ void __launch_bounds__(kPullThreads) k_carries(PullArgs a)
+{
+    using Op = PullOp<APP>;
+    using T = typename Op::T;
+    const T *acc = reinterpret_cast<const T *>(a.acc);
+    const T *lead = reinterpret_cast<const T *>(a.lead);
+    T *carry = reinterpret_cast<T *>(a.carry);
+    const uint32_t nnz = *a.nnz;
+    const long long nt = ((long long)nnz + kPT - 1) / kPT;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += stride) {
+        const int2 op = __ldg(a.topen + t);
+        if (op.y < 0 || op.y >= t) continue;   // long row, or the tile starts with a row
+        T c = acc[op.x];
+        for (long long u = (long long)op.y + 1; u < t; ++u) c = Op::op(c, lead[u]);
+        carry[t] = c;
+    }
+}
+
 // ------------------------------------------------------ correction flags ----
 // Second pass of a PageRank correction (Sec. 3.4, Alg. 2 GG-Gather influence
 // and GG-EStatus) over the full in-edge list, after k_pull_arcs stored every
 // arc's contribution: the running sum of its row before and after each arc,
 // influence (after - before) / after > theta tested as
 // (after - before) > theta * after, one flag bit per arc. The row continued
-// from earlier tiles starts from its carry: its part in the tile of its first
-// arc (acc[v]) plus the leading parts of the tiles in between, in tile order.
-__device__ __forceinline__ float warp_sum_fixed(float x)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
-    return __shfl_sync(0xFFFFFFFFu, x, 0);
-}
-
+// from earlier tiles starts from its carry (k_carries / k_long_rows): its
+// part in the tile of its first arc plus the leading parts of the tiles in
+// between, in tile order.
 __global__ void __launch_bounds__(kPullThreads, 4) k_prc_flags(PullArgs a)
 {
     constexpr uint32_t FULL = 0xFFFFFFFFu;
@@ -351,15 +435,27 @@ __global__ void __launch_bounds__(kPullThreads, 4) k_prc_flags(PullArgs a)
     const long long nt = ((long long)nnz + kPT - 1) / kPT;
     const long long mask_words = ((long long)nnz + 31) / 32;
     const long long W = (long long)gridDim.x * (kPullThreads / 32);
+    uint4 pf0 = make_uint4(0u, 0u, 0u, 0u), pf1 = pf0;   // the next full tile's values, loaded ahead
+    bool have_pf = false;
     for (long long t = (long long)blockIdx.x * (kPullThreads / 32) + (threadIdx.x >> 5); t < nt; t += W) {
         const long long a0 = t * kPT;
         const uint32_t rel = nnz - (uint32_t)a0 < (uint32_t)kPT ? nnz - (uint32_t)a0 : (uint32_t)kPT;
         float v[8];
         if (rel == (uint32_t)kPT) {
-            const float4 x = reinterpret_cast<const float4 *>(a.vals + a0)[lane];
-            const float4 y = reinterpret_cast<const float4 *>(a.vals + a0 + 128)[lane];
-            v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
-            v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
+            uint4 x = pf0, y = pf1;
+            if (!have_pf) {
+                x = reinterpret_cast<const uint4 *>(a.vals + a0)[lane];
+                y = reinterpret_cast<const uint4 *>(a.vals + a0 + 128)[lane];
+            }
+            v[0] = __uint_as_float(x.x); v[1] = __uint_as_float(x.y); v[2] = __uint_as_float(x.z);
+            v[3] = __uint_as_float(x.w); v[4] = __uint_as_float(y.x); v[5] = __uint_as_float(y.y);
+            v[6] = __uint_as_float(y.z); v[7] = __uint_as_float(y.w);
+            const long long tn = t + W;
+            have_pf = tn < nt && (tn + 1) * kPT <= (long long)nnz;
+            if (have_pf) {
+                pf0 = reinterpret_cast<const uint4 *>(a.vals + tn * kPT)[lane];
+                pf1 = reinterpret_cast<const uint4 *>(a.vals + tn * kPT + 128)[lane];
+            }
         } else {
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -376,17 +472,8 @@ __global__ void __launch_bounds__(kPullThreads, 4) k_prc_flags(PullArgs a)
             h1.x = tail_bits(h1.x, 4, rel); h1.y = tail_bits(h1.y, 5, rel);
             h1.z = tail_bits(h1.z, 6, rel); h1.w = tail_bits(h1.w, 7, rel);
         }
-        // carry of the row open at the tile start (tiles that start mid-row)
-        float carry = 0.0f;
-        if (!(h0.x & 1u)) {
-            const int32_t vr = __ldg(a.nzv + __ldg(a.trow + t));
-            const long long j0 = __ldg(a.row_ptr + vr) / kPT;   // tile of the row's first arc (< t)
-            carry = a.acc[vr];
-            for (long long u0 = j0 + 1; u0 < t; u0 += 32) {
-                const long long u = u0 + lane;
-                carry = carry + warp_sum_fixed(u < t ? a.lead[u] : 0.0f);
-            }
-        }
+        // carry of the row open at the tile start (k_carries, k_long_rows)
+        float carry = (h0.x & 1u) ? 0.0f : a.carry[t];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const uint4 hw = h ? h1 : h0;
@@ -454,17 +541,26 @@ __global__ void __launch_bounds__(kPullThreads, 4) k_minc_flags(PullArgs a)
     const long long mask_words = ((long long)nnz + 31) / 32;
     const long long W = (long long)gridDim.x * (kPullThreads / 32);
     const uint32_t *cv = reinterpret_cast<const uint32_t *>(a.vals);
-    const uint32_t *acc = reinterpret_cast<const uint32_t *>(a.acc);
-    const uint32_t *lead = reinterpret_cast<const uint32_t *>(a.lead);
+    uint4 pf0 = make_uint4(0u, 0u, 0u, 0u), pf1 = pf0;   // the next full tile's candidates, loaded ahead
+    bool have_pf = false;
     for (long long t = (long long)blockIdx.x * (kPullThreads / 32) + (threadIdx.x >> 5); t < nt; t += W) {
         const long long a0 = t * kPT;
         const uint32_t rel = nnz - (uint32_t)a0 < (uint32_t)kPT ? nnz - (uint32_t)a0 : (uint32_t)kPT;
         uint32_t v[8];
         if (rel == (uint32_t)kPT) {
-            const uint4 x = reinterpret_cast<const uint4 *>(cv + a0)[lane];
-            const uint4 y = reinterpret_cast<const uint4 *>(cv + a0 + 128)[lane];
+            uint4 x = pf0, y = pf1;
+            if (!have_pf) {
+                x = reinterpret_cast<const uint4 *>(cv + a0)[lane];
+                y = reinterpret_cast<const uint4 *>(cv + a0 + 128)[lane];
+            }
             v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
             v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
+            const long long tn = t + W;
+            have_pf = tn < nt && (tn + 1) * kPT <= (long long)nnz;
+            if (have_pf) {
+                pf0 = reinterpret_cast<const uint4 *>(cv + tn * kPT)[lane];
+                pf1 = reinterpret_cast<const uint4 *>(cv + tn * kPT + 128)[lane];
+            }
         } else {
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -481,18 +577,8 @@ __global__ void __launch_bounds__(kPullThreads, 4) k_minc_flags(PullArgs a)
             h1.x = tail_bits(h1.x, 4, rel); h1.y = tail_bits(h1.y, 5, rel);
             h1.z = tail_bits(h1.z, 6, rel); h1.w = tail_bits(h1.w, 7, rel);
         }
-        // running minimum of the row open at the tile start (tiles that start mid-row)
-        uint32_t carry = kInf;
-        if (!(h0.x & 1u)) {
-            const int32_t vr = __ldg(a.nzv + __ldg(a.trow + t));
-            const long long j0 = __ldg(a.row_ptr + vr) / kPT;
-            uint32_t m = acc[vr];
-            for (long long u0 = j0 + 1; u0 < t; u0 += 32) {
-                const long long u = u0 + lane;
-                m = min(m, __reduce_min_sync(FULL, u < t ? lead[u] : kInf));
-            }
-            carry = m;
-        }
+        // running minimum of the row open at the tile start (k_carries, k_long_rows)
+        uint32_t carry = (h0.x & 1u) ? kInf : reinterpret_cast<const uint32_t *>(a.carry)[t];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const uint4 hw = h ? h1 : h0;
@@ -550,14 +636,17 @@ __global__ void __launch_bounds__(kPullThreads, 4) k_minc_flags(PullArgs a)
 
 // GG-Apply + GG-VStatus for SSSP / BFS / CC: new = min(old, the row's
 // minimum candidate); a vertex whose value decreased joins the next frontier
-// (vertex, new value), appended once per warp.
+// (vertex, new value); each block reserves its entries with one atomic per
+// step (many vertices change in the first iterations).
 template <int APP>
 __global__ void __launch_bounds__(kPullThreads) k_min_apply(PullArgs a)
 {
     constexpr int U = 4;
     const uint32_t *acc_u = reinterpret_cast<const uint32_t *>(a.acc);
     const uint32_t *lead = reinterpret_cast<const uint32_t *>(a.lead);
-    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    __shared__ uint32_t s_cnt[kPullThreads / 32];
+    __shared__ uint32_t s_base;
     unsigned long long changed = 0, sum = 0;
     uint32_t mx = 0;
     const long long S = (long long)gridDim.x * blockDim.x;
@@ -581,13 +670,16 @@ __global__ void __launch_bounds__(kPullThreads) k_min_apply(PullArgs a)
         for (int i = 0; i < U; ++i) {
             if (re[i] > rs[i]) {
                 const int32_t t0 = rs[i] / kPT, t1 = (re[i] - 1) / kPT;
-                uint32_t m = ac[i];
-                for (int32_t u = t0 + 1; u <= t1; ++u) m = min(m, lead[u]);
-                ac[i] = m;
+                if (t1 - t0 <= kLongTiles) {   // a long row's total is complete already
+                    uint32_t m = ac[i];
+                    for (int32_t u = t0 + 1; u <= t1; ++u) m = min(m, lead[u]);
+                    ac[i] = m;
+                }
             } else {
                 ac[i] = kInf;
             }
         }
+        uint32_t chm = 0, nwv[U];
 #pragma unroll
         for (int i = 0; i < U; ++i) {
             const long long v = v0 + i * S;
@@ -605,19 +697,41 @@ __global__ void __launch_bounds__(kPullThreads) k_min_apply(PullArgs a)
                     mx = (old[i] - nw) > mx ? (old[i] - nw) : mx;
                 }
             }
-            if (a.q_out) {
-                const uint32_t b = __ballot_sync(0xFFFFFFFFu, ch);
-                if (b) {
-                    uint32_t base = 0;
-                    if (lane == 0) base = atomicAdd(a.q_out_len, (uint32_t)__popc(b));
-                    base = __shfl_sync(0xFFFFFFFFu, base, 0);
-                    if (ch) {
-                        const uint32_t pos = base + (uint32_t)__popc(b & ((1u << lane) - 1u));
-                        a.q_out[pos] = (int32_t)v;
-                        a.q_out_val[pos] = nw;
-                    }
+            chm |= ch ? 1u << i : 0u;
+            nwv[i] = nw;
+        }
+        // frontier: the block's changed vertices at one offset (one atomic per block and step)
+        if (a.q_out) {
+            const uint32_t c = (uint32_t)__popc(chm);
+            uint32_t incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if ((int)lane >= o) incl += y;
+            }
+            if (lane == 31) s_cnt[wid] = incl;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                uint32_t tot = 0;
+#pragma unroll
+                for (int i = 0; i < kPullThreads / 32; ++i) {
+                    const uint32_t x = s_cnt[i];
+                    s_cnt[i] = tot;
+                    tot += x;
+                }
+                s_base = tot ? atomicAdd(a.q_out_len, tot) : 0u;
+            }
+            __syncthreads();
+            uint32_t pos = s_base + s_cnt[wid] + incl - c;
+#pragma unroll
+            for (int i = 0; i < U; ++i) {
+                if ((chm >> i) & 1u) {
+                    a.q_out[pos] = (int32_t)(v0 + i * S);
+                    a.q_out_val[pos] = nwv[i];
+                    ++pos;
                 }
             }
+            __syncthreads();
         }
     }
     if (!a.stats) return;
@@ -667,10 +781,11 @@ __global__ void __launch_bounds__(kPullThreads) k_pr_apply(PullArgs a)
         for (int i = 0; i < U; ++i) {
             if (re[i] > rs[i]) {
                 const int32_t t0 = rs[i] / kPT, t1 = (re[i] - 1) / kPT;
-                float x = acc[i];
-#pragma unroll 4
-                for (int32_t u = t0 + 1; u <= t1; ++u) x += a.lead[u];
-                acc[i] = x;
+                if (t1 - t0 <= kLongTiles) {   // a long row's total is complete already
+                    float x = acc[i];
+                    for (int32_t u = t0 + 1; u <= t1; ++u) x += a.lead[u];
+                    acc[i] = x;
+                }
             } else {
                 acc[i] = 0.0f;
             }
@@ -741,10 +856,18 @@ void launch_apply(const PullArgs &a, int num_sms, cudaStream_t s)
 }
 
 template <int APP>
-cudaError_t pull_iteration(const PullArgs &a, bool correct, uint32_t max_tiles, int num_sms, cudaStream_t s)
+cudaError_t pull_iteration(PullArgs a, bool correct, uint32_t max_tiles, int num_sms, cudaStream_t s)
 {
     launch_arcs<APP>(a, max_tiles, num_sms, s);
-    if (correct) launch_flags<APP>(a, max_tiles, num_sms, s);
+    if (!correct) a.carry = nullptr;
+    k_long_rows<APP><<<(unsigned)(num_sms * 4), kPullThreads, 0, s>>>(a);
+    if (correct) {
+        long long cb = ((long long)max_tiles + kPullThreads - 1) / kPullThreads;
+        if (cb > (long long)num_sms * 8) cb = (long long)num_sms * 8;
+        if (cb < 1) cb = 1;
+        k_carries<APP><<<(unsigned)cb, kPullThreads, 0, s>>>(a);
+        launch_flags<APP>(a, max_tiles, num_sms, s);
+    }
     launch_apply<APP>(a, num_sms, s);
     return cudaGetLastError();
 }
@@ -768,15 +891,20 @@ gg_status ensure_pull(gg_graph *g)
     if (g->pull_ready) return GG_OK;
     const size_t tiles = ((size_t)g->m + kPT - 1) / kPT + 1;
     const size_t nzw = ((size_t)g->n + 31) / 32 + 1;
-    // per plan: hb (8 words per tile + 8), trow (tiles + 1), nzb, nzc, nzcnt, nzv (n + 4)
-    const size_t words = 8 * tiles + 8 + (tiles + 1) + 3 * nzw + ((size_t)g->n + 4) + 8;
+    // per plan: hb (8 words per tile + 8), topen (2 words per tile + 2), trow (tiles + 1), lrows, nlong,
+    // nzb, nzc, nzcnt, nzv (n + 4)
+    const size_t nlr = tiles / kLongTiles + 2;
+    const size_t words = 8 * tiles + 8 + 2 * (tiles + 1) + (tiles + 1) + nlr + 4 + 3 * nzw + ((size_t)g->n + 4) + 8;
     for (int i = 0; i < 2; ++i) {
         PullPlan &p = g->plan[i];
         gg_status st = p.buf.alloc(4 * words, g->stream);
         if (st != GG_OK) return st;
         uint32_t *w = p.buf.u32();
         p.hb = w; w += 8 * tiles + 8;
+        p.topen = (int2 *)w; w += 2 * (tiles + 1);
         p.trow = (int32_t *)w; w += tiles + 1;
+        p.lrows = (int32_t *)w; w += nlr;
+        p.nlong = w; w += 4;
         p.nzb = w; w += nzw;
         p.nzc = w; w += nzw;
         p.nzcnt = w; w += nzw;
@@ -786,10 +914,11 @@ gg_status ensure_pull(gg_graph *g)
         p.nzw = nzw;
         p.valid = false;
     }
-    gg_status st = g->b_pull.alloc(4 * ((size_t)g->n + tiles + 8), g->stream);
+    gg_status st = g->b_pull.alloc(4 * ((size_t)g->n + 2 * tiles + 16), g->stream);
     if (st != GG_OK) return st;
     g->pull_acc = g->b_pull.f32();
     g->pull_lead = g->pull_acc + g->n + 4;
+    g->pull_carry = g->pull_lead + tiles + 4;
     g->pull_ready = true;
     return GG_OK;
 }
@@ -801,6 +930,7 @@ gg_status build_pull_plan(gg_graph *g, int which)
     const int32_t *ptr = which ? g->sp_ptr : g->in_ptr;
     cudaStream_t s = g->stream;
     GG_CUDA(cudaMemsetAsync(p.hb, 0, 4 * p.hb_words, s));
+    GG_CUDA(cudaMemsetAsync(p.nlong, 0, 4, s));
     int grid = (int)(((size_t)g->n + 255) / 256);
     if (grid > g->num_sms * 8) grid = g->num_sms * 8;
     if (grid < 1) grid = 1;
@@ -810,9 +940,9 @@ gg_status build_pull_plan(gg_graph *g, int which)
     // nzc[words], inside the array: nzw = words + 1)
     const size_t words = ((size_t)g->n + 31) / 32;
     GG_CUDA(launch_scan_u32(p.nzcnt, p.nzc, words, g->scan_tmp, s));
-    k_plan_heads<<<grid, 256, 0, s>>>(ptr, g->n, p.nzb, p.nzc, p.hb, p.trow, p.nzv);
+    k_plan_heads<<<grid, 256, 0, s>>>(ptr, g->n, p.nzb, p.nzc, p.hb, p.trow, p.nzv, p.topen, p.lrows, p.nlong);
     GG_CUDA(cudaGetLastError());
-    g->launches += 7;
+    g->launches += 8;
     p.valid = true;
     return GG_OK;
 }
