@@ -572,7 +572,7 @@ def learned_section(g, source, train_graphs):
     torch.cuda.empty_cache()
     return {"evaluated_on": f"rmat{int(np.log2(g.n))} directed", "trained_on": "rmat12 + rmat22 directed traces",
             "training": tr, "alpha": learned_eval.ALPHA, "theta": learned_eval.THETA,
-            "results": learned_eval.compare(gg, g, source, P, sigmas=(0.5,))}
+            "results": learned_eval.compare(gg, g, source, P, sigmas=(0.5, 0.9))}
 
 
 # ------------------------------------------------------------- oracle (CPU) --

@@ -130,6 +130,9 @@ typedef struct {
     float select_logit;   /* GG_POLICY_LEARNED: vertices whose logit exceeds this are corrected */
     float fallback_frac;  /* GG_POLICY_LEARNED: a selection with more in-edges than this x m runs
                              the full correction (1 = never; < 0 = always) */
+    float select_cost;    /* GG_POLICY_LEARNED: a vertex with in-degree d is selected when its logit
+                             exceeds fmaf(select_cost, L(d), select_logit), L(d) = bit length of d
+                             (0 for d = 0): hub rows need stronger scores (0 = plain threshold) */
 } gg_params;
 
 typedef struct {
@@ -279,15 +282,18 @@ gg_status gg_set_trace(gg_graph *g, float *features, uint8_t *labels, uint64_t c
 gg_status gg_mlp_score(const float *features, uint64_t rows, const float *params, float *logits, void *stream);
 
 /*
- * gg_mlp_train - `steps` steps of minibatch SGD on the mean logistic loss,
- * in one block: step s uses rows ((start + s*batch + j) mod rows) * stride
- * mod rows, j < batch (stride coprime to rows makes this a permutation).
- * Forward in the scorer's arithmetic; gradients in FP32 with the bfloat16
- * rounding treated as the identity, summed in row order (deterministic).
+ * gg_mlp_train - `steps` steps of minibatch SGD on the mean logistic loss:
+ * step s uses rows ((start + s*batch + j) mod rows) * stride mod rows,
+ * j < batch (stride coprime to rows makes this a permutation). Forward in the
+ * scorer's arithmetic; the backward contractions on the tensor cores
+ * (bfloat16 operands, the FP32 gradients split into two bfloat16 parts, FP32
+ * accumulation), one block per 128 rows of a step, the blocks' partial
+ * gradients summed in block order (deterministic). Allocates its scratch
+ * (about 19 KB per 128 rows of the batch) from the library's pool.
  *   features  device float[rows][8]; labels device uint8[rows] (0 / 1)
  *   rows      1 .. 2^32-1; stride < rows
  *   params    device float[GG_MLP_NPARAM], updated in place (FP32 masters)
- *   batch     1 .. 128
+ *   batch     1 .. 16384
  *   losses    device float[steps] (nullable): each step's mean loss
  *   grad_last device float[GG_MLP_NPARAM] (nullable): the last step's gradient
  */
@@ -327,8 +333,14 @@ typedef struct {
     int64_t big_arcs;     /* graphs with at least this many arcs get cluster teams */
     int32_t small_first;  /* every small_first-th cluster serves the single-CTA queries first,
                              the rest start with the cluster-team queries (0: all start there) */
-    int32_t reserved;     /* 0 */
+    int32_t order;        /* order in which teams claim queries: GG_ORDER_MOST_WORK (0, the largest
+                             estimated work first: shortest makespan), GG_ORDER_LEAST_WORK (1, the
+                             smallest first: lowest median latency), GG_ORDER_TRAVERSALS_FIRST (2,
+                             BFS / SSSP before personalized PageRank, each largest first) */
 } gg_batch_config;
+#define GG_ORDER_MOST_WORK 0
+#define GG_ORDER_LEAST_WORK 1
+#define GG_ORDER_TRAVERSALS_FIRST 2
 
 typedef struct {
     uint64_t latency_ns;  /* from the launch's start to the query's completion */

@@ -65,7 +65,7 @@ class _Params(ctypes.Structure):
                 ("fallback_frac", ctypes.c_double), ("replay_select", ctypes.POINTER(ctypes.c_uint8)),
                 ("n_replay_select", ctypes.c_int32), ("replay_select_tol", ctypes.c_double),
                 ("trace_x", ctypes.POINTER(ctypes.c_float)), ("trace_y", ctypes.POINTER(ctypes.c_uint8)),
-                ("trace_cap", ctypes.c_int64), ("label_tol", ctypes.c_double)]
+                ("trace_cap", ctypes.c_int64), ("label_tol", ctypes.c_double), ("select_cost", ctypes.c_float)]
 
 
 class _Out(ctypes.Structure):
@@ -188,7 +188,7 @@ def run(n, rowptr, colidx, weights=None, *, app="pagerank", policy="exact", sigm
         seed=0, alpha=4, theta=0.05, max_iters=20, damping=0.85, epsilon=0.0, source=0,
         flags=0, symmetric=False, nthreads=1, replay_masks=None, replay_tol=1e-5,
         trigger_ratio=0.5, replay_modes=None, mlp=None, select_logit=0.0, fallback_frac=1.0,
-        replay_select=None, replay_select_tol=0.05, trace_cap=0, label_tol=1e-3):
+        replay_select=None, replay_select_tol=0.05, trace_cap=0, label_tol=1e-3, select_cost=0.0):
     """Run one GraphGuess execution on the CPU; returns a dict with ``values``
     (float64 for PageRank, uint32 otherwise), the final CSC-order ``mask`` and
     per-iteration statistics. ``damping`` and ``theta`` are given as the float32
@@ -202,7 +202,9 @@ def run(n, rowptr, colidx, weights=None, *, app="pagerank", policy="exact", sigm
     follow the given modes instead of its policy's (iterations past the given
     ones are approximate). ``policy="learned"`` scores every vertex with the
     MLP ``mlp`` (MLP_NPARAM float32) at each correction and corrects only
-    those with a logit above ``select_logit``; ``replay_select`` (uint8[n] per
+    those with a logit above ``select_logit`` (plus ``select_cost`` times the bit
+    length of the vertex's in-degree, as one fused float operation);
+    ``replay_select`` (uint8[n] per
     learned correction) adopts the given selections after checking that every
     differing one lies within ``replay_select_tol`` of the threshold.
     ``trace_cap`` > 0 records features / labels of every vertex at each full
@@ -238,7 +240,8 @@ def run(n, rowptr, colidx, weights=None, *, app="pagerank", policy="exact", sigm
                   _p(rep, ctypes.c_uint8), n_rep, replay_tol, float(np.float32(trigger_ratio)),
                   _p(modes, ctypes.c_int8), _p(mlp_a, ctypes.c_float), float(select_logit),
                   float(fallback_frac), _p(rsel, ctypes.c_uint8), n_rsel, float(replay_select_tol),
-                  _p(tx, ctypes.c_float), _p(ty, ctypes.c_uint8), int(trace_cap), float(label_tol))
+                  _p(tx, ctypes.c_float), _p(ty, ctypes.c_uint8), int(trace_cap), float(label_tol),
+                  float(np.float32(select_cost)))
     T = max(max_iters, 1)
     pr = np.empty(n, np.float64) if a in (PAGERANK, PPR) else None
     iv = np.empty(n, np.uint32) if a not in (PAGERANK, PPR) else None

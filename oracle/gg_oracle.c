@@ -120,6 +120,8 @@ typedef struct {
     uint8_t *trace_y;            /* labels of those rows */
     int64_t trace_cap;           /* rows available in trace_x / trace_y */
     double label_tol;            /* PageRank label: |new-old| > label_tol * |new| */
+    float select_cost;           /* ORC_LEARNED: the threshold of a vertex with in-degree d is
+                                    fmaf(select_cost, L(d), select_logit) in float, L(d) = bit length of d */
 } orc_params;
 
 typedef struct {
@@ -365,6 +367,19 @@ static int min_app_estatus(int app, uint32_t acc, uint32_t cand, double theta)
     return lhs > rhs;
 }
 
+/* Learned selection threshold of a vertex with in-degree d: select_logit
+ * plus select_cost times the bit length of d, computed as one fused float
+ * operation (the library computes it the same way). */
+static double select_threshold(const orc_params *p, int64_t d)
+{
+    int bits = 0;
+    while (d > 0) {
+        bits += 1;
+        d >>= 1;
+    }
+    return (double)fmaf(p->select_cost, (float)bits, (float)p->select_logit);
+}
+
 int orc_run(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx,
             const uint32_t *weights, const orc_params *p, orc_out *o)
 {
@@ -464,14 +479,14 @@ int orc_run(int32_t n, int64_t m, const int32_t *rowptr, const int32_t *colidx,
                 float x[ORC_MLP_IN];
                 vertex_features(u, n, i, p->app, in_ptr, outdeg, mask, hist, executed, x);
                 logit[u] = mlp_row(p->mlp, x, 1, NULL, NULL, NULL, NULL);
-                sel[u] = logit[u] > p->select_logit;
+                sel[u] = logit[u] > select_threshold(p, in_ptr[u + 1] - in_ptr[u]);
             }
             if (o->logits) memcpy(o->logits, logit, (size_t)n * sizeof(double));
             if (p->replay_select && select_next < p->n_replay_select) {
                 const uint8_t *given = p->replay_select + (size_t)select_next * (size_t)n;
                 for (int32_t u = 0; u < n; ++u) {
                     if ((given[u] != 0) != (sel[u] != 0)) {
-                        const double margin = fabs(logit[u] - p->select_logit);
+                        const double margin = fabs(logit[u] - select_threshold(p, in_ptr[u + 1] - in_ptr[u]));
                         o->select_mismatch += 1;
                         if (margin > o->select_max_margin) o->select_max_margin = margin;
                         if (!(margin <= p->replay_select_tol)) o->select_violations += 1;

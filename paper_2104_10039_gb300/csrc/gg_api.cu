@@ -344,8 +344,8 @@ static gg_status learned_select(gg_graph *g, gg_app app, const gg_params *p, uin
                                 uint32_t *nsel, uint32_t *total)
 {
     *learned = false;
-    GG_CUDA(launch_mlp_select(feat_args(g, app, i), g->mlp, p->select_logit, g->sel_flag, g->sel_off, g->logits,
-                              g->num_sms, g->stream));
+    GG_CUDA(launch_mlp_select(feat_args(g, app, i), g->mlp, p->select_logit, p->select_cost, g->sel_flag,
+                              g->sel_off, g->logits, g->num_sms, g->stream));
     GG_CUDA(launch_scan_u32(g->sel_flag, g->sel_pos, (size_t)g->n, g->scan_tmp, g->stream));
     GG_CUDA(launch_scan_u32(g->sel_off, g->sel_off, (size_t)g->n, g->scan_tmp, g->stream));
     GG_CUDA(launch_sel_compact(g->n, g->sel_flag, g->sel_pos, g->sel_off, g->sel_rows, g->sub_ptr, g->sel_counts,
@@ -817,8 +817,9 @@ gg_status run(gg_graph *g, gg_app app, double ratio, gg_policy policy, const gg_
     if ((int)policy < GG_POLICY_EXACT || (int)policy > GG_POLICY_LEARNED) { set_error("gg_run: unknown policy %d", (int)policy); return GG_ERR_INVALID_ARG; }
     if (policy == GG_POLICY_LEARNED) {
         if (!g->has_scorer) { set_error("gg_run: GG_POLICY_LEARNED needs a scorer (gg_set_scorer)"); return GG_ERR_STATE; }
-        if (p->fallback_frac != p->fallback_frac || p->select_logit != p->select_logit) {
-            set_error("gg_run: select_logit / fallback_frac is NaN");
+        if (p->fallback_frac != p->fallback_frac || p->select_logit != p->select_logit ||
+            p->select_cost != p->select_cost) {
+            set_error("gg_run: select_logit / fallback_frac / select_cost is NaN");
             return GG_ERR_INVALID_ARG;
         }
     }
@@ -1293,13 +1294,16 @@ gg_status gg_mlp_train(const float *features, const uint8_t *labels, uint64_t ro
 {
     if (!features || !labels || !params) { set_error("gg_mlp_train: NULL argument"); return GG_ERR_INVALID_ARG; }
     if (rows < 1 || rows > 0xFFFFFFFFull) { set_error("gg_mlp_train: rows must be in [1, 2^32)"); return GG_ERR_INVALID_ARG; }
-    if (batch < 1 || batch > 128) { set_error("gg_mlp_train: batch must be in [1, 128]"); return GG_ERR_INVALID_ARG; }
+    if (batch < 1 || batch > 16384) { set_error("gg_mlp_train: batch must be in [1, 16384]"); return GG_ERR_INVALID_ARG; }
     if (stride >= rows && rows > 1) { set_error("gg_mlp_train: stride must be < rows"); return GG_ERR_INVALID_ARG; }
     if (!(lr == lr)) { set_error("gg_mlp_train: lr is NaN"); return GG_ERR_INVALID_ARG; }
     if (((uintptr_t)features) & 7u) { set_error("gg_mlp_train: features must be 8-byte aligned"); return GG_ERR_INVALID_ARG; }
     if (steps == 0) return GG_OK;
+    DevBuf scratch;   // partial gradients of the blocks, released in stream order
+    gg_status st = scratch.alloc(4 * mlp_train_scratch((int)batch), (cudaStream_t)stream);
+    if (st != GG_OK) return st;
     GG_CUDA(launch_mlp_train(features, labels, rows, params, (int)batch, (int)steps, lr, rows > 1 ? stride : 0,
-                             start, losses, grad_last, (cudaStream_t)stream));
+                             start, losses, grad_last, scratch.f32(), (cudaStream_t)stream));
     return GG_OK;
 }
 

@@ -6,7 +6,8 @@
 // (its CTAs split each iteration's work and meet at the hardware cluster
 // barrier between iterations); the rest by single CTAs (__syncthreads). A
 // team claims its next query with one atomic on a global counter (queries in
-// descending order of estimated work), so no block ever waits for another
+// the batch's order: by estimated work, descending or ascending, or BFS /
+// SSSP before personalized PageRank), so no block ever waits for another
 // team: the only waits are the cluster barriers inside a team, which every
 // CTA of the cluster reaches the same number of times.
 //
@@ -497,6 +498,10 @@ gg_status gg_batch_create(gg_graph *const *graphs, int32_t n_graphs, const gg_qu
         return GG_ERR_INVALID_ARG;
     }
     if (cfg->small_first < 0) { set_error("gg_batch_create: small_first must be >= 0"); return GG_ERR_INVALID_ARG; }
+    if (cfg->order < GG_ORDER_MOST_WORK || cfg->order > GG_ORDER_TRAVERSALS_FIRST) {
+        set_error("gg_batch_create: unknown order %d", (int)cfg->order);
+        return GG_ERR_INVALID_ARG;
+    }
     if (!(cfg->threads == 0 || cfg->threads == 256 || cfg->threads == 512 || cfg->threads == 1024)) {
         set_error("gg_batch_create: threads must be 0 (256), 256, 512 or 1024");
         return GG_ERR_INVALID_ARG;
@@ -552,10 +557,14 @@ gg_status gg_batch_create(gg_graph *const *graphs, int32_t n_graphs, const gg_qu
             b->hn[q] = g->n;
             words += 4ull * (unsigned long long)g->n + 8ull;
             words = (words + 31ull) & ~31ull;
-            // estimated work: PPR iters * m; traversals ~ m (each arc relaxed about once)
+            // estimated work: PPR iters * m; traversals ~ m (each arc relaxed about once);
+            // the sort key gives the claim order (ascending key first)
             const double work = (Q.app == GG_APP_PPR ? (double)Q.iters : 1.0) * ((double)g->m + (double)g->n);
-            if (cfg->cluster > 1 && (int64_t)g->m >= cfg->big_arcs) big.push_back({-work, q});
-            else small.push_back({-work, q});
+            double key = -work;
+            if (cfg->order == GG_ORDER_LEAST_WORK) key = work;
+            else if (cfg->order == GG_ORDER_TRAVERSALS_FIRST) key = (Q.app == GG_APP_PPR ? 1e300 : 0.0) - work;
+            if (cfg->cluster > 1 && (int64_t)g->m >= cfg->big_arcs) big.push_back({key, q});
+            else small.push_back({key, q});
         }
         if (st != GG_OK) break;
         std::stable_sort(big.begin(), big.end());

@@ -299,14 +299,15 @@ cudaError_t launch_contrib(int32_t n, const float *rank, const int32_t *deg, con
 // Scorer (gg_mlp.cu).
 cudaError_t launch_mlp_score(const float *x, long long rows, const float *P, float *logits, int num_sms,
                              cudaStream_t s);
-cudaError_t launch_mlp_select(const FeatArgs &fa, const float *P, float tau, uint32_t *sel_flag, uint32_t *sel_deg,
-                              float *logits, int num_sms, cudaStream_t s);
+cudaError_t launch_mlp_select(const FeatArgs &fa, const float *P, float tau, float cost, uint32_t *sel_flag,
+                              uint32_t *sel_deg, float *logits, int num_sms, cudaStream_t s);
 cudaError_t launch_trace_features(const FeatArgs &fa, float *out, int num_sms, cudaStream_t s);
 cudaError_t launch_trace_labels(int32_t n, const float *rc, const float *rn, const uint32_t *vc, const uint32_t *vn,
                                 float tol, uint8_t *y, int num_sms, cudaStream_t s);
 cudaError_t launch_mlp_train(const float *x, const uint8_t *y, unsigned long long rows, float *params, int B,
                              int steps, float lr, unsigned long long stride, unsigned long long start, float *losses,
-                             float *grad_last, cudaStream_t s);
+                             float *grad_last, float *scratch, cudaStream_t s);
+size_t mlp_train_scratch(int B);
 // Learned correction plumbing (gg_learned.cu).
 cudaError_t launch_sel_compact(int32_t n, const uint32_t *sel_flag, const uint32_t *sel_pos, const uint32_t *sel_off,
                                int32_t *rows, int32_t *sub_ptr, uint32_t *counts, int num_sms, cudaStream_t s);

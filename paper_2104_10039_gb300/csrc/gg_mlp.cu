@@ -4,7 +4,8 @@
 //
 // Arithmetic: weights and each layer's inputs in bfloat16 (round to nearest
 // even), products accumulated in FP32 on the tensor cores (mma.sync
-// m16n8k16, one warp per 16 rows), FP32 biases. A layer's FP32 output
+// m16n8k16, one warp per 16 rows), FP32 biases. Training runs its forward and
+// backward contractions on the tensor cores too (k_train_grad). A layer's FP32 output
 // fragment is, element for element, the next layer's input fragment, so the
 // activations never leave registers.
 //
@@ -216,8 +217,9 @@ __device__ __forceinline__ float2 feature_pair(const FeatArgs &fa, int32_t u, in
     }
 }
 
-// Learned correction, step 1: score every vertex; select those above tau.
-__global__ void __launch_bounds__(256) k_mlp_select(FeatArgs fa, const float *__restrict__ P, float tau,
+// Learned correction, step 1: score every vertex; select those whose logit
+// exceeds fmaf(cost, L(d), tau), L(d) the bit length of the in-degree d.
+__global__ void __launch_bounds__(256) k_mlp_select(FeatArgs fa, const float *__restrict__ P, float tau, float cost,
                                                     uint32_t *__restrict__ sel_flag, uint32_t *__restrict__ sel_deg,
                                                     float *__restrict__ logits)
 {
@@ -242,13 +244,13 @@ __global__ void __launch_bounds__(256) k_mlp_select(FeatArgs fa, const float *__
         const float2 z = mlp_forward16(f, x0, x1);
         if (t == 0) {
             if (u0 < fa.n) {
-                const bool s = z.x > tau;
+                const bool s = z.x > __fmaf_rn(cost, (float)(32 - __clz(d0)), tau);
                 sel_flag[u0] = s;
                 sel_deg[u0] = s ? (uint32_t)d0 : 0u;
                 if (logits) logits[u0] = z.x;
             }
             if (u1 < fa.n) {
-                const bool s = z.y > tau;
+                const bool s = z.y > __fmaf_rn(cost, (float)(32 - __clz(d1)), tau);
                 sel_flag[u1] = s;
                 sel_deg[u1] = s ? (uint32_t)d1 : 0u;
                 if (logits) logits[u1] = z.y;
@@ -287,132 +289,227 @@ __global__ void k_trace_labels(int32_t n, const float *__restrict__ rc, const fl
     }
 }
 
-// --------------------------------------------------------------- training --
-// One block runs `steps` SGD steps over minibatches of B <= 128 rows: row j of
-// step s is ((start + s*B + j) mod rows) * stride mod rows. Forward on the
-// tensor cores (the scorer's own arithmetic), backward in FP32 on the CUDA
-// cores with the rounding treated as the identity; every gradient entry is
-// summed over the batch in row order by one thread, so runs are
-// deterministic. Loss: mean logistic loss of the logits against 0/1 labels.
-constexpr int kTrainB = 128;
+// ---------------------------------------------------------------- training ---
+// One SGD step on the mean logistic loss over a minibatch of B rows, in two
+// launches: k_train_grad (one block per 128 rows) runs the forward pass and
+// the backward contractions on the tensor cores and writes the block's
+// partial gradient; k_train_update sums the blocks' partials in block order
+// and updates the parameters (deterministic). The backward contractions
+//   dH1 = (dH2 W2) .* [H1 > 0],   gW2 = dH2^T H1,   gW1 = dH1^T X
+// run as mma.sync m16n8k16 (bfloat16 operands, FP32 accumulation). H1 and X
+// are bfloat16 values already; the FP32 gradients dH2 and dH1 enter as two
+// bfloat16 parts (hi = bf16(v), lo = bf16(v - hi)) in two products, so the
+// operands lose almost nothing to the rounding. Biases and w3: FP32 column
+// sums in row order.
+constexpr int kTrainRows = 128;   // rows per block (8 warps x 16)
 
-struct TrainSmem {
-    float P[4804];
-    float W2r[64 * 64];       // bfloat16 values of W2 and w3
-    float w3r[64];
-    MlpFrag f;
-    float X[kTrainB][8];      // bfloat16 values of the inputs
-    float H1[kTrainB][64];
-    float H2[kTrainB][64];
-    float DH2[kTrainB][64];
-    float DH1[kTrainB][64];
-    float Z[kTrainB];
-    float DZ[kTrainB];
+struct GradSmem {
+    MlpFrag f;                    // forward fragments
+    uint2 w2b[4][8][32];          // backward B fragments: B[k = j][n = i] = W2[j][i], k-chunk, n-tile, lane
+    float w3r[64];                // bfloat16 values of w3
+    float X[kTrainRows][8];       // bfloat16 values of the inputs
+    float H1[kTrainRows][64];
+    float H2[kTrainRows][64];
+    float DH2[kTrainRows][64];
+    float DH1[kTrainRows][64];
+    float Z[kTrainRows];
+    float DZ[kTrainRows];
     float red[8];
-    unsigned long long idx[kTrainB];
+    unsigned long long idx[kTrainRows];
 };
 
-__global__ void __launch_bounds__(256) k_mlp_train(const float *__restrict__ x, const uint8_t *__restrict__ y,
-                                                   unsigned long long rows, float *__restrict__ params, int B,
-                                                   int steps, float lr, unsigned long long stride,
-                                                   unsigned long long start, float *__restrict__ losses,
-                                                   float *__restrict__ grad_last)
+// hi / lo bfloat16 parts of two FP32 values, packed
+__device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t &lo)
+{
+    hi = pack_bf16(a, b);
+    const float2 h = unpack_bf16(hi);
+    lo = pack_bf16(a - h.x, b - h.y);
+}
+
+__global__ void __launch_bounds__(256) k_train_grad(const float *__restrict__ x, const uint8_t *__restrict__ y,
+                                                    unsigned long long rows, const float *__restrict__ params, int B,
+                                                    unsigned long long first, unsigned long long stride,
+                                                    float *__restrict__ part, float *__restrict__ loss_part)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    TrainSmem &s = *reinterpret_cast<TrainSmem *>(smem_raw);
+    GradSmem &s = *reinterpret_cast<GradSmem *>(smem_raw);
     const int tid = threadIdx.x, w = tid >> 5;
     const int l = (int)lane_id(), g = l >> 2, t = l & 3;
-    for (int i = tid; i < 4801; i += blockDim.x) s.P[i] = params[i];
-    __syncthreads();
-    for (int step = 0; step < steps; ++step) {
-        mlp_build(s.P, s.f);
-        for (int i = tid; i < 4096; i += blockDim.x) s.W2r[i] = bf16r(s.P[kOffW2 + i]);
-        if (tid < 64) s.w3r[tid] = bf16r(s.P[kOffW3 + tid]);
-        if (tid < kTrainB) {
-            const unsigned long long j = (start + (unsigned long long)step * (unsigned long long)B + tid) % rows;
-            s.idx[tid] = (j * stride) % rows;
-        }
-        __syncthreads();
-        {
-            const int r0 = 16 * w + g, r1 = r0 + 8;
-            const float2 xa = r0 < B ? *reinterpret_cast<const float2 *>(x + s.idx[r0] * 8 + 2 * t)
-                                     : make_float2(0.0f, 0.0f);
-            const float2 xb = r1 < B ? *reinterpret_cast<const float2 *>(x + s.idx[r1] * 8 + 2 * t)
-                                     : make_float2(0.0f, 0.0f);
-            s.X[r0][2 * t] = bf16r(xa.x);
-            s.X[r0][2 * t + 1] = bf16r(xa.y);
-            s.X[r1][2 * t] = bf16r(xb.x);
-            s.X[r1][2 * t + 1] = bf16r(xb.y);
-            const float2 z = mlp_forward16(s.f, xa, xb, &s.H1[16 * w][0], &s.H2[16 * w][0]);
-            if (t == 0) {
-                s.Z[r0] = z.x;
-                s.Z[r1] = z.y;
-            }
-        }
-        __syncthreads();
-        float lpart = 0.0f;
-        if (tid < kTrainB) {
-            float dz = 0.0f;
-            if (tid < B) {
-                const float z = s.Z[tid];
-                const float lab = y[s.idx[tid]] ? 1.0f : 0.0f;
-                dz = (1.0f / (1.0f + expf(-z)) - lab) / (float)B;
-                lpart = fmaxf(z, 0.0f) - z * lab + log1pf(expf(-fabsf(z)));
-            }
-            s.DZ[tid] = dz;
-        }
-        if (losses) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) lpart += __shfl_xor_sync(0xFFFFFFFFu, lpart, o);
-            if (l == 0) s.red[w] = lpart;
-        }
-        __syncthreads();
-        if (losses && tid == 0) {
-            float sum = 0.0f;
-            for (int i = 0; i < 8; ++i) sum += s.red[i];
-            losses[step] = sum / (float)B;
-        }
-        for (int i = tid; i < kTrainB * 64; i += blockDim.x) {
-            const int r = i >> 6, j = i & 63;
-            s.DH2[r][j] = s.H2[r][j] > 0.0f ? s.DZ[r] * s.w3r[j] : 0.0f;
-        }
-        __syncthreads();
-        for (int i = tid; i < kTrainB * 64; i += blockDim.x) {
-            const int r = i >> 6, k = i & 63;
-            float acc = 0.0f;
-            if (s.H1[r][k] > 0.0f) {
-                for (int j = 0; j < 64; ++j) acc = fmaf(s.W2r[j * 64 + k], s.DH2[r][j], acc);
-            }
-            s.DH1[r][k] = acc;
-        }
-        __syncthreads();
-        const bool last = step == steps - 1;
-        for (int o = tid; o < 4801; o += blockDim.x) {
-            float gsum = 0.0f;
-            if (o < kOffB1) {                          // W1[k][f]
-                const int k = o >> 3, fi = o & 7;
-                for (int r = 0; r < B; ++r) gsum = fmaf(s.DH1[r][k], s.X[r][fi], gsum);
-            } else if (o < kOffW2) {                   // b1[k]
-                const int k = o - kOffB1;
-                for (int r = 0; r < B; ++r) gsum += s.DH1[r][k];
-            } else if (o < kOffB2) {                   // W2[j][k]
-                const int j = (o - kOffW2) >> 6, k = (o - kOffW2) & 63;
-                for (int r = 0; r < B; ++r) gsum = fmaf(s.DH2[r][j], s.H1[r][k], gsum);
-            } else if (o < kOffW3) {                   // b2[j]
-                const int j = o - kOffB2;
-                for (int r = 0; r < B; ++r) gsum += s.DH2[r][j];
-            } else if (o < kOffB3) {                   // w3[j]
-                const int j = o - kOffW3;
-                for (int r = 0; r < B; ++r) gsum = fmaf(s.DZ[r], s.H2[r][j], gsum);
-            } else {                                   // b3
-                for (int r = 0; r < B; ++r) gsum += s.DZ[r];
-            }
-            if (last && grad_last) grad_last[o] = gsum;
-            s.P[o] = s.P[o] - lr * gsum;
-        }
-        __syncthreads();
+    const int row0 = kTrainRows * (int)blockIdx.x;
+    mlp_build(params, s.f);
+    for (int i = tid; i < 4 * 8 * 32; i += blockDim.x) {
+        const int kc = i >> 8, j = (i >> 5) & 7, ln = i & 31, gg_ = ln >> 2, tt = ln & 3;
+        const float *p0 = params + kOffW2 + (16 * kc + 2 * tt) * 64 + 8 * j + gg_;
+        s.w2b[kc][j][ln] = make_uint2(pack_bf16(p0[0], p0[64]), pack_bf16(p0[8 * 64], p0[9 * 64]));
     }
-    for (int i = tid; i < 4801; i += blockDim.x) params[i] = s.P[i];
+    if (tid < 64) s.w3r[tid] = bf16r(params[kOffW3 + tid]);
+    if (tid < kTrainRows) {
+        const unsigned long long j = (first + (unsigned long long)(row0 + tid)) % rows;
+        s.idx[tid] = (j * stride) % rows;
+    }
+    __syncthreads();
+    // ---- forward (16 rows per warp), activations kept -----------------------
+    {
+        const int r0 = 16 * w + g, r1 = r0 + 8;
+        const bool v0 = row0 + r0 < B, v1 = row0 + r1 < B;
+        const float2 xa = v0 ? *reinterpret_cast<const float2 *>(x + s.idx[r0] * 8 + 2 * t) : make_float2(0.0f, 0.0f);
+        const float2 xb = v1 ? *reinterpret_cast<const float2 *>(x + s.idx[r1] * 8 + 2 * t) : make_float2(0.0f, 0.0f);
+        s.X[r0][2 * t] = bf16r(xa.x);
+        s.X[r0][2 * t + 1] = bf16r(xa.y);
+        s.X[r1][2 * t] = bf16r(xb.x);
+        s.X[r1][2 * t + 1] = bf16r(xb.y);
+        const float2 z = mlp_forward16(s.f, xa, xb, &s.H1[16 * w][0], &s.H2[16 * w][0]);
+        if (t == 0) {
+            s.Z[r0] = z.x;
+            s.Z[r1] = z.y;
+        }
+    }
+    __syncthreads();
+    // ---- loss and dL/dz (rows past the batch contribute nothing) -------------
+    float lpart = 0.0f;
+    if (tid < kTrainRows) {
+        float dz = 0.0f;
+        if (row0 + tid < B) {
+            const float z = s.Z[tid];
+            const float lab = y[s.idx[tid]] ? 1.0f : 0.0f;
+            dz = (1.0f / (1.0f + expf(-z)) - lab) / (float)B;
+            lpart = fmaxf(z, 0.0f) - z * lab + log1pf(expf(-fabsf(z)));
+        }
+        s.DZ[tid] = dz;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lpart += __shfl_xor_sync(0xFFFFFFFFu, lpart, o);
+    if (l == 0) s.red[w] = lpart;
+    __syncthreads();
+    if (tid == 0) {
+        float sum = 0.0f;
+        for (int i = 0; i < 8; ++i) sum += s.red[i];
+        loss_part[blockIdx.x] = sum;
+    }
+    for (int i = tid; i < kTrainRows * 64; i += blockDim.x) {
+        const int r = i >> 6, j = i & 63;
+        s.DH2[r][j] = s.H2[r][j] > 0.0f ? s.DZ[r] * s.w3r[j] : 0.0f;
+    }
+    __syncthreads();
+    // ---- dH1 = (dH2 W2) .* [H1 > 0]: warp w, rows 16w .. 16w + 15 -----------
+    {
+        const int ra = 16 * w + g, rb = ra + 8;
+        uint32_t ah[4][4], al[4][4];
+#pragma unroll
+        for (int kc = 0; kc < 4; ++kc) {
+            const int c = 16 * kc + 2 * t;
+            split2(s.DH2[ra][c], s.DH2[ra][c + 1], ah[kc][0], al[kc][0]);
+            split2(s.DH2[rb][c], s.DH2[rb][c + 1], ah[kc][1], al[kc][1]);
+            split2(s.DH2[ra][c + 8], s.DH2[ra][c + 9], ah[kc][2], al[kc][2]);
+            split2(s.DH2[rb][c + 8], s.DH2[rb][c + 9], ah[kc][3], al[kc][3]);
+        }
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int kc = 0; kc < 4; ++kc) {
+                const uint2 b = s.w2b[kc][nt][l];
+                mma_bf16(d, ah[kc][0], ah[kc][1], ah[kc][2], ah[kc][3], b.x, b.y);
+                mma_bf16(d, al[kc][0], al[kc][1], al[kc][2], al[kc][3], b.x, b.y);
+            }
+            const int c = 8 * nt + 2 * t;
+            s.DH1[ra][c] = s.H1[ra][c] > 0.0f ? d[0] : 0.0f;
+            s.DH1[ra][c + 1] = s.H1[ra][c + 1] > 0.0f ? d[1] : 0.0f;
+            s.DH1[rb][c] = s.H1[rb][c] > 0.0f ? d[2] : 0.0f;
+            s.DH1[rb][c + 1] = s.H1[rb][c + 1] > 0.0f ? d[3] : 0.0f;
+        }
+    }
+    __syncthreads();
+    float *pb = part + (size_t)blockIdx.x * GG_MLP_NPARAM;
+    // ---- gW2[j][i] = sum_r dH2[r][j] H1[r][i]: warp w, j-tile w & 3, i-tiles 4 (w >> 2) .. +3
+    {
+        const int mt = w & 3, nt0 = 4 * (w >> 2);
+        float d[4][4] = {};
+#pragma unroll 2
+        for (int kc = 0; kc < kTrainRows / 16; ++kc) {
+            const int r = 16 * kc + 2 * t, jr = 16 * mt + g;
+            uint32_t h0, l0, h1, l1, h2, l2, h3, l3;
+            split2(s.DH2[r][jr], s.DH2[r + 1][jr], h0, l0);
+            split2(s.DH2[r][jr + 8], s.DH2[r + 1][jr + 8], h1, l1);
+            split2(s.DH2[r + 8][jr], s.DH2[r + 9][jr], h2, l2);
+            split2(s.DH2[r + 8][jr + 8], s.DH2[r + 9][jr + 8], h3, l3);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int ic = 8 * (nt0 + q) + g;
+                const uint32_t b0 = pack_bf16(s.H1[r][ic], s.H1[r + 1][ic]);
+                const uint32_t b1 = pack_bf16(s.H1[r + 8][ic], s.H1[r + 9][ic]);
+                mma_bf16(d[q], h0, h1, h2, h3, b0, b1);
+                mma_bf16(d[q], l0, l1, l2, l3, b0, b1);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j0 = 16 * mt + g, i0 = 8 * (nt0 + q) + 2 * t;
+            pb[kOffW2 + j0 * 64 + i0] = d[q][0];
+            pb[kOffW2 + j0 * 64 + i0 + 1] = d[q][1];
+            pb[kOffW2 + (j0 + 8) * 64 + i0] = d[q][2];
+            pb[kOffW2 + (j0 + 8) * 64 + i0 + 1] = d[q][3];
+        }
+    }
+    if (w < 4) {
+        // ---- gW1[k][f] = sum_r dH1[r][k] X[r][f]: warp w, k-tile w ----------
+        float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 2
+        for (int kc = 0; kc < kTrainRows / 16; ++kc) {
+            const int r = 16 * kc + 2 * t, kr = 16 * w + g;
+            uint32_t h0, l0, h1, l1, h2, l2, h3, l3;
+            split2(s.DH1[r][kr], s.DH1[r + 1][kr], h0, l0);
+            split2(s.DH1[r][kr + 8], s.DH1[r + 1][kr + 8], h1, l1);
+            split2(s.DH1[r + 8][kr], s.DH1[r + 9][kr], h2, l2);
+            split2(s.DH1[r + 8][kr + 8], s.DH1[r + 9][kr + 8], h3, l3);
+            const uint32_t b0 = pack_bf16(s.X[r][g], s.X[r + 1][g]);
+            const uint32_t b1 = pack_bf16(s.X[r + 8][g], s.X[r + 9][g]);
+            mma_bf16(d, h0, h1, h2, h3, b0, b1);
+            mma_bf16(d, l0, l1, l2, l3, b0, b1);
+        }
+        const int k0 = 16 * w + g, f0 = 2 * t;
+        pb[kOffW1 + k0 * 8 + f0] = d[0];
+        pb[kOffW1 + k0 * 8 + f0 + 1] = d[1];
+        pb[kOffW1 + (k0 + 8) * 8 + f0] = d[2];
+        pb[kOffW1 + (k0 + 8) * 8 + f0 + 1] = d[3];
+    } else {
+        // ---- biases and w3: column sums in row order --------------------------
+        for (int c = tid - 128; c < 193; c += 128) {
+            float acc = 0.0f;
+            if (c < 64) {
+                for (int r = 0; r < kTrainRows; ++r) acc += s.DH1[r][c];
+                pb[kOffB1 + c] = acc;
+            } else if (c < 128) {
+                for (int r = 0; r < kTrainRows; ++r) acc += s.DH2[r][c - 64];
+                pb[kOffB2 + c - 64] = acc;
+            } else if (c < 192) {
+                for (int r = 0; r < kTrainRows; ++r) acc = fmaf(s.DZ[r], s.H2[r][c - 128], acc);
+                pb[kOffW3 + c - 128] = acc;
+            } else {
+                for (int r = 0; r < kTrainRows; ++r) acc += s.DZ[r];
+                pb[kOffB3] = acc;
+            }
+        }
+    }
+}
+
+// Sum of the blocks' partial gradients in block order; parameters updated.
+__global__ void __launch_bounds__(256) k_train_update(const float *__restrict__ part, int nb,
+                                                      const float *__restrict__ loss_part, float *__restrict__ params,
+                                                      float lr, float inv_b, float *__restrict__ loss_out,
+                                                      float *__restrict__ grad_out)
+{
+    for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < GG_MLP_NPARAM; o += gridDim.x * blockDim.x) {
+        float gsum = 0.0f;
+        for (int b = 0; b < nb; ++b) gsum += part[(size_t)b * GG_MLP_NPARAM + o];
+        if (grad_out) grad_out[o] = gsum;
+        params[o] = params[o] - lr * gsum;
+    }
+    if (loss_out && blockIdx.x == 0 && threadIdx.x == 0) {
+        float sum = 0.0f;
+        for (int b = 0; b < nb; ++b) sum += loss_part[b];
+        *loss_out = sum * inv_b;
+    }
 }
 
 }  // namespace
@@ -428,13 +525,14 @@ cudaError_t launch_mlp_score(const float *x, long long rows, const float *P, flo
     return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_select(const FeatArgs &fa, const float *P, float tau, uint32_t *sel_flag, uint32_t *sel_deg,
+cudaError_t launch_mlp_select(const FeatArgs &fa, const float *P, float tau, float cost, uint32_t *sel_flag,
+                              uint32_t *sel_deg,
                               float *logits, int num_sms, cudaStream_t s)
 {
     long long blocks = ((long long)fa.n + 127) / 128;
     if (blocks > (long long)num_sms * 8) blocks = (long long)num_sms * 8;
     if (blocks < 1) blocks = 1;
-    k_mlp_select<<<(unsigned)blocks, 256, 0, s>>>(fa, P, tau, sel_flag, sel_deg, logits);
+    k_mlp_select<<<(unsigned)blocks, 256, 0, s>>>(fa, P, tau, cost, sel_flag, sel_deg, logits);
     return cudaGetLastError();
 }
 
@@ -454,22 +552,36 @@ cudaError_t launch_trace_labels(int32_t n, const float *rc, const float *rn, con
     return cudaGetLastError();
 }
 
-size_t mlp_train_smem() { return sizeof(TrainSmem); }
+size_t mlp_train_smem() { return sizeof(GradSmem); }
 
 cudaError_t launch_mlp_train(const float *x, const uint8_t *y, unsigned long long rows, float *params, int B,
                              int steps, float lr, unsigned long long stride, unsigned long long start, float *losses,
-                             float *grad_last, cudaStream_t s)
+                             float *grad_last, float *scratch, cudaStream_t s)
 {
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sizeof(TrainSmem));
+        cudaError_t e = cudaFuncSetAttribute(k_train_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sizeof(GradSmem));
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    k_mlp_train<<<1, 256, sizeof(TrainSmem), s>>>(x, y, rows, params, B, steps, lr, stride, start, losses,
-                                                  grad_last);
+    const int nb = (B + kTrainRows - 1) / kTrainRows;
+    float *part = scratch, *loss_part = scratch + (size_t)nb * GG_MLP_NPARAM;
+    for (int step = 0; step < steps; ++step) {
+        const unsigned long long first = start + (unsigned long long)step * (unsigned long long)B;
+        k_train_grad<<<nb, 256, sizeof(GradSmem), s>>>(x, y, rows, params, B, first, stride, part, loss_part);
+        k_train_update<<<(GG_MLP_NPARAM + 255) / 256, 256, 0, s>>>(part, nb, loss_part, params, lr, 1.0f / (float)B,
+                                                                   losses ? losses + step : nullptr,
+                                                                   step == steps - 1 ? grad_last : nullptr);
+    }
     return cudaGetLastError();
+}
+
+// Scratch (floats) of launch_mlp_train: the blocks' partial gradients and losses.
+size_t mlp_train_scratch(int B)
+{
+    const size_t nb = (size_t)(B + kTrainRows - 1) / kTrainRows;
+    return nb * GG_MLP_NPARAM + nb;
 }
 
 }  // namespace gg

@@ -53,7 +53,7 @@ class gg_params(ctypes.Structure):
                 ("epsilon", ctypes.c_float), ("source", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("flags", ctypes.c_uint32),
                 ("trigger_ratio", ctypes.c_float), ("select_logit", ctypes.c_float),
-                ("fallback_frac", ctypes.c_float)]
+                ("fallback_frac", ctypes.c_float), ("select_cost", ctypes.c_float)]
 
 
 class gg_stats(ctypes.Structure):
@@ -151,9 +151,9 @@ def gg_sample_edges(g: int, sample_ratio: float, seed: int):
 
 
 def make_params(alpha=4, theta=0.05, max_iters=20, damping=0.85, epsilon=0.0, source=0, seed=0,
-                flags=0, trigger_ratio=0.5, select_logit=0.0, fallback_frac=1.0) -> gg_params:
+                flags=0, trigger_ratio=0.5, select_logit=0.0, fallback_frac=1.0, select_cost=0.0) -> gg_params:
     return gg_params(alpha, theta, max_iters, damping, epsilon, source,
-                     seed & 0xFFFFFFFFFFFFFFFF, flags, trigger_ratio, select_logit, fallback_frac)
+                     seed & 0xFFFFFFFFFFFFFFFF, flags, trigger_ratio, select_logit, fallback_frac, select_cost)
 
 
 def gg_run(g: int, app, sample_ratio: float, policy, params: gg_params):
@@ -273,7 +273,7 @@ class gg_query(ctypes.Structure):
 class gg_batch_config(ctypes.Structure):
     _fields_ = [("cluster", ctypes.c_int32), ("warp_deg", ctypes.c_int32), ("cta_deg", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("big_arcs", ctypes.c_int64), ("small_first", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("order", ctypes.c_int32)]
 
 
 class gg_query_stats(ctypes.Structure):
@@ -300,12 +300,15 @@ def make_query(graph: int, app, source: int, iters: int = 20, damping: float = 0
     return gg_query(graph, a, source, iters, damping, warp_deg, cta_deg)
 
 
+GG_ORDER_MOST_WORK, GG_ORDER_LEAST_WORK, GG_ORDER_TRAVERSALS_FIRST = 0, 1, 2
+
+
 def gg_batch_create(graphs, queries, cluster=4, warp_deg=32, cta_deg=1024, big_arcs=1 << 22, threads=256,
-                    small_first=0) -> int:
+                    small_first=0, order=GG_ORDER_MOST_WORK) -> int:
     """Plan a batch over loaded graph handles; returns the batch handle."""
     ga = (_vp * len(graphs))(*graphs)
     qa = (gg_query * len(queries))(*queries)
-    cfg = gg_batch_config(cluster, warp_deg, cta_deg, threads, big_arcs, small_first, 0)
+    cfg = gg_batch_config(cluster, warp_deg, cta_deg, threads, big_arcs, small_first, order)
     h = _vp()
     _check(_lib.gg_batch_create(ga, len(graphs), qa, len(queries), ctypes.byref(cfg), ctypes.byref(h)),
            "gg_batch_create")

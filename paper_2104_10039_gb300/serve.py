@@ -13,6 +13,11 @@ scale, the warp and CTA degree bins on that scale's queries; each query
 then runs with its graph scale's bins.
 Every timed run is the library's persistent launch replayed from its
 captured CUDA graph; this module only arranges calls and reduces results.
+The measurement also runs the tuned batch under each claim order (most
+estimated work first, least first, traversals before personalized
+PageRank) and two unbatched baselines of the same queries, one after
+another: each query alone in its own launch, and BFS / SSSP through the
+library's per-graph engine (gg_run, exact).
 """
 from __future__ import annotations
 
@@ -112,7 +117,51 @@ def autotune(gg, handles, queries, graph_scales, calib=128, per_scale=48, seed=5
                                 "team_candidates": len(teams), "bins_by_scale_ms": bin_table}
 
 
-def measure(gg, graphs, queries, scales, tune=True, reps=5, ppr_iters=20):
+def _latency_summary(lat, queries):
+    """p50 / p99 latency (ms) over all queries and per application."""
+    lat = np.asarray(lat, np.float64)
+    out = {"p50": round(float(np.percentile(lat, 50)), 3), "p99": round(float(np.percentile(lat, 99)), 3),
+           "max": round(float(lat.max()), 3)}
+    for app in APPS:
+        sel = np.array([q[1] == app for q in queries])
+        if sel.any():
+            out[f"{app}_p50"] = round(float(np.percentile(lat[sel], 50)), 3)
+            out[f"{app}_p99"] = round(float(np.percentile(lat[sel], 99)), 3)
+    return out
+
+
+def unbatched(gg, handles, queries, cfg, bins):
+    """Baseline without batching: every query alone in its own persistent
+    launch (the same kernel and team shape), launched one after another.
+    Returns each query's device time (ms, replayed launch)."""
+    times = []
+    for i, (gi, app, s, it) in enumerate(queries):
+        b, t, _ = _run(gg, handles, [(gi, app, s, it)], cfg, reps=1, warm=1, bins=[bins[i]])
+        gg.gg_batch_free(b)
+        times.append(t[0])
+    return np.asarray(times)
+
+
+def engine_baseline(gg, handles, queries, single_times):
+    """Baseline through the library's per-graph engine: each BFS / SSSP query
+    as an exact gg_run to its fixed point (push / pull direction switch), one
+    after another; personalized PageRank has no gg_run form, so those
+    queries keep their single-query launch time. Returns device ms per query."""
+    times = np.array(single_times, np.float64)
+    for i, (gi, app, s, it) in enumerate(queries):
+        if app == "ppr":
+            continue
+        p = gg.make_params(max_iters=1 << 20, source=s, flags=gg.GG_TIMING)
+        gg.gg_run(handles[gi], app, 1.0, "exact", p)   # warm
+        gg.gg_run(handles[gi], app, 1.0, "exact", p)
+        times[i] = gg.stats(handles[gi]).ms_run
+    return times
+
+
+ORDERS = {"most_work_first": 0, "least_work_first": 1, "traversals_first": 2}
+
+
+def measure(gg, graphs, queries, scales, tune=True, reps=5, ppr_iters=20, baseline=True):
     """Load the graphs, autotune, serve every query `reps` times; returns the
     JSON-ready summary (makespan, GTEPS, latency percentiles)."""
     t0 = time.perf_counter()
@@ -126,6 +175,21 @@ def measure(gg, graphs, queries, scales, tune=True, reps=5, ppr_iters=20):
         bins = [bins_by_scale.get(int(scales[gi]), (cfg["warp_deg"], cfg["cta_deg"])) for gi, _, _, _ in queries]
         b, times, st = _run(gg, handles, queries, cfg, reps=reps, warm=1, bins=bins)
         gg.gg_batch_free(b)
+        by_order = {}
+        for name, o in ORDERS.items():
+            bo, to, sto = _run(gg, handles, queries, {**cfg, "order": o}, reps=3, warm=1, bins=bins)
+            gg.gg_batch_free(bo)
+            by_order[name] = {"makespan_ms": round(float(np.median(to)), 3),
+                              "latency_ms": _latency_summary(sto["latency_ns"].astype(np.float64) / 1e6, queries)}
+        base = None
+        if baseline:
+            single = unbatched(gg, handles, queries, cfg, bins)
+            engine = engine_baseline(gg, handles, queries, single)
+            base = {}
+            for name, t in (("one_launch_per_query", single), ("gg_run_per_query", engine)):
+                base[name] = {"makespan_ms": round(float(t.sum()), 3),
+                              "latency_ms": _latency_summary(np.cumsum(t), queries),
+                              "gteps": round(float(st["arcs"].sum()) / (float(t.sum()) * 1e-3) / 1e9, 3)}
     finally:
         for h in handles:
             gg.gg_free_graph(h)
@@ -152,6 +216,10 @@ def measure(gg, graphs, queries, scales, tune=True, reps=5, ppr_iters=20):
                        "max": round(float(lat.max()), 3)},
         "service_ms": {"p50": round(float(np.percentile(svc, 50)), 3), "p99": round(float(np.percentile(svc, 99)), 3)},
         "by_app": by_app, "cuda_graph": True, "load_s": round(t_load, 2),
+        "by_order": by_order,
+        **({"baseline": {**base, "note": "the same queries unbatched, run one after another; latency = "
+                                            "completion time in workload order"},
+            "speedup": {k: round(v["makespan_ms"] / ms, 3) for k, v in base.items()}} if base else {}),
     }
 
 

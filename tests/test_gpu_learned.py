@@ -92,13 +92,13 @@ def test_training_gradient_loss_and_update(gg, torch):
     y = (np.random.default_rng(5).random(rows) < 0.4).astype(np.uint8)
     P = _rand_params(6)
     dx, dy = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
-    for batch in (128, 37):
+    for batch in (128, 37, 300, 1000):   # one block, a partial block, several blocks (rows wrap around)
         dp = torch.from_numpy(P.copy()).cuda()
         grad = torch.empty(scorer.N_PARAM, device="cuda")
         loss = torch.empty(1, device="cuda")
         gg.gg_mlp_train(dx, dy, rows, dp, batch, 1, 0.5, 1, 7, losses=loss, grad_last=grad)
         torch.cuda.synchronize()
-        want, want_loss = oracle.mlp_grad(P, x, y, idx=np.arange(7, 7 + batch))
+        want, want_loss = oracle.mlp_grad(P, x, y, idx=(7 + np.arange(batch)) % rows)
         got = grad.cpu().numpy().astype(np.float64)
         assert np.linalg.norm(got - want) <= 5e-3 * np.linalg.norm(want)
         assert abs(float(loss.cpu()[0]) - want_loss) <= 1e-4 * want_loss
@@ -197,10 +197,10 @@ def _indeg_scorer(d):
     return P
 
 
-def _gpu_learned(gg, h, g, app, P, T, alpha, theta, sigma, s, flags=0, tau=0.0, frac=1.0):
+def _gpu_learned(gg, h, g, app, P, T, alpha, theta, sigma, s, flags=0, tau=0.0, frac=1.0, cost=0.0):
     gg.gg_set_scorer(h, P)
     p = gg.make_params(alpha=alpha, theta=theta, max_iters=T, source=s, seed=5, flags=flags, select_logit=tau,
-                       fallback_frac=frac)
+                       fallback_frac=frac, select_cost=cost)
     gg.gg_run(h, app, sigma, "learned", p)
     return gg.values(h, app), gg.mask_bits(h, g.m), gg.stats(h), gg.result_array(h, gg.GG_RESULT_ITER_STATS)
 
@@ -226,6 +226,30 @@ def test_learned_min_apps_bit_exact(gg, app, flags):
                 sel = np.where((it["mode"] & gg.GG_ITER_LEARNED) != 0, it["selected"].astype(np.int64), -1)
                 assert np.array_equal(sel, ref["iter_selected"]), case
                 assert np.array_equal(it["changed"], ref["iter_changed"].astype(np.uint64)), case
+        finally:
+            gg.gg_free_graph(h)
+
+
+@pytest.mark.parametrize("app", ["sssp", "bfs"])
+def test_learned_selection_cost_bit_exact(gg, app):
+    """Cost-aware selection (select_cost: the threshold rises with the bit
+    length of the in-degree) with a scorer whose decisions are exact: values,
+    flags and the selected counts equal the oracle's."""
+    for g in _graphs():
+        h = gc.load(gg, g)
+        try:
+            s = int(graphgen.sources(g, 1, seed=2)[0]) if g.m else 0
+            for d, tau, cost in ((4, 0.0, 2.0 ** -7), (1, -0.02, 2.0 ** -9)):
+                P = _indeg_scorer(d)
+                vals, mask, st, it = _gpu_learned(gg, h, g, app, P, 100000, 2, 0.2, 0.4, s, 0, tau, 1.0, cost)
+                ref = oracle.run(g.n, g.rowptr, g.colidx, g.weights, app=app, policy="learned", mlp=P, sigma=0.4,
+                                 seed=5, alpha=2, theta=0.2, source=s, max_iters=100000, select_logit=tau,
+                                 select_cost=cost)
+                case = (g.name, d, tau, cost)
+                assert np.array_equal(vals, ref["values"]), case
+                assert np.array_equal(mask, ref["mask"]), case
+                sel = np.where((it["mode"] & gg.GG_ITER_LEARNED) != 0, it["selected"].astype(np.int64), -1)
+                assert np.array_equal(sel, ref["iter_selected"]), case
         finally:
             gg.gg_free_graph(h)
 
@@ -299,7 +323,7 @@ def test_learned_errors(gg, torch):
         y = torch.zeros(4, dtype=torch.uint8, device="cuda")
         p = torch.zeros(scorer.N_PARAM, device="cuda")
         with pytest.raises(gg.GGError) as e:
-            gg.gg_mlp_train(x, y, 4, p, 129, 1, 0.1, 1)
+            gg.gg_mlp_train(x, y, 4, p, 16385, 1, 0.1, 1)
         assert e.value.status == gg.GG_ERR_INVALID_ARG
         with pytest.raises(gg.GGError) as e:
             gg.gg_mlp_train(x, y, 4, p, 4, 1, 0.1, 4)

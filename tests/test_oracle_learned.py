@@ -240,3 +240,44 @@ def test_learned_min_app_terminates_at_exact_fixed_point():
                            source=s, max_iters=10000)
             assert np.array_equal(r["values"], brute.dijkstra(g, s))
             assert r["iterations"] < 10000
+
+
+def _bitlen(d):
+    d = np.asarray(d, np.int64)
+    out = np.zeros(d.shape, np.int64)
+    x = d.copy()
+    while np.any(x > 0):
+        out += x > 0
+        x >>= 1
+    return out
+
+
+def test_learned_selection_cost():
+    """select_cost (beyond the paper): a vertex with in-degree d is selected
+    when its logit exceeds fmaf(select_cost, bit length of d, select_logit).
+    Cost 0 is the plain threshold; a cost no logit can reach selects only rows
+    without in-edges, which corrects nothing, so the run equals selecting none;
+    in between, the count selected at a learned correction is the number of
+    logits above each vertex's own threshold."""
+    g = graphgen.add_weights(graphgen.rmat(8, seed=6), seed=5)
+    s = int(graphgen.sources(g, 1, seed=2)[0])
+    P = scorer.init_params(1)
+    indeg = np.bincount(g.colidx, minlength=g.n)
+    for app, T in (("pagerank", 14), ("sssp", 1000)):
+        kw = dict(app=app, sigma=0.3, seed=3, alpha=3, theta=0.1, source=s, max_iters=T, policy="learned", mlp=P)
+        plain = oracle.run(g.n, g.rowptr, g.colidx, g.weights, select_logit=0.1, **kw)
+        zero = oracle.run(g.n, g.rowptr, g.colidx, g.weights, select_logit=0.1, select_cost=0.0, **kw)
+        for key in ("values", "mask", "iter_selected"):
+            assert np.array_equal(plain[key], zero[key]), (app, key)
+        none = oracle.run(g.n, g.rowptr, g.colidx, g.weights, select_logit=np.inf, **kw)
+        huge = oracle.run(g.n, g.rowptr, g.colidx, g.weights, select_logit=0.0, select_cost=1e30, **kw)
+        assert np.array_equal(none["values"], huge["values"]) and np.array_equal(none["mask"], huge["mask"])
+        mid = oracle.run(g.n, g.rowptr, g.colidx, g.weights, select_logit=0.05, select_cost=0.01, **kw)
+        learned_its = [i for i, c in enumerate(mid["iter_selected"]) if c >= 0]
+        assert learned_its, app
+        thr = np.float32(np.float64(np.float32(0.01)) * _bitlen(indeg) + np.float64(np.float32(0.05)))
+        want = int(np.sum(mid["logits"] > thr.astype(np.float64)))
+        assert mid["iter_selected"][learned_its[-1]] == want, app
+        # the cost lowers the selection below the plain one at the same logit threshold
+        flat = oracle.run(g.n, g.rowptr, g.colidx, g.weights, select_logit=0.05, **kw)
+        assert int(np.sum(flat["logits"] > np.float32(0.05))) >= want
