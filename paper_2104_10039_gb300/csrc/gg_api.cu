@@ -168,8 +168,8 @@ static void fill_list(const gg_graph *g, bool sparse, TileArgs &a)
         a.arc_src = g->sp_src;
         a.arc_w = g->has_w ? g->sp_w : nullptr;
         a.list_nnz = g->sp_nnz;
-        a.tile_info = g->sp_tile_info;
-        a.num_tiles = g->sp_num_tiles;
+        a.tile_info = nullptr;   // the pull path walks the packed list through its plan
+        a.num_tiles = nullptr;
     } else {
         a.row_ptr = g->in_ptr;
         a.arc_src = g->in_src_h;
@@ -188,25 +188,7 @@ static void fill_list(const gg_graph *g, bool sparse, TileArgs &a)
     a.stash = g->stash;
 }
 
-// After a correction or sampling pass: place the tiles' local packs into the
-// packed active in-edge list and partition it for the next gathers.
-// plain: pack vertex ids (the pull path reads them) rather than the
-// hub-coded sources of the merge-path kernels.
-static gg_status finish_pack(gg_graph *g, bool weighted, IterStatsDev *stats, bool plain = false)
-{
-    GG_CUDA(launch_scan_u32(g->tile_cnt, g->tile_off, g->full_tiles, g->scan_tmp, g->stream));
-    GG_CUDA(launch_pack(g->full_tile_info, g->tile_off, g->full_tiles, (long long)g->n + g->m, g->mask,
-                        plain ? g->in_src : g->in_src_h, weighted ? g->in_w : nullptr, g->sp_ptr, g->sp_src,
-                        weighted ? g->sp_w : nullptr, g->sp_nnz, stats, g->num_sms, g->stream));
-    g->sp_is_plain = plain;
-    g->plan[1].valid = false;
-    GG_CUDA(launch_partition(g->sp_ptr, g->n, g->sp_nnz, g->max_tiles, g->sp_tile_info, g->sp_num_tiles,
-                             g->stream));
-    g->launches += 5;
-    return GG_OK;
-}
-
-gg_status sample_edges(gg_graph *g, double ratio, uint64_t seed, bool plain)
+gg_status sample_edges(gg_graph *g, double ratio, uint64_t seed)
 {
     if (!(ratio > 0.0 && ratio <= 1.0)) {
         set_error("sample_ratio must be in (0, 1], got %g", ratio);
@@ -216,10 +198,8 @@ gg_status sample_edges(gg_graph *g, double ratio, uint64_t seed, bool plain)
     // the hash keys on vertex ids (in_src, not the hub-coded copy)
     GG_CUDA(launch_sample(g->in_src, g->in_dst, g->m, g->symmetric ? 1 : 0, seed,
                           (unsigned long long)std::floor(ratio * 4294967296.0), g->mask, g->num_sms, g->stream));
-    GG_CUDA(launch_tile_counts(g->full_tile_info, g->full_tiles, (long long)g->n + g->m, g->in_ptr, g->mask,
-                               g->tile_cnt, g->sp_ptr, g->num_sms, g->stream));
-    g->launches += 2;
-    gg_status st = finish_pack(g, g->has_w, nullptr, plain);
+    g->launches += 1;
+    gg_status st = pack_active(g, g->has_w, nullptr, false);
     if (st != GG_OK) return st;
     GG_CUDA(cudaEventRecord(g->ev_s1, g->stream));
     g->sample_timed = true;
@@ -398,9 +378,7 @@ static gg_status learned_correct(gg_graph *g, gg_app app, TileArgs a, uint32_t n
         else GG_CUDA(launch_tile_min((int)app, K_CORRECT, a, (int)sub_tiles, g->num_sms, g->stream));
     }
     GG_CUDA(launch_scatter_flags(g->sub_pos, g->sub_mask, total, g->mask, g->num_sms, g->stream));
-    GG_CUDA(launch_tile_counts(g->full_tile_info, g->full_tiles, (long long)g->n + g->m, g->in_ptr, g->mask,
-                               g->tile_cnt, g->sp_ptr, g->num_sms, g->stream));
-    g->launches += 8;
+    g->launches += 7;
     g->stats.learned_corrections += 1;
     return GG_OK;
 }
@@ -497,6 +475,7 @@ static gg_status run_pagerank(gg_graph *g, gg_policy policy, const gg_params *p)
             a.theta = p->theta;
         }
         bool learned = false;
+        bool counted = false;   // the correction's flag pass counted each tile's active arcs
         uint32_t nsel = 0, sel_arcs = 0;
         if (kind == K_CORRECT && learned_policy && !g->force_full) {
             gg_status st = learned_select(g, GG_APP_PAGERANK, p, i, &learned, &nsel, &sel_arcs);
@@ -531,12 +510,12 @@ static gg_status run_pagerank(gg_graph *g, gg_policy policy, const gg_params *p)
                 } else {
                     pa.vals = reinterpret_cast<float *>(g->stash);
                     pa.mask = g->mask;
+                    pa.tcnt = g->tile_cnt;
                     pa.theta = p->theta;
                     GG_CUDA(launch_pull(GG_APP_PAGERANK, pa, true, (uint32_t)g->plan[which].tiles, g->num_sms,
                                         g->stream));
-                    GG_CUDA(launch_tile_counts(g->full_tile_info, g->full_tiles, (long long)g->n + g->m, g->in_ptr,
-                                               g->mask, g->tile_cnt, g->sp_ptr, g->num_sms, g->stream));
-                    g->launches += 4;
+                    counted = true;
+                    g->launches += 3;
                 }
                 timed_end(g, slot);
             } else {
@@ -552,7 +531,7 @@ static gg_status run_pagerank(gg_graph *g, gg_policy policy, const gg_params *p)
             }
         }
         if (kind == K_CORRECT) {
-            gg_status st = finish_pack(g, false, a.stats, true);
+            gg_status st = pack_active(g, false, a.stats, counted);
             if (st != GG_OK) return st;
             g->sample_clean = false;
             g->stats.corrections += 1;
@@ -745,25 +724,22 @@ static gg_status run_min(gg_graph *g, gg_app app, gg_policy policy, const gg_par
                 if (kind == K_CORRECT) {
                     pa.vals = reinterpret_cast<float *>(g->stash);
                     pa.mask = g->mask;
+                    pa.tcnt = g->tile_cnt;
                     pa.theta_case = theta_case;
                     pa.theta_fx = theta_fx;
                     pa.est_strict = (p->flags & GG_EST_STRICT) ? 1 : 0;
                 }
                 GG_CUDA(launch_pull((int)app, pa, kind == K_CORRECT, (uint32_t)g->plan[which].tiles, g->num_sms,
                                     g->stream));
-                if (kind == K_CORRECT) {
-                    GG_CUDA(launch_tile_counts(g->full_tile_info, g->full_tiles, (long long)g->n + g->m, g->in_ptr,
-                                               g->mask, g->tile_cnt, g->sp_ptr, g->num_sms, g->stream));
-                }
                 timed_end(g, slot);
-                g->launches += kind == K_CORRECT ? 4 : 2;
+                g->launches += kind == K_CORRECT ? 3 : 2;
                 if (tracing) {
                     st = trace_labels(g, false);
                     if (st != GG_OK) return st;
                 }
             }
             if (kind == K_CORRECT) {
-                st = finish_pack(g, app == GG_APP_SSSP && g->has_w, sti, true);
+                st = pack_active(g, app == GG_APP_SSSP && g->has_w, sti, !learned);
                 if (st != GG_OK) return st;
                 g->sample_clean = false;
                 g->stats.corrections += 1;
@@ -870,7 +846,7 @@ gg_status run(gg_graph *g, gg_app app, double ratio, gg_policy policy, const gg_
     GG_CUDA(cudaEventRecord(g->ev_run0, g->stream));
     if (policy != GG_POLICY_EXACT &&
         !(g->sampled && g->sample_clean && g->sample_ratio == ratio && g->sample_seed == p->seed)) {
-        st = sample_edges(g, ratio, p->seed, true);
+        st = sample_edges(g, ratio, p->seed);
         if (st != GG_OK) return st;
     }
     st = app == GG_APP_PAGERANK ? run_pagerank(g, policy, p) : run_min(g, app, policy, p);
@@ -913,7 +889,6 @@ static gg_status alloc_graph(gg_graph *g)
     g->full_tiles = (uint32_t)(((uint64_t)n + m + kWT - 1) / kWT);
     g->max_tiles = g->full_tiles + 1;
     GG_ALLOC(g->b_full_tile_info, 4 * ((size_t)g->max_tiles + 2));
-    GG_ALLOC(g->b_sp_tile_info, 4 * ((size_t)g->max_tiles + 2));
     GG_ALLOC(g->b_tile_cnt, 4 * (2 * (size_t)g->max_tiles + 4));
     GG_ALLOC(g->b_act, 4 * n);
     GG_ALLOC(g->b_part, 12 * ((size_t)g->max_tiles + 2));
@@ -942,7 +917,6 @@ static gg_status alloc_graph(gg_graph *g)
     g->sp_src = g->b_sp_src.i32();
     g->sp_w = g->has_w ? g->b_sp_w.u32() : nullptr;
     g->full_tile_info = g->b_full_tile_info.i32();
-    g->sp_tile_info = g->b_sp_tile_info.i32();
     g->tile_cnt = g->b_tile_cnt.u32();
     g->tile_off = g->tile_cnt + g->max_tiles + 2;
     g->act_outdeg = g->b_act.i32();
@@ -1068,7 +1042,7 @@ gg_status gg_load_csr(gg_graph **out, int32_t n, int64_t m, const int32_t *rowpt
 gg_status gg_sample_edges(gg_graph *g, double sample_ratio, uint64_t seed)
 {
     if (!g) { set_error("gg_sample_edges: graph is NULL"); return GG_ERR_INVALID_ARG; }
-    return sample_edges(g, sample_ratio, seed, true);
+    return sample_edges(g, sample_ratio, seed);
 }
 
 gg_status gg_run(gg_graph *g, gg_app app, double sample_ratio, gg_policy policy, const gg_params *p)

@@ -51,81 +51,6 @@ cudaError_t launch_partition(const int32_t *row_ptr, int32_t n, const uint32_t *
     return cudaGetLastError();
 }
 
-// ----------------------------------------------------------------- pack ----
-// One warp per tile of the full in-edge list: the tile's active arcs (flag
-// bits) go to their place in the packed list, tile_off[t] + rank among the
-// tile's active arcs, in chunks of 32 arcs (coalesced reads and writes); the
-// tile-local row ends get the tile's offset. Tile order = list order, so rows
-// split over tiles end up contiguous.
-__global__ void k_pack(const int32_t *__restrict__ tile_info, const uint32_t *__restrict__ tile_off,
-                       uint32_t num_tiles, long long total_items, const uint32_t *__restrict__ mask,
-                       const int32_t *__restrict__ in_src, const uint32_t *__restrict__ in_w,
-                       int32_t *__restrict__ sp_ptr, int32_t *__restrict__ sp_src, uint32_t *__restrict__ sp_w,
-                       uint32_t *__restrict__ sp_nnz, IterStatsDev *stats)
-{
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t lt = (1u << lane) - 1u;
-    const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < num_tiles; t += warps) {
-        const int32_t r0 = tile_info[t] & 0x7FFFFFFF, r1 = tile_info[t + 1] & 0x7FFFFFFF;
-        const long long d1 = (t + 1) * kWT < total_items ? (t + 1) * kWT : total_items;
-        const int32_t a0 = (int32_t)(t * kWT - r0), a1 = (int32_t)(d1 - r1);
-        // the tile's flag words (at most kWords) in one load per lane, then
-        // every chunk's source loads issued before any store
-        constexpr int kWords = kWT / 32 + 1;
-        const int32_t wb = a0 >> 5;
-        const int nw = a1 > a0 ? ((a1 - 1) >> 5) - wb + 1 : 0;
-        const uint32_t myw = (int)lane < nw ? mask[wb + (int)lane] : 0u;
-        int32_t sv[kWords];
-        uint32_t wv[kWords];
-        uint32_t onbits = 0;
-#pragma unroll
-        for (int c = 0; c < kWords; ++c) {
-            sv[c] = 0;
-            wv[c] = 0;
-            const uint32_t word = __shfl_sync(0xFFFFFFFFu, myw, c);
-            const int32_t k = (wb + c) * 32 + (int32_t)lane;
-            const bool on = c < nw && k >= a0 && k < a1 && ((word >> lane) & 1u);
-            if (on) {
-                sv[c] = __ldg(in_src + k);
-                if (sp_w) wv[c] = __ldg(in_w + k);
-                onbits |= 1u << c;
-            }
-        }
-        uint32_t pos = tile_off[t];
-#pragma unroll
-        for (int c = 0; c < kWords; ++c) {
-            const bool on = (onbits >> c) & 1u;
-            const uint32_t b = __ballot_sync(0xFFFFFFFFu, on);
-            if (on) {
-                const uint32_t q = pos + __popc(b & lt);
-                sp_src[q] = sv[c];
-                if (sp_w) sp_w[q] = wv[c];
-            }
-            pos += __popc(b);
-        }
-        const uint32_t off = tile_off[t];
-        for (int32_t u = r0 + (int32_t)lane; u < r1; u += 32) sp_ptr[u + 1] += (int32_t)off;
-        if (t == 0 && lane == 0) {
-            sp_ptr[0] = 0;
-            *sp_nnz = tile_off[num_tiles];
-            if (stats) stats->active_after = tile_off[num_tiles];
-        }
-    }
-}
-
-cudaError_t launch_pack(const int32_t *tile_info, const uint32_t *tile_off, uint32_t num_tiles, long long total_items,
-                        const uint32_t *mask, const int32_t *in_src, const uint32_t *in_w, int32_t *sp_ptr,
-                        int32_t *sp_src, uint32_t *sp_w, uint32_t *sp_nnz, IterStatsDev *stats, int num_sms,
-                        cudaStream_t s)
-{
-    long long blocks = ((long long)num_tiles * 32 + 255) / 256;
-    if (blocks > (long long)num_sms * 16) blocks = (long long)num_sms * 16;
-    if (blocks < 1) blocks = 1;
-    k_pack<<<(unsigned)blocks, 256, 0, s>>>(tile_info, tile_off, num_tiles, total_items, mask, in_src, in_w, sp_ptr,
-                                            sp_src, sp_w, sp_nnz, stats);
-    return cudaGetLastError();
-}
 
 // ------------------------------------------------------------------ scan ----
 constexpr int kScanThreads = 256;

@@ -92,9 +92,9 @@ struct gg_graph {
     int32_t *in_src_h = nullptr, *hub_slot = nullptr, *hub_ids = nullptr;
     int32_t n_hubs = 0;
     uint32_t *in_w = nullptr;
-    // partitions: full CSC and packed active CSC
-    gg::DevBuf b_full_tile_info, b_sp_tile_info, b_scalars;
-    int32_t *full_tile_info = nullptr, *sp_tile_info = nullptr;
+    // partition of the full CSC (merge-path kernels)
+    gg::DevBuf b_full_tile_info, b_scalars;
+    int32_t *full_tile_info = nullptr;
     uint32_t *full_num_tiles = nullptr, *sp_num_tiles = nullptr, *full_nnz = nullptr, *sp_nnz = nullptr;
     uint32_t *dev_err = nullptr, *q_len = nullptr;  // q_len[2]
     uint32_t max_tiles = 0;     // upper bound on tiles of any list
@@ -188,7 +188,10 @@ namespace gg {
 gg_status build_csc(gg_graph *g);
 gg_status build_hubs(gg_graph *g);
 gg_status validate_csr(gg_graph *g);
-gg_status sample_edges(gg_graph *g, double ratio, uint64_t seed, bool plain);
+gg_status sample_edges(gg_graph *g, double ratio, uint64_t seed);
+// Packed active in-edges from the flag bitmap (gg_pack.cu); have_counts: the
+// per-tile active counts are in tile_cnt already (a correction's flag pass).
+gg_status pack_active(gg_graph *g, bool weighted, IterStatsDev *stats, bool have_counts);
 gg_status run(gg_graph *g, gg_app app, double ratio, gg_policy policy, const gg_params *p);
 uint32_t next_epoch(gg_graph *g);
 gg_status ensure_pull(gg_graph *g);

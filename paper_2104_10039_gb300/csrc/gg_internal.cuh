@@ -131,6 +131,7 @@ struct PullArgs {
     const int32_t *lrows;       // plan: the long rows (vertices)
     const uint32_t *nlong;      // plan: device scalar, number of long rows
     float *carry;               // correction: per tile inside a long row, the row's value before the tile
+    uint32_t *tcnt;             // correction: per tile, its arcs flagged active (for the pack)
     const float *contrib;       // gathered vector (rank / degree of the previous iteration)
     float *acc;                 // per vertex: its row's sum over the tile holding the row's first arc
     float *lead;                // per tile: the part before its first row start
@@ -238,12 +239,6 @@ struct Graph;
 cudaError_t launch_partition(const int32_t *row_ptr, int32_t n, const uint32_t *list_nnz,
                              uint32_t max_tiles, int32_t *tile_info, uint32_t *num_tiles,
                              cudaStream_t s);
-// Packed active in-edges from the flag bitmap of the full in-edge list:
-// tile_off is the exclusive scan of the tiles' active counts (num_tiles + 1).
-cudaError_t launch_pack(const int32_t *tile_info, const uint32_t *tile_off, uint32_t num_tiles, long long total_items,
-                        const uint32_t *mask, const int32_t *in_src, const uint32_t *in_w, int32_t *sp_ptr,
-                        int32_t *sp_src, uint32_t *sp_w, uint32_t *sp_nnz, IterStatsDev *stats, int num_sms,
-                        cudaStream_t s);
 // Tile kernels run a persistent grid: min(max_tiles, resident warps).
 cudaError_t launch_tile_pr(int kind, const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s);
 cudaError_t launch_tile_min(int app, int kind, const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s);
@@ -252,11 +247,6 @@ cudaError_t launch_tile_min(int app, int kind, const TileArgs &a, int max_tiles,
 cudaError_t launch_sample(const int32_t *in_src, const int32_t *in_dst, long long m, int symmetric,
                           unsigned long long seed, unsigned long long thr, uint32_t *mask, int num_sms,
                           cudaStream_t s);
-// Per merge-path tile of a list: its active arcs (flags in the bitmap) and the
-// tile-local row ends of the packed list, as k_pack expects them.
-cudaError_t launch_tile_counts(const int32_t *tile_info, uint32_t num_tiles, long long total_items,
-                               const int32_t *row_ptr, const uint32_t *mask, uint32_t *tile_cnt, int32_t *sp_ptr,
-                               int num_sms, cudaStream_t s);
 // Rows a gather left open at tile starts (one launch after every gather).
 cudaError_t launch_fixup(int app, const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s);
 cudaError_t launch_push(const PushArgs &a, uint32_t max_arcs, int grid, cudaStream_t s);

@@ -27,7 +27,8 @@
 //                a correction's second pass: every arc's influence from the
 //                running value of its row before and after it (the values kept
 //                by the first pass, the carry of a continued row from acc and
-//                the leads), one flag bit per arc.
+//                the leads), one flag bit per arc, and each tile's count of
+//                active arcs for the pack.
 //   k_pr_apply, k_min_apply
 //                one thread per vertex: the row's total (acc[v] folded with the
 //                later tiles' leading parts of a row continued across tile
@@ -474,6 +475,7 @@ __global__ void __launch_bounds__(kPullThreads, 4) k_prc_flags(PullArgs a)
         }
         // carry of the row open at the tile start (k_carries, k_long_rows)
         float carry = (h0.x & 1u) ? 0.0f : a.carry[t];
+        uint32_t tile_active = 0;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const uint4 hw = h ? h1 : h0;
@@ -517,8 +519,11 @@ __global__ void __launch_bounds__(kPullThreads, 4) k_prc_flags(PullArgs a)
             word |= __shfl_xor_sync(FULL, word, 4);
             const long long wi = t * 8 + 4 * h + (lane >> 3);
             if ((lane & 7u) == 0 && wi < mask_words) a.mask[wi] = word;
+            if ((lane & 7u) == 0) tile_active += (uint32_t)__popc(word);
             carry = __shfl_sync(FULL, x, 31);
         }
+        tile_active = __reduce_add_sync(FULL, tile_active);
+        if (lane == 0 && a.tcnt) a.tcnt[t] = tile_active;
     }
 }
 
@@ -579,6 +584,7 @@ __global__ void __launch_bounds__(kPullThreads, 4) k_minc_flags(PullArgs a)
         }
         // running minimum of the row open at the tile start (k_carries, k_long_rows)
         uint32_t carry = (h0.x & 1u) ? kInf : reinterpret_cast<const uint32_t *>(a.carry)[t];
+        uint32_t tile_active = 0;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const uint4 hw = h ? h1 : h0;
@@ -629,8 +635,11 @@ __global__ void __launch_bounds__(kPullThreads, 4) k_minc_flags(PullArgs a)
             word |= __shfl_xor_sync(FULL, word, 2);
             word |= __shfl_xor_sync(FULL, word, 4);
             if ((lane & 7u) == 0 && wi < mask_words) a.mask[wi] = word;
+            if ((lane & 7u) == 0) tile_active += (uint32_t)__popc(word);
             carry = __shfl_sync(FULL, x, 31);
         }
+        tile_active = __reduce_add_sync(FULL, tile_active);
+        if (lane == 0 && a.tcnt) a.tcnt[t] = tile_active;
     }
 }
 
