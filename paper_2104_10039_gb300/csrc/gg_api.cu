@@ -237,14 +237,19 @@ static gg_status refresh_active_outdeg(gg_graph *g)
         if (s_ != GG_OK) return s_;                               \
     } while (0)
 
+// Stride between the per-vertex arrays carved from one buffer: n rounded up
+// to a multiple of 4, so each array starts on a 16-byte boundary (the apply
+// passes use 16-byte loads and stores).
+static size_t vstride(const gg_graph *g) { return ((size_t)g->n + 3) & ~(size_t)3; }
+
 // ---------------------------------------------- learned correction, traces --
 static gg_status ensure_hist(gg_graph *g)
 {
     if (!g->hist) {
-        GG_ALLOC_BUF(g->b_hist, 4 * 3 * (size_t)g->n);
+        GG_ALLOC_BUF(g->b_hist, 4 * 3 * vstride(g));
         g->hist = g->b_hist.f32();
     }
-    GG_CUDA(cudaMemsetAsync(g->hist, 0, 4 * 3 * (size_t)g->n, g->stream));
+    GG_CUDA(cudaMemsetAsync(g->hist, 0, 4 * 3 * vstride(g), g->stream));
     return GG_OK;
 }
 
@@ -276,7 +281,7 @@ static gg_status ensure_learned(gg_graph *g)
 // Change-feature slot of the iteration about to execute (or nullptr).
 static float *hist_slot(gg_graph *g)
 {
-    return g->keep_hist ? g->hist + (size_t)(g->executed % 3u) * (size_t)g->n : nullptr;
+    return g->keep_hist ? g->hist + (size_t)(g->executed % 3u) * vstride(g) : nullptr;
 }
 
 static FeatArgs feat_args(gg_graph *g, gg_app app, uint32_t i)
@@ -287,9 +292,9 @@ static FeatArgs feat_args(gg_graph *g, gg_app app, uint32_t i)
     fa.out_ptr = g->out_ptr;
     fa.sp_ptr = g->sp_ptr;
     const uint32_t e = g->executed;
-    fa.hist1 = g->hist + (size_t)((e + 2u) % 3u) * (size_t)g->n;
-    fa.hist2 = g->hist + (size_t)((e + 1u) % 3u) * (size_t)g->n;
-    fa.hist3 = g->hist + (size_t)(e % 3u) * (size_t)g->n;
+    fa.hist1 = g->hist + (size_t)((e + 2u) % 3u) * vstride(g);
+    fa.hist2 = g->hist + (size_t)((e + 1u) % 3u) * vstride(g);
+    fa.hist3 = g->hist + (size_t)(e % 3u) * vstride(g);
     fa.iter_f = (float)i * 0.015625f;
     fa.app_f = (float)app;
     return fa;
@@ -896,7 +901,8 @@ static gg_status alloc_graph(gg_graph *g)
     GG_ALLOC(g->b_scalars, 4 * 16);
     g->mask_words = (m + 31) / 32;
     GG_ALLOC(g->b_mask, 4 * (g->mask_words + 1));
-    GG_ALLOC(g->b_vals, 4 * 4 * n);
+    const size_t nv = (n + 3) & ~(size_t)3;   // 16-byte aligned per-vertex arrays
+    GG_ALLOC(g->b_vals, 4 * 4 * nv);
     GG_ALLOC(g->b_front, 4 * (6 * n + 2));
     GG_ALLOC(g->b_sched, sizeof(TileSched) * 2);
     GG_ALLOC(g->b_status, sizeof(unsigned long long) * ((size_t)g->max_tiles + 2));
@@ -934,9 +940,9 @@ static gg_status alloc_graph(gg_graph *g)
     g->mask = g->b_mask.u32();
     float *v = g->b_vals.f32();
     g->rank[0] = v;
-    g->rank[1] = v + n;
-    g->contrib[0] = v + 2 * n;
-    g->contrib[1] = v + 3 * n;
+    g->rank[1] = v + nv;
+    g->contrib[0] = v + 2 * nv;
+    g->contrib[1] = v + 3 * nv;
     g->val[0] = (uint32_t *)g->rank[0];
     g->val[1] = (uint32_t *)g->rank[1];
     uint32_t *f = g->b_front.u32();

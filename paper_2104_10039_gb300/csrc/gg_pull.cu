@@ -643,15 +643,125 @@ __global__ void __launch_bounds__(kPullThreads, 4) k_minc_flags(PullArgs a)
     }
 }
 
-// GG-Apply + GG-VStatus for SSSP / BFS / CC: new = min(old, the row's
-// minimum candidate); a vertex whose value decreased joins the next frontier
-// (vertex, new value); each block reserves its entries with one atomic per
-// step (many vertices change in the first iterations).
+// ----------------------------------------------------------------- apply ----
+// Loads of the four consecutive vertices v0 .. v0 + 3 (16-byte loads when
+// all four exist): row pointers (5), row sums, old values, degrees.
+struct Quad {
+    int32_t rp[5];
+    uint32_t acc[4], old[4];
+    int32_t deg[4];
+};
+
+template <bool PR>
+__device__ __forceinline__ void load_quad(const PullArgs &a, long long v0, Quad &q)
+{
+    const uint32_t *accu = reinterpret_cast<const uint32_t *>(a.acc);
+    const uint32_t *oldu = PR ? reinterpret_cast<const uint32_t *>(a.rank_cur) : a.val_cur;
+    if (v0 + 4 <= a.n) {
+        const int4 r = __ldg(reinterpret_cast<const int4 *>(a.row_ptr + v0));
+        q.rp[0] = r.x; q.rp[1] = r.y; q.rp[2] = r.z; q.rp[3] = r.w;
+        q.rp[4] = __ldg(a.row_ptr + v0 + 4);
+        const uint4 c = *reinterpret_cast<const uint4 *>(accu + v0);
+        q.acc[0] = c.x; q.acc[1] = c.y; q.acc[2] = c.z; q.acc[3] = c.w;
+        const uint4 o = *reinterpret_cast<const uint4 *>(oldu + v0);
+        q.old[0] = o.x; q.old[1] = o.y; q.old[2] = o.z; q.old[3] = o.w;
+        if (PR) {
+            if (a.deg_apply) {
+                const int4 d = *reinterpret_cast<const int4 *>(a.deg_apply + v0);
+                q.deg[0] = d.x; q.deg[1] = d.y; q.deg[2] = d.z; q.deg[3] = d.w;
+            } else {
+                const int4 p = __ldg(reinterpret_cast<const int4 *>(a.out_ptr + v0));
+                const int32_t pn = __ldg(a.out_ptr + v0 + 4);
+                q.deg[0] = p.y - p.x; q.deg[1] = p.z - p.y; q.deg[2] = p.w - p.z; q.deg[3] = pn - p.w;
+            }
+        }
+    } else {
+        // the last, partial group: rows past n read as empty (row_ptr[n])
+#pragma unroll
+        for (int i = 0; i < 5; ++i) q.rp[i] = __ldg(a.row_ptr + (v0 + i < a.n ? v0 + i : (long long)a.n));
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const long long v = v0 + i;
+            const bool live = v < a.n;
+            q.acc[i] = live ? accu[v] : 0u;
+            q.old[i] = live ? oldu[v] : 0u;
+            q.deg[i] = 0;
+            if (PR && live) q.deg[i] = a.deg_apply ? a.deg_apply[v] : __ldg(a.out_ptr + v + 1) - __ldg(a.out_ptr + v);
+        }
+    }
+}
+
+// GG-Apply + GG-VStatus (Alg. 2) for PageRank, four consecutive vertices per
+// thread and step. A row's sum is acc[v] (written by the tile holding its
+// first arc), plus, for a row continued across at most kLongTiles tile ends,
+// the leading parts of the later tiles it covers, in tile order (a long row's
+// acc[v] is complete already); a row with no arcs in the list sums to 0.
+__global__ void __launch_bounds__(kPullThreads) k_pr_apply(PullArgs a)
+{
+    unsigned long long changed = 0, sum = 0;
+    uint32_t mx = 0;
+    const long long S = (long long)gridDim.x * blockDim.x;
+    const long long ng = ((long long)a.n + 3) / 4;
+    for (long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x; gi < ng; gi += S) {
+        const long long v0 = 4 * gi;
+        Quad q;
+        load_quad<true>(a, v0, q);
+        float nw[4], cb[4], hv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float acc = 0.0f;
+            if (q.rp[i + 1] > q.rp[i]) {
+                acc = __uint_as_float(q.acc[i]);
+                const int32_t t0 = q.rp[i] / kPT, t1 = (q.rp[i + 1] - 1) / kPT;
+                if (t1 - t0 <= kLongTiles)
+                    for (int32_t u = t0 + 1; u <= t1; ++u) acc += a.lead[u];
+            }
+            nw[i] = __fmaf_rn(a.damping, acc, a.base);
+            const float delta = fabsf(__fsub_rn(nw[i], __uint_as_float(q.old[i])));
+            cb[i] = q.deg[i] > 0 ? __fdiv_rn(nw[i], (float)q.deg[i]) : 0.0f;
+            hv[i] = __fmul_rn(a.n_f, delta);
+            if (v0 + i < a.n) {
+                changed += delta > a.epsilon ? 1ull : 0ull;
+                sum += __float2ull_rz(delta * 1099511627776.0f);   // fixed point 2^-40
+                const uint32_t db = __float_as_uint(delta);
+                mx = db > mx ? db : mx;
+            }
+        }
+        if (v0 + 4 <= a.n) {
+            *reinterpret_cast<float4 *>(a.rank_next + v0) = make_float4(nw[0], nw[1], nw[2], nw[3]);
+            *reinterpret_cast<float4 *>(a.contrib_next + v0) = make_float4(cb[0], cb[1], cb[2], cb[3]);
+            if (a.hist_out) *reinterpret_cast<float4 *>(a.hist_out + v0) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+        } else {
+            for (int i = 0; i < 4 && v0 + i < a.n; ++i) {
+                a.rank_next[v0 + i] = nw[i];
+                a.contrib_next[v0 + i] = cb[i];
+                if (a.hist_out) a.hist_out[v0 + i] = hv[i];
+            }
+        }
+    }
+    if (!a.stats) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        changed += __shfl_xor_sync(0xFFFFFFFFu, changed, o);
+        sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+        const uint32_t om = __shfl_xor_sync(0xFFFFFFFFu, mx, o);
+        mx = om > mx ? om : mx;
+    }
+    if ((threadIdx.x & 31u) == 0 && (changed | sum | mx)) {
+        atomicAdd(&a.stats->changed, changed);
+        atomicAdd(&a.stats->sum_delta, sum);
+        atomicMax(&a.stats->max_delta_bits, mx);
+    }
+}
+
+// GG-Apply + GG-VStatus for SSSP / BFS / CC, four consecutive vertices per
+// thread and step: new = min(old, the row's minimum candidate); a vertex
+// whose value decreased joins the next frontier (vertex, new value); each
+// block reserves its entries with one atomic per step (many vertices change
+// in the first iterations).
 template <int APP>
 __global__ void __launch_bounds__(kPullThreads) k_min_apply(PullArgs a)
 {
-    constexpr int U = 4;
-    const uint32_t *acc_u = reinterpret_cast<const uint32_t *>(a.acc);
     const uint32_t *lead = reinterpret_cast<const uint32_t *>(a.lead);
     const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
     __shared__ uint32_t s_cnt[kPullThreads / 32];
@@ -659,57 +769,48 @@ __global__ void __launch_bounds__(kPullThreads) k_min_apply(PullArgs a)
     unsigned long long changed = 0, sum = 0;
     uint32_t mx = 0;
     const long long S = (long long)gridDim.x * blockDim.x;
-    const long long nround = ((long long)a.n + U * S - 1) / (U * S) * (U * S);   // whole warps stay in the loop
-    for (long long v0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; v0 < nround; v0 += U * S) {
-        int32_t rs[U], re[U];
-        uint32_t old[U], ac[U];
+    const long long ng = ((long long)a.n + 3) / 4;
+    const long long nround = (ng + S - 1) / S * S;   // whole blocks stay in the loop (block-wide reservation)
+    for (long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x; gi < nround; gi += S) {
+        const long long v0 = 4 * gi;
+        Quad q;
+        uint32_t nw[4];
+        uint32_t chm = 0;
+        if (gi < ng) {
+            load_quad<false>(a, v0, q);
 #pragma unroll
-        for (int i = 0; i < U; ++i) {
-            const long long v = v0 + i * S;
-            rs[i] = re[i] = 0;
-            old[i] = ac[i] = kInf;
-            if (v < a.n) {
-                rs[i] = __ldg(a.row_ptr + v);
-                re[i] = __ldg(a.row_ptr + v + 1);
-                ac[i] = acc_u[v];   // stale for a row without arcs: replaced by INF below
-                old[i] = a.val_cur[v];
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < U; ++i) {
-            if (re[i] > rs[i]) {
-                const int32_t t0 = rs[i] / kPT, t1 = (re[i] - 1) / kPT;
-                if (t1 - t0 <= kLongTiles) {   // a long row's total is complete already
-                    uint32_t m = ac[i];
-                    for (int32_t u = t0 + 1; u <= t1; ++u) m = min(m, lead[u]);
-                    ac[i] = m;
+            for (int i = 0; i < 4; ++i) {
+                uint32_t m = kInf;
+                if (q.rp[i + 1] > q.rp[i]) {
+                    m = q.acc[i];
+                    const int32_t t0 = q.rp[i] / kPT, t1 = (q.rp[i + 1] - 1) / kPT;
+                    if (t1 - t0 <= kLongTiles)
+                        for (int32_t u = t0 + 1; u <= t1; ++u) m = min(m, lead[u]);
                 }
+                nw[i] = min(q.old[i], m);
+                if (v0 + i < a.n && nw[i] < q.old[i]) {
+                    chm |= 1u << i;
+                    changed += 1;
+                    if (q.old[i] != kInf) {
+                        sum += q.old[i] - nw[i];
+                        mx = (q.old[i] - nw[i]) > mx ? (q.old[i] - nw[i]) : mx;
+                    }
+                }
+            }
+            if (v0 + 4 <= a.n) {
+                *reinterpret_cast<uint4 *>(a.val_next + v0) = make_uint4(nw[0], nw[1], nw[2], nw[3]);
+                if (a.hist_out)
+                    *reinterpret_cast<float4 *>(a.hist_out + v0) =
+                        make_float4(chm & 1u ? 1.0f : 0.0f, chm & 2u ? 1.0f : 0.0f, chm & 4u ? 1.0f : 0.0f,
+                                    chm & 8u ? 1.0f : 0.0f);
             } else {
-                ac[i] = kInf;
-            }
-        }
-        uint32_t chm = 0, nwv[U];
-#pragma unroll
-        for (int i = 0; i < U; ++i) {
-            const long long v = v0 + i * S;
-            const bool live = v < a.n;
-            const uint32_t nw = min(old[i], ac[i]);
-            const bool ch = live && nw < old[i];
-            if (live) {
-                a.val_next[v] = nw;
-                if (a.hist_out) a.hist_out[v] = ch ? 1.0f : 0.0f;
-            }
-            if (ch) {
-                changed += 1;
-                if (old[i] != kInf) {
-                    sum += old[i] - nw;
-                    mx = (old[i] - nw) > mx ? (old[i] - nw) : mx;
+                for (int i = 0; i < 4 && v0 + i < a.n; ++i) {
+                    a.val_next[v0 + i] = nw[i];
+                    if (a.hist_out) a.hist_out[v0 + i] = (chm >> i) & 1u ? 1.0f : 0.0f;
                 }
             }
-            chm |= ch ? 1u << i : 0u;
-            nwv[i] = nw;
         }
-        // frontier: the block's changed vertices at one offset (one atomic per block and step)
+        // frontier: the block's changed vertices at one offset
         if (a.q_out) {
             const uint32_t c = (uint32_t)__popc(chm);
             uint32_t incl = c;
@@ -733,10 +834,10 @@ __global__ void __launch_bounds__(kPullThreads) k_min_apply(PullArgs a)
             __syncthreads();
             uint32_t pos = s_base + s_cnt[wid] + incl - c;
 #pragma unroll
-            for (int i = 0; i < U; ++i) {
+            for (int i = 0; i < 4; ++i) {
                 if ((chm >> i) & 1u) {
-                    a.q_out[pos] = (int32_t)(v0 + i * S);
-                    a.q_out_val[pos] = nwv[i];
+                    a.q_out[pos] = (int32_t)(v0 + i);
+                    a.q_out_val[pos] = nw[i];
                     ++pos;
                 }
             }
@@ -752,77 +853,6 @@ __global__ void __launch_bounds__(kPullThreads) k_min_apply(PullArgs a)
         mx = om > mx ? om : mx;
     }
     if (lane == 0 && (changed | sum | mx)) {
-        atomicAdd(&a.stats->changed, changed);
-        atomicAdd(&a.stats->sum_delta, sum);
-        atomicMax(&a.stats->max_delta_bits, mx);
-    }
-}
-
-// ----------------------------------------------------------------- apply ----
-// GG-Apply + GG-VStatus (Alg. 2) for every vertex, in vertex order. A row's
-// sum is acc[v] (written by the tile holding its first arc), plus, for a row
-// continued across tile ends, the leading parts of the later tiles it covers,
-// in tile order; a row with no arcs in the list sums to 0. Each thread takes
-// four vertices a stride apart per step, all loads issued first.
-__global__ void __launch_bounds__(kPullThreads) k_pr_apply(PullArgs a)
-{
-    constexpr int U = 4;
-    unsigned long long changed = 0, sum = 0;
-    uint32_t mx = 0;
-    const long long S = (long long)gridDim.x * blockDim.x;
-    for (long long v0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; v0 < a.n; v0 += U * S) {
-        int32_t rs[U], re[U], d[U];
-        float old[U], acc[U];
-#pragma unroll
-        for (int i = 0; i < U; ++i) {
-            const long long v = v0 + i * S;
-            rs[i] = re[i] = d[i] = 0;
-            old[i] = acc[i] = 0.0f;
-            if (v < a.n) {
-                rs[i] = __ldg(a.row_ptr + v);
-                re[i] = __ldg(a.row_ptr + v + 1);
-                acc[i] = a.acc[v];   // stale for a row without arcs: replaced by 0 below
-                old[i] = a.rank_cur[v];
-                d[i] = a.deg_apply ? a.deg_apply[v] : __ldg(a.out_ptr + v + 1) - __ldg(a.out_ptr + v);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < U; ++i) {
-            if (re[i] > rs[i]) {
-                const int32_t t0 = rs[i] / kPT, t1 = (re[i] - 1) / kPT;
-                if (t1 - t0 <= kLongTiles) {   // a long row's total is complete already
-                    float x = acc[i];
-                    for (int32_t u = t0 + 1; u <= t1; ++u) x += a.lead[u];
-                    acc[i] = x;
-                }
-            } else {
-                acc[i] = 0.0f;
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < U; ++i) {
-            const long long v = v0 + i * S;
-            if (v >= a.n) continue;
-            const float nw = __fmaf_rn(a.damping, acc[i], a.base);
-            const float delta = fabsf(__fsub_rn(nw, old[i]));
-            a.rank_next[v] = nw;
-            a.contrib_next[v] = d[i] > 0 ? __fdiv_rn(nw, (float)d[i]) : 0.0f;
-            if (a.hist_out) a.hist_out[v] = __fmul_rn(a.n_f, delta);
-            changed += delta > a.epsilon ? 1ull : 0ull;
-            sum += __float2ull_rz(delta * 1099511627776.0f);   // fixed point 2^-40
-            const uint32_t db = __float_as_uint(delta);
-            mx = db > mx ? db : mx;
-        }
-    }
-    if (!a.stats) return;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        changed += __shfl_xor_sync(0xFFFFFFFFu, changed, o);
-        sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
-        const uint32_t om = __shfl_xor_sync(0xFFFFFFFFu, mx, o);
-        mx = om > mx ? om : mx;
-    }
-    if ((threadIdx.x & 31u) == 0 && (changed | sum | mx)) {
         atomicAdd(&a.stats->changed, changed);
         atomicAdd(&a.stats->sum_delta, sum);
         atomicMax(&a.stats->max_delta_bits, mx);
@@ -856,9 +886,11 @@ void launch_flags(const PullArgs &a, uint32_t max_tiles, int num_sms, cudaStream
 template <int APP>
 void launch_apply(const PullArgs &a, int num_sms, cudaStream_t s)
 {
-    // persistent: the blocks one wave holds (5 blocks of 256 per SM)
-    long long ab = ((long long)a.n + kPullThreads - 1) / kPullThreads;
-    if (ab > (long long)num_sms * 5) ab = (long long)num_sms * 5;
+    // persistent: the blocks one wave holds (PageRank's apply 4 blocks of 256
+    // per SM, the min apply 8), four vertices per thread and step
+    const int per_sm = APP == GG_APP_PAGERANK ? 4 : 8;
+    long long ab = ((long long)a.n / 4 + kPullThreads) / kPullThreads;
+    if (ab > (long long)num_sms * per_sm) ab = (long long)num_sms * per_sm;
     if (ab < 1) ab = 1;
     if constexpr (APP == GG_APP_PAGERANK) k_pr_apply<<<(unsigned)ab, kPullThreads, 0, s>>>(a);
     else k_min_apply<APP><<<(unsigned)ab, kPullThreads, 0, s>>>(a);
