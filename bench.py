@@ -129,19 +129,22 @@ def params(gg, app, source, timing=True, iters=None, theta=THETA, extra_flags=0)
 
 
 # --------------------------------------------------------- algorithmic bytes --
-# Bytes an iteration must move by the method's definition (value vectors are
-# gathered from L2; see the design notes). n = vertices, e = arcs of the
-# iteration's edge set, e_new = arcs active after a correction, m = all arcs.
+# Bytes an iteration must move by the method's definition (the gathered value
+# vector is read from L2 and counted once per vertex). n = vertices, e = arcs of the
+# iteration's edge set, m = all arcs.
 def gather_bytes(app, n, e):
     if app == "pagerank":        # sources 4e; row ptr, rank, degree, rank', contrib' 20n; contrib 4n
         return 4 * e + 24 * n
     return 8 * e + 16 * n         # sources + weights 8e; row ptr, value, value', gathered value 16n
 
 
-def correct_bytes(app, n, m, e_new):
-    if app == "pagerank":
-        return 4 * m + 4 * e_new + m // 8 + 28 * n
-    return 8 * m + 8 * e_new + m // 4 + 20 * n
+def correct_bytes(app, n, m):
+    """A correction over all m arcs: sources (and weights) read, flags
+    written (and read: the min applications keep some), per-vertex state;
+    rebuilding the packed list is not part of it."""
+    if app == "pagerank":        # sources 4m; flags m/8; row ptr, rank, degree, rank', contrib', contrib, acc 28n
+        return 4 * m + m // 8 + 28 * n
+    return 8 * m + m // 4 + 20 * n
 
 
 def clocks_sampler():
@@ -353,11 +356,11 @@ def roofline(collected, n, m):
             c[0] += ms_c
             c[1] += n_c
         for row in it:
-            mode = int(row["mode"])
+            mode = int(row["mode"]) & ~0x400   # a pull that read frontier sources only (GG_ITER_FILTER)
             if mode in (0, 1):    # pull gathers (push iterations carry the GG_ITER_PUSH bit)
                 classes[(app, "gather")][2] += gather_bytes(app, n, int(row["arcs"]))
             elif mode == 2:
-                classes[(app, "correct")][2] += correct_bytes(app, n, m, int(row["active_after"]))
+                classes[(app, "correct")][2] += correct_bytes(app, n, m)
     cands = [k for k in classes if classes[k][2] > 0 and classes[k][1]]
     if not cands:
         return None
@@ -375,10 +378,13 @@ def roofline(collected, n, m):
             "ms_last_step": {f"{k[0]}/{k[1]}": round(v[0], 3) for k, v in classes.items()}}
 
 
-KERNEL_NAMES = {("pagerank", "gather"): "k_pr_arcs + k_pr_apply",
-                ("pagerank", "correct"): "k_pr_arcs (values kept) + k_prc_flags + k_pr_apply + k_tile_counts",
-                "gather": "k_arcs<{a}, K_GATHER> + k_fixup<{a}>",
-                "correct": "k_arcs<{a}, K_STASH> + k_correct2<{a}>"}
+KERNEL_NAMES = {("pagerank", "gather"): "k_pull_arcs<PR> + k_long_rows<PR> + k_pr_apply",
+                ("pagerank", "correct"): ("k_pull_arcs<PR> (values kept) + k_long_rows + k_carries + k_prc_flags "
+                                          "+ k_pr_apply + scan + k_pack_arcs + k_pack_ptr"),
+                "gather": "k_pull_arcs<{a}> + k_long_rows<{a}> + k_min_apply<{a}>",
+                "correct": ("k_pull_arcs<{a}> (values kept) + k_long_rows + k_carries + k_minc_flags<{a}> "
+                            "+ k_min_apply<{a}> + scan + k_pack_arcs + k_pack_ptr"),
+                "push": "k_push<{a}> + k_append_frontier"}
 
 
 def accuracy_table(g, source, collected, full=True):

@@ -111,10 +111,14 @@ typedef enum {
                                  (order-free) instead of the running-prefix form of Alg. 2 */
 #define GG_RENORM 64u         /* PageRank: approximate iterations divide a source's rank by its number
                                  of active out-arcs (no rank mass leaks through inactive arcs) */
+#define GG_PULL_FILTER 128u   /* min applications: pull gathers read only the values of frontier sources
+                                 (a bitmap of the frontier). Same results; off by default, since on
+                                 GB300 the bitmap lookup per arc costs more than the reads it saves */
 
 #define GG_INF 0xFFFFFFFFu
 #define GG_ITER_PUSH 0x100u   /* gg_iter_stats.mode bit: iteration done by the push frontier */
 #define GG_ITER_LEARNED 0x200u /* gg_iter_stats.mode bit: a correction of the selected vertices only */
+#define GG_ITER_FILTER 0x400u /* gg_iter_stats.mode bit: a pull gather that read frontier sources only */
 
 typedef struct {
     uint32_t alpha;       /* approximate window: approximate iterations between corrections (Sec. 3.4) */

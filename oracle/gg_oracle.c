@@ -12,7 +12,7 @@
  * Arithmetic: PageRank in FP64; SSSP / BFS / CC in exact integers
  * (uint32 values, 0xFFFFFFFF = unreached).
  *
- * Readings of the paper taken here (each also listed in the design notes):
+ * Readings of the paper taken here:
  *  - Sec. 3.3: approximate mode gathers over active in-edges only, accurate
  *    mode over all in-edges; one flag per edge, no new graph.
  *  - Sec. 3.4: start from a sigma-fraction of active edges, run alpha

@@ -199,7 +199,7 @@ gg_status sample_edges(gg_graph *g, double ratio, uint64_t seed)
     GG_CUDA(launch_sample(g->in_src, g->in_dst, g->m, g->symmetric ? 1 : 0, seed,
                           (unsigned long long)std::floor(ratio * 4294967296.0), g->mask, g->num_sms, g->stream));
     g->launches += 1;
-    gg_status st = pack_active(g, g->has_w, nullptr, false);
+    gg_status st = pack_active(g, nullptr, false);
     if (st != GG_OK) return st;
     GG_CUDA(cudaEventRecord(g->ev_s1, g->stream));
     g->sample_timed = true;
@@ -225,6 +225,8 @@ static gg_status ensure_iter_cap(gg_graph *g, uint32_t iters)
 // Active out-degrees of the current flags (GG_RENORM).
 static gg_status refresh_active_outdeg(gg_graph *g)
 {
+    gg_status st = ensure_packed(g, false);
+    if (st != GG_OK) return st;
     GG_CUDA(launch_active_outdeg(g->sp_src, g->sp_nnz, (uint32_t)g->m, g->n, g->hub_ids, g->act_outdeg, g->num_sms,
                                  g->stream));
     g->launches += 2;
@@ -305,6 +307,8 @@ static gg_status trace_features(gg_graph *g, gg_app app, uint32_t i, bool *traci
 {
     *tracing = g->trace_x && g->trace_rows + (uint64_t)g->n <= g->trace_cap;
     if (!*tracing) return GG_OK;
+    gg_status st = ensure_packed(g, false);   // the active in-degree feature
+    if (st != GG_OK) return st;
     GG_CUDA(launch_trace_features(feat_args(g, app, i), g->trace_x + g->trace_rows * 8, g->num_sms, g->stream));
     g->launches += 1;
     return GG_OK;
@@ -329,6 +333,8 @@ static gg_status learned_select(gg_graph *g, gg_app app, const gg_params *p, uin
                                 uint32_t *nsel, uint32_t *total)
 {
     *learned = false;
+    gg_status st = ensure_packed(g, false);   // the active in-degree feature
+    if (st != GG_OK) return st;
     GG_CUDA(launch_mlp_select(feat_args(g, app, i), g->mlp, p->select_logit, p->select_cost, g->sel_flag,
                               g->sel_off, g->logits, g->num_sms, g->stream));
     GG_CUDA(launch_scan_u32(g->sel_flag, g->sel_pos, (size_t)g->n, g->scan_tmp, g->stream));
@@ -462,6 +468,10 @@ static gg_status run_pagerank(gg_graph *g, gg_policy policy, const gg_params *p)
         a.infl_share = (p->flags & GG_INFL_SHARE) ? 1 : 0;
         // the next iteration gathers active arcs only: renormalised contributions
         a.deg_apply = (renorm && next == MODE_APPROX && kind != K_CORRECT) ? g->act_outdeg : nullptr;
+        if (mode == MODE_APPROX) {
+            gg_status st = ensure_packed(g, false);
+            if (st != GG_OK) return st;
+        }
         fill_list(g, mode == MODE_APPROX, a);
         a.contrib_cur = g->contrib[g->cur];
         a.rank_cur = g->rank[g->cur];
@@ -519,8 +529,8 @@ static gg_status run_pagerank(gg_graph *g, gg_policy policy, const gg_params *p)
                     pa.theta = p->theta;
                     GG_CUDA(launch_pull(GG_APP_PAGERANK, pa, true, (uint32_t)g->plan[which].tiles, g->num_sms,
                                         g->stream));
+                    g->launches += 5;
                     counted = true;
-                    g->launches += 3;
                 }
                 timed_end(g, slot);
             } else {
@@ -536,7 +546,8 @@ static gg_status run_pagerank(gg_graph *g, gg_policy policy, const gg_params *p)
             }
         }
         if (kind == K_CORRECT) {
-            gg_status st = pack_active(g, false, a.stats, counted);
+            // the packed list itself is built when an approximate gather needs it
+            gg_status st = pack_active(g, a.stats, counted);
             if (st != GG_OK) return st;
             g->sample_clean = false;
             g->stats.corrections += 1;
@@ -682,6 +693,10 @@ static gg_status run_min(gg_graph *g, gg_app app, gg_policy policy, const gg_par
         } else {
             const int kind = mode == MODE_CORRECTION ? K_CORRECT : K_GATHER;
             TileArgs a{};
+            if (mode == MODE_APPROX) {
+                st = ensure_packed(g, app == GG_APP_SSSP && g->has_w);
+                if (st != GG_OK) return st;
+            }
             fill_list(g, mode == MODE_APPROX, a);
             a.val_cur = g->val[g->cur];
             a.val_next = g->val[g->cur ^ 1];
@@ -719,13 +734,23 @@ static gg_status run_min(gg_graph *g, gg_app app, gg_policy policy, const gg_par
                     st = trace_features(g, app, i, &tracing);
                     if (st != GG_OK) return st;
                 }
-                GG_CUDA(launch_iter_header(sti, (uint32_t)mode, nullptr, list_nnz, g->stream));
+                // GG_PULL_FILTER: a gather skips the arcs of sources outside the
+                // frontier, whose values were taken in when they last changed (as
+                // a push does)
+                const bool filter = kind == K_GATHER && (p->flags & GG_PULL_FILTER) != 0;
+                GG_CUDA(launch_iter_header(sti, (uint32_t)mode | (filter ? GG_ITER_FILTER : 0u), nullptr, list_nnz,
+                                           g->stream));
                 const int which = mode == MODE_APPROX ? 1 : 0;
                 PullArgs pa{};
                 st = pull_args(g, which, a, &pa);
                 if (st != GG_OK) return st;
                 pa.w = (app == GG_APP_SSSP && g->has_w) ? (which ? g->sp_w : g->in_w) : nullptr;
                 timed_begin(g, timing, kind == K_CORRECT ? 1 : 0, &slot);
+                if (filter) {
+                    GG_CUDA(launch_front_bits(g->q[qc], &g->q_len[qc], g->pull_front, g->n, g->num_sms, g->stream));
+                    g->launches += 1;
+                    pa.front = g->pull_front;
+                }
                 if (kind == K_CORRECT) {
                     pa.vals = reinterpret_cast<float *>(g->stash);
                     pa.mask = g->mask;
@@ -737,14 +762,15 @@ static gg_status run_min(gg_graph *g, gg_app app, gg_policy policy, const gg_par
                 GG_CUDA(launch_pull((int)app, pa, kind == K_CORRECT, (uint32_t)g->plan[which].tiles, g->num_sms,
                                     g->stream));
                 timed_end(g, slot);
-                g->launches += kind == K_CORRECT ? 3 : 2;
+                g->launches += kind == K_CORRECT ? 5 : 3;
                 if (tracing) {
                     st = trace_labels(g, false);
                     if (st != GG_OK) return st;
                 }
             }
             if (kind == K_CORRECT) {
-                st = pack_active(g, app == GG_APP_SSSP && g->has_w, sti, !learned);
+                // the packed list itself is built when an approximate pull needs it
+                st = pack_active(g, sti, !learned);
                 if (st != GG_OK) return st;
                 g->sample_clean = false;
                 g->stats.corrections += 1;
@@ -1086,11 +1112,13 @@ static gg_status result_size(gg_graph *g, gg_result_kind kind, const void **src,
         break;
     case GG_RESULT_SPARSE_PTR:
         if (!g->sampled) break;
+        if (ensure_packed(g, false) != GG_OK) return GG_ERR_CUDA;
         *src = g->sp_ptr;
         *bytes = 4 * (n + 1);
         break;
     case GG_RESULT_SPARSE_SRC:
         if (!g->sampled) break;
+        if (ensure_packed(g, false) != GG_OK) return GG_ERR_CUDA;
         GG_CUDA(cudaMemcpyAsync(&g->sp_nnz_host, g->sp_nnz, 4, cudaMemcpyDeviceToHost, g->stream));
         GG_CUDA(cudaStreamSynchronize(g->stream));
         *src = g->sp_src;

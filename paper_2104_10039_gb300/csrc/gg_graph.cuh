@@ -175,8 +175,11 @@ struct gg_graph {
     gg::PullPlan plan[2];
     gg::DevBuf b_pull;
     float *pull_acc = nullptr, *pull_lead = nullptr, *pull_carry = nullptr;
+    uint32_t *pull_front = nullptr;   // frontier bitmap of a filtered pull (n bits)
     bool pull_ready = false;
     bool sp_is_plain = false;
+    bool sp_stale = false;     // the mask's tile counts are scanned, the packed list not yet built
+    bool sp_has_w = false;     // the packed list carries the weights
     // training trace (caller-owned device buffers)
     float *trace_x = nullptr;
     uint8_t *trace_y = nullptr;
@@ -191,7 +194,14 @@ gg_status validate_csr(gg_graph *g);
 gg_status sample_edges(gg_graph *g, double ratio, uint64_t seed);
 // Packed active in-edges from the flag bitmap (gg_pack.cu); have_counts: the
 // per-tile active counts are in tile_cnt already (a correction's flag pass).
-gg_status pack_active(gg_graph *g, bool weighted, IterStatsDev *stats, bool have_counts);
+// After the flags changed: counts the active arcs of the bitmap per 256-arc
+// tile (unless the correction's flag pass did: have_counts) and scans them;
+// the packed list's arc count (and stats->active_after) are then set. The
+// list itself is built by ensure_packed.
+gg_status pack_active(gg_graph *g, IterStatsDev *stats, bool have_counts);
+// Builds the packed list of the current flags if it is not built yet, or
+// lacks the weights a caller needs (weighted).
+gg_status ensure_packed(gg_graph *g, bool weighted);
 gg_status run(gg_graph *g, gg_app app, double ratio, gg_policy policy, const gg_params *p);
 uint32_t next_epoch(gg_graph *g);
 gg_status ensure_pull(gg_graph *g);

@@ -142,6 +142,8 @@ struct PullArgs {
     unsigned long long theta_fx;   // ... floor(theta 2^32)
     int est_strict;             // ... arcs without a candidate lose their flag
     const uint32_t *w;          // SSSP: list arcs' weights, or nullptr (weight 1)
+    const uint32_t *front;      // SSSP / BFS / CC gathers: bitmap of the frontier (bit v: v changed in the
+                                // previous iteration); only its vertices' arcs are read. nullptr: every arc
     const uint32_t *val_cur;    // SSSP / BFS / CC values
     uint32_t *val_next;
     int32_t *q_out;             // SSSP / BFS / CC: next frontier (vertex, value), length
@@ -281,6 +283,8 @@ cudaError_t launch_decode_src(const int32_t *coded, const uint32_t *count, uint3
                               int32_t *out, int num_sms, cudaStream_t s);
 // Pull iteration of an application (gg_pull.cu): arcs, then apply; with
 // `correct`, arcs (values kept), influence and flags, then apply.
+cudaError_t launch_front_bits(const int32_t *q, const uint32_t *q_len, uint32_t *bits, int32_t n, int num_sms,
+                              cudaStream_t s);
 cudaError_t launch_pull(int app, const PullArgs &a, bool correct, uint32_t max_tiles, int num_sms, cudaStream_t s);
 // contrib[u] = rank[u] / deg[u], or / the full out-degree when deg is null (0 when the degree is 0).
 cudaError_t launch_contrib(int32_t n, const float *rank, const int32_t *deg, const int32_t *out_ptr,

@@ -9,12 +9,16 @@
 //   (scan)         tile offsets in the packed list
 //   k_pack_arcs    one warp per tile: each active arc's source (and weight)
 //                  to tile offset + its rank among the tile's active arcs,
-//                  sources read with 16-byte loads
+//                  sources read with 16-byte loads, staged in shared memory
+//                  and stored by consecutive lanes
 //   k_pack_ptr     one thread per vertex: its packed row start = the offset
 //                  of the tile holding its first arc + the active arcs of
 //                  that tile before it
 // The packed order is the list order, so the result is the same whatever
-// the tiling.
+// the tiling. The last two steps wait until an approximate gather or a
+// result needs the list (ensure_packed): a min application that only pushes
+// before its next correction, or a run that ends on a correction, never
+// builds it; PageRank builds it without weights.
 #include "gg_graph.cuh"
 
 namespace gg {
@@ -53,7 +57,13 @@ __global__ void __launch_bounds__(256) k_pack_arcs(const uint32_t *__restrict__ 
                                                    const uint32_t *__restrict__ w, int32_t *__restrict__ sp_src,
                                                    uint32_t *__restrict__ sp_w)
 {
+    // each warp stages its tile's active arcs in order, then stores them with
+    // consecutive lanes on consecutive positions
+    __shared__ int32_t s_src[8 * kPT];
+    __shared__ uint32_t s_w[WEIGHTED ? 8 * kPT : 1];
     const uint32_t lane = threadIdx.x & 31u;
+    int32_t *st = s_src + (threadIdx.x >> 5) * kPT;
+    uint32_t *sw = s_w + (WEIGHTED ? (threadIdx.x >> 5) * kPT : 0);
     const long long nt = (m + kPT - 1) / kPT;
     const long long nw = (m + 31) / 32;
     const long long W = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -97,8 +107,8 @@ __global__ void __launch_bounds__(256) k_pack_arcs(const uint32_t *__restrict__ 
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     if ((f >> j) & 1u) {
-                        sp_src[base + rank] = s4[j];
-                        if (WEIGHTED) sp_w[base + rank] = w4[j];
+                        st[rank] = s4[j];
+                        if (WEIGHTED) sw[rank] = w4[j];
                         ++rank;
                     }
                 }
@@ -108,6 +118,12 @@ __global__ void __launch_bounds__(256) k_pack_arcs(const uint32_t *__restrict__ 
             for (int k = 0; k < 4; ++k) hw += (uint32_t)__popc(__shfl_sync(0xFFFFFFFFu, mw, 4 * h + k));
             before += hw;
         }
+        __syncwarp();
+        for (uint32_t k = lane; k < before; k += 32u) {
+            sp_src[base + k] = st[k];
+            if (WEIGHTED) sp_w[base + k] = sw[k];
+        }
+        __syncwarp();
     }
 }
 
@@ -134,9 +150,50 @@ __global__ void k_pack_ptr(const int32_t *__restrict__ in_ptr, int32_t n, const 
     }
 }
 
+// The arc count of a deferred pack (the scan's total) and the correction's
+// active_after statistic.
+__global__ void k_pack_total(const uint32_t *__restrict__ off, long long nt, uint32_t *__restrict__ sp_nnz,
+                             IterStatsDev *stats)
+{
+    const uint32_t q = off[nt];
+    *sp_nnz = q;
+    if (stats) stats->active_after = q;
+}
+
+// The packed arcs and row pointers from the scanned tile counts.
+gg_status pack_lists(gg_graph *g, bool weighted, IterStatsDev *stats)
+{
+    cudaStream_t s = g->stream;
+    const long long m = g->m;
+    const long long nt = (m + kPT - 1) / kPT;
+    long long ab = (nt * 32 + 255) / 256;
+    if (ab > (long long)g->num_sms * 8) ab = (long long)g->num_sms * 8;
+    if (ab < 1) ab = 1;
+    if (nt > 0) {
+        if (weighted) {
+            k_pack_arcs<true><<<(unsigned)ab, 256, 0, s>>>(g->mask, m, g->tile_off, g->in_src, g->in_w, g->sp_src,
+                                                           g->sp_w);
+        } else {
+            k_pack_arcs<false><<<(unsigned)ab, 256, 0, s>>>(g->mask, m, g->tile_off, g->in_src, nullptr, g->sp_src,
+                                                            nullptr);
+        }
+        GG_CUDA(cudaGetLastError());
+        g->launches += 1;
+    }
+    long long vb = ((long long)g->n + 1 + 255) / 256;
+    if (vb > (long long)g->num_sms * 8) vb = (long long)g->num_sms * 8;
+    k_pack_ptr<<<(unsigned)vb, 256, 0, s>>>(g->in_ptr, g->n, g->mask, m, g->tile_off, g->sp_ptr, g->sp_nnz, stats);
+    GG_CUDA(cudaGetLastError());
+    g->launches += 1;
+    g->sp_stale = false;
+    g->sp_is_plain = true;
+    g->plan[1].valid = false;
+    return GG_OK;
+}
+
 }  // namespace
 
-gg_status pack_active(gg_graph *g, bool weighted, IterStatsDev *stats, bool have_counts)
+gg_status pack_active(gg_graph *g, IterStatsDev *stats, bool have_counts)
 {
     cudaStream_t s = g->stream;
     const long long m = g->m;
@@ -150,27 +207,23 @@ gg_status pack_active(gg_graph *g, bool weighted, IterStatsDev *stats, bool have
         g->launches += 1;
     }
     GG_CUDA(launch_scan_u32(g->tile_cnt, g->tile_off, (size_t)nt, g->scan_tmp, s));
-    long long ab = (nt * 32 + 255) / 256;
-    if (ab > (long long)g->num_sms * 8) ab = (long long)g->num_sms * 8;
-    if (ab < 1) ab = 1;
-    if (nt > 0) {
-        if (weighted) {
-            k_pack_arcs<true><<<(unsigned)ab, 256, 0, s>>>(g->mask, m, g->tile_off, g->in_src, g->in_w, g->sp_src,
-                                                           g->sp_w);
-        } else {
-            k_pack_arcs<false><<<(unsigned)ab, 256, 0, s>>>(g->mask, m, g->tile_off, g->in_src, nullptr, g->sp_src,
-                                                            nullptr);
-        }
-        GG_CUDA(cudaGetLastError());
-    }
-    long long vb = ((long long)g->n + 1 + 255) / 256;
-    if (vb > (long long)g->num_sms * 8) vb = (long long)g->num_sms * 8;
-    k_pack_ptr<<<(unsigned)vb, 256, 0, s>>>(g->in_ptr, g->n, g->mask, m, g->tile_off, g->sp_ptr, g->sp_nnz, stats);
+    k_pack_total<<<1, 1, 0, s>>>(g->tile_off, nt, g->sp_nnz, stats);
     GG_CUDA(cudaGetLastError());
-    g->launches += 5;
-    g->sp_is_plain = true;
+    g->launches += nt > 0 ? 4 : 2;   // scan: three launches over a non-empty list, one otherwise
+    g->sp_stale = true;
     g->plan[1].valid = false;
     return GG_OK;
+}
+
+// tile_off holds the scan of the current flags' tile counts: pack_active
+// runs after every change of the flags, and nothing else writes it.
+gg_status ensure_packed(gg_graph *g, bool weighted)
+{
+    weighted = weighted && g->has_w;
+    if (!g->sp_stale && (g->sp_has_w || !weighted)) return GG_OK;
+    gg_status st = pack_lists(g, weighted, nullptr);
+    if (st == GG_OK) g->sp_has_w = weighted;
+    return st;
 }
 
 }  // namespace gg

@@ -160,7 +160,7 @@ struct PullOp<GG_APP_PAGERANK> {
 // PF: the next tile's sources (and weights) are loaded while this tile's
 // values are in flight (full tiles only). a.vals != nullptr (a correction's
 // first pass): every arc's value is also stored, in list order.
-template <int APP, int MINB, bool PF>
+template <int APP, int MINB, bool PF, bool FILT = false>
 __global__ void __launch_bounds__(kPullThreads, MINB) k_pull_arcs(PullArgs a)
 {
     using Op = PullOp<APP>;
@@ -216,8 +216,19 @@ __global__ void __launch_bounds__(kPullThreads, MINB) k_pull_arcs(PullArgs a)
             }
         }
         T v[8];
+        if constexpr (FILT) {
+            // only a frontier source can lower a row: every other source's
+            // value was taken in when it last changed
+            uint32_t fw[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = s[i] >= 0 ? Op::cand(a, s[i], kW ? w[kW ? i : 0] : 1u) : Op::id();
+            for (int i = 0; i < 8; ++i) fw[i] = s[i] >= 0 ? __ldg(a.front + (s[i] >> 5)) : 0u;
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                v[i] = ((fw[i] >> (s[i] & 31)) & 1u) ? Op::cand(a, s[i], kW ? w[kW ? i : 0] : 1u) : Op::id();
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[i] = s[i] >= 0 ? Op::cand(a, s[i], kW ? w[kW ? i : 0] : 1u) : Op::id();
+        }
         if (a.vals) {
             uint32_t *vb = reinterpret_cast<uint32_t *>(a.vals);
             uint32_t b[8];
@@ -427,7 +438,9 @@ __global__ void __launch_bounds__(kPullThreads) k_carries(PullArgs a)
 // (after - before) > theta * after, one flag bit per arc. The row continued
 // from earlier tiles starts from its carry (k_carries / k_long_rows): its
 // part in the tile of its first arc plus the leading parts of the tiles in
-// between, in tile order.
+// between, in tile order. Lane L takes the tile's arcs 8L .. 8L + 7 (two
+// 16-byte loads of the kept values, one byte of a flag word), so a single
+// segmented warp scan covers the tile.
 __global__ void __launch_bounds__(kPullThreads, 4) k_prc_flags(PullArgs a)
 {
     constexpr uint32_t FULL = 0xFFFFFFFFu;
@@ -436,17 +449,19 @@ __global__ void __launch_bounds__(kPullThreads, 4) k_prc_flags(PullArgs a)
     const long long nt = ((long long)nnz + kPT - 1) / kPT;
     const long long mask_words = ((long long)nnz + 31) / 32;
     const long long W = (long long)gridDim.x * (kPullThreads / 32);
+    const uint32_t sh = 8u * (lane & 3u);                // this lane's byte in its flag word
     uint4 pf0 = make_uint4(0u, 0u, 0u, 0u), pf1 = pf0;   // the next full tile's values, loaded ahead
     bool have_pf = false;
     for (long long t = (long long)blockIdx.x * (kPullThreads / 32) + (threadIdx.x >> 5); t < nt; t += W) {
         const long long a0 = t * kPT;
         const uint32_t rel = nnz - (uint32_t)a0 < (uint32_t)kPT ? nnz - (uint32_t)a0 : (uint32_t)kPT;
+        // lane L: arcs 8L .. 8L + 7 of the tile
         float v[8];
         if (rel == (uint32_t)kPT) {
             uint4 x = pf0, y = pf1;
             if (!have_pf) {
-                x = reinterpret_cast<const uint4 *>(a.vals + a0)[lane];
-                y = reinterpret_cast<const uint4 *>(a.vals + a0 + 128)[lane];
+                x = reinterpret_cast<const uint4 *>(a.vals + a0 + 8 * lane)[0];
+                y = reinterpret_cast<const uint4 *>(a.vals + a0 + 8 * lane)[1];
             }
             v[0] = __uint_as_float(x.x); v[1] = __uint_as_float(x.y); v[2] = __uint_as_float(x.z);
             v[3] = __uint_as_float(x.w); v[4] = __uint_as_float(y.x); v[5] = __uint_as_float(y.y);
@@ -454,75 +469,57 @@ __global__ void __launch_bounds__(kPullThreads, 4) k_prc_flags(PullArgs a)
             const long long tn = t + W;
             have_pf = tn < nt && (tn + 1) * kPT <= (long long)nnz;
             if (have_pf) {
-                pf0 = reinterpret_cast<const uint4 *>(a.vals + tn * kPT)[lane];
-                pf1 = reinterpret_cast<const uint4 *>(a.vals + tn * kPT + 128)[lane];
+                pf0 = reinterpret_cast<const uint4 *>(a.vals + tn * kPT + 8 * lane)[0];
+                pf1 = reinterpret_cast<const uint4 *>(a.vals + tn * kPT + 8 * lane)[1];
             }
         } else {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const uint32_t q = 4u * lane + (uint32_t)j;
+            for (int j = 0; j < 8; ++j) {
+                const uint32_t q = 8u * lane + (uint32_t)j;
                 v[j] = q < rel ? a.vals[a0 + q] : 0.0f;
-                v[4 + j] = q + 128u < rel ? a.vals[a0 + 128 + q] : 0.0f;
             }
         }
-        uint4 h0 = __ldg(reinterpret_cast<const uint4 *>(a.hb + t * 8));
-        uint4 h1 = __ldg(reinterpret_cast<const uint4 *>(a.hb + t * 8 + 4));
-        if (rel < (uint32_t)kPT) {
-            h0.x = tail_bits(h0.x, 0, rel); h0.y = tail_bits(h0.y, 1, rel);
-            h0.z = tail_bits(h0.z, 2, rel); h0.w = tail_bits(h0.w, 3, rel);
-            h1.x = tail_bits(h1.x, 4, rel); h1.y = tail_bits(h1.y, 5, rel);
-            h1.z = tail_bits(h1.z, 6, rel); h1.w = tail_bits(h1.w, 7, rel);
-        }
+        uint32_t hw = __ldg(a.hb + t * 8 + (lane >> 2));
+        if (rel < (uint32_t)kPT) hw = tail_bits(hw, (int)(lane >> 2), rel);
+        const uint32_t f = (hw >> sh) & 0xFFu;   // bit j: arc j of this lane starts a row
         // carry of the row open at the tile start (k_carries, k_long_rows)
-        float carry = (h0.x & 1u) ? 0.0f : a.carry[t];
-        uint32_t tile_active = 0;
+        float carry = 0.0f;
+        if (lane == 0 && !(hw & 1u)) carry = a.carry[t];
+        // the lane's tail: its arcs from its last row start (or all of them)
+        float r = v[0];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const uint4 hw = h ? h1 : h0;
-            const uint32_t sh = 4u * (lane & 7u);
-            const uint32_t f = (pick4(hw, lane >> 3) >> sh) & 0xFu;
-            const float v0 = v[4 * h], v1 = v[4 * h + 1], v2 = v[4 * h + 2], v3 = v[4 * h + 3];
-            // lane tails for the scan (as in k_pull_arcs)
-            const float r0 = v0;
-            const float r1 = (f & 2u) ? v1 : r0 + v1;
-            const float r2 = (f & 4u) ? v2 : r1 + v2;
-            const float r3 = (f & 8u) ? v3 : r2 + v3;
-            const uint32_t heads = __ballot_sync(FULL, f != 0u);
-            const uint32_t le = heads & (FULL >> (31u - lane));
-            const int start = le ? 31 - __clz(le) : -1;
-            float x = r3;
-            if (lane == 0 && f == 0u) x = carry + r3;
+        for (int j = 1; j < 8; ++j) r = ((f >> j) & 1u) ? v[j] : r + v[j];
+        // warp segmented inclusive scan of the tails
+        const uint32_t heads = __ballot_sync(FULL, f != 0u);
+        const uint32_t le = heads & (FULL >> (31u - lane));
+        const int start = le ? 31 - __clz(le) : -1;   // lane where the segment open at this lane's end starts
+        float x = r;
+        if (lane == 0 && f == 0u) x = carry + r;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const float y = __shfl_up_sync(FULL, x, o);
-                if ((int)lane >= o && (int)lane - o >= start) x = y + x;
-            }
-            float run = __shfl_up_sync(FULL, x, 1);
-            if (lane == 0) run = carry;
-            // running sums before / after each arc, in arc order from the
-            // segment's value at the lane start
-            uint32_t nib = 0;
-            const float vv[4] = {v0, v1, v2, v3};
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const uint32_t q = 128u * (uint32_t)h + 4u * lane + (uint32_t)j;
-                const float before = ((f >> j) & 1u) ? 0.0f : run;
-                const float after = __fadd_rn(before, vv[j]);
-                run = after;
-                const bool fl = after != 0.0f ? __fsub_rn(after, before) > __fmul_rn(a.theta, after)
-                                              : 0.0f > a.theta;
-                if (fl && q < rel) nib |= 1u << j;
-            }
-            uint32_t word = nib << sh;
-            word |= __shfl_xor_sync(FULL, word, 1);
-            word |= __shfl_xor_sync(FULL, word, 2);
-            word |= __shfl_xor_sync(FULL, word, 4);
-            const long long wi = t * 8 + 4 * h + (lane >> 3);
-            if ((lane & 7u) == 0 && wi < mask_words) a.mask[wi] = word;
-            if ((lane & 7u) == 0) tile_active += (uint32_t)__popc(word);
-            carry = __shfl_sync(FULL, x, 31);
+        for (int o = 1; o < 32; o <<= 1) {
+            const float y = __shfl_up_sync(FULL, x, o);
+            if ((int)lane >= o && (int)lane - o >= start) x = y + x;
         }
-        tile_active = __reduce_add_sync(FULL, tile_active);
+        float run = __shfl_up_sync(FULL, x, 1);
+        if (lane == 0) run = carry;
+        // running sums before / after each arc, in arc order from the
+        // segment's value at the lane start
+        uint32_t byte = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint32_t q = 8u * lane + (uint32_t)j;
+            const float before = ((f >> j) & 1u) ? 0.0f : run;
+            const float after = __fadd_rn(before, v[j]);
+            run = after;
+            const bool fl = after != 0.0f ? __fsub_rn(after, before) > __fmul_rn(a.theta, after) : 0.0f > a.theta;
+            if (fl && q < rel) byte |= 1u << j;
+        }
+        uint32_t word = byte << sh;
+        word |= __shfl_xor_sync(FULL, word, 1);
+        word |= __shfl_xor_sync(FULL, word, 2);
+        const long long wi = t * 8 + (lane >> 2);
+        if ((lane & 3u) == 0 && wi < mask_words) a.mask[wi] = word;
+        const uint32_t tile_active = __reduce_add_sync(FULL, (uint32_t)__popc(byte));
         if (lane == 0 && a.tcnt) a.tcnt[t] = tile_active;
     }
 }
@@ -546,99 +543,83 @@ __global__ void __launch_bounds__(kPullThreads, 4) k_minc_flags(PullArgs a)
     const long long mask_words = ((long long)nnz + 31) / 32;
     const long long W = (long long)gridDim.x * (kPullThreads / 32);
     const uint32_t *cv = reinterpret_cast<const uint32_t *>(a.vals);
+    const uint32_t sh = 8u * (lane & 3u);                // this lane's byte in its flag word
     uint4 pf0 = make_uint4(0u, 0u, 0u, 0u), pf1 = pf0;   // the next full tile's candidates, loaded ahead
     bool have_pf = false;
     for (long long t = (long long)blockIdx.x * (kPullThreads / 32) + (threadIdx.x >> 5); t < nt; t += W) {
         const long long a0 = t * kPT;
         const uint32_t rel = nnz - (uint32_t)a0 < (uint32_t)kPT ? nnz - (uint32_t)a0 : (uint32_t)kPT;
+        // lane L: arcs 8L .. 8L + 7 of the tile
         uint32_t v[8];
         if (rel == (uint32_t)kPT) {
             uint4 x = pf0, y = pf1;
             if (!have_pf) {
-                x = reinterpret_cast<const uint4 *>(cv + a0)[lane];
-                y = reinterpret_cast<const uint4 *>(cv + a0 + 128)[lane];
+                x = reinterpret_cast<const uint4 *>(cv + a0 + 8 * lane)[0];
+                y = reinterpret_cast<const uint4 *>(cv + a0 + 8 * lane)[1];
             }
             v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
             v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
             const long long tn = t + W;
             have_pf = tn < nt && (tn + 1) * kPT <= (long long)nnz;
             if (have_pf) {
-                pf0 = reinterpret_cast<const uint4 *>(cv + tn * kPT)[lane];
-                pf1 = reinterpret_cast<const uint4 *>(cv + tn * kPT + 128)[lane];
+                pf0 = reinterpret_cast<const uint4 *>(cv + tn * kPT + 8 * lane)[0];
+                pf1 = reinterpret_cast<const uint4 *>(cv + tn * kPT + 8 * lane)[1];
             }
         } else {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const uint32_t q = 4u * lane + (uint32_t)j;
+            for (int j = 0; j < 8; ++j) {
+                const uint32_t q = 8u * lane + (uint32_t)j;
                 v[j] = q < rel ? cv[a0 + q] : kInf;
-                v[4 + j] = q + 128u < rel ? cv[a0 + 128 + q] : kInf;
             }
         }
-        uint4 h0 = __ldg(reinterpret_cast<const uint4 *>(a.hb + t * 8));
-        uint4 h1 = __ldg(reinterpret_cast<const uint4 *>(a.hb + t * 8 + 4));
-        if (rel < (uint32_t)kPT) {
-            h0.x = tail_bits(h0.x, 0, rel); h0.y = tail_bits(h0.y, 1, rel);
-            h0.z = tail_bits(h0.z, 2, rel); h0.w = tail_bits(h0.w, 3, rel);
-            h1.x = tail_bits(h1.x, 4, rel); h1.y = tail_bits(h1.y, 5, rel);
-            h1.z = tail_bits(h1.z, 6, rel); h1.w = tail_bits(h1.w, 7, rel);
-        }
+        const long long wi = t * 8 + (lane >> 2);
+        uint32_t hw = __ldg(a.hb + t * 8 + (lane >> 2));
+        if (rel < (uint32_t)kPT) hw = tail_bits(hw, (int)(lane >> 2), rel);
+        const uint32_t f = (hw >> sh) & 0xFFu;   // bit j: arc j of this lane starts a row
+        const uint32_t old = ((wi < mask_words) ? a.mask[wi] : 0u) >> sh;   // this lane's flags, before
         // running minimum of the row open at the tile start (k_carries, k_long_rows)
-        uint32_t carry = (h0.x & 1u) ? kInf : reinterpret_cast<const uint32_t *>(a.carry)[t];
-        uint32_t tile_active = 0;
+        uint32_t carry = kInf;
+        if (lane == 0 && !(hw & 1u)) carry = reinterpret_cast<const uint32_t *>(a.carry)[t];
+        uint32_t r = v[0];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const uint4 hw = h ? h1 : h0;
-            const uint32_t sh = 4u * (lane & 7u);
-            const long long wi = t * 8 + 4 * h + (lane >> 3);
-            const uint32_t f = (pick4(hw, lane >> 3) >> sh) & 0xFu;
-            const uint32_t oldw = (wi < mask_words) ? a.mask[wi] : 0u;   // this tile's flag words, before
-            const uint32_t v0 = v[4 * h], v1 = v[4 * h + 1], v2 = v[4 * h + 2], v3 = v[4 * h + 3];
-            const uint32_t r0 = v0;
-            const uint32_t r1 = (f & 2u) ? v1 : min(r0, v1);
-            const uint32_t r2 = (f & 4u) ? v2 : min(r1, v2);
-            const uint32_t r3 = (f & 8u) ? v3 : min(r2, v3);
-            const uint32_t heads = __ballot_sync(FULL, f != 0u);
-            const uint32_t le = heads & (FULL >> (31u - lane));
-            const int start = le ? 31 - __clz(le) : -1;
-            uint32_t x = r3;
-            if (lane == 0 && f == 0u) x = min(carry, r3);
+        for (int j = 1; j < 8; ++j) r = ((f >> j) & 1u) ? v[j] : min(r, v[j]);
+        const uint32_t heads = __ballot_sync(FULL, f != 0u);
+        const uint32_t le = heads & (FULL >> (31u - lane));
+        const int start = le ? 31 - __clz(le) : -1;
+        uint32_t x = r;
+        if (lane == 0 && f == 0u) x = min(carry, r);
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(FULL, x, o);
-                if ((int)lane >= o && (int)lane - o >= start) x = min(y, x);
-            }
-            uint32_t run = __shfl_up_sync(FULL, x, 1);
-            if (lane == 0) run = carry;
-            uint32_t nib = 0;
-            const uint32_t vv[4] = {v0, v1, v2, v3};
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const uint32_t q = 128u * (uint32_t)h + 4u * lane + (uint32_t)j;
-                const uint32_t before = ((f >> j) & 1u) ? kInf : run;
-                const uint32_t c = vv[j];
-                run = min(before, c);
-                uint32_t fl = 0;
-                if (c == kInf) {
-                    fl = a.est_strict ? 0u : (oldw >> (sh + (uint32_t)j)) & 1u;
-                } else if (a.theta_case == 1) {
-                    fl = 1u;
-                } else if (a.theta_case == 2) {
-                    fl = 0u;
-                } else if (c < before) {
-                    if (before == kInf || APP == GG_APP_CC) fl = 1u;
-                    else fl = ((unsigned long long)(before - c) << 32) > a.theta_fx * (unsigned long long)before ? 1u : 0u;
-                }
-                if (fl && q < rel) nib |= 1u << j;
-            }
-            uint32_t word = nib << sh;
-            word |= __shfl_xor_sync(FULL, word, 1);
-            word |= __shfl_xor_sync(FULL, word, 2);
-            word |= __shfl_xor_sync(FULL, word, 4);
-            if ((lane & 7u) == 0 && wi < mask_words) a.mask[wi] = word;
-            if ((lane & 7u) == 0) tile_active += (uint32_t)__popc(word);
-            carry = __shfl_sync(FULL, x, 31);
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, x, o);
+            if ((int)lane >= o && (int)lane - o >= start) x = min(y, x);
         }
-        tile_active = __reduce_add_sync(FULL, tile_active);
+        uint32_t run = __shfl_up_sync(FULL, x, 1);
+        if (lane == 0) run = carry;
+        uint32_t byte = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint32_t q = 8u * lane + (uint32_t)j;
+            const uint32_t before = ((f >> j) & 1u) ? kInf : run;
+            const uint32_t c = v[j];
+            run = min(before, c);
+            uint32_t fl = 0;
+            if (c == kInf) {
+                fl = a.est_strict ? 0u : (old >> j) & 1u;
+            } else if (a.theta_case == 1) {
+                fl = 1u;
+            } else if (a.theta_case == 2) {
+                fl = 0u;
+            } else if (c < before) {
+                if (before == kInf || APP == GG_APP_CC) fl = 1u;
+                else fl = ((unsigned long long)(before - c) << 32) > a.theta_fx * (unsigned long long)before ? 1u : 0u;
+            }
+            if (fl && q < rel) byte |= 1u << j;
+        }
+        uint32_t word = byte << sh;
+        word |= __shfl_xor_sync(FULL, word, 1);
+        word |= __shfl_xor_sync(FULL, word, 2);
+        if ((lane & 3u) == 0 && wi < mask_words) a.mask[wi] = word;
+        const uint32_t tile_active = __reduce_add_sync(FULL, (uint32_t)__popc(byte));
         if (lane == 0 && a.tcnt) a.tcnt[t] = tile_active;
     }
 }
@@ -859,6 +840,17 @@ __global__ void __launch_bounds__(kPullThreads) k_min_apply(PullArgs a)
     }
 }
 
+// bit v of bits: vertex v is in the frontier queue (bits cleared beforehand)
+__global__ void k_front_bits(const int32_t *__restrict__ q, const uint32_t *__restrict__ q_len,
+                             uint32_t *__restrict__ bits, int32_t n)
+{
+    const uint32_t len = *q_len;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x) {
+        const int32_t v = q[i];
+        if (v >= 0 && v < n) atomicOr(bits + (v >> 5), 1u << (v & 31));
+    }
+}
+
 }  // namespace
 
 namespace {
@@ -870,6 +862,12 @@ void launch_arcs(const PullArgs &a, uint32_t max_tiles, int num_sms, cudaStream_
     long long blocks = ((long long)max_tiles + kPullThreads / 32 - 1) / (kPullThreads / 32);
     if (blocks > (long long)num_sms * arc_blocks_per_sm) blocks = (long long)num_sms * arc_blocks_per_sm;
     if (blocks < 1) blocks = 1;
+    if constexpr (APP != GG_APP_PAGERANK) {
+        if (a.front) {
+            k_pull_arcs<APP, arc_blocks_per_sm, true, true><<<(unsigned)blocks, kPullThreads, 0, s>>>(a);
+            return;
+        }
+    }
     k_pull_arcs<APP, arc_blocks_per_sm, true><<<(unsigned)blocks, kPullThreads, 0, s>>>(a);
 }
 
@@ -915,6 +913,15 @@ cudaError_t pull_iteration(PullArgs a, bool correct, uint32_t max_tiles, int num
 
 }  // namespace
 
+cudaError_t launch_front_bits(const int32_t *q, const uint32_t *q_len, uint32_t *bits, int32_t n, int num_sms,
+                              cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(bits, 0, 4 * (((size_t)n + 31) / 32), s);
+    if (e != cudaSuccess) return e;
+    k_front_bits<<<(unsigned)(num_sms * 8), 256, 0, s>>>(q, q_len, bits, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pull(int app, const PullArgs &a, bool correct, uint32_t max_tiles, int num_sms, cudaStream_t s)
 {
     switch (app) {
@@ -955,11 +962,13 @@ gg_status ensure_pull(gg_graph *g)
         p.nzw = nzw;
         p.valid = false;
     }
-    gg_status st = g->b_pull.alloc(4 * ((size_t)g->n + 2 * tiles + 16), g->stream);
+    const size_t fwords = ((size_t)g->n + 31) / 32 + 4;
+    gg_status st = g->b_pull.alloc(4 * ((size_t)g->n + 2 * tiles + 16 + fwords), g->stream);
     if (st != GG_OK) return st;
     g->pull_acc = g->b_pull.f32();
     g->pull_lead = g->pull_acc + g->n + 4;
     g->pull_carry = g->pull_lead + tiles + 4;
+    g->pull_front = reinterpret_cast<uint32_t *>(g->pull_carry + tiles + 4);
     g->pull_ready = true;
     return GG_OK;
 }

@@ -34,10 +34,11 @@ GG_POLICY_EXACT, GG_POLICY_NONE, GG_POLICY_STATIC_SWITCH, GG_POLICY_ADAPTIVE, GG
  GG_RESULT_OUT_TO_IN, GG_RESULT_SCORES) = range(11)
 GG_DIRECTED, GG_SYMMETRIC, GG_DEVICE_PTRS = 0, 1, 2
 GG_STOP_QUIESCE, GG_EST_STRICT, GG_FORCE_PULL, GG_FORCE_PUSH, GG_TIMING = 1, 2, 4, 8, 16
-GG_INFL_SHARE, GG_RENORM = 32, 64
+GG_INFL_SHARE, GG_RENORM, GG_PULL_FILTER = 32, 64, 128
 GG_INF = 0xFFFFFFFF
 GG_ITER_PUSH = 0x100
 GG_ITER_LEARNED = 0x200
+GG_ITER_FILTER = 0x400
 
 APPS = {"pagerank": GG_APP_PAGERANK, "pr": GG_APP_PAGERANK, "sssp": GG_APP_SSSP,
         "bfs": GG_APP_BFS, "cc": GG_APP_CC, "ppr": GG_APP_PPR}

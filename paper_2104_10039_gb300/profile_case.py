@@ -34,6 +34,8 @@ def main(argv=None):
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--force-pull", action="store_true")
     ap.add_argument("--timing", action="store_true")
+    ap.add_argument("--pull-filter", action="store_true",
+                    help="min applications: pulls read frontier sources only (GG_PULL_FILTER)")
     a = ap.parse_args(argv)
 
     import graphgen
@@ -48,6 +50,7 @@ def main(argv=None):
                        gg.GG_SYMMETRIC if a.symmetric else gg.GG_DIRECTED)
     try:
         flags = (gg.GG_FORCE_PULL if a.force_pull else 0) | (gg.GG_TIMING if a.timing else 0)
+        flags |= gg.GG_PULL_FILTER if a.pull_filter else 0
         for _ in range(a.repeat):
             gg.gg_run(h, a.app, a.sigma, a.policy,
                       gg.make_params(alpha=a.alpha, theta=a.theta, max_iters=a.iters, source=src,

@@ -1,20 +1,22 @@
-"""DRAM traffic of the pull kernels from ncu captures, for bench.py's
+"""DRAM traffic of the pull kernels from ncu launch lists, for bench.py's
 roofline line.
 
-Each capture is one case run by ``profile_case`` under ``ncu`` (one launch
-of each kernel of a class: the gather, or the two correction launches). This
-tool reads the captures' raw pages (``ncu -i <rep> --page raw --csv``), sums
-dram__bytes_read.sum + dram__bytes_write.sum over the class's launches, and
-records that traffic next to the case's algorithmic bytes (the same per-unit
-model bench.py uses), together with a hash of the tile-engine sources, in
-profiles/traffic.json. bench.py scales the traffic to its own launches by
-their algorithmic bytes (traffic grows with the arcs and vertices a launch
-processes) and reports null when the kernel sources changed since.
+Each launch list is one case run by ``profile_case`` under ``ncu`` with the
+one-pass metrics dram__bytes_read.sum, dram__bytes_write.sum and
+gpu__time_duration.sum on every launch (``--csv --log-file``). This tool
+finds the class's last launch sequence in the list (a gather: k_pull_arcs,
+k_long_rows and the apply pass; a correction: k_pull_arcs, k_long_rows,
+k_carries, the flag pass and the apply pass), sums its DRAM bytes and records them next to the
+case's algorithmic bytes (the same per-unit model bench.py uses), together
+with a hash of the kernel sources, in profiles/traffic.json. bench.py scales
+the traffic to its own launches by their algorithmic bytes (traffic grows
+with the arcs and vertices a launch processes) and reports null when the
+kernel sources changed since.
 
-    python -m paper_2104_10039_gb300.profile_traffic CLASS REP N M E_NEW [CLASS REP N M E_NEW ...]
+    python -m paper_2104_10039_gb300.profile_traffic CLASS CSV N M [CLASS CSV N M ...]
 
-CLASS is app/gather or app/correct; N, M the case's vertices and arcs;
-E_NEW the arcs active after a correction (0 for a gather of all M arcs).
+CLASS is app/gather or app/correct; N, M the case's vertices and arcs (a
+gather of the full list, a correction).
 """
 from __future__ import annotations
 
@@ -23,16 +25,14 @@ import hashlib
 import json
 import os
 import re
-import subprocess
 import sys
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
-# the pull kernels (gathers and corrections of every application) and the
-# tile count kernel a correction ends with
-KERNEL_FILES = ("gg_pull.cu", "gg_sample.cu")
+# the pull kernels (gathers and corrections of every application)
+KERNEL_FILES = ("gg_pull.cu",)
 
 
 def _code(text: str) -> str:
@@ -65,39 +65,76 @@ def gather_bytes(app, n, e):
     return 8 * e + 16 * n
 
 
-def correct_bytes(app, n, m, e_new):
-    if app == "pagerank":
-        return 4 * m + 4 * e_new + m // 8 + 28 * n
-    return 8 * m + 8 * e_new + m // 4 + 20 * n
+def correct_bytes(app, n, m):
+    """A correction over all m arcs: sources (and weights) read, flags
+    written (and read: the min applications keep some), per-vertex state;
+    rebuilding the packed list is not part of it."""
+    if app == "pagerank":        # sources 4m; flags m/8; row ptr, rank, degree, rank', contrib', contrib, acc 28n
+        return 4 * m + m // 8 + 28 * n
+    return 8 * m + m // 4 + 20 * n
 
 
-def dram_bytes(rep: str) -> tuple:
-    out = subprocess.run(["ncu", "-i", rep, "--page", "raw", "--csv"], capture_output=True, text=True,
-                         check=True).stdout
-    rows = list(csv.reader(out.splitlines()))
-    hdr, units = rows[0], rows[1]
-    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
-    total, names = 0.0, []
-    for r in rows[2:]:
-        for key in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
-            i = hdr.index(key)
-            total += float(r[i].replace(",", "")) * scale[units[i]]
-        names.append(r[hdr.index("Kernel Name")])
-    return total, names
+def _launches(path: str) -> list:
+    """[(kernel name, dram bytes, ns)] in launch order from an ncu --csv log."""
+    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "ns": 1, "nsecond": 1, "us": 1e3,
+             "usecond": 1e3, "ms": 1e6, "msecond": 1e6}
+    out, hdr = {}, None
+    with open(path) as f:
+        for r in csv.reader(f):
+            if not r:
+                continue
+            if r[0] == "ID":
+                hdr = r
+                continue
+            if hdr is None:
+                continue
+            d = dict(zip(hdr, r))
+            rec = out.setdefault(int(d["ID"]), [d["Kernel Name"], 0.0, 0.0])
+            v = float(d["Metric Value"].replace(",", "")) * scale[d["Metric Unit"]]
+            if d["Metric Name"] in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+                rec[1] += v
+            elif d["Metric Name"] == "gpu__time_duration.sum":
+                rec[2] += v
+    return [tuple(out[k]) for k in sorted(out)]
+
+
+def _is(name: str, kernel: str) -> bool:
+    return re.search(r"\b%s\b" % kernel, name) is not None
+
+
+def class_window(launches: list, kind: str) -> list:
+    """The last launch sequence of a gather (kind 'gather') or a correction
+    ('correct') in the list."""
+    found = None
+    for i, (name, _, _) in enumerate(launches):
+        if not _is(name, "k_pull_arcs") or i + 2 >= len(launches) or not _is(launches[i + 1][0], "k_long_rows"):
+            continue
+        corr = _is(launches[i + 2][0], "k_carries")
+        if corr != (kind == "correct"):
+            continue
+        for j in range(i + 2, len(launches)):
+            if _is(launches[j][0], r"k_(pr|min)_apply"):
+                found = launches[i:j + 1]
+                break
+    if found is None:
+        raise SystemExit(f"no {kind} launch sequence in the list")
+    return found
 
 
 def main(argv):
-    if len(argv) % 5 or not argv:
+    if len(argv) % 4 or not argv:
         raise SystemExit(__doc__)
     rec = {"kernel_hash": kernel_hash(), "classes": {}}
-    for i in range(0, len(argv), 5):
-        cls, rep, n, m, e_new = argv[i], argv[i + 1], int(argv[i + 2]), int(argv[i + 3]), int(argv[i + 4])
+    for i in range(0, len(argv), 4):
+        cls, path, n, m = argv[i], argv[i + 1], int(argv[i + 2]), int(argv[i + 3])
         app, kind = cls.split("/")
-        algo = gather_bytes(app, n, m) if kind == "gather" else correct_bytes(app, n, m, e_new)
-        dram, names = dram_bytes(rep)
+        algo = gather_bytes(app, n, m) if kind == "gather" else correct_bytes(app, n, m)
+        win = class_window(_launches(path), kind)
+        dram = sum(x[1] for x in win)
         rec["classes"][cls] = {"dram_bytes": int(dram), "algorithmic_bytes": int(algo),
-                               "ratio": round(dram / algo, 4), "kernels": names,
-                               "capture": os.path.basename(rep), "vertices": n, "arcs": m}
+                               "ratio": round(dram / algo, 4), "us": round(sum(x[2] for x in win) / 1e3, 1),
+                               "kernels": [re.sub(r"\(.*", "", x[0]) for x in win],
+                               "capture": os.path.basename(path), "vertices": n, "arcs": m}
     with open(TRAFFIC, "w") as f:
         json.dump(rec, f, indent=1)
     print(json.dumps(rec, indent=1))

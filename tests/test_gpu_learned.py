@@ -151,6 +151,19 @@ def test_trace_min_apps_bit_exact(gg, torch, app):
         assert np.array_equal(X, ref["trace_x"]) and np.array_equal(Y, ref["trace_y"])
 
 
+@pytest.mark.parametrize("app", ["sssp", "bfs"])
+def test_trace_consecutive_corrections(gg, torch, app):
+    """alpha 0: every iteration is a correction, so each one's features read
+    the flags (active in-degrees) that the previous correction left."""
+    g = _graphs()[0]
+    s = int(graphgen.sources(g, 1, seed=2)[0])
+    X, Y = _trace(gg, torch, g, app, T=6, alpha=0, s=s)
+    ref = oracle.run(g.n, g.rowptr, g.colidx, g.weights, app=app, policy="gg", sigma=0.5, seed=3, alpha=0,
+                     theta=0.1, source=s, max_iters=6, trace_cap=len(X) + g.n)
+    assert len(X) == len(ref["trace_x"]) > g.n
+    assert np.array_equal(X, ref["trace_x"]) and np.array_equal(Y, ref["trace_y"])
+
+
 def test_trace_push_frontier_keeps_the_change_features(gg, torch):
     g = _graphs()[0]
     s = int(graphgen.sources(g, 1, seed=2)[0])
@@ -206,7 +219,7 @@ def _gpu_learned(gg, h, g, app, P, T, alpha, theta, sigma, s, flags=0, tau=0.0, 
 
 
 @pytest.mark.parametrize("app", ["sssp", "bfs", "cc"])
-@pytest.mark.parametrize("flags", [0, 4, 8])
+@pytest.mark.parametrize("flags", [0, 4, 8, 4 | 128])   # auto, pull, push, pull of frontier sources only
 def test_learned_min_apps_bit_exact(gg, app, flags):
     graphs = _sym_graphs() if app == "cc" else _graphs()
     for g in graphs:

@@ -87,6 +87,44 @@ def test_sampler_bit_exact(gg, sigma):
             gg.gg_free_graph(h)
 
 
+def _check_packed(gg, h, g, mask):
+    """The library's packed active in-edges equal the packing of `mask`."""
+    ip, isrc, _, _ = oracle.csc_from_csr(g.n, g.rowptr, g.colidx, g.weights)
+    sp_ptr = gg.result_array(h, gg.GG_RESULT_SPARSE_PTR)
+    sp_src = gg.result_array(h, gg.GG_RESULT_SPARSE_SRC)
+    cs = np.concatenate([[0], np.cumsum(mask.astype(np.int64))])
+    assert np.array_equal(sp_ptr, cs[ip])
+    assert np.array_equal(sp_src, isrc[mask.astype(bool)])
+
+
+@pytest.mark.parametrize("app", ["pagerank", "sssp"])
+def test_packed_list_built_when_needed(gg, app):
+    """The packed list after a correction (or a sampling) is built when a
+    gather or a result needs it: runs that end on a correction, or whose
+    approximate iterations all push, still give the packing of the final flags
+    and the right active-arc count."""
+    g = graphgen.rmat(12, seed=1)
+    graphgen.add_weights(g, seed=11)
+    s = int(graphgen.sources(g, 1, seed=2)[0])
+    h = gc.load(gg, g)
+    try:
+        for T, flags in ((3, 0), (6, 0), (7, 8), (11, 4)):   # 8: GG_FORCE_PUSH, 4: GG_FORCE_PULL
+            if app == "pagerank" and flags:
+                continue
+            p = gg.make_params(alpha=2, theta=0.05, max_iters=T, source=s, seed=13, flags=flags)
+            gg.gg_run(h, app, 0.5, "gg", p)
+            mask = gg.mask_bits(h, g.m)
+            _check_packed(gg, h, g, mask)
+            it = gg.result_array(h, gg.GG_RESULT_ITER_STATS)
+            corr = np.flatnonzero((it["mode"] & 3) == 2)
+            if len(corr):
+                assert int(it["active_after"][corr[-1]]) == int(mask.sum()), (T, flags)
+        gg.gg_sample_edges(h, 0.3, 77)
+        _check_packed(gg, h, g, gg.mask_bits(h, g.m))
+    finally:
+        gg.gg_free_graph(h)
+
+
 # ------------------------------------------------------------- pagerank --
 
 @pytest.mark.parametrize("T", [1, 3, 20])
@@ -150,7 +188,11 @@ MIN_CASES = [("exact", 4, 0.05, 1.0), ("sp", 4, 0.05, 0.3), ("sms", 2, 0.2, 0.5)
              ("gg", 2, 1.5, 0.6)]
 
 
-@pytest.mark.parametrize("flags", [0, 4, 8])   # auto, GG_FORCE_PULL, GG_FORCE_PUSH
+# auto, GG_FORCE_PULL, GG_FORCE_PUSH, pull reading frontier sources only (GG_PULL_FILTER)
+DIR_FLAGS = [0, 4, 8, 4 | 128]
+
+
+@pytest.mark.parametrize("flags", DIR_FLAGS)
 @pytest.mark.parametrize("app", ["sssp", "bfs"])
 def test_traversal_bit_exact(gg, app, flags):
     for g in _graphs():
@@ -174,7 +216,7 @@ def test_traversal_bit_exact(gg, app, flags):
             gg.gg_free_graph(h)
 
 
-@pytest.mark.parametrize("flags", [0, 4, 8])
+@pytest.mark.parametrize("flags", DIR_FLAGS)
 def test_cc_bit_exact(gg, flags):
     for g in _sym_graphs():
         h = gc.load(gg, g)
@@ -190,6 +232,39 @@ def test_cc_bit_exact(gg, flags):
                 assert st.iterations == ref["iterations"]
         finally:
             gg.gg_free_graph(h)
+
+
+@pytest.mark.parametrize("app", ["sssp", "bfs", "cc"])
+def test_filtered_pull_marks_its_gathers(gg, app):
+    """GG_PULL_FILTER: every pull gather reads frontier sources only (mode bit
+    GG_ITER_FILTER), corrections never do; values, flags and per-iteration
+    change counts equal the unfiltered pull's and the oracle's."""
+    g = graphgen.rmat(14, seed=5, symmetric=app == "cc")
+    graphgen.add_weights(g, seed=11)
+    s = int(graphgen.sources(g, 1, seed=2)[0]) if app != "cc" else 0
+    h = gc.load(gg, g)
+    try:
+        runs = {}
+        for fl in (4 | 128, 4):
+            p = gg.make_params(alpha=2, theta=0.05, max_iters=100000, source=s, seed=9, flags=fl)
+            gg.gg_run(h, app, 0.4, "gg", p)
+            runs[fl] = (gg.values(h, app), gg.mask_bits(h, g.m), gg.result_array(h, gg.GG_RESULT_ITER_STATS))
+        ref = oracle.run(g.n, g.rowptr, g.colidx, g.weights, app=app, policy="gg", sigma=0.4, seed=9, alpha=2,
+                         theta=0.05, max_iters=100000, source=s, symmetric=app == "cc")
+        for fl, (vals, mask, it) in runs.items():
+            assert np.array_equal(vals, ref["values"]), fl
+            assert np.array_equal(mask, ref["mask"]), fl
+            kinds = it["mode"] & 3
+            filt = (it["mode"] & gg.GG_ITER_FILTER) != 0
+            if fl & 128:
+                assert np.all(filt[kinds < 2]) and not np.any(filt[kinds == 2])
+                assert np.any(kinds == 2) and np.any(kinds < 2)
+            else:
+                assert not np.any(filt)
+        a, b = runs[4 | 128][2], runs[4][2]
+        assert np.array_equal(a["changed"], b["changed"]) and np.array_equal(a["arcs"], b["arcs"])
+    finally:
+        gg.gg_free_graph(h)
 
 
 def test_est_strict_and_iteration_cap(gg):
