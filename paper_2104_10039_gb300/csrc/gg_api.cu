@@ -225,7 +225,7 @@ static gg_status ensure_iter_cap(gg_graph *g, uint32_t iters)
 // Active out-degrees of the current flags (GG_RENORM).
 static gg_status refresh_active_outdeg(gg_graph *g)
 {
-    gg_status st = ensure_packed(g, false);
+    gg_status st = ensure_packed(g, false, PACK_HUBS);   // PageRank's coding
     if (st != GG_OK) return st;
     GG_CUDA(launch_active_outdeg(g->sp_src, g->sp_nnz, (uint32_t)g->m, g->n, g->hub_ids, g->act_outdeg, g->num_sms,
                                  g->stream));
@@ -307,7 +307,8 @@ static gg_status trace_features(gg_graph *g, gg_app app, uint32_t i, bool *traci
 {
     *tracing = g->trace_x && g->trace_rows + (uint64_t)g->n <= g->trace_cap;
     if (!*tracing) return GG_OK;
-    gg_status st = ensure_packed(g, false);   // the active in-degree feature
+    // the active in-degree feature (coded as the application's gathers read it)
+    gg_status st = ensure_packed(g, false, app == GG_APP_PAGERANK ? PACK_HUBS : PACK_PLAIN);
     if (st != GG_OK) return st;
     GG_CUDA(launch_trace_features(feat_args(g, app, i), g->trace_x + g->trace_rows * 8, g->num_sms, g->stream));
     g->launches += 1;
@@ -333,7 +334,8 @@ static gg_status learned_select(gg_graph *g, gg_app app, const gg_params *p, uin
                                 uint32_t *nsel, uint32_t *total)
 {
     *learned = false;
-    gg_status st = ensure_packed(g, false);   // the active in-degree feature
+    // the active in-degree feature (coded as the application's gathers read it)
+    gg_status st = ensure_packed(g, false, app == GG_APP_PAGERANK ? PACK_HUBS : PACK_PLAIN);
     if (st != GG_OK) return st;
     GG_CUDA(launch_mlp_select(feat_args(g, app, i), g->mlp, p->select_logit, p->select_cost, g->sel_flag,
                               g->sel_off, g->logits, g->num_sms, g->stream));
@@ -394,21 +396,32 @@ static gg_status learned_correct(gg_graph *g, gg_app app, TileArgs a, uint32_t n
     return GG_OK;
 }
 
+// Kernels one pull iteration launches: the hubs' values (when the graph has
+// hubs), the arcs, the long rows, (a correction's carries and flags,) the
+// apply.
+static int pull_launches(const gg_graph *g, bool correct, bool pr)
+{
+    return (correct ? 5 : 3) + (pr && g->n_hubs > 0 ? 1 : 0);
+}
+
 // Arguments of the pull path over the full in-edge list (which 0) or the
 // packed active list (1), from the iteration's tile arguments; builds the
 // list's plan if it is not current (and, on the graph's first pull, the
 // plans' and row sums' buffers).
-static gg_status pull_args(gg_graph *g, int which, const TileArgs &a, PullArgs *pa)
+static gg_status pull_args(gg_graph *g, int which, bool pagerank, const TileArgs &a, PullArgs *pa)
 {
     gg_status st = ensure_pull(g);   // plans and row-sum buffers (first pull on this graph)
-    if (st == GG_OK && which == 1) st = sp_plain(g);
     if (st != GG_OK) return st;
     if (!g->plan[which].valid) {
         st = build_pull_plan(g, which);
         if (st != GG_OK) return st;
     }
     const PullPlan &pl = g->plan[which];
-    pa->src = which ? g->sp_src : g->in_src;
+    // PageRank reads hub-coded sources (the packed list was built to match)
+    pa->src = which ? g->sp_src : (pagerank ? g->in_src_h : g->in_src);
+    pa->hub_ids = g->hub_ids;
+    pa->n_hubs = pagerank ? g->n_hubs : 0;
+    pa->hubv = g->pull_hubv;
     pa->row_ptr = which ? g->sp_ptr : g->in_ptr;
     pa->nnz = which ? g->sp_nnz : g->full_nnz;
     pa->hb = pl.hb;
@@ -469,7 +482,7 @@ static gg_status run_pagerank(gg_graph *g, gg_policy policy, const gg_params *p)
         // the next iteration gathers active arcs only: renormalised contributions
         a.deg_apply = (renorm && next == MODE_APPROX && kind != K_CORRECT) ? g->act_outdeg : nullptr;
         if (mode == MODE_APPROX) {
-            gg_status st = ensure_packed(g, false);
+            gg_status st = ensure_packed(g, false, PACK_HUBS);
             if (st != GG_OK) return st;
         }
         fill_list(g, mode == MODE_APPROX, a);
@@ -515,13 +528,13 @@ static gg_status run_pagerank(gg_graph *g, gg_policy policy, const gg_params *p)
                 // pull path: gathers over either list, corrections over the full one
                 const int which = mode == MODE_APPROX ? 1 : 0;
                 PullArgs pa{};
-                gg_status st = pull_args(g, which, a, &pa);
+                gg_status st = pull_args(g, which, true, a, &pa);
                 if (st != GG_OK) return st;
                 timed_begin(g, timing, kind == K_CORRECT ? 1 : 0, &slot);
                 if (kind == K_GATHER) {
                     GG_CUDA(launch_pull(GG_APP_PAGERANK, pa, false, (uint32_t)g->plan[which].tiles, g->num_sms,
                                         g->stream));
-                    g->launches += 2;
+                    g->launches += pull_launches(g, false, true);
                 } else {
                     pa.vals = reinterpret_cast<float *>(g->stash);
                     pa.mask = g->mask;
@@ -529,7 +542,7 @@ static gg_status run_pagerank(gg_graph *g, gg_policy policy, const gg_params *p)
                     pa.theta = p->theta;
                     GG_CUDA(launch_pull(GG_APP_PAGERANK, pa, true, (uint32_t)g->plan[which].tiles, g->num_sms,
                                         g->stream));
-                    g->launches += 5;
+                    g->launches += pull_launches(g, true, true);
                     counted = true;
                 }
                 timed_end(g, slot);
@@ -694,7 +707,7 @@ static gg_status run_min(gg_graph *g, gg_app app, gg_policy policy, const gg_par
             const int kind = mode == MODE_CORRECTION ? K_CORRECT : K_GATHER;
             TileArgs a{};
             if (mode == MODE_APPROX) {
-                st = ensure_packed(g, app == GG_APP_SSSP && g->has_w);
+                st = ensure_packed(g, app == GG_APP_SSSP && g->has_w, PACK_PLAIN);
                 if (st != GG_OK) return st;
             }
             fill_list(g, mode == MODE_APPROX, a);
@@ -742,7 +755,7 @@ static gg_status run_min(gg_graph *g, gg_app app, gg_policy policy, const gg_par
                                            g->stream));
                 const int which = mode == MODE_APPROX ? 1 : 0;
                 PullArgs pa{};
-                st = pull_args(g, which, a, &pa);
+                st = pull_args(g, which, false, a, &pa);
                 if (st != GG_OK) return st;
                 pa.w = (app == GG_APP_SSSP && g->has_w) ? (which ? g->sp_w : g->in_w) : nullptr;
                 timed_begin(g, timing, kind == K_CORRECT ? 1 : 0, &slot);
@@ -762,7 +775,7 @@ static gg_status run_min(gg_graph *g, gg_app app, gg_policy policy, const gg_par
                 GG_CUDA(launch_pull((int)app, pa, kind == K_CORRECT, (uint32_t)g->plan[which].tiles, g->num_sms,
                                     g->stream));
                 timed_end(g, slot);
-                g->launches += kind == K_CORRECT ? 5 : 3;
+                g->launches += pull_launches(g, kind == K_CORRECT, false);
                 if (tracing) {
                     st = trace_labels(g, false);
                     if (st != GG_OK) return st;
@@ -908,7 +921,7 @@ static gg_status alloc_graph(gg_graph *g)
     GG_ALLOC(g->b_in_ptr, 4 * (n + 1));
     GG_ALLOC(g->b_in_src, 4 * m);
     GG_ALLOC(g->b_in_dst, 4 * m);
-    GG_ALLOC(g->b_hub, 4 * (m + n + (size_t)kHubs + 4));
+    GG_ALLOC(g->b_hub, 4 * (m + n + (size_t)kHubCodes + 4));
     GG_ALLOC(g->b_out_to_in, 4 * m);
     GG_ALLOC(g->b_sp_ptr, 4 * (n + 1));
     GG_ALLOC(g->b_sp_src, 4 * m);
@@ -1112,13 +1125,13 @@ static gg_status result_size(gg_graph *g, gg_result_kind kind, const void **src,
         break;
     case GG_RESULT_SPARSE_PTR:
         if (!g->sampled) break;
-        if (ensure_packed(g, false) != GG_OK) return GG_ERR_CUDA;
+        if (ensure_packed(g, false, PACK_ANY) != GG_OK) return GG_ERR_CUDA;
         *src = g->sp_ptr;
         *bytes = 4 * (n + 1);
         break;
     case GG_RESULT_SPARSE_SRC:
         if (!g->sampled) break;
-        if (ensure_packed(g, false) != GG_OK) return GG_ERR_CUDA;
+        if (ensure_packed(g, false, PACK_ANY) != GG_OK) return GG_ERR_CUDA;
         GG_CUDA(cudaMemcpyAsync(&g->sp_nnz_host, g->sp_nnz, 4, cudaMemcpyDeviceToHost, g->stream));
         GG_CUDA(cudaStreamSynchronize(g->stream));
         *src = g->sp_src;

@@ -494,10 +494,9 @@ gg_status build_csc(gg_graph *g)
 
 // ------------------------------------------------------------ hub cache ----
 // The sources read most often by pull gathers are the vertices with the most
-// out-arcs: the (at most kHubs) vertices with out-degree >= T, T the smallest
-// threshold that admits no more than kHubs of them (and at least 2), get a
-// slot; the last pass of the in-edge sort codes their in-arcs as -(slot + 1)
-// in in_src_h, so the slots are chosen before the sort.
+// out-arcs. They get slots (build_hubs), and the last pass of the in-edge sort
+// codes their in-arcs as -(slot + 1) in in_src_h, so the slots are chosen
+// before the sort.
 constexpr uint32_t kDegBins = 65536;
 
 // Out-degree histogram (degrees clamped to kDegBins - 1); the many small
@@ -520,51 +519,66 @@ __global__ void k_deg_hist(const int32_t *__restrict__ out_ptr, int32_t n, uint3
         if (low[i]) atomicAdd(&hist[i], low[i]);
 }
 
-__global__ void k_hub_flag(const int32_t *__restrict__ out_ptr, int32_t n, int32_t thr, uint32_t *__restrict__ flag)
-{
-    for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-        flag[v] = (out_ptr[v + 1] - out_ptr[v]) >= thr ? 1u : 0u;
-}
-
-__global__ void k_hub_fill(int32_t n, const uint32_t *__restrict__ flag, const uint32_t *__restrict__ pos,
-                           int32_t *__restrict__ hub_slot, int32_t *__restrict__ hub_ids)
+// Tier of each vertex: 1 (out-degree >= thr1), 2 (thr2 <= out-degree < thr1)
+// or none.
+__global__ void k_hub_flag(const int32_t *__restrict__ out_ptr, int32_t n, int32_t thr1, int32_t thr2,
+                           uint32_t *__restrict__ flag1, uint32_t *__restrict__ flag2)
 {
     for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        if (flag[v]) {
-            hub_slot[v] = (int32_t)pos[v];
-            hub_ids[pos[v]] = v;
-        } else {
-            hub_slot[v] = -1;
-        }
+        const int32_t d = out_ptr[v + 1] - out_ptr[v];
+        flag1[v] = d >= thr1 ? 1u : 0u;
+        flag2[v] = (d >= thr2 && d < thr1) ? 1u : 0u;
     }
 }
 
+// Slots: tier 1 in vertex order, then tier 2 in vertex order.
+__global__ void k_hub_fill(int32_t n, const uint32_t *__restrict__ flag1, const uint32_t *__restrict__ pos1,
+                           const uint32_t *__restrict__ flag2, const uint32_t *__restrict__ pos2, uint32_t n1,
+                           int32_t *__restrict__ hub_slot, int32_t *__restrict__ hub_ids)
+{
+    for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        int32_t slot = -1;
+        if (flag1[v]) slot = (int32_t)pos1[v];
+        else if (flag2[v]) slot = (int32_t)(n1 + pos2[v]);
+        hub_slot[v] = slot;
+        if (slot >= 0) hub_ids[slot] = v;
+    }
+}
+
+// The hubs: with out-degree >= T1 (the smallest threshold, at least 2, that
+// admits no more than kHubs vertices) the first tier; with T2 <= out-degree
+// < T1 (T2 the same for kHubCodes) the second.
 gg_status build_hubs(gg_graph *g)
 {
     cudaStream_t s = g->stream;
     const int32_t n = g->n;
     const int grid = g->num_sms * 8;
     DevBuf tmp;
-    gg_status st = tmp.alloc(4 * ((size_t)kDegBins + 2 * ((size_t)n + 1)), s);
+    gg_status st = tmp.alloc(4 * ((size_t)kDegBins + 4 * ((size_t)n + 1)), s);
     if (st != GG_OK) return st;
-    uint32_t *hist = tmp.u32(), *flag = hist + kDegBins, *pos = flag + n + 1;
+    uint32_t *hist = tmp.u32(), *flag1 = hist + kDegBins, *pos1 = flag1 + n + 1, *flag2 = pos1 + n + 1,
+             *pos2 = flag2 + n + 1;
     GG_CUDA(cudaMemsetAsync(hist, 0, 4 * (size_t)kDegBins, s));
     k_deg_hist<<<grid, 256, 0, s>>>(g->out_ptr, n, hist);
     std::vector<uint32_t> h(kDegBins);
     GG_CUDA(cudaMemcpyAsync(h.data(), hist, 4 * (size_t)kDegBins, cudaMemcpyDeviceToHost, s));
     GG_CUDA(cudaStreamSynchronize(s));
-    uint64_t above = 0;
-    int32_t thr = (int32_t)kDegBins;   // no hub
+    uint64_t above = 0, n1 = 0;
+    int32_t thr1 = 0x7FFFFFFF, thr2 = 0x7FFFFFFF;   // no hub
+    bool tier1 = true;
     for (int32_t d = (int32_t)kDegBins - 1; d >= 2; --d) {
-        if (above + h[d] > (uint64_t)kHubs) break;
+        if (tier1 && above + h[d] > (uint64_t)kHubs) tier1 = false;
+        if (above + h[d] > (uint64_t)kHubCodes) break;
         above += h[d];
-        thr = d;
+        thr2 = d;
+        if (tier1) { thr1 = d; n1 = above; }
     }
-    k_hub_flag<<<grid, 256, 0, s>>>(g->out_ptr, n, thr, flag);
-    GG_CUDA(launch_scan_u32(flag, pos, (size_t)n, g->scan_tmp, s));
-    k_hub_fill<<<grid, 256, 0, s>>>(n, flag, pos, g->hub_slot, g->hub_ids);
+    k_hub_flag<<<grid, 256, 0, s>>>(g->out_ptr, n, thr1, thr2, flag1, flag2);
+    GG_CUDA(launch_scan_u32(flag1, pos1, (size_t)n, g->scan_tmp, s));
+    GG_CUDA(launch_scan_u32(flag2, pos2, (size_t)n, g->scan_tmp, s));
+    k_hub_fill<<<grid, 256, 0, s>>>(n, flag1, pos1, flag2, pos2, (uint32_t)n1, g->hub_slot, g->hub_ids);
     g->n_hubs = (int32_t)above;
-    g->load_launches += 7;
+    g->load_launches += 10;
     GG_CUDA(cudaGetLastError());
     GG_CUDA(cudaStreamSynchronize(s));
     return GG_OK;

@@ -54,8 +54,8 @@ k_arcs(TileArgs a)
     ArcSmem<APP, KIND> &s = smem[threadIdx.x >> 5];
     // hub cache: the values of the most-read sources, one copy per block
     __shared__ uint32_t s_hub[kHubs];
+    const int nh = a.n_hubs < kHubs ? a.n_hubs : kHubs;   // slots past these are read from global memory
     {
-        const int nh = a.n_hubs < kHubs ? a.n_hubs : kHubs;
         for (int j = (int)threadIdx.x; j < nh; j += kThreads) {
             const int32_t v = a.hub_ids[j];
             if constexpr (APP == GG_APP_PAGERANK) s_hub[j] = __float_as_uint(__ldg(a.contrib_cur + v));
@@ -112,10 +112,12 @@ k_arcs(TileArgs a)
         for (int i = 0; i < kIPT; ++i) {
             const int k = (int)lane + 32 * i;
             const int32_t sv = src_cur[i];   // a hub is coded -(slot + 1)
+            const int32_t hs = -sv - 1;
+            const int32_t u = (sv < 0 && hs >= nh) ? __ldg(a.hub_ids + hs) : sv;
             if constexpr (APP == GG_APP_PAGERANK)
-                gv[i] = k < narcs ? (sv < 0 ? s_hub[-sv - 1] : __float_as_uint(__ldg(a.contrib_cur + sv))) : 0u;
+                gv[i] = k < narcs ? (u < 0 ? s_hub[hs] : __float_as_uint(__ldg(a.contrib_cur + u))) : 0u;
             else
-                gv[i] = k < narcs ? (sv < 0 ? s_hub[-sv - 1] : __ldg(a.val_cur + sv)) : kInf;
+                gv[i] = k < narcs ? (u < 0 ? s_hub[hs] : __ldg(a.val_cur + u)) : kInf;
         }
         if (lane < kWT / 32 + 2) s.head[lane] = 0u;
         __syncwarp();

@@ -176,10 +176,11 @@ struct gg_graph {
     gg::DevBuf b_pull;
     float *pull_acc = nullptr, *pull_lead = nullptr, *pull_carry = nullptr;
     uint32_t *pull_front = nullptr;   // frontier bitmap of a filtered pull (n bits)
+    uint32_t *pull_hubv = nullptr;    // hub slots' values for the pull gathers (kHubCodes)
     bool pull_ready = false;
-    bool sp_is_plain = false;
     bool sp_stale = false;     // the mask's tile counts are scanned, the packed list not yet built
     bool sp_has_w = false;     // the packed list carries the weights
+    bool sp_hubs = false;      // ... and hub-coded sources
     // training trace (caller-owned device buffers)
     float *trace_x = nullptr;
     uint8_t *trace_y = nullptr;
@@ -199,12 +200,14 @@ gg_status sample_edges(gg_graph *g, double ratio, uint64_t seed);
 // the packed list's arc count (and stats->active_after) are then set. The
 // list itself is built by ensure_packed.
 gg_status pack_active(gg_graph *g, IterStatsDev *stats, bool have_counts);
-// Builds the packed list of the current flags if it is not built yet, or
-// lacks the weights a caller needs (weighted).
-gg_status ensure_packed(gg_graph *g, bool weighted);
+// Source coding of the packed list: vertex ids, hubs coded -(slot + 1) (the
+// PageRank pull gathers), or whichever it has.
+enum PackCoding { PACK_PLAIN = 0, PACK_HUBS = 1, PACK_ANY = 2 };
+// Builds the packed list of the current flags if it is not built yet, lacks
+// the weights a caller needs (weighted) or has another source coding.
+gg_status ensure_packed(gg_graph *g, bool weighted, PackCoding coding);
 gg_status run(gg_graph *g, gg_app app, double ratio, gg_policy policy, const gg_params *p);
 uint32_t next_epoch(gg_graph *g);
 gg_status ensure_pull(gg_graph *g);
 gg_status build_pull_plan(gg_graph *g, int which);
-gg_status sp_plain(gg_graph *g);
 }  // namespace gg

@@ -19,10 +19,14 @@ constexpr int kWT = 32 * kIPT;
 constexpr int kTile = kThreads * kIPT;   // push-frontier tiles (block-wide)
 constexpr int kWarps = kThreads / 32;
 constexpr uint32_t kInf = 0xFFFFFFFFu;
-// Hub cache: the values of the (at most) kHubs sources with the most
-// out-arcs sit in each gathering block's shared memory; the gathers' source
-// list codes such a source as -(slot + 1).
-constexpr int kHubs = 3072;   // 12 KB: 4 blocks of the gather still fit an SM
+// Hub coding: the (at most) kHubCodes sources with the most out-arcs are
+// coded -(slot + 1) in in_src_h, slots in two tiers (the kHubs with the most
+// out-arcs first). The PageRank pull gathers read a hub's contribution from
+// a dense per-launch copy (64 KB, L1-resident); the merge-path kernels keep
+// the first kHubs slots in each block's shared memory. The pull gathers of
+// SSSP / BFS / CC read plain ids: with the hub copy they ran slower.
+constexpr int kHubs = 3072;   // 12 KB: 4 blocks of the merge-path gather still fit an SM
+constexpr int kHubCodes = 16384;
 
 // Device error flags (the graph's error word; k_validate sets them).
 enum DevErr : uint32_t {
@@ -121,7 +125,7 @@ enum TileKind { K_GATHER = 0, K_CORRECT = 1, K_STASH = 2 };
 // The PageRank pull path (gg_pull.cu): a list (sources as vertex ids), its
 // plan, and the vertex state of one iteration.
 struct PullArgs {
-    const int32_t *src;         // list arcs: source vertex (no hub coding)
+    const int32_t *src;         // list arcs: source vertex (PageRank: hubs coded -(slot + 1))
     const int32_t *row_ptr;     // list row pointers (n + 1)
     const uint32_t *nnz;        // device scalar: arcs in the list
     const uint32_t *hb;         // plan: row-start bit per arc
@@ -144,6 +148,9 @@ struct PullArgs {
     const uint32_t *w;          // SSSP: list arcs' weights, or nullptr (weight 1)
     const uint32_t *front;      // SSSP / BFS / CC gathers: bitmap of the frontier (bit v: v changed in the
                                 // previous iteration); only its vertices' arcs are read. nullptr: every arc
+    const int32_t *hub_ids;     // PageRank: vertex of each hub slot (sources coded -(slot + 1) in src)
+    int32_t n_hubs;
+    uint32_t *hubv;             // ... the contribution of each hub slot (k_hub_values, per launch)
     const uint32_t *val_cur;    // SSSP / BFS / CC values
     uint32_t *val_next;
     int32_t *q_out;             // SSSP / BFS / CC: next frontier (vertex, value), length

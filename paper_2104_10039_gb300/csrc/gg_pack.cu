@@ -161,8 +161,9 @@ __global__ void k_pack_total(const uint32_t *__restrict__ off, long long nt, uin
 }
 
 // The packed arcs and row pointers from the scanned tile counts.
-gg_status pack_lists(gg_graph *g, bool weighted, IterStatsDev *stats)
+gg_status pack_lists(gg_graph *g, bool weighted, bool hubs, IterStatsDev *stats)
 {
+    const int32_t *src = hubs ? g->in_src_h : g->in_src;
     cudaStream_t s = g->stream;
     const long long m = g->m;
     const long long nt = (m + kPT - 1) / kPT;
@@ -171,10 +172,10 @@ gg_status pack_lists(gg_graph *g, bool weighted, IterStatsDev *stats)
     if (ab < 1) ab = 1;
     if (nt > 0) {
         if (weighted) {
-            k_pack_arcs<true><<<(unsigned)ab, 256, 0, s>>>(g->mask, m, g->tile_off, g->in_src, g->in_w, g->sp_src,
+            k_pack_arcs<true><<<(unsigned)ab, 256, 0, s>>>(g->mask, m, g->tile_off, src, g->in_w, g->sp_src,
                                                            g->sp_w);
         } else {
-            k_pack_arcs<false><<<(unsigned)ab, 256, 0, s>>>(g->mask, m, g->tile_off, g->in_src, nullptr, g->sp_src,
+            k_pack_arcs<false><<<(unsigned)ab, 256, 0, s>>>(g->mask, m, g->tile_off, src, nullptr, g->sp_src,
                                                             nullptr);
         }
         GG_CUDA(cudaGetLastError());
@@ -186,7 +187,8 @@ gg_status pack_lists(gg_graph *g, bool weighted, IterStatsDev *stats)
     GG_CUDA(cudaGetLastError());
     g->launches += 1;
     g->sp_stale = false;
-    g->sp_is_plain = true;
+    g->sp_has_w = weighted;
+    g->sp_hubs = hubs;
     g->plan[1].valid = false;
     return GG_OK;
 }
@@ -217,13 +219,12 @@ gg_status pack_active(gg_graph *g, IterStatsDev *stats, bool have_counts)
 
 // tile_off holds the scan of the current flags' tile counts: pack_active
 // runs after every change of the flags, and nothing else writes it.
-gg_status ensure_packed(gg_graph *g, bool weighted)
+gg_status ensure_packed(gg_graph *g, bool weighted, PackCoding coding)
 {
     weighted = weighted && g->has_w;
-    if (!g->sp_stale && (g->sp_has_w || !weighted)) return GG_OK;
-    gg_status st = pack_lists(g, weighted, nullptr);
-    if (st == GG_OK) g->sp_has_w = weighted;
-    return st;
+    const bool hubs = coding == PACK_ANY ? (g->sp_stale ? false : g->sp_hubs) : coding == PACK_HUBS;
+    if (!g->sp_stale && (g->sp_has_w || !weighted) && g->sp_hubs == hubs) return GG_OK;
+    return pack_lists(g, weighted, hubs, nullptr);
 }
 
 }  // namespace gg

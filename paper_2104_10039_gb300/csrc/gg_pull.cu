@@ -54,6 +54,7 @@ namespace {
 
 constexpr int kPT = 256;          // arcs per pull tile
 constexpr int kPullThreads = 256;
+constexpr int32_t kNoArc = (int32_t)0x80000000;   // a lane's position past the list's end
 // A row whose arcs reach more than kLongTiles tiles past the tile of its
 // first arc is "long": one block completes its sum and its tiles' carries
 // (k_long_rows); shorter rows fold at most kLongTiles leading parts inline.
@@ -95,16 +96,6 @@ __global__ void k_plan_heads(const int32_t *__restrict__ ptr, int32_t n, const u
             trow[t] = k;
             topen[t] = make_int2((int32_t)v, t0 | (is_long ? (int32_t)0x80000000 : 0));
         }
-    }
-}
-
-// Hub-coded sources of a packed list back to vertex ids, in place.
-__global__ void k_decode_inplace(int32_t *src, const uint32_t *count, const int32_t *__restrict__ hub_ids)
-{
-    const uint32_t c = *count;
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < c; k += gridDim.x * blockDim.x) {
-        const int32_t v = src[k];
-        if (v < 0) src[k] = hub_ids[-v - 1];
     }
 }
 
@@ -152,7 +143,8 @@ struct PullOp<GG_APP_PAGERANK> {
     static __device__ __forceinline__ T op(T x, T y) { return x + y; }
     static __device__ __forceinline__ T cand(const PullArgs &a, int32_t src, uint32_t)
     {
-        return __ldg(a.contrib + src);
+        // one load: a hub's contribution from the dense hub copy, any other from the vector
+        return __ldg(src < 0 ? reinterpret_cast<const float *>(a.hubv) + (-src - 1) : a.contrib + src);
     }
 };
 
@@ -207,8 +199,8 @@ __global__ void __launch_bounds__(kPullThreads, MINB) k_pull_arcs(PullArgs a)
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const uint32_t q = 4u * lane + (uint32_t)j;
-                s[j] = q < rel ? a.src[a0 + q] : -1;
-                s[4 + j] = q + 128u < rel ? a.src[a0 + 128 + q] : -1;
+                s[j] = q < rel ? a.src[a0 + q] : kNoArc;
+                s[4 + j] = q + 128u < rel ? a.src[a0 + 128 + q] : kNoArc;
                 if constexpr (kW) {
                     w[j] = (has_w && q < rel) ? a.w[a0 + q] : 1u;
                     w[4 + j] = (has_w && q + 128u < rel) ? a.w[a0 + 128 + q] : 1u;
@@ -221,13 +213,13 @@ __global__ void __launch_bounds__(kPullThreads, MINB) k_pull_arcs(PullArgs a)
             // value was taken in when it last changed
             uint32_t fw[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) fw[i] = s[i] >= 0 ? __ldg(a.front + (s[i] >> 5)) : 0u;
-#pragma unroll
             for (int i = 0; i < 8; ++i)
-                v[i] = ((fw[i] >> (s[i] & 31)) & 1u) ? Op::cand(a, s[i], kW ? w[kW ? i : 0] : 1u) : Op::id();
+                fw[i] = s[i] != kNoArc ? (__ldg(a.front + (s[i] >> 5)) >> (s[i] & 31)) & 1u : 0u;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[i] = fw[i] ? Op::cand(a, s[i], kW ? w[kW ? i : 0] : 1u) : Op::id();
         } else {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) v[i] = s[i] >= 0 ? Op::cand(a, s[i], kW ? w[kW ? i : 0] : 1u) : Op::id();
+            for (int i = 0; i < 8; ++i) v[i] = s[i] != kNoArc ? Op::cand(a, s[i], kW ? w[kW ? i : 0] : 1u) : Op::id();
         }
         if (a.vals) {
             uint32_t *vb = reinterpret_cast<uint32_t *>(a.vals);
@@ -840,6 +832,15 @@ __global__ void __launch_bounds__(kPullThreads) k_min_apply(PullArgs a)
     }
 }
 
+// The contribution of every hub slot, which the PageRank pull gathers read in
+// place of the hubs' scattered contributions.
+__global__ void k_hub_values(PullArgs a)
+{
+    const uint32_t *v = reinterpret_cast<const uint32_t *>(a.contrib);
+    for (int32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < a.n_hubs; j += gridDim.x * blockDim.x)
+        a.hubv[j] = v[a.hub_ids[j]];
+}
+
 // bit v of bits: vertex v is in the frontier queue (bits cleared beforehand)
 __global__ void k_front_bits(const int32_t *__restrict__ q, const uint32_t *__restrict__ q_len,
                              uint32_t *__restrict__ bits, int32_t n)
@@ -897,6 +898,8 @@ void launch_apply(const PullArgs &a, int num_sms, cudaStream_t s)
 template <int APP>
 cudaError_t pull_iteration(PullArgs a, bool correct, uint32_t max_tiles, int num_sms, cudaStream_t s)
 {
+    if (APP == GG_APP_PAGERANK && a.n_hubs > 0)
+        k_hub_values<<<(unsigned)((a.n_hubs + kPullThreads - 1) / kPullThreads), kPullThreads, 0, s>>>(a);
     launch_arcs<APP>(a, max_tiles, num_sms, s);
     if (!correct) a.carry = nullptr;
     k_long_rows<APP><<<(unsigned)(num_sms * 4), kPullThreads, 0, s>>>(a);
@@ -963,12 +966,13 @@ gg_status ensure_pull(gg_graph *g)
         p.valid = false;
     }
     const size_t fwords = ((size_t)g->n + 31) / 32 + 4;
-    gg_status st = g->b_pull.alloc(4 * ((size_t)g->n + 2 * tiles + 16 + fwords), g->stream);
+    gg_status st = g->b_pull.alloc(4 * ((size_t)g->n + 2 * tiles + 16 + fwords + kHubCodes), g->stream);
     if (st != GG_OK) return st;
     g->pull_acc = g->b_pull.f32();
     g->pull_lead = g->pull_acc + g->n + 4;
     g->pull_carry = g->pull_lead + tiles + 4;
     g->pull_front = reinterpret_cast<uint32_t *>(g->pull_carry + tiles + 4);
+    g->pull_hubv = g->pull_front + fwords;
     g->pull_ready = true;
     return GG_OK;
 }
@@ -994,21 +998,6 @@ gg_status build_pull_plan(gg_graph *g, int which)
     GG_CUDA(cudaGetLastError());
     g->launches += 8;
     p.valid = true;
-    return GG_OK;
-}
-
-// The packed list as vertex ids (a correction or sampling pass of another
-// application may have packed hub-coded sources).
-gg_status sp_plain(gg_graph *g)
-{
-    if (!g->sampled || g->sp_is_plain) return GG_OK;
-    int grid = (int)(((size_t)g->m + 255) / 256);
-    if (grid > g->num_sms * 8) grid = g->num_sms * 8;
-    if (grid < 1) grid = 1;
-    k_decode_inplace<<<grid, 256, 0, g->stream>>>(g->sp_src, g->sp_nnz, g->hub_ids);
-    GG_CUDA(cudaGetLastError());
-    g->launches += 1;
-    g->sp_is_plain = true;
     return GG_OK;
 }
 
