@@ -378,12 +378,12 @@ def roofline(collected, n, m):
             "ms_last_step": {f"{k[0]}/{k[1]}": round(v[0], 3) for k, v in classes.items()}}
 
 
-KERNEL_NAMES = {("pagerank", "gather"): "k_pull_arcs<PR> + k_long_rows<PR> + k_pr_apply",
-                ("pagerank", "correct"): ("k_pull_arcs<PR> (values kept) + k_long_rows + k_carries + k_prc_flags "
-                                          "+ k_pr_apply + scan + k_pack_arcs + k_pack_ptr"),
+KERNEL_NAMES = {("pagerank", "gather"): "k_hub_values + k_pull_arcs<PR> + k_long_rows<PR> + k_pr_apply",
+                ("pagerank", "correct"): ("k_hub_values + k_pull_arcs<PR> (values kept) + k_long_rows + k_carries "
+                                          "+ k_prc_flags + k_pr_apply"),
                 "gather": "k_pull_arcs<{a}> + k_long_rows<{a}> + k_min_apply<{a}>",
                 "correct": ("k_pull_arcs<{a}> (values kept) + k_long_rows + k_carries + k_minc_flags<{a}> "
-                            "+ k_min_apply<{a}> + scan + k_pack_arcs + k_pack_ptr"),
+                            "+ k_min_apply<{a}>"),
                 "push": "k_push<{a}> + k_append_frontier"}
 
 

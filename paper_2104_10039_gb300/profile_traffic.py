@@ -6,7 +6,8 @@ one-pass metrics dram__bytes_read.sum, dram__bytes_write.sum and
 gpu__time_duration.sum on every launch (``--csv --log-file``). This tool
 finds the class's last launch sequence in the list (a gather: k_pull_arcs,
 k_long_rows and the apply pass; a correction: k_pull_arcs, k_long_rows,
-k_carries, the flag pass and the apply pass), sums its DRAM bytes and records them next to the
+k_carries, the flag pass and the apply pass; for PageRank each preceded by
+k_hub_values), sums its DRAM bytes and records them next to the
 case's algorithmic bytes (the same per-unit model bench.py uses), together
 with a hash of the kernel sources, in profiles/traffic.json. bench.py scales
 the traffic to its own launches by their algorithmic bytes (traffic grows
@@ -53,7 +54,8 @@ def kernel_hash() -> str:
             h.update(_code(fh.read()).encode())
     with open(os.path.join(CSRC, "gg_internal.cuh")) as fh:
         text = fh.read()
-    for pat in (r"constexpr int kThreads.*?constexpr uint32_t kInf[^\n]*", r"struct PullArgs \{.*?\n\};"):
+    for pat in (r"constexpr int kThreads.*?constexpr uint32_t kInf[^\n]*", r"constexpr int kHubCodes[^\n]*",
+                r"struct PullArgs \{.*?\n\};"):
         m = re.search(pat, text, re.S)
         h.update(_code(m.group(0) if m else "").encode())
     return h.hexdigest()[:16]
@@ -112,9 +114,10 @@ def class_window(launches: list, kind: str) -> list:
         corr = _is(launches[i + 2][0], "k_carries")
         if corr != (kind == "correct"):
             continue
+        first = i - 1 if i > 0 and _is(launches[i - 1][0], "k_hub_values") else i
         for j in range(i + 2, len(launches)):
             if _is(launches[j][0], r"k_(pr|min)_apply"):
-                found = launches[i:j + 1]
+                found = launches[first:j + 1]
                 break
     if found is None:
         raise SystemExit(f"no {kind} launch sequence in the list")

@@ -31,11 +31,13 @@ def test_bench_uses_the_same_per_unit_model():
 
 def test_class_window_picks_the_last_sequence(tmp_path):
     """The launch-list reader sums a class's last launch sequence: a gather
-    and a correction each end at their apply pass."""
+    and a correction each end at their apply pass, and begin at k_hub_values
+    when it precedes the arcs pass."""
     names = ["k_validate(int)", "k_pull_arcs<0, 4, 1>(PullArgs)", "k_long_rows<0>(PullArgs)", "k_pr_apply(PullArgs)",
              "k_pull_arcs<0, 4, 1>(PullArgs)", "k_long_rows<0>(PullArgs)", "k_carries<0>(PullArgs)",
              "k_prc_flags(PullArgs)", "k_pr_apply(PullArgs)", "k_scan_reduce(int)", "k_pack_arcs<0>(int)",
-             "k_pack_ptr(int)", "k_pull_arcs<0, 4, 1>(PullArgs)", "k_long_rows<0>(PullArgs)", "k_pr_apply(PullArgs)"]
+             "k_hub_values(PullArgs)", "k_pull_arcs<0, 4, 1>(PullArgs)", "k_long_rows<0>(PullArgs)",
+             "k_pr_apply(PullArgs)"]
     hdr = ["ID", "Kernel Name", "Metric Name", "Metric Unit", "Metric Value"]
     lines = [",".join(f'"{h}"' for h in hdr)]
     for i, nm in enumerate(names):
@@ -47,7 +49,7 @@ def test_class_window_picks_the_last_sequence(tmp_path):
     launches = pt._launches(str(p))
     assert len(launches) == len(names) and launches[3][1] == 8e6 and launches[3][2] == 3e3
     g = pt.class_window(launches, "gather")
-    assert [x[0] for x in g] == names[12:15]
+    assert [x[0] for x in g] == names[11:15]   # with the hub values written before it
     c = pt.class_window(launches, "correct")
     assert [x[0] for x in c] == names[4:9]
     assert sum(x[1] for x in c) == sum(2e6 * (i + 1) for i in range(4, 9))
