@@ -199,7 +199,9 @@ gg_status gg_load_csr(gg_graph **g, int32_t n, int64_t m, const int32_t *rowptr,
  * gg_sample_edges - set the initial edge flags by uniform sparsification
  * (Sec. 3.4, Fig. 1a): arc src->dst is active iff
  * SplitMix64(seed ^ (src<<32 | dst)) >> 32 < floor(sample_ratio * 2^32)
- * (the unordered pair on GG_SYMMETRIC graphs), and pack the active in-edges.
+ * (the unordered pair on GG_SYMMETRIC graphs), and count the active in-edges.
+ * The packed list of the active in-edges (GG_RESULT_SPARSE_*) is built when a
+ * run's approximate gather or gg_result first needs it.
  *   sample_ratio  sigma in (0, 1]
  * Enqueued on the stream; returns before the work completes.
  */

@@ -182,7 +182,6 @@ static void fill_list(const gg_graph *g, bool sparse, TileArgs &a)
     a.err = g->dev_err;
     a.hub_ids = g->hub_ids;
     a.n_hubs = g->n_hubs;
-    a.tile_cnt = g->tile_cnt;
     a.part = g->part;
     a.part_head = g->part_head;
     a.stash = g->stash;
@@ -382,8 +381,6 @@ static gg_status learned_correct(gg_graph *g, gg_app app, TileArgs a, uint32_t n
     a.num_tiles = g->sub_num_tiles;
     a.row_vtx = g->sel_rows;
     a.mask = g->sub_mask;
-    a.sp_ptr = nullptr;
-    a.tile_cnt = nullptr;
     a.hist_out = hs;
     a.epoch = next_epoch(g);
     if (nsel > 0) {
@@ -499,7 +496,6 @@ static gg_status run_pagerank(gg_graph *g, gg_policy policy, const gg_params *p)
         a.n_f = (float)g->n;
         if (kind == K_CORRECT) {
             a.mask = g->mask;
-            a.sp_ptr = g->sp_ptr;
             a.theta = p->theta;
         }
         bool learned = false;
@@ -722,7 +718,6 @@ static gg_status run_min(gg_graph *g, gg_app app, gg_policy policy, const gg_par
             if (app != GG_APP_SSSP) a.arc_w = nullptr;
             if (kind == K_CORRECT) {
                 a.mask = g->mask;
-                a.sp_ptr = g->sp_ptr;
                 a.theta_case = theta_case;
                 a.theta_fx = theta_fx;
                 a.est_strict = (p->flags & GG_EST_STRICT) ? 1 : 0;

@@ -78,12 +78,8 @@ struct TileArgs {
     float epsilon;
     const int32_t *deg_apply;   // degrees for the next contributions (renormalised), or nullptr = out-degree
     int infl_share;             // PageRank corrections: influence = share of the row total
-    // flags and compaction (correction, sampling)
+    // flags (correction)
     uint32_t *mask;             // CSC-order bitmap
-    int32_t *sp_ptr;
-    int32_t *sp_src;
-    uint32_t *sp_w;
-    uint32_t *sp_nnz;
     float theta;
     unsigned long long theta_fx;
     int theta_case;             // 0 compare, 1 theta < 0, 2 theta >= 1
@@ -96,8 +92,6 @@ struct TileArgs {
     // value before the arc within its tile (rows continued from an earlier
     // tile start from the identity there) and the arc's value (candidate)
     uint2 *stash;
-    // active arcs per tile (correction)
-    uint32_t *tile_cnt;
     // set by the host, not read by the current kernels
     unsigned long long *st_carry;
     uint32_t epoch;

@@ -224,8 +224,8 @@ __device__ __forceinline__ void flush_stats(const TileArgs &a, ApplyStats st)
 // up rows with a warp segmented scan, finds the total of every row in the tile
 // (the row still open at the tile end adds the later tiles' partials), tests
 // each arc's share against theta (GG-EStatus), applies the rows ending in the
-// tile (GG-Apply, GG-VStatus) and writes the new flags with the tile's active
-// count and tile-local row ends for the pack.
+// tile (GG-Apply, GG-VStatus) and writes the new flags (the pack recounts
+// them).
 struct ShareSmem {
     int32_t rowend[kWT + 1];
     uint32_t val[kPadded];      // arc values
@@ -402,7 +402,7 @@ k_share(TileArgs a)
         }
         __syncwarp();
         // ---- flags: share c / total > theta, tested as c > theta * total -----
-        uint32_t my_active = 0, my_flags = 0;
+        uint32_t my_flags = 0;
         {
             int x = lx;
 #pragma unroll
@@ -411,36 +411,25 @@ k_share(TileArgs a)
                     const float tot = s.rowtot[x];
                     const bool hit = tot != 0.0f ? __uint_as_float(item_v[i]) > __fmul_rn(a.theta, tot)
                                                  : 0.0f > a.theta;
-                    const uint32_t fl = hit ? 1u : 0u;
-                    my_flags |= fl << i;
-                    my_active += fl;
+                    my_flags |= (hit ? 1u : 0u) << i;
                 } else if ((endmask >> i) & 1u) {
                     ++x;
                 }
             }
         }
 
-        // ---- new flags into the bitmap; tile count and tile-local row ends --
+        // ---- new flags into the bitmap ----------------------------------------
         {
-            const uint32_t incl = warp_incl_sum_u32(my_active);
-            if (lane == 31 && a.tile_cnt) a.tile_cnt[t] = incl;
-            uint32_t off = incl - my_active;   // active arcs of the tile before this lane's items
             // this lane's arcs are the consecutive list positions a0+ly ..,
             // so its flags form one run of at most kIPT bits: at most two
             // shared-memory ORs per lane
             uint32_t run = 0;
-            int na = 0, x = lx;
+            int na = 0;
 #pragma unroll
             for (int i = 0; i < kIPT; ++i) {
                 if ((arcmask >> i) & 1u) {
-                    if ((my_flags >> i) & 1u) {
-                        run |= 1u << na;
-                        ++off;
-                    }
+                    if ((my_flags >> i) & 1u) run |= 1u << na;
                     ++na;
-                } else if ((endmask >> i) & 1u) {
-                    if (a.sp_ptr) a.sp_ptr[r0 + x + 1] = (int32_t)off;   // tile-local; k_pack adds the tile offset
-                    ++x;
                 }
             }
             if (run) {
@@ -538,11 +527,11 @@ k_fixup(TileArgs a)
 // warp tile: the carry of the row continued from earlier tiles (the finished
 // partials), each arc's influence test (Alg. 2 GG-EStatus) from (carry +) its
 // running values, the new flag words, every row ending in the tile applied
-// (GG-Apply, GG-VStatus), and the tile's active count and tile-local row ends
-// for the pack. The stash pairs, the ends of the tile's first 32 rows and the
-// old flag words are loaded one tile ahead; the pairs are also staged in
-// shared memory, where a row finds its total (the pair at its last arc); the
-// first 32 rows' vertex data are requested before the flag work.
+// (GG-Apply, GG-VStatus); the pack recounts the flags. The stash pairs, the
+// ends of the tile's first 32 rows and the old flag words are loaded one tile
+// ahead; the pairs are also staged in shared memory, where a row finds its
+// total (the pair at its last arc); the first 32 rows' vertex data are
+// requested before the flag work.
 template <int APP>
 __global__ void __launch_bounds__(kThreads, 4)
 k_correct2(TileArgs a)
@@ -552,11 +541,10 @@ k_correct2(TileArgs a)
     constexpr bool kMin = APP != GG_APP_PAGERANK;
     constexpr int kW = kWT / 32 + 2;
     __shared__ uint32_t s_bits[kWarps][kW];
-    __shared__ uint32_t s_cnt[kWarps][kW];
     __shared__ uint32_t s_old[kWarps][kMin ? kW : 1];
     __shared__ uint2 s_pair[kWarps][kWT];
     const int wi = (int)(threadIdx.x >> 5);
-    uint32_t *bits = s_bits[wi], *cnt = s_cnt[wi], *oldw = s_old[wi];
+    uint32_t *bits = s_bits[wi], *oldw = s_old[wi];
     uint2 *pair = s_pair[wi];
     const uint32_t lane = lane_id();
     const int gw = (int)((blockIdx.x * kThreads + threadIdx.x) >> 5);
@@ -682,15 +670,8 @@ k_correct2(TileArgs a)
             }
         }
         __syncwarp();
-        // active arcs before each word (tile-local)
-        {
-            uint32_t pc = (int)lane < nwords ? __popc(bits[lane]) : 0u;
-            const uint32_t incl = warp_incl_sum_u32(pc);
-            if ((int)lane < nwords) cnt[lane] = incl - pc;
-        }
-        if (lane == 0 && a.tile_cnt) a.tile_cnt[t] = active;
         __syncwarp();
-        // ---- rows ending in this tile: apply, tile-local row ends -----------
+        // ---- rows ending in this tile: apply ---------------------------------
         int32_t prev_e = a0;   // where the batch's first row starts (row r0: the tile start)
         for (int rb = 0; rb < nrows; rb += 32) {
             const int ri = rb + (int)lane;
@@ -714,15 +695,6 @@ k_correct2(TileArgs a)
                     const uint2 sv = pair[e - 1 - a0];
                     tot = A::op(A::from_bits(sv.x), A::from_bits(sv.y));
                     if (continued) tot = A::op(c, tot);
-                }
-                if (a.sp_ptr) {
-                    const int32_t pe = e - a0;   // tile-local end
-                    uint32_t before = 0;
-                    if (pe > 0) {
-                        const int32_t wl = ((e - 1) >> 5) - w0, b = ((e - 1) & 31) + 1;
-                        before = cnt[wl] + __popc(bits[wl] & (b == 32 ? 0xFFFFFFFFu : ((1u << b) - 1u)));
-                    }
-                    a.sp_ptr[r + 1] = (int32_t)before;
                 }
                 int32_t u = u_first;
                 uint32_t old = old_first;
