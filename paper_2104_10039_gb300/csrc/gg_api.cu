@@ -193,17 +193,12 @@ gg_status sample_edges(gg_graph *g, double ratio, uint64_t seed)
         set_error("sample_ratio must be in (0, 1], got %g", ratio);
         return GG_ERR_INVALID_ARG;
     }
-    // the arcs' rows come from the full list's plan (built once per graph)
-    gg_status st = ensure_pull(g);
-    if (st == GG_OK && !g->plan[0].valid) st = build_pull_plan(g, 0);
-    if (st != GG_OK) return st;
     GG_CUDA(cudaEventRecord(g->ev_s0, g->stream));
     // the hash keys on vertex ids (in_src, not the hub-coded copy)
-    const PullPlan &pl = g->plan[0];
-    GG_CUDA(launch_sample(g->in_src, pl.hb, pl.trow, pl.nzv, g->m, g->symmetric ? 1 : 0, seed,
+    GG_CUDA(launch_sample(g->in_src, g->in_dst, g->m, g->symmetric ? 1 : 0, seed,
                           (unsigned long long)std::floor(ratio * 4294967296.0), g->mask, g->num_sms, g->stream));
     g->launches += 1;
-    st = pack_active(g, nullptr, false);
+    gg_status st = pack_active(g, nullptr, false);
     if (st != GG_OK) return st;
     GG_CUDA(cudaEventRecord(g->ev_s1, g->stream));
     g->sample_timed = true;

@@ -246,11 +246,10 @@ cudaError_t launch_partition(const int32_t *row_ptr, int32_t n, const uint32_t *
 cudaError_t launch_tile_pr(int kind, const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s);
 cudaError_t launch_tile_min(int app, int kind, const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s);
 // Sampling (Sec. 3.4): the flag of every arc of the full in-edge list from
-// the hash of its endpoints (each arc's row from the full list's pull plan:
-// row-start bits hb, tile rows trow, non-empty rows' vertices nzv).
-cudaError_t launch_sample(const int32_t *in_src, const uint32_t *hb, const int32_t *trow, const int32_t *nzv,
-                          long long m, int symmetric, unsigned long long seed, unsigned long long thr, uint32_t *mask,
-                          int num_sms, cudaStream_t s);
+// the hash of its endpoints (in_dst: each arc's row).
+cudaError_t launch_sample(const int32_t *in_src, const int32_t *in_dst, long long m, int symmetric,
+                          unsigned long long seed, unsigned long long thr, uint32_t *mask, int num_sms,
+                          cudaStream_t s);
 // Rows a gather left open at tile starts (one launch after every gather).
 cudaError_t launch_fixup(int app, const TileArgs &a, int max_tiles, int num_sms, cudaStream_t s);
 cudaError_t launch_push(const PushArgs &a, uint32_t max_arcs, int grid, cudaStream_t s);
