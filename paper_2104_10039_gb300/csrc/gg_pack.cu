@@ -7,8 +7,9 @@
 //   k_pack_counts  active arcs per tile (popcount of its 8 flag words); a
 //                  correction's flag pass writes these itself
 //   (scan)         tile offsets in the packed list
-//   k_pack_arcs    one warp per tile: each active arc's source (and weight)
-//                  to tile offset + its rank among the tile's active arcs,
+//   k_pack_arcs    one warp per tile: each active arc's source (hub-coded for
+//                  PageRank, as its gathers read them) and weight to tile
+//                  offset + its rank among the tile's active arcs,
 //                  sources read with 16-byte loads, staged in shared memory
 //                  and stored by consecutive lanes
 //   k_pack_ptr     one thread per vertex: its packed row start = the offset
@@ -19,6 +20,9 @@
 // result needs the list (ensure_packed): a min application that only pushes
 // before its next correction, or a run that ends on a correction, never
 // builds it; PageRank builds it without weights.
+//
+// The active-arc count (scan total) is always set at once: the push/pull
+// switch and the iteration statistics need it.
 #include "gg_graph.cuh"
 
 namespace gg {
@@ -128,8 +132,7 @@ __global__ void __launch_bounds__(256) k_pack_arcs(const uint32_t *__restrict__ 
 }
 
 __global__ void k_pack_ptr(const int32_t *__restrict__ in_ptr, int32_t n, const uint32_t *__restrict__ mask,
-                           long long m, const uint32_t *__restrict__ off, int32_t *__restrict__ sp_ptr,
-                           uint32_t *__restrict__ sp_nnz, IterStatsDev *stats)
+                           long long m, const uint32_t *__restrict__ off, int32_t *__restrict__ sp_ptr)
 {
     const long long nt = (m + kPT - 1) / kPT;
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += (long long)gridDim.x * blockDim.x) {
@@ -141,12 +144,7 @@ __global__ void k_pack_ptr(const int32_t *__restrict__ in_ptr, int32_t n, const 
             for (long long wd = 8 * t; wd < wp; ++wd) r += (uint32_t)__popc(mask[wd]);   // words wholly before p (< m)
             if ((p & 31) != 0) r += (uint32_t)__popc(mask[wp] & ((1u << (uint32_t)(p & 31)) - 1u));
         }
-        const uint32_t q = off[t < nt ? t : nt] + r;
-        sp_ptr[v] = (int32_t)q;
-        if (v == n) {
-            *sp_nnz = q;
-            if (stats) stats->active_after = q;
-        }
+        sp_ptr[v] = (int32_t)(off[t < nt ? t : nt] + r);
     }
 }
 
@@ -161,7 +159,7 @@ __global__ void k_pack_total(const uint32_t *__restrict__ off, long long nt, uin
 }
 
 // The packed arcs and row pointers from the scanned tile counts.
-gg_status pack_lists(gg_graph *g, bool weighted, bool hubs, IterStatsDev *stats)
+gg_status pack_lists(gg_graph *g, bool weighted, bool hubs)
 {
     const int32_t *src = hubs ? g->in_src_h : g->in_src;
     cudaStream_t s = g->stream;
@@ -183,7 +181,7 @@ gg_status pack_lists(gg_graph *g, bool weighted, bool hubs, IterStatsDev *stats)
     }
     long long vb = ((long long)g->n + 1 + 255) / 256;
     if (vb > (long long)g->num_sms * 8) vb = (long long)g->num_sms * 8;
-    k_pack_ptr<<<(unsigned)vb, 256, 0, s>>>(g->in_ptr, g->n, g->mask, m, g->tile_off, g->sp_ptr, g->sp_nnz, stats);
+    k_pack_ptr<<<(unsigned)vb, 256, 0, s>>>(g->in_ptr, g->n, g->mask, m, g->tile_off, g->sp_ptr);
     GG_CUDA(cudaGetLastError());
     g->launches += 1;
     g->sp_stale = false;
@@ -224,7 +222,7 @@ gg_status ensure_packed(gg_graph *g, bool weighted, PackCoding coding)
     weighted = weighted && g->has_w;
     const bool hubs = coding == PACK_ANY ? (g->sp_stale ? false : g->sp_hubs) : coding == PACK_HUBS;
     if (!g->sp_stale && (g->sp_has_w || !weighted) && g->sp_hubs == hubs) return GG_OK;
-    return pack_lists(g, weighted, hubs, nullptr);
+    return pack_lists(g, weighted, hubs);
 }
 
 }  // namespace gg

@@ -19,18 +19,22 @@
 //                candidates for SSSP / BFS / CC. A row whose first arc lies in
 //                the tile writes its total (or, if it continues past the tile,
 //                the part in the tile) to acc[v]; the part of the tile before
-//                its first row start goes to lead[tile].
+//                its first row start goes to lead[tile]. PageRank's sources
+//                are hub-coded: a hub's contribution comes from the dense copy
+//                k_hub_values writes before the launch. With a frontier
+//                bitmap (k_front_bits, GG_PULL_FILTER) the min applications
+//                read only the frontier sources' values.
 //   k_long_rows  one block per long row: its total and, for a correction,
 //                every tile's carry (the row's value before the tile).
 //   k_carries    a correction's carries of the tiles inside shorter rows.
 //   k_prc_flags, k_minc_flags
-//                a correction's second pass: every arc's influence from the
-//                running value of its row before and after it (the values kept
-//                by the first pass, the carry of a continued row from acc and
-//                the leads), one flag bit per arc, and each tile's count of
-//                active arcs for the pack.
+//                a correction's second pass (lane L: arcs 8L..8L+7): every
+//                arc's influence from the running value of its row before and
+//                after it (the values kept by the first pass, the carry of a
+//                continued row from acc and the leads), one flag bit per arc,
+//                and each tile's count of active arcs for the pack.
 //   k_pr_apply, k_min_apply
-//                one thread per vertex: the row's total (acc[v] folded with the
+//                one thread per four consecutive vertices: the row's total (acc[v] folded with the
 //                later tiles' leading parts of a row continued across tile
 //                ends, in tile order; the identity for a row with no arcs in
 //                the list), then GG-Apply and GG-VStatus (PageRank: rank',
@@ -38,8 +42,9 @@
 //                the old value, the changed vertices appended to the frontier).
 //
 // The sums use a fixed grouping (lane-local prefix, warp scan, tile order),
-// so PageRank results are deterministic (the minimum is exact anyway). The plan of a list (built by build_pull_plan
-// whenever the list changes):
+// so PageRank results are deterministic (the minimum is exact anyway).
+//
+// The plan of a list (built by build_pull_plan whenever the list changes):
 //   hb[w]     bit j: arc 32w + j is the first arc of a row
 //   trow[t]   rank among non-empty rows of the row holding arc 256t
 //   nzv[k]    vertex of the k-th non-empty row
